@@ -1,0 +1,183 @@
+/*
+ * facert: differentiable ray-traced rendering of a morphable face inside a
+ * virtual light stage, and its gradient, on one GB300 GPU.
+ *
+ * Method: Dib et al., "Face Reflectance and Geometry Modeling via
+ * Differentiable Ray Tracing" (CVMP 2019).
+ *   - Face Modeling paragraph: N = 20 fixed square area lights on the
+ *     vertices of an isotropically sampled hemisphere, pointing at the origin;
+ *     parameters l_j in R^3 (light off = 0), identity alpha in R^80,
+ *     expression beta in R^90, pose [R t] in R^6, albedo coefficients
+ *     delta in R^80, a 32x32 grey specular map c_spec; Cook-Torrance
+ *     reflectance f_r = k_d f_lambert + k_s f_ct on vertex normals
+ *     n_i(alpha, beta, R, t).
+ *   - Optimization paragraph, Eq. 1: argmin E_data + w1 E_prior + w2 E_light
+ *     with E_data = sum_i |p_i^T - p_i^R|^2, E_light = sum_j |l_j - m_j|^2,
+ *     p^T = F(f_r, l_j, alpha, beta, R, t) the Monte-Carlo estimator of the
+ *     lighting equation; gradients by backpropagation through the
+ *     differentiable ray tracer of Li et al. 2018 (edge sampling).
+ *
+ * Conventions for every entry point:
+ *   - Returns FR_OK (0) or a negative FR_ERR_* code; never throws.  The
+ *     context keeps a message for the last failure (fr_last_error).
+ *   - Pointers documented "device" must be CUDA device memory of the
+ *     context's device; pointers documented "host" are host memory read
+ *     before the call returns.  The library owns the context and its copies
+ *     of the mesh, bases and acceleration structures; the caller owns every
+ *     buffer it passes.
+ *   - Work is enqueued asynchronously on the context stream (fr_set_stream;
+ *     default: the legacy default stream).  Calls on one context must not
+ *     overlap: the context's scratch buffers are shared.
+ *   - The packed parameter vector theta (FP32, device) has the layout
+ *       alpha[K_id] | beta[K_exp] | delta[K_alb] | c_spec[32*32] (row v,
+ *       column u) | pose[6] = (rx, ry, rz, tx, ty, tz) | lights[20*3] (RGB)
+ *     with R = Rz(rz) Ry(ry) Rx(rx) in radians; P = fr_n_params(ctx).
+ *   - Images are H x W x 3 FP32, row-major, pixel (px, py) at index
+ *     3*(py*W + px), py = 0 at the top.
+ */
+#ifndef FACERT_H
+#define FACERT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FR_OK 0
+#define FR_ERR_INVALID_ARG (-1)   /* null pointer, bad size or value */
+#define FR_ERR_SHAPE (-2)         /* mesh/basis sizes inconsistent, non-manifold mesh */
+#define FR_ERR_CUDA (-3)          /* a CUDA runtime call failed */
+#define FR_ERR_OOM (-4)           /* device allocation failed */
+#define FR_ERR_DEVICE_LIMIT (-5)  /* a traversal stack or step limit was hit on the device */
+#define FR_ERR_NOT_READY (-6)     /* mesh or bases not uploaded yet */
+
+typedef struct fr_ctx fr_ctx;
+
+/* Scene constants.  The paper fixes only N = 20 and the parameter sizes; the
+ * remaining values are one reading of the Face Modeling paragraph (pinhole
+ * camera at (0, 0, d_cam) looking down -z, square lights of side light_side
+ * at distance light_radius, Beckmann roughness beckmann_m).  eps_pedge
+ * (pixels) and eps_sedge (light-plane units) are the offsets at which edge
+ * samples evaluate the two sides of a visibility boundary; shadow rays
+ * accept hits with segment parameter in (shadow_tmin, 1 - shadow_tmin);
+ * clip_kappa is the minimum height of an occluder point above the shading
+ * point, measured along the light direction. */
+typedef struct fr_config {
+  float tan_half_fov;
+  float d_cam;
+  float light_radius;
+  float light_side;
+  float beckmann_m;
+  float eps_pedge;
+  float eps_sedge;
+  float shadow_tmin;
+  float clip_kappa;
+  int32_t n_lights;  /* 1..32 */
+} fr_config;
+
+/* Fill *cfg with the library defaults (tan_half_fov 0.275, d_cam 4,
+ * light_radius 3, light_side 0.6, beckmann_m 0.3, eps_pedge 1e-3,
+ * eps_sedge 2e-4, shadow_tmin 1e-4, clip_kappa 1e-5, n_lights 20). */
+void fr_default_config(fr_config* cfg);
+
+/* Per-call render options.  Samples are drawn from Philox4x32-10 keyed by
+ * (seed, iter); W, H >= 1, spp >= 1.  terms selects the gradient terms of
+ * fr_render_backward: 1 interior, 2 primary-visibility edges, 4 shadow
+ * edges (0 = all). */
+typedef struct fr_render_opts {
+  int32_t W, H, spp;
+  uint32_t seed, iter;
+  int32_t terms;
+} fr_render_opts;
+
+/* Create a context on CUDA device `device`.  *out receives the context. */
+int fr_create(fr_ctx** out, const fr_config* cfg, int32_t device);
+void fr_destroy(fr_ctx* ctx);
+/* Stream (a cudaStream_t) on which all later work of this context runs. */
+int fr_set_stream(fr_ctx* ctx, void* stream);
+const char* fr_last_error(const fr_ctx* ctx);
+const char* fr_strerror(int32_t code);
+
+/* Topology and mean shape (host pointers).  mean[V*3] FP32 (mu of the
+ * morphable model), tris[F*3] int32 counter-clockwise seen from outside,
+ * uv[V*2] FP32 specular-map coordinates in [0,1]^2.  Builds the edge list,
+ * the vertex-face adjacency and the two bounding-volume hierarchies (over
+ * triangles and over edges) from the mean shape; they are refitted on every
+ * render.  Fails with FR_ERR_SHAPE on an edge shared by more than two
+ * triangles or an out-of-range index. */
+int fr_upload_mesh(fr_ctx* ctx, const float* mean, int32_t V, const int32_t* tris, int32_t F,
+                   const float* uv);
+
+/* Morphable bases (host pointers, row-major, row 3v+c = coordinate c of
+ * vertex v): B_id[3V*K_id], B_exp[3V*K_exp], alb_mean[3V], B_alb[3V*K_alb].
+ * Face Modeling paragraph: X = mu + B_id alpha + B_exp beta, albedo =
+ * alb_mean + B_alb delta.  Must follow fr_upload_mesh. */
+int fr_upload_bases(fr_ctx* ctx, const float* B_id, int32_t K_id, const float* B_exp, int32_t K_exp,
+                    const float* alb_mean, const float* B_alb, int32_t K_alb);
+
+/* Number of parameters P of theta for the uploaded bases. */
+int32_t fr_n_params(const fr_ctx* ctx);
+
+/* Forward render (Optimization paragraph: p^T = F(...), the Monte-Carlo
+ * estimator of the lighting equation).  theta[P] device; image[H*W*3]
+ * device, overwritten with the mean over spp of the per-sample radiance:
+ * one jittered camera ray per sample, one uniform point per light that is
+ * on, a shadow ray for self-shadows, Cook-Torrance shading.  Lights with
+ * l_j = 0 are skipped.  Returns FR_ERR_NOT_READY before both uploads. */
+int fr_render(fr_ctx* ctx, const float* theta, const fr_render_opts* opts, float* image);
+
+/* Gradient of <d_image, image(theta)> with respect to theta (Face Modeling
+ * paragraph: backpropagation through the differentiable ray tracer).  Uses
+ * the same samples as fr_render with the same opts, recomputes every
+ * intersection (no path storage) and adds the edge-sampling terms of Li et
+ * al. 2018 for primary visibility and for shadow boundaries on the lights.
+ * d_image[H*W*3] FP32 device; grad[P] FP64 device, overwritten
+ * (accumulate = 0) or added to (accumulate = 1). */
+int fr_render_backward(fr_ctx* ctx, const float* theta, const fr_render_opts* opts, const float* d_image,
+                       double* grad, int32_t accumulate);
+
+/* Eq. 1: loss = E_data + w1 E_prior + w2 E_light with
+ *   E_data  = sum over pixels with mask != 0 of |image - target|^2,
+ *   E_prior = |alpha|^2 + |beta|^2 + |delta|^2 (the statistical prior; the
+ *             landmark term needs detected landmarks and is not computed),
+ *   E_light = sum_j |l_j - m_j|^2, j = 1..N.
+ * theta[P], image/target[H*W*3] FP32 device; mask[H*W] uint8 device or NULL
+ * (all pixels); m[3N] FP32 device or NULL (zero); loss: one FP64 device
+ * scalar, overwritten; d_image[H*W*3] FP32 device or NULL, overwritten with
+ * dE_data/d image; grad[P] FP64 device or NULL: the gradient of
+ * w1 E_prior + w2 E_light is ADDED to it. */
+int fr_loss(fr_ctx* ctx, const float* theta, int32_t W, int32_t H, const float* image, const float* target,
+            const uint8_t* mask, const float* m, float w1, float w2, double* loss, float* d_image,
+            double* grad);
+
+/* Geometry stage alone (Face Modeling paragraph), for inspection and tests:
+ * posed vertices X[V*3] FP32, unit vertex normals N[V*3] FP32 and albedo
+ * A[V*3] FP32, all device (any may be NULL).  Returns the number of camera
+ * silhouette edges (>= 0) or an error. */
+int fr_geometry(fr_ctx* ctx, const float* theta, float* X, float* N, float* A);
+
+/* Light stage frames (host, out[n_lights*12]: centre, e1, e2, direction). */
+int fr_light_stage(const fr_ctx* ctx, float* out);
+
+/* Wait for the context stream; returns FR_ERR_DEVICE_LIMIT (and clears the
+ * flag) if a kernel hit its traversal stack or step limit since the last
+ * fr_sync, FR_ERR_CUDA if the stream reported an error, else FR_OK. */
+int fr_sync(fr_ctx* ctx);
+
+/* Counts of the last fr_render / fr_render_backward call, read back after a
+ * stream synchronisation: BVH nodes visited, triangle tests, edge-BVH nodes
+ * visited, edge tests, in that order (out[8]: forward then backward).
+ * Collected only when enabled with fr_set_counters(ctx, 1). */
+int fr_set_counters(fr_ctx* ctx, int32_t enable);
+int fr_get_counters(fr_ctx* ctx, uint64_t* out);
+
+/* Number of kernels this context has launched since it was created. */
+uint64_t fr_launch_count(const fr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FACERT_H */

@@ -1,0 +1,714 @@
+// C-ABI of the facert library (declared in include/facert.h): context,
+// uploads, acceleration-structure build, and the render / backward / loss
+// entry points, each a fixed sequence of kernel launches on the context
+// stream.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/facert.h"
+#include "kernels.cuh"
+
+using namespace fr;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Device buffer owned by the context.
+template <class T> struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  void free_() { if (p) cudaFree(p); p = nullptr; n = 0; }
+  cudaError_t alloc(size_t count) {
+    free_();
+    if (count == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e == cudaSuccess) n = count;
+    return e;
+  }
+};
+
+// Binary BVH in the device layout of common.cuh plus the refit topology.
+struct HostBVH {
+  std::vector<float4> nodes;          // 4 per node
+  std::vector<int> perm;              // leaf slot -> primitive id
+  std::vector<int> leaf_first, leaf_count, leaf_parent, leaf_slot;
+  std::vector<int> node_parent, node_slot;
+};
+
+struct Box {
+  float lo[3], hi[3];
+  void reset() { for (int i = 0; i < 3; ++i) { lo[i] = 3e38f; hi[i] = -3e38f; } }
+  void grow(const float* p) { for (int i = 0; i < 3; ++i) { lo[i] = std::min(lo[i], p[i]); hi[i] = std::max(hi[i], p[i]); } }
+  void grow(const Box& b) { for (int i = 0; i < 3; ++i) { lo[i] = std::min(lo[i], b.lo[i]); hi[i] = std::max(hi[i], b.hi[i]); } }
+  float area() const {
+    float d[3];
+    for (int i = 0; i < 3; ++i) d[i] = std::max(0.0f, hi[i] - lo[i]);
+    return 2.0f * (d[0] * d[1] + d[1] * d[2] + d[2] * d[0]);
+  }
+};
+
+// Binned surface-area-heuristic build (12 bins per axis, leaves of <= 4).
+struct Builder {
+  const std::vector<Box>& boxes;
+  std::vector<float> cen;            // [n*3]
+  std::vector<int>& perm;
+  HostBVH& out;
+  static constexpr int LEAF = 4, BINS = 12;
+  Builder(const std::vector<Box>& b, HostBVH& o) : boxes(b), perm(o.perm), out(o) {
+    size_t n = b.size();
+    cen.resize(3 * n);
+    perm.resize(n);
+    for (size_t i = 0; i < n; ++i) {
+      perm[i] = (int)i;
+      for (int k = 0; k < 3; ++k) cen[3 * i + k] = 0.5f * (b[i].lo[k] + b[i].hi[k]);
+    }
+  }
+  int new_node(int parent, int slot) {
+    int id = (int)out.node_parent.size();
+    out.node_parent.push_back(parent);
+    out.node_slot.push_back(slot);
+    for (int i = 0; i < 4; ++i) out.nodes.push_back(make_float4(0, 0, 0, 0));
+    return id;
+  }
+  void set_child(int node, int slot, int code) {
+    int* c = reinterpret_cast<int*>(&out.nodes[4 * node + 3]);
+    c[slot] = code;
+  }
+  void empty_box(int node, int slot) {
+    float* N = reinterpret_cast<float*>(&out.nodes[4 * node]);
+    int o = slot ? 6 : 0;
+    N[o] = N[o + 1] = N[o + 2] = 3e38f;
+    N[o + 3] = N[o + 4] = N[o + 5] = -3e38f;
+  }
+  int make_leaf(int b, int e, int parent, int slot) {
+    int id = (int)out.leaf_first.size();
+    out.leaf_first.push_back(b);
+    out.leaf_count.push_back(e - b);
+    out.leaf_parent.push_back(parent);
+    out.leaf_slot.push_back(slot);
+    (void)id;
+    return ~((b << 3) | (e - b - 1));
+  }
+  // returns the split position in perm (b < m < e)
+  int split(int b, int e) {
+    Box cb;
+    cb.reset();
+    for (int i = b; i < e; ++i) cb.grow(&cen[3 * perm[i]]);
+    float best = 3e38f;
+    int best_axis = -1, best_bin = -1;
+    for (int ax = 0; ax < 3; ++ax) {
+      float ext = cb.hi[ax] - cb.lo[ax];
+      if (!(ext > 0)) continue;
+      Box bb[BINS];
+      int cnt[BINS] = {0};
+      for (int k = 0; k < BINS; ++k) bb[k].reset();
+      for (int i = b; i < e; ++i) {
+        int k = std::min(BINS - 1, (int)((cen[3 * perm[i] + ax] - cb.lo[ax]) / ext * BINS));
+        cnt[k]++;
+        bb[k].grow(boxes[perm[i]]);
+      }
+      float la[BINS], ra[BINS];
+      int lc[BINS], rc[BINS];
+      Box acc;
+      acc.reset();
+      int c = 0;
+      for (int k = 0; k < BINS; ++k) { acc.grow(bb[k]); c += cnt[k]; la[k] = acc.area(); lc[k] = c; }
+      acc.reset();
+      c = 0;
+      for (int k = BINS - 1; k >= 0; --k) { acc.grow(bb[k]); c += cnt[k]; ra[k] = acc.area(); rc[k] = c; }
+      for (int k = 0; k < BINS - 1; ++k) {
+        if (lc[k] == 0 || rc[k + 1] == 0) continue;
+        float cost = la[k] * lc[k] + ra[k + 1] * rc[k + 1];
+        if (cost < best) { best = cost; best_axis = ax; best_bin = k; }
+      }
+    }
+    int m = -1;
+    if (best_axis >= 0) {
+      float ext = cb.hi[best_axis] - cb.lo[best_axis];
+      auto mid = std::partition(perm.begin() + b, perm.begin() + e, [&](int p) {
+        int k = std::min(BINS - 1, (int)((cen[3 * p + best_axis] - cb.lo[best_axis]) / ext * BINS));
+        return k <= best_bin;
+      });
+      m = (int)(mid - perm.begin());
+    }
+    if (m <= b || m >= e) {   // degenerate: median split along the largest extent
+      int ax = 0;
+      for (int k = 1; k < 3; ++k) if (cb.hi[k] - cb.lo[k] > cb.hi[ax] - cb.lo[ax]) ax = k;
+      m = (b + e) / 2;
+      std::nth_element(perm.begin() + b, perm.begin() + m, perm.begin() + e,
+                       [&](int p, int q) { return cen[3 * p + ax] < cen[3 * q + ax]; });
+    }
+    return m;
+  }
+  // Build the subtree over perm[b, e) hanging below (parent, slot).
+  int build(int b, int e, int parent, int slot) {
+    if (e - b <= LEAF) return make_leaf(b, e, parent, slot);
+    int m = split(b, e);
+    int id = new_node(parent, slot);
+    int c0 = build(b, m, id, 0);
+    set_child(id, 0, c0);
+    int c1 = build(m, e, id, 1);
+    set_child(id, 1, c1);
+    return id;
+  }
+  void run() {
+    int n = (int)boxes.size();
+    int root = new_node(-1, 0);
+    if (n <= LEAF) {
+      set_child(root, 0, make_leaf(0, n, root, 0));
+      set_child(root, 1, EMPTY_CHILD);
+      empty_box(root, 1);
+      return;
+    }
+    int m = split(0, n);
+    set_child(root, 0, build(0, m, root, 0));
+    set_child(root, 1, build(m, n, root, 1));
+  }
+};
+
+struct DevBVH {
+  DBuf<float4> nodes;
+  DBuf<int> leaf_first, leaf_count, leaf_parent, leaf_slot, node_parent, node_slot, counter;
+  int n_nodes = 0, n_leaves = 0;
+};
+
+}  // namespace
+
+struct fr_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  fr_config cfg;
+  std::string err;
+  std::vector<Light> lights;
+  // mesh
+  int V = 0, F = 0, E = 0;
+  bool have_mesh = false, have_bases = false;
+  DBuf<float> mean, uv;
+  DBuf<int4> tris, edges_canon, edges_leaf;
+  DBuf<int> vf_off, vf_idx, tri_perm, edge_id_leaf;
+  DevBVH tbvh, ebvh;
+  // bases
+  int K_id = 0, K_exp = 0, K_alb = 0;
+  DBuf<float> BidT, BexpT, alb_mean, BalbT;
+  // per-render state
+  DBuf<float4> X, Xm, alb, nrm, ng, tv;
+  DBuf<int> sil, n_sil, block_count, err_flag;
+  DBuf<unsigned long long> counters;
+  bool counters_on = false;
+  uint64_t launches = 0;
+  // gradient accumulators
+  DBuf<float4> dX, dN, dA, gs;
+  DBuf<float> dXm, dC, dL;
+  int n_params() const { return K_id + K_exp + K_alb + CS * CS + 6 + 3 * cfg.n_lights; }
+  int off_cspec() const { return K_id + K_exp + K_alb; }
+  int off_pose() const { return off_cspec() + CS * CS; }
+  int off_lights() const { return off_pose() + 6; }
+};
+
+namespace {
+
+int fail(fr_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? FR_ERR_OOM : FR_ERR_CUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                          \
+  } while (0)
+
+#define CKL()                                                                                 \
+  do {                                                                                        \
+    ++ctx->launches;                                                                          \
+    cudaError_t e_ = cudaGetLastError();                                                      \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(ctx, FR_ERR_CUDA, "kernel launch: %s (%s:%d)", cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+template <class T> cudaError_t upload(DBuf<T>& b, const T* h, size_t n, cudaStream_t s) {
+  cudaError_t e = b.alloc(n);
+  if (e != cudaSuccess || n == 0) return e;
+  e = cudaMemcpyAsync(b.p, h, n * sizeof(T), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);
+}
+
+// Light stage: Fibonacci points on the hemisphere z >= 0, squares facing the origin.
+std::vector<Light> make_lights(int n, double radius) {
+  std::vector<Light> L(n);
+  const double ga = 3.14159265358979323846 * (3.0 - std::sqrt(5.0));
+  for (int k = 0; k < n; ++k) {
+    double z = (k + 0.5) / n, r = std::sqrt(1.0 - z * z), ph = k * ga;
+    double d[3] = {r * std::cos(ph), r * std::sin(ph), z};
+    double e1[3] = {d[2], 0.0, -d[0]};
+    double n1 = std::sqrt(e1[0] * e1[0] + e1[2] * e1[2]);
+    e1[0] /= n1; e1[2] /= n1;
+    double e2[3] = {d[1] * e1[2] - d[2] * e1[1], d[2] * e1[0] - d[0] * e1[2], d[0] * e1[1] - d[1] * e1[0]};
+    L[k].c = V3{(float)(radius * d[0]), (float)(radius * d[1]), (float)(radius * d[2])};
+    L[k].e1 = V3{(float)e1[0], (float)e1[1], (float)e1[2]};
+    L[k].e2 = V3{(float)e2[0], (float)e2[1], (float)e2[2]};
+    L[k].dl = V3{(float)d[0], (float)d[1], (float)d[2]};
+  }
+  return L;
+}
+
+int upload_bvh(fr_ctx* ctx, const HostBVH& h, DevBVH& d) {
+  d.n_nodes = (int)(h.nodes.size() / 4);
+  d.n_leaves = (int)h.leaf_first.size();
+  CK(upload(d.nodes, h.nodes.data(), h.nodes.size(), ctx->stream));
+  CK(upload(d.leaf_first, h.leaf_first.data(), h.leaf_first.size(), ctx->stream));
+  CK(upload(d.leaf_count, h.leaf_count.data(), h.leaf_count.size(), ctx->stream));
+  CK(upload(d.leaf_parent, h.leaf_parent.data(), h.leaf_parent.size(), ctx->stream));
+  CK(upload(d.leaf_slot, h.leaf_slot.data(), h.leaf_slot.size(), ctx->stream));
+  CK(upload(d.node_parent, h.node_parent.data(), h.node_parent.size(), ctx->stream));
+  CK(upload(d.node_slot, h.node_slot.data(), h.node_slot.size(), ctx->stream));
+  CK(d.counter.alloc(d.n_nodes));
+  return FR_OK;
+}
+
+GeoArgs geo_args(fr_ctx* c) {
+  GeoArgs g;
+  g.V = c->V; g.F = c->F; g.K_id = c->K_id; g.K_exp = c->K_exp; g.K_alb = c->K_alb; g.off_pose = c->off_pose();
+  g.mean = c->mean.p; g.BidT = c->BidT.p; g.BexpT = c->BexpT.p; g.alb_mean = c->alb_mean.p; g.BalbT = c->BalbT.p;
+  g.tris = c->tris.p; g.tri_perm = c->tri_perm.p; g.vf_off = c->vf_off.p; g.vf_idx = c->vf_idx.p;
+  g.X = c->X.p; g.Xm = c->Xm.p; g.alb = c->alb.p; g.nrm = c->nrm.p; g.ng = c->ng.p; g.tv = c->tv.p;
+  return g;
+}
+
+Cam make_cam(const fr_ctx* c, int W, int H) {
+  Cam cam;
+  cam.o = V3{0.0f, 0.0f, c->cfg.d_cam};
+  cam.k = (float)(2.0 * (double)c->cfg.tan_half_fov / (double)H);
+  cam.cx = (float)((double)c->cfg.tan_half_fov * (double)W / (double)H);
+  cam.cy = c->cfg.tan_half_fov;
+  cam.dcam = c->cfg.d_cam;
+  return cam;
+}
+
+int refit(fr_ctx* ctx, DevBVH& b, bool is_edge) {
+  if (b.n_leaves == 0) return FR_OK;
+  CK(cudaMemsetAsync(b.counter.p, 0, sizeof(int) * b.n_nodes, ctx->stream));
+  RefitArgs r;
+  r.n_leaves = b.n_leaves;
+  r.leaf_first = b.leaf_first.p; r.leaf_count = b.leaf_count.p; r.leaf_parent = b.leaf_parent.p;
+  r.leaf_slot = b.leaf_slot.p; r.node_parent = b.node_parent.p; r.node_slot = b.node_slot.p;
+  r.counter = b.counter.p; r.nodes = b.nodes.p; r.is_edge = is_edge ? 1 : 0;
+  r.tv = ctx->tv.p; r.edges = ctx->edges_leaf.p; r.X = ctx->X.p;
+  k_refit<<<(b.n_leaves + 255) / 256, 256, 0, ctx->stream>>>(r);
+  CKL();
+  return FR_OK;
+}
+
+// Geometry, normals, refits and camera silhouettes for theta.
+int prepare(fr_ctx* ctx, const float* theta, int W, int H) {
+  if (!ctx->have_mesh || !ctx->have_bases) return fail(ctx, FR_ERR_NOT_READY, "mesh and bases must be uploaded first");
+  if (!theta) return fail(ctx, FR_ERR_INVALID_ARG, "theta is null");
+  GeoArgs g = geo_args(ctx);
+  cudaStream_t s = ctx->stream;
+  k_geometry<<<(ctx->V + 127) / 128, 128, 0, s>>>(g, theta);
+  CKL();
+  k_faces<<<(ctx->F + 255) / 256, 256, 0, s>>>(g);
+  CKL();
+  k_vertex_normals<<<(ctx->V + 255) / 256, 256, 0, s>>>(g);
+  CKL();
+  int rc = refit(ctx, ctx->tbvh, false);
+  if (rc) return rc;
+  rc = refit(ctx, ctx->ebvh, true);
+  if (rc) return rc;
+  SilArgs sa;
+  sa.E = ctx->E; sa.edges = ctx->edges_canon.p; sa.tris = ctx->tris.p; sa.ng = ctx->ng.p; sa.X = ctx->X.p;
+  sa.cam_o = V3{0.0f, 0.0f, ctx->cfg.d_cam};
+  sa.block_count = ctx->block_count.p; sa.sil = ctx->sil.p; sa.n_sil = ctx->n_sil.p;
+  int nb = (ctx->E + 255) / 256;
+  k_silhouette_flags<<<nb, 256, 0, s>>>(sa);
+  CKL();
+  k_silhouette_scan<<<1, 1024, 0, s>>>(sa, nb);
+  CKL();
+  k_silhouette_scatter<<<nb, 256, 0, s>>>(sa);
+  CKL();
+  (void)W; (void)H;
+  return FR_OK;
+}
+
+int check_opts(fr_ctx* ctx, const fr_render_opts* o) {
+  if (!o) return fail(ctx, FR_ERR_INVALID_ARG, "opts is null");
+  if (o->W < 1 || o->H < 1 || o->spp < 1) return fail(ctx, FR_ERR_INVALID_ARG, "W, H, spp must be >= 1");
+  if ((long long)o->W * o->H > (1LL << 26) || (long long)o->W * o->H * o->spp > (1LL << 31) - 1)
+    return fail(ctx, FR_ERR_INVALID_ARG, "image or sample count too large");
+  return FR_OK;
+}
+
+RenderArgs render_args(fr_ctx* c, const float* theta, const fr_render_opts* o) {
+  RenderArgs a;
+  a.W = o->W; a.H = o->H; a.spp = o->spp; a.seed = o->seed; a.iter = o->iter;
+  a.n_lights = c->cfg.n_lights;
+  a.side = c->cfg.light_side; a.m = c->cfg.beckmann_m; a.eps_pedge = c->cfg.eps_pedge;
+  a.eps_sedge = c->cfg.eps_sedge; a.tmin = c->cfg.shadow_tmin; a.kappa = c->cfg.clip_kappa;
+  a.cam = make_cam(c, o->W, o->H);
+  for (int j = 0; j < c->cfg.n_lights; ++j) a.lights[j] = c->lights[j];
+  a.mesh.X = c->X.p; a.mesh.ng = c->ng.p; a.mesh.tris = c->tris.p; a.mesh.tv = c->tv.p;
+  a.mesh.bvh.nodes = c->tbvh.nodes.p; a.mesh.bvh.n_nodes = c->tbvh.n_nodes;
+  a.ebvh.bvh.nodes = c->ebvh.nodes.p; a.ebvh.bvh.n_nodes = c->ebvh.n_nodes;
+  a.ebvh.edges = c->edges_leaf.p; a.ebvh.edge_id = c->edge_id_leaf.p;
+  a.nrm = c->nrm.p; a.alb = c->alb.p; a.uv = reinterpret_cast<const float2*>(c->uv.p);
+  a.cspec = theta + c->off_cspec(); a.lights_dev = theta + c->off_lights();
+  a.sil = c->sil.p; a.n_sil = c->n_sil.p; a.edges_canon = c->edges_canon.p;
+  a.err = c->err_flag.p;
+  a.counters = c->counters_on ? c->counters.p : nullptr;
+  return a;
+}
+
+unsigned grid_for(long long threads, int block) { return (unsigned)((threads + block - 1) / block); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void fr_default_config(fr_config* c) {
+  if (!c) return;
+  c->tan_half_fov = 0.275f; c->d_cam = 4.0f; c->light_radius = 3.0f; c->light_side = 0.6f; c->beckmann_m = 0.3f;
+  c->eps_pedge = 1e-3f; c->eps_sedge = 2e-4f; c->shadow_tmin = 1e-4f; c->clip_kappa = 1e-5f; c->n_lights = 20;
+}
+
+const char* fr_strerror(int32_t code) {
+  switch (code) {
+    case FR_OK: return "ok";
+    case FR_ERR_INVALID_ARG: return "invalid argument";
+    case FR_ERR_SHAPE: return "inconsistent shapes";
+    case FR_ERR_CUDA: return "CUDA error";
+    case FR_ERR_OOM: return "out of device memory";
+    case FR_ERR_DEVICE_LIMIT: return "device traversal limit reached";
+    case FR_ERR_NOT_READY: return "mesh or bases not uploaded";
+    default: return "unknown error";
+  }
+}
+
+const char* fr_last_error(const fr_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int fr_create(fr_ctx** out, const fr_config* cfg, int32_t device) {
+  fr_ctx* ctx = nullptr;
+  if (!out) return FR_ERR_INVALID_ARG;
+  *out = nullptr;
+  fr_config c;
+  if (cfg) c = *cfg; else fr_default_config(&c);
+  if (c.n_lights < 1 || c.n_lights > MAX_LIGHTS) return FR_ERR_INVALID_ARG;
+  if (!(c.light_side > 0) || !(c.d_cam > 0) || !(c.tan_half_fov > 0) || !(c.beckmann_m > 0)) return FR_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return FR_ERR_CUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return FR_ERR_CUDA;
+  ctx = new fr_ctx();
+  ctx->device = device;
+  ctx->cfg = c;
+  ctx->lights = make_lights(c.n_lights, c.light_radius);
+  if (ctx->err_flag.alloc(1) != cudaSuccess || ctx->counters.alloc(8) != cudaSuccess ||
+      ctx->n_sil.alloc(1) != cudaSuccess) {
+    delete ctx;
+    return FR_ERR_OOM;
+  }
+  cudaMemset(ctx->err_flag.p, 0, sizeof(int));
+  cudaMemset(ctx->counters.p, 0, 8 * sizeof(unsigned long long));
+  cudaMemset(ctx->n_sil.p, 0, sizeof(int));
+  if (cudaDeviceSynchronize() != cudaSuccess) { delete ctx; return FR_ERR_CUDA; }
+  *out = ctx;
+  return FR_OK;
+}
+
+void fr_destroy(fr_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  ctx->mean.free_(); ctx->uv.free_(); ctx->tris.free_(); ctx->edges_canon.free_(); ctx->edges_leaf.free_();
+  ctx->vf_off.free_(); ctx->vf_idx.free_(); ctx->tri_perm.free_(); ctx->edge_id_leaf.free_();
+  for (DevBVH* b : {&ctx->tbvh, &ctx->ebvh}) {
+    b->nodes.free_(); b->leaf_first.free_(); b->leaf_count.free_(); b->leaf_parent.free_(); b->leaf_slot.free_();
+    b->node_parent.free_(); b->node_slot.free_(); b->counter.free_();
+  }
+  ctx->BidT.free_(); ctx->BexpT.free_(); ctx->alb_mean.free_(); ctx->BalbT.free_();
+  ctx->X.free_(); ctx->Xm.free_(); ctx->alb.free_(); ctx->nrm.free_(); ctx->ng.free_(); ctx->tv.free_();
+  ctx->sil.free_(); ctx->n_sil.free_(); ctx->block_count.free_(); ctx->err_flag.free_(); ctx->counters.free_();
+  ctx->dX.free_(); ctx->dN.free_(); ctx->dA.free_(); ctx->gs.free_(); ctx->dXm.free_(); ctx->dC.free_(); ctx->dL.free_();
+  delete ctx;
+}
+
+int fr_set_stream(fr_ctx* ctx, void* stream) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  ctx->stream = (cudaStream_t)stream;
+  return FR_OK;
+}
+
+int fr_upload_mesh(fr_ctx* ctx, const float* mean, int32_t V, const int32_t* tris, int32_t F, const float* uv) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  if (!mean || !tris || !uv || V < 3 || F < 1) return fail(ctx, FR_ERR_INVALID_ARG, "mesh arrays null or too small");
+  if (F > (1 << 27) || V > (1 << 27)) return fail(ctx, FR_ERR_INVALID_ARG, "mesh too large");
+  CK(cudaSetDevice(ctx->device));
+  for (int i = 0; i < 3 * F; ++i)
+    if (tris[i] < 0 || tris[i] >= V) return fail(ctx, FR_ERR_SHAPE, "triangle index %d out of range", tris[i]);
+  // canonical edges: sorted by (min vertex, max vertex); f0 < f1, f1 = -1 on the boundary
+  std::vector<std::array<int, 3>> he;
+  he.reserve(3 * (size_t)F);
+  for (int f = 0; f < F; ++f)
+    for (int k = 0; k < 3; ++k) {
+      int a = tris[3 * f + k], b = tris[3 * f + (k + 1) % 3];
+      if (a == b) return fail(ctx, FR_ERR_SHAPE, "degenerate triangle %d", f);
+      he.push_back({std::min(a, b), std::max(a, b), f});
+    }
+  std::sort(he.begin(), he.end());
+  std::vector<int4> edges;
+  for (size_t i = 0; i < he.size();) {
+    size_t j = i;
+    while (j < he.size() && he[j][0] == he[i][0] && he[j][1] == he[i][1]) ++j;
+    if (j - i > 2) return fail(ctx, FR_ERR_SHAPE, "edge (%d,%d) shared by %d triangles", he[i][0], he[i][1], (int)(j - i));
+    edges.push_back(make_int4(he[i][0], he[i][1], he[i][2], j - i == 2 ? he[i + 1][2] : -1));
+    i = j;
+  }
+  const int E = (int)edges.size();
+  // vertex -> face CSR
+  std::vector<int> vf_off(V + 1, 0), vf_idx(3 * (size_t)F);
+  for (int i = 0; i < 3 * F; ++i) vf_off[tris[i] + 1]++;
+  for (int v = 0; v < V; ++v) vf_off[v + 1] += vf_off[v];
+  {
+    std::vector<int> pos(vf_off.begin(), vf_off.end() - 1);
+    for (int f = 0; f < F; ++f)
+      for (int k = 0; k < 3; ++k) vf_idx[pos[tris[3 * f + k]]++] = f;
+  }
+  // BVHs over the mean shape
+  std::vector<Box> tb(F), eb(E);
+  for (int f = 0; f < F; ++f) {
+    tb[f].reset();
+    for (int k = 0; k < 3; ++k) tb[f].grow(&mean[3 * tris[3 * f + k]]);
+  }
+  for (int e = 0; e < E; ++e) {
+    eb[e].reset();
+    eb[e].grow(&mean[3 * edges[e].x]);
+    eb[e].grow(&mean[3 * edges[e].y]);
+  }
+  HostBVH ht, he2;
+  { Builder b(tb, ht); b.run(); }
+  { Builder b(eb, he2); b.run(); }
+  std::vector<int4> tris4(F), edges_leaf(E);
+  for (int f = 0; f < F; ++f) tris4[f] = make_int4(tris[3 * f], tris[3 * f + 1], tris[3 * f + 2], 0);
+  for (int i = 0; i < E; ++i) edges_leaf[i] = edges[he2.perm[i]];
+  cudaStream_t s = ctx->stream;
+  CK(upload(ctx->mean, mean, 3 * (size_t)V, s));
+  CK(upload(ctx->uv, uv, 2 * (size_t)V, s));
+  CK(upload(ctx->tris, tris4.data(), F, s));
+  CK(upload(ctx->edges_canon, edges.data(), E, s));
+  CK(upload(ctx->edges_leaf, edges_leaf.data(), E, s));
+  CK(upload(ctx->edge_id_leaf, he2.perm.data(), E, s));
+  CK(upload(ctx->tri_perm, ht.perm.data(), F, s));
+  CK(upload(ctx->vf_off, vf_off.data(), V + 1, s));
+  CK(upload(ctx->vf_idx, vf_idx.data(), 3 * (size_t)F, s));
+  int rc = upload_bvh(ctx, ht, ctx->tbvh);
+  if (rc) return rc;
+  rc = upload_bvh(ctx, he2, ctx->ebvh);
+  if (rc) return rc;
+  ctx->V = V; ctx->F = F; ctx->E = E;
+  CK(ctx->X.alloc(V)); CK(ctx->Xm.alloc(V)); CK(ctx->alb.alloc(V)); CK(ctx->nrm.alloc(V));
+  CK(ctx->ng.alloc(F)); CK(ctx->tv.alloc(3 * (size_t)F));
+  CK(ctx->sil.alloc(E)); CK(ctx->block_count.alloc((E + 255) / 256));
+  CK(ctx->dX.alloc(V)); CK(ctx->dN.alloc(V)); CK(ctx->dA.alloc(V)); CK(ctx->gs.alloc(V));
+  CK(ctx->dXm.alloc(3 * (size_t)V)); CK(ctx->dC.alloc(CS * CS)); CK(ctx->dL.alloc(3 * MAX_LIGHTS));
+  ctx->have_mesh = true;
+  ctx->have_bases = false;
+  return FR_OK;
+}
+
+int fr_upload_bases(fr_ctx* ctx, const float* B_id, int32_t K_id, const float* B_exp, int32_t K_exp,
+                    const float* alb_mean, const float* B_alb, int32_t K_alb) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  if (!ctx->have_mesh) return fail(ctx, FR_ERR_NOT_READY, "upload the mesh first");
+  if (K_id < 0 || K_exp < 0 || K_alb < 0 || K_id + K_exp + K_alb > 512)
+    return fail(ctx, FR_ERR_INVALID_ARG, "basis sizes must be >= 0 with K_id + K_exp + K_alb <= 512");
+  if (!alb_mean || (K_id && !B_id) || (K_exp && !B_exp) || (K_alb && !B_alb))
+    return fail(ctx, FR_ERR_INVALID_ARG, "basis pointer is null");
+  CK(cudaSetDevice(ctx->device));
+  const size_t n3 = 3 * (size_t)ctx->V;
+  auto transpose = [&](const float* B, int K) {
+    std::vector<float> T((size_t)K * n3);
+    for (size_t i = 0; i < n3; ++i)
+      for (int k = 0; k < K; ++k) T[(size_t)k * n3 + i] = B[i * K + k];
+    return T;
+  };
+  std::vector<float> t;
+  t = transpose(B_id, K_id);
+  CK(upload(ctx->BidT, t.data(), t.size(), ctx->stream));
+  t = transpose(B_exp, K_exp);
+  CK(upload(ctx->BexpT, t.data(), t.size(), ctx->stream));
+  t = transpose(B_alb, K_alb);
+  CK(upload(ctx->BalbT, t.data(), t.size(), ctx->stream));
+  CK(upload(ctx->alb_mean, alb_mean, n3, ctx->stream));
+  ctx->K_id = K_id; ctx->K_exp = K_exp; ctx->K_alb = K_alb;
+  ctx->have_bases = true;
+  return FR_OK;
+}
+
+int32_t fr_n_params(const fr_ctx* ctx) { return ctx ? ctx->n_params() : FR_ERR_INVALID_ARG; }
+
+int fr_render(fr_ctx* ctx, const float* theta, const fr_render_opts* opts, float* image) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  int rc = check_opts(ctx, opts);
+  if (rc) return rc;
+  if (!image) return fail(ctx, FR_ERR_INVALID_ARG, "image is null");
+  CK(cudaSetDevice(ctx->device));
+  rc = prepare(ctx, theta, opts->W, opts->H);
+  if (rc) return rc;
+  RenderArgs a = render_args(ctx, theta, opts);
+  if (ctx->counters_on) CK(cudaMemsetAsync(ctx->counters.p, 0, 8 * sizeof(unsigned long long), ctx->stream));
+  bool shuffle = opts->spp <= 32 && (32 % opts->spp) == 0;
+  if (!shuffle) CK(cudaMemsetAsync(image, 0, sizeof(float) * 3 * (size_t)opts->W * opts->H, ctx->stream));
+  long long threads = (long long)(((opts->W + 7) / 8) * ((opts->H + 7) / 8)) * 64 * opts->spp;
+  k_render_fwd<<<grid_for(threads, 256), 256, 0, ctx->stream>>>(a, image);
+  CKL();
+  return FR_OK;
+}
+
+int fr_render_backward(fr_ctx* ctx, const float* theta, const fr_render_opts* opts, const float* d_image,
+                       double* grad, int32_t accumulate) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  int rc = check_opts(ctx, opts);
+  if (rc) return rc;
+  if (!d_image || !grad) return fail(ctx, FR_ERR_INVALID_ARG, "d_image or grad is null");
+  CK(cudaSetDevice(ctx->device));
+  rc = prepare(ctx, theta, opts->W, opts->H);
+  if (rc) return rc;
+  cudaStream_t s = ctx->stream;
+  const int V = ctx->V;
+  if (!accumulate) CK(cudaMemsetAsync(grad, 0, sizeof(double) * ctx->n_params(), s));
+  CK(cudaMemsetAsync(ctx->dX.p, 0, sizeof(float4) * V, s));
+  CK(cudaMemsetAsync(ctx->dN.p, 0, sizeof(float4) * V, s));
+  CK(cudaMemsetAsync(ctx->dA.p, 0, sizeof(float4) * V, s));
+  CK(cudaMemsetAsync(ctx->dC.p, 0, sizeof(float) * CS * CS, s));
+  CK(cudaMemsetAsync(ctx->dL.p, 0, sizeof(float) * 3 * MAX_LIGHTS, s));
+  if (ctx->counters_on) CK(cudaMemsetAsync(ctx->counters.p, 0, 8 * sizeof(unsigned long long), s));
+  RenderArgs a = render_args(ctx, theta, opts);
+  GradBufs gb;
+  gb.dX = ctx->dX.p; gb.dN = ctx->dN.p; gb.dA = ctx->dA.p; gb.dC = ctx->dC.p; gb.dL = ctx->dL.p;
+  gb.d_image = d_image;
+  const int terms = opts->terms ? opts->terms : (TERM_INTERIOR | TERM_PEDGE | TERM_SEDGE);
+  long long tiled = (long long)(((opts->W + 7) / 8) * ((opts->H + 7) / 8)) * 64 * opts->spp;
+  if (terms & TERM_INTERIOR) {
+    k_bwd_interior<<<grid_for(tiled, 256), 256, 0, s>>>(a, gb);
+    CKL();
+  }
+  if (terms & TERM_PEDGE) {
+    k_bwd_pedge<<<grid_for((long long)opts->W * opts->H * opts->spp, 256), 256, 0, s>>>(a, gb);
+    CKL();
+  }
+  if (terms & TERM_SEDGE) {
+    k_bwd_sedge<<<grid_for(tiled, 256), 256, 0, s>>>(a, gb);
+    CKL();
+  }
+  GeoArgs g = geo_args(ctx);
+  k_normals_bwd_vertex<<<(V + 255) / 256, 256, 0, s>>>(g, ctx->dN.p, ctx->gs.p);
+  CKL();
+  k_normals_bwd_gather<<<(V + 255) / 256, 256, 0, s>>>(g, ctx->gs.p, ctx->dX.p);
+  CKL();
+  k_pose_bwd<<<152, 256, 0, s>>>(g, theta, ctx->dX.p, ctx->dXm.p, grad);
+  CKL();
+  const int n3 = 3 * V;
+  if (ctx->K_id) { k_basis_T<<<ctx->K_id, 256, 0, s>>>(ctx->BidT.p, ctx->K_id, n3, ctx->dXm.p, nullptr, grad, 0); CKL(); }
+  if (ctx->K_exp) { k_basis_T<<<ctx->K_exp, 256, 0, s>>>(ctx->BexpT.p, ctx->K_exp, n3, ctx->dXm.p, nullptr, grad, ctx->K_id); CKL(); }
+  if (ctx->K_alb) {
+    k_basis_T<<<ctx->K_alb, 256, 0, s>>>(ctx->BalbT.p, ctx->K_alb, n3, nullptr, ctx->dA.p, grad, ctx->K_id + ctx->K_exp);
+    CKL();
+  }
+  k_add_small<<<(CS * CS + 255) / 256, 256, 0, s>>>(ctx->dC.p, CS * CS, grad, ctx->off_cspec());
+  CKL();
+  k_add_small<<<1, 128, 0, s>>>(ctx->dL.p, 3 * ctx->cfg.n_lights, grad, ctx->off_lights());
+  CKL();
+  return FR_OK;
+}
+
+int fr_loss(fr_ctx* ctx, const float* theta, int32_t W, int32_t H, const float* image, const float* target,
+            const uint8_t* mask, const float* m, float w1, float w2, double* loss, float* d_image, double* grad) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  if (!theta || !image || !target || !loss || W < 1 || H < 1)
+    return fail(ctx, FR_ERR_INVALID_ARG, "loss: null pointer or bad size");
+  if (!ctx->have_bases) return fail(ctx, FR_ERR_NOT_READY, "bases not uploaded");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemsetAsync(loss, 0, sizeof(double), s));
+  int n = W * H;
+  int blocks = std::min((n + 255) / 256, 4 * 152);
+  k_loss_data<<<blocks, 256, 0, s>>>(n, image, target, mask, loss, d_image);
+  CKL();
+  k_loss_reg<<<1, 256, 0, s>>>(theta, ctx->K_id + ctx->K_exp + ctx->K_alb, ctx->off_lights(), 3 * ctx->cfg.n_lights,
+                               m, w1, w2, loss, grad);
+  CKL();
+  return FR_OK;
+}
+
+int fr_geometry(fr_ctx* ctx, const float* theta, float* X, float* N, float* A) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  CK(cudaSetDevice(ctx->device));
+  int rc = prepare(ctx, theta, 1, 1);
+  if (rc) return rc;
+  const int V = ctx->V;
+  cudaStream_t s = ctx->stream;
+  if (X) CK(cudaMemcpy2DAsync(X, 3 * sizeof(float), ctx->X.p, sizeof(float4), 3 * sizeof(float), V, cudaMemcpyDeviceToDevice, s));
+  if (N) CK(cudaMemcpy2DAsync(N, 3 * sizeof(float), ctx->nrm.p, sizeof(float4), 3 * sizeof(float), V, cudaMemcpyDeviceToDevice, s));
+  if (A) CK(cudaMemcpy2DAsync(A, 3 * sizeof(float), ctx->alb.p, sizeof(float4), 3 * sizeof(float), V, cudaMemcpyDeviceToDevice, s));
+  int nsil = 0;
+  CK(cudaMemcpyAsync(&nsil, ctx->n_sil.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return nsil;
+}
+
+int fr_light_stage(const fr_ctx* ctx, float* out) {
+  if (!ctx || !out) return FR_ERR_INVALID_ARG;
+  for (int k = 0; k < ctx->cfg.n_lights; ++k) {
+    const Light& L = ctx->lights[k];
+    float v[12] = {L.c.x, L.c.y, L.c.z, L.e1.x, L.e1.y, L.e1.z, L.e2.x, L.e2.y, L.e2.z, L.dl.x, L.dl.y, L.dl.z};
+    std::memcpy(out + 12 * k, v, sizeof v);
+  }
+  return FR_OK;
+}
+
+int fr_set_counters(fr_ctx* ctx, int32_t enable) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  ctx->counters_on = enable != 0;
+  return FR_OK;
+}
+
+int fr_get_counters(fr_ctx* ctx, uint64_t* out) {
+  if (!ctx || !out) return FR_ERR_INVALID_ARG;
+  unsigned long long c[8];
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy(c, ctx->counters.p, sizeof c, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < 8; ++i) out[i] = c[i];
+  return FR_OK;
+}
+
+uint64_t fr_launch_count(const fr_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+// Wait for the context stream and report device-side limit hits (traversal
+// stack overflow or step cap) raised since the last call, clearing the flag.
+int fr_sync(fr_ctx* ctx) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  int flag = 0;
+  CK(cudaMemcpy(&flag, ctx->err_flag.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    CK(cudaMemset(ctx->err_flag.p, 0, sizeof(int)));
+    return fail(ctx, FR_ERR_DEVICE_LIMIT, "device traversal limit reached (flags 0x%x)", flag);
+  }
+  return FR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,393 @@
+// Device helpers shared by the facert kernels.
+//
+// Decision arithmetic.  Every discrete decision of the renderer (which
+// triangle a ray hits, whether a shadow ray is blocked, whether an edge is a
+// silhouette or can cast a shadow onto a light, which pixel an edge sample
+// lands in) is computed in FP32 with explicitly rounded intrinsics
+// (__fmul_rn, __fadd_rn, ...), which the compiler never fuses into FMAs.  The
+// order of operations of each predicate is part of its definition, so the
+// decisions are reproducible by any IEEE FP32 implementation of the same
+// formula.  Values (radiance, derivatives) use ordinary FP32 arithmetic.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define FR_DEV __device__ __forceinline__
+
+namespace fr {
+
+constexpr int CS = 32;              // specular map resolution
+constexpr int MAX_LIGHTS = 32;
+constexpr float PI_F = 3.14159265358979323846f;
+
+// Stream tags of the Philox counter word 2 (tag << 8 | light).
+enum { TAG_CAMERA = 0, TAG_LIGHT = 1, TAG_PEDGE = 2, TAG_PEDGE_LIGHT = 3, TAG_SEDGE_POINT = 4,
+       TAG_SEDGE_PICK = 5 };
+enum { TERM_INTERIOR = 1, TERM_PEDGE = 2, TERM_SEDGE = 4 };
+enum { ERR_STACK = 1, ERR_STEPS = 2 };
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
+struct U4 { uint32_t x, y, z, w; };
+
+FR_DEV U4 philox(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+  }
+  return U4{c0, c1, c2, c3};
+}
+// 24-bit uniform in [0, 1), exact in FP32.
+FR_DEV float unitf(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
+
+// ---------------------------------------------------------------------------
+// small vector type (values)
+struct V3 { float x, y, z; };
+FR_DEV V3 v3(float x, float y, float z) { return V3{x, y, z}; }
+FR_DEV V3 v3(float4 a) { return V3{a.x, a.y, a.z}; }
+FR_DEV V3 operator+(V3 a, V3 b) { return V3{a.x + b.x, a.y + b.y, a.z + b.z}; }
+FR_DEV V3 operator-(V3 a, V3 b) { return V3{a.x - b.x, a.y - b.y, a.z - b.z}; }
+FR_DEV V3 operator-(V3 a) { return V3{-a.x, -a.y, -a.z}; }
+FR_DEV V3 operator*(V3 a, float s) { return V3{a.x * s, a.y * s, a.z * s}; }
+FR_DEV V3 operator*(float s, V3 a) { return V3{a.x * s, a.y * s, a.z * s}; }
+FR_DEV V3& operator+=(V3& a, V3 b) { a.x += b.x; a.y += b.y; a.z += b.z; return a; }
+FR_DEV V3& operator-=(V3& a, V3 b) { a.x -= b.x; a.y -= b.y; a.z -= b.z; return a; }
+FR_DEV float dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+FR_DEV V3 cross(V3 a, V3 b) { return V3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
+FR_DEV float len(V3 a) { return sqrtf(dot(a, a)); }
+FR_DEV V3 normalize(V3 a) { return a * rsqrtf(dot(a, a)); }
+
+// ---------------------------------------------------------------------------
+// exactly rounded decision arithmetic
+FR_DEV float dot3r(V3 a, V3 b) {
+  float p = __fmul_rn(a.x, b.x);
+  p = __fadd_rn(p, __fmul_rn(a.y, b.y));
+  p = __fadd_rn(p, __fmul_rn(a.z, b.z));
+  return p;
+}
+FR_DEV V3 sub3r(V3 a, V3 b) { return V3{__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y), __fsub_rn(a.z, b.z)}; }
+FR_DEV V3 cross3r(V3 a, V3 b) {
+  return V3{__fsub_rn(__fmul_rn(a.y, b.z), __fmul_rn(a.z, b.y)),
+            __fsub_rn(__fmul_rn(a.z, b.x), __fmul_rn(a.x, b.z)),
+            __fsub_rn(__fmul_rn(a.x, b.y), __fmul_rn(a.y, b.x))};
+}
+FR_DEV float comp(V3 a, int k) { return k == 0 ? a.x : (k == 1 ? a.y : a.z); }
+
+// Watertight ray/triangle test (Woop, Benthin, Wald, JCGT 2(1), 2013).
+struct RayPre { int kx, ky, kz; float Sx, Sy, Sz; V3 o; };
+
+FR_DEV RayPre ray_pre(V3 o, V3 d) {
+  RayPre r;
+  float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+  int kz = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
+  int kx = kz + 1; if (kx == 3) kx = 0;
+  int ky = kx + 1; if (ky == 3) ky = 0;
+  float dz = comp(d, kz);
+  if (dz < 0.0f) { int t = kx; kx = ky; ky = t; }
+  r.kx = kx; r.ky = ky; r.kz = kz;
+  r.Sx = __fdiv_rn(comp(d, kx), dz);
+  r.Sy = __fdiv_rn(comp(d, ky), dz);
+  r.Sz = __fdiv_rn(1.0f, dz);
+  r.o = o;
+  return r;
+}
+
+// Line/triangle crossing; writes the ray parameter t (unrestricted).
+FR_DEV bool tri_hit(const RayPre& r, V3 v0, V3 v1, V3 v2, float& t) {
+  V3 A = sub3r(v0, r.o), B = sub3r(v1, r.o), C = sub3r(v2, r.o);
+  float Akz = comp(A, r.kz), Bkz = comp(B, r.kz), Ckz = comp(C, r.kz);
+  float Ax = __fsub_rn(comp(A, r.kx), __fmul_rn(r.Sx, Akz)), Ay = __fsub_rn(comp(A, r.ky), __fmul_rn(r.Sy, Akz));
+  float Bx = __fsub_rn(comp(B, r.kx), __fmul_rn(r.Sx, Bkz)), By = __fsub_rn(comp(B, r.ky), __fmul_rn(r.Sy, Bkz));
+  float Cx = __fsub_rn(comp(C, r.kx), __fmul_rn(r.Sx, Ckz)), Cy = __fsub_rn(comp(C, r.ky), __fmul_rn(r.Sy, Ckz));
+  float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+  float Vv = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+  float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+  if (U == 0.0f || Vv == 0.0f || W == 0.0f) {
+    U = (float)__dsub_rn(__dmul_rn((double)Cx, (double)By), __dmul_rn((double)Cy, (double)Bx));
+    Vv = (float)__dsub_rn(__dmul_rn((double)Ax, (double)Cy), __dmul_rn((double)Ay, (double)Cx));
+    W = (float)__dsub_rn(__dmul_rn((double)Bx, (double)Ay), __dmul_rn((double)By, (double)Ax));
+  }
+  if ((U < 0.0f || Vv < 0.0f || W < 0.0f) && (U > 0.0f || Vv > 0.0f || W > 0.0f)) return false;
+  float det = __fadd_rn(__fadd_rn(U, Vv), W);
+  if (det == 0.0f) return false;
+  float T = __fmul_rn(U, __fmul_rn(r.Sz, Akz));
+  T = __fadd_rn(T, __fmul_rn(Vv, __fmul_rn(r.Sz, Bkz)));
+  T = __fadd_rn(T, __fmul_rn(W, __fmul_rn(r.Sz, Ckz)));
+  t = __fdiv_rn(T, det);
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Scene-level constants passed by value to kernels.
+struct Light { V3 c, e1, e2, dl; };
+
+struct Cam {
+  V3 o;
+  float k, cx, cy, dcam;
+};
+
+FR_DEV V3 camera_dir(const Cam& c, float sx, float sy) {
+  return V3{__fsub_rn(__fmul_rn(sx, c.k), c.cx), __fsub_rn(c.cy, __fmul_rn(sy, c.k)), -1.0f};
+}
+FR_DEV V3 hit_point(V3 o, V3 d, float t) {
+  return V3{__fadd_rn(o.x, __fmul_rn(t, d.x)), __fadd_rn(o.y, __fmul_rn(t, d.y)), __fadd_rn(o.z, __fmul_rn(t, d.z))};
+}
+FR_DEV V3 light_point(const Light& L, float side, float u2, float u3) {
+  float a = __fmul_rn(__fsub_rn(u2, 0.5f), side), b = __fmul_rn(__fsub_rn(u3, 0.5f), side);
+  return V3{__fadd_rn(__fadd_rn(L.c.x, __fmul_rn(a, L.e1.x)), __fmul_rn(b, L.e2.x)),
+            __fadd_rn(__fadd_rn(L.c.y, __fmul_rn(a, L.e1.y)), __fmul_rn(b, L.e2.y)),
+            __fadd_rn(__fadd_rn(L.c.z, __fmul_rn(a, L.e1.z)), __fmul_rn(b, L.e2.z))};
+}
+FR_DEV void project(const Cam& c, V3 p, float& sx, float& sy) {
+  float q = __fsub_rn(c.dcam, p.z);
+  float X = __fdiv_rn(p.x, q), Y = __fdiv_rn(p.y, q);
+  sx = __fdiv_rn(__fadd_rn(X, c.cx), c.k);
+  sy = __fdiv_rn(__fsub_rn(c.cy, Y), c.k);
+}
+
+// ---------------------------------------------------------------------------
+// Bounding-volume hierarchy (binary; both child boxes stored in the parent).
+// Node = 4 float4: (lo0.xyz, hi0.x) (hi0.yz, lo1.xy) (lo1.z, hi1.xyz) (child0, child1, -, -).
+// child >= 0: internal node index; child < 0: leaf, ~child = first << 3 | (count - 1).
+struct BVHView {
+  const float4* nodes;   // [n_nodes * 4]
+  int n_nodes;
+};
+
+// Child code of an absent child (root of a hierarchy with a single leaf).
+constexpr int EMPTY_CHILD = (int)0x80000000;
+FR_DEV bool leaf_child(int c) { return c < 0; }
+FR_DEV int leaf_first(int c) { return (~c) >> 3; }
+FR_DEV int leaf_count(int c) { return ((~c) & 7) + 1; }
+
+// Slab test of a ray against a box; NaN-safe (fminf/fmaxf drop NaN operands,
+// which only widens the accepted interval).
+FR_DEV bool box_hit(V3 lo, V3 hi, V3 o, V3 inv, float tmin, float tmax, float& tenter) {
+  float tx0 = (lo.x - o.x) * inv.x, tx1 = (hi.x - o.x) * inv.x;
+  float ty0 = (lo.y - o.y) * inv.y, ty1 = (hi.y - o.y) * inv.y;
+  float tz0 = (lo.z - o.z) * inv.z, tz1 = (hi.z - o.z) * inv.z;
+  float t0 = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), tmin));
+  float t1 = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
+  tenter = t0;
+  return t0 <= t1;
+}
+
+constexpr int STACK = 48;
+constexpr int MAX_STEPS = 1 << 16;   // node visits per traversal before the error flag is raised
+
+struct Mesh {
+  const float4* X;      // posed vertices [V] (w unused)
+  const float4* ng;     // FP32 face normals [F] (decision form)
+  const int4* tris;     // [F] (v0, v1, v2, -)
+  const float4* tv;     // triangle vertices in BVH leaf order [F*3]; tv[3i].w = original face id bits
+  BVHView bvh;
+};
+
+// Closest hit with ties broken toward the smaller face index.
+FR_DEV int closest_hit(const Mesh& m, V3 o, V3 d, float& t_best, int* err, unsigned long long* cnt) {
+  RayPre rp = ray_pre(o, d);
+  V3 inv = V3{1.0f / d.x, 1.0f / d.y, 1.0f / d.z};
+  int best = -1;
+  t_best = __int_as_float(0x7f800000);
+  int stack[STACK];
+  int sp = 0;
+  int node = 0;
+  int steps = 0;
+  unsigned long long nvis = 0, ntri = 0;
+  if (m.bvh.n_nodes == 0) return -1;
+  while (true) {
+    if (++steps > MAX_STEPS) { atomicOr(err, ERR_STEPS); break; }
+    ++nvis;
+    const float4* N = m.bvh.nodes + 4 * node;
+    float4 a = N[0], b = N[1], c = N[2];
+    int4 ch = *reinterpret_cast<const int4*>(N + 3);
+    float te0, te1;
+    bool h0 = box_hit(V3{a.x, a.y, a.z}, V3{a.w, b.x, b.y}, o, inv, 0.0f, t_best, te0);
+    bool h1 = box_hit(V3{b.z, b.w, c.x}, V3{c.y, c.z, c.w}, o, inv, 0.0f, t_best, te1);
+    int todo[2];
+    int nt = 0;
+    // near child first
+    if (h0 && h1) {
+      if (te1 < te0) { todo[0] = ch.y; todo[1] = ch.x; } else { todo[0] = ch.x; todo[1] = ch.y; }
+      nt = 2;
+    } else if (h0) { todo[0] = ch.x; nt = 1; }
+    else if (h1) { todo[0] = ch.y; nt = 1; }
+    int next = -1;
+    for (int k = 0; k < nt; ++k) {
+      int c2 = todo[k];
+      if (c2 == EMPTY_CHILD) continue;
+      if (leaf_child(c2)) {
+        int f0 = leaf_first(c2), n = leaf_count(c2);
+        for (int i = 0; i < n; ++i) {
+          const float4* T = m.tv + 3 * (f0 + i);
+          float4 p0 = T[0], p1 = T[1], p2 = T[2];
+          int fid = __float_as_int(p0.w);
+          float tt;
+          ++ntri;
+          if (tri_hit(rp, V3{p0.x, p0.y, p0.z}, V3{p1.x, p1.y, p1.z}, V3{p2.x, p2.y, p2.z}, tt) && tt > 0.0f) {
+            if (tt < t_best || (tt == t_best && fid < best)) { t_best = tt; best = fid; }
+          }
+        }
+      } else if (next < 0) {
+        next = c2;
+      } else {
+        if (sp >= STACK) { atomicOr(err, ERR_STACK); goto done; }
+        stack[sp++] = c2;
+      }
+    }
+    if (next >= 0) { node = next; continue; }
+    if (sp == 0) break;
+    node = stack[--sp];
+  }
+done:
+  if (cnt) { atomicAdd(cnt, nvis); atomicAdd(cnt + 1, ntri); }
+  return best;
+}
+
+// Is any face other than `skip` crossed by x + t w, t in (tlo, thi)?
+FR_DEV bool occluded(const Mesh& m, V3 x, V3 w, int skip, float tlo, float thi, int* err, unsigned long long* cnt) {
+  RayPre rp = ray_pre(x, w);
+  V3 inv = V3{1.0f / w.x, 1.0f / w.y, 1.0f / w.z};
+  int stack[STACK];
+  int sp = 0;
+  int node = 0;
+  int steps = 0;
+  bool hit = false;
+  unsigned long long nvis = 0, ntri = 0;
+  if (m.bvh.n_nodes == 0) return false;
+  while (true) {
+    if (++steps > MAX_STEPS) { atomicOr(err, ERR_STEPS); break; }
+    ++nvis;
+    const float4* N = m.bvh.nodes + 4 * node;
+    float4 a = N[0], b = N[1], c = N[2];
+    int4 ch = *reinterpret_cast<const int4*>(N + 3);
+    float te0, te1;
+    bool h0 = box_hit(V3{a.x, a.y, a.z}, V3{a.w, b.x, b.y}, x, inv, 0.0f, thi, te0);
+    bool h1 = box_hit(V3{b.z, b.w, c.x}, V3{c.y, c.z, c.w}, x, inv, 0.0f, thi, te1);
+    int todo[2];
+    int nt = 0;
+    if (h0) todo[nt++] = ch.x;
+    if (h1) todo[nt++] = ch.y;
+    int next = -1;
+    for (int k = 0; k < nt; ++k) {
+      int c2 = todo[k];
+      if (c2 == EMPTY_CHILD) continue;
+      if (leaf_child(c2)) {
+        int f0 = leaf_first(c2), n = leaf_count(c2);
+        for (int i = 0; i < n; ++i) {
+          const float4* T = m.tv + 3 * (f0 + i);
+          float4 p0 = T[0];
+          int fid = __float_as_int(p0.w);
+          if (fid == skip) continue;
+          float4 p1 = T[1], p2 = T[2];
+          float tt;
+          ++ntri;
+          if (tri_hit(rp, V3{p0.x, p0.y, p0.z}, V3{p1.x, p1.y, p1.z}, V3{p2.x, p2.y, p2.z}, tt) && tt > tlo &&
+              tt < thi) {
+            hit = true;
+            goto done;
+          }
+        }
+      } else if (next < 0) {
+        next = c2;
+      } else {
+        if (sp >= STACK) { atomicOr(err, ERR_STACK); goto done; }
+        stack[sp++] = c2;
+      }
+    }
+    if (next >= 0) { node = next; continue; }
+    if (sp == 0) break;
+    node = stack[--sp];
+  }
+done:
+  if (cnt) { atomicAdd(cnt, nvis); atomicAdd(cnt + 1, ntri); }
+  return hit;
+}
+
+FR_DEV int face_flip(const Mesh& m, int f, V3 d) {
+  float4 n = m.ng[f];
+  return dot3r(V3{n.x, n.y, n.z}, d) > 0.0f ? -1 : 1;
+}
+
+// Visibility of light point y from hit point x on face f seen from side `flip`.
+FR_DEV bool visible(const Mesh& m, V3 x, V3 y, int f, int flip, float tmin, int* err, unsigned long long* cnt) {
+  V3 w = sub3r(y, x);
+  float4 n = m.ng[f];
+  float g = dot3r(V3{n.x, n.y, n.z}, w);
+  bool gate = flip > 0 ? g > 0.0f : g < 0.0f;
+  if (!gate) return false;
+  return !occluded(m, x, w, f, tmin, __fsub_rn(1.0f, tmin), err, cnt);
+}
+
+// ---------------------------------------------------------------------------
+// Surface at a hit (values).
+struct Surf {
+  V3 x, ns, wo, rho;
+  float b0, b1, b2;
+  float u, v;
+  float inv_nlen;   // 1 / |interpolated normal|
+  V3 nraw;          // interpolated (unnormalised, unflipped) normal
+  int flip;
+};
+
+// Bilinear specular-map lookup with clamp to edge, texel centres at (k+0.5)/32.
+FR_DEV float cspec_lookup(const float* C, float u, float v, int* idx, float* w, float& fu, float& fv) {
+  float su = u * (float)CS - 0.5f, sv = v * (float)CS - 0.5f;
+  float fu0 = floorf(su), fv0 = floorf(sv);
+  fu = su - fu0; fv = sv - fv0;
+  int iu = (int)fu0, iv = (int)fv0;
+  int iu0 = min(max(iu, 0), CS - 1), iu1 = min(max(iu + 1, 0), CS - 1);
+  int iv0 = min(max(iv, 0), CS - 1), iv1 = min(max(iv + 1, 0), CS - 1);
+  idx[0] = iv0 * CS + iu0; idx[1] = iv0 * CS + iu1; idx[2] = iv1 * CS + iu0; idx[3] = iv1 * CS + iu1;
+  w[0] = (1.0f - fu) * (1.0f - fv); w[1] = fu * (1.0f - fv); w[2] = (1.0f - fu) * fv; w[3] = fu * fv;
+  return w[0] * C[idx[0]] + w[1] * C[idx[1]] + w[2] * C[idx[2]] + w[3] * C[idx[3]];
+}
+
+// Shading of one light: returns h = l (x) f_r cos_x cos_y / d^2 (RGB) and, if
+// requested, the pieces the adjoint needs.
+struct ShadeOut {
+  V3 h;       // RGB integrand
+  float geo;  // cos_x cos_y / d^2
+  float spec; // specular factor before c_s
+  bool active;
+};
+
+FR_DEV ShadeOut shade_light(const Surf& S, float cs, V3 l, V3 y, V3 dl, float m) {
+  ShadeOut o;
+  o.active = false;
+  o.h = V3{0, 0, 0};
+  o.geo = 0; o.spec = 0;
+  V3 w = y - S.x;
+  float d2 = dot(w, w);
+  V3 wi = w * rsqrtf(d2);
+  float ci = dot(S.ns, wi);
+  if (!(ci > 0.0f)) return o;
+  float cy = dot(dl, wi);
+  if (!(cy > 0.0f)) return o;
+  float co = dot(S.ns, S.wo);
+  float spec = 0.0f;
+  if (co > 0.0f) {
+    V3 h = normalize(wi + S.wo);
+    float ch = dot(S.ns, h), oh = dot(S.wo, h);
+    float ch2 = ch * ch;
+    float tan2 = (1.0f - ch2) / ch2;
+    float D = __expf(-tan2 / (m * m)) / (PI_F * m * m * ch2 * ch2);
+    float G = fminf(1.0f, fminf(2.0f * ch * co / oh, 2.0f * ch * ci / oh));
+    spec = D * G / (4.0f * ci * co);
+  }
+  float geo = ci * cy / d2;
+  float sp = cs * spec;
+  o.h = V3{l.x * (S.rho.x * (1.0f / PI_F) + sp) * geo, l.y * (S.rho.y * (1.0f / PI_F) + sp) * geo,
+           l.z * (S.rho.z * (1.0f / PI_F) + sp) * geo};
+  o.geo = geo;
+  o.spec = spec;
+  o.active = true;
+  return o;
+}
+
+}  // namespace fr

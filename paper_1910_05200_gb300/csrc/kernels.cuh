@@ -1,0 +1,128 @@
+// Kernel argument structures and declarations of the facert CUDA kernels.
+#pragma once
+
+#include "common.cuh"
+
+namespace fr {
+
+struct GeoArgs {
+  int V, F, K_id, K_exp, K_alb, off_pose;
+  const float* mean;      // [3V]
+  const float* BidT;      // [K_id][3V]
+  const float* BexpT;     // [K_exp][3V]
+  const float* alb_mean;  // [3V]
+  const float* BalbT;     // [K_alb][3V]
+  const int4* tris;       // [F]
+  const int* tri_perm;    // leaf slot -> face id
+  const int* vf_off;      // [V+1] vertex -> incident faces (CSR)
+  const int* vf_idx;
+  float4* X;              // posed vertices
+  float4* Xm;             // model-space vertices
+  float4* alb;            // albedo
+  float4* nrm;            // unit vertex normals, w = 1/|sum|
+  float4* ng;             // decision-form face normals
+  float4* tv;             // leaf-ordered triangle vertices
+};
+
+struct RefitArgs {
+  int n_leaves;
+  const int* leaf_first;
+  const int* leaf_count;
+  const int* leaf_parent;
+  const int* leaf_slot;
+  const int* node_parent;
+  const int* node_slot;
+  int* counter;           // [n_nodes], zeroed before the launch
+  float4* nodes;
+  int is_edge;
+  const float4* tv;       // triangles (is_edge = 0)
+  const int4* edges;      // leaf-ordered edges (is_edge = 1)
+  const float4* X;
+};
+
+struct SilArgs {
+  int E;
+  const int4* edges;      // canonical order (v0, v1, f0, f1)
+  const int4* tris;
+  const float4* ng;
+  const float4* X;
+  V3 cam_o;
+  int* block_count;
+  int* sil;
+  int* n_sil;
+};
+
+struct EdgeBVH {
+  BVHView bvh;
+  const int4* edges;      // leaf-ordered (v0, v1, f0, f1)
+  const int* edge_id;     // leaf slot -> canonical edge id
+};
+
+struct RenderArgs {
+  int W, H, spp;
+  uint32_t seed, iter;
+  int n_lights;
+  float side, m, eps_pedge, eps_sedge, tmin, kappa;
+  Cam cam;
+  Light lights[MAX_LIGHTS];
+  Mesh mesh;
+  EdgeBVH ebvh;
+  const float4* nrm;
+  const float4* alb;
+  const float2* uv;
+  const float* cspec;     // theta + off_cspec
+  const float* lights_dev;// theta + off_lights
+  const int* sil;         // camera silhouette edges
+  const int* n_sil;
+  const int4* edges_canon;
+  int* err;
+  unsigned long long* counters;  // [8] or null
+};
+
+struct GradBufs {
+  float4* dX;             // [V]
+  float4* dN;             // [V]
+  float4* dA;             // [V]
+  float* dC;              // [1024]
+  float* dL;              // [3N]
+  const float* d_image;   // [H*W*3]
+};
+
+__global__ void k_geometry(GeoArgs g, const float* __restrict__ theta);
+__global__ void k_faces(GeoArgs g);
+__global__ void k_vertex_normals(GeoArgs g);
+__global__ void k_refit(RefitArgs r);
+__global__ void k_silhouette_flags(SilArgs s);
+__global__ void k_silhouette_scan(SilArgs s, int nblocks);
+__global__ void k_silhouette_scatter(SilArgs s);
+__global__ void k_normals_bwd_vertex(GeoArgs g, const float4* __restrict__ dN, float4* __restrict__ gs);
+__global__ void k_normals_bwd_gather(GeoArgs g, const float4* __restrict__ gs, float4* __restrict__ dX);
+__global__ void k_pose_bwd(GeoArgs g, const float* __restrict__ theta, const float4* __restrict__ dX,
+                           float* __restrict__ dXm, double* __restrict__ grad);
+__global__ void k_basis_T(const float* __restrict__ BT, int K, int n, const float* __restrict__ y,
+                          const float4* __restrict__ y4, double* __restrict__ grad, int out_off);
+__global__ void k_add_small(const float* __restrict__ src, int n, double* __restrict__ grad, int off);
+
+__global__ void k_render_fwd(RenderArgs a, float* __restrict__ image);
+__global__ void k_bwd_interior(RenderArgs a, GradBufs gb);
+__global__ void k_bwd_pedge(RenderArgs a, GradBufs gb);
+__global__ void k_bwd_sedge(RenderArgs a, GradBufs gb);
+
+__global__ void k_loss_data(int n_pix, const float* __restrict__ image, const float* __restrict__ target,
+                            const uint8_t* __restrict__ mask, double* __restrict__ loss, float* __restrict__ d_image);
+__global__ void k_loss_reg(const float* __restrict__ theta, int n_prior, int off_lights, int n_light_vals,
+                           const float* __restrict__ m, float w1, float w2, double* __restrict__ loss,
+                           double* __restrict__ grad);
+
+// Pixel order: 8x8 tiles, row-major tiles; returns false for pixels outside the image.
+FR_DEV bool tile_pixel(int idx, int W, int H, int& px, int& py) {
+  int tiles_x = (W + 7) >> 3;
+  int tile = idx >> 6, in = idx & 63;
+  int tx = tile % tiles_x, ty = tile / tiles_x;
+  px = (tx << 3) + (in & 7);
+  py = (ty << 3) + (in >> 3);
+  return px < W && py < H;
+}
+FR_DEV int tiled_pixel_count(int W, int H) { return ((W + 7) >> 3) * ((H + 7) >> 3) * 64; }
+
+}  // namespace fr

@@ -1,0 +1,576 @@
+// Monte-Carlo render of the light stage and its gradient.
+//
+// Forward (Optimization paragraph, p^T = F(f_r, l_j, alpha, beta, R, t)):
+// one thread per (pixel, sample): jittered camera ray, closest hit, one
+// uniform point on every light that is on, a shadow ray for self-shadows,
+// Cook-Torrance shading (Face Modeling paragraph).
+//
+// Backward (Face Modeling paragraph: backpropagation through Li et al.'s
+// differentiable ray tracer): every intersection is recomputed with the same
+// samples.  Three kernels add into per-vertex and per-parameter FP32
+// accumulators:
+//   k_bwd_interior  exact derivative of each sample's estimate with its
+//                   decisions held fixed (all lights, for dL/dl_j);
+//   k_bwd_pedge     primary-visibility edge sampling: one sample per camera
+//                   sample index, uniform over camera-silhouette edges and
+//                   uniform along the edge, radiance differenced across it;
+//   k_bwd_sedge     shadow-boundary edge sampling: per camera sample and light
+//                   that is on, one edge picked uniformly (minimum Philox key)
+//                   among the edges that are silhouettes seen from the shading
+//                   point and whose central projection crosses the light square.
+#include "kernels.cuh"
+
+namespace fr {
+
+FR_DEV Surf surface(const RenderArgs& a, int f, V3 o, V3 d, int flip) {
+  int4 t = a.mesh.tris[f];
+  V3 P0 = v3(a.mesh.X[t.x]), P1 = v3(a.mesh.X[t.y]), P2 = v3(a.mesh.X[t.z]);
+  V3 e1 = P1 - P0, e2 = P2 - P0, s = o - P0;
+  V3 pv = cross(d, e2);
+  float inv = 1.0f / dot(e1, pv);
+  V3 qv = cross(s, e1);
+  Surf S;
+  S.b1 = dot(s, pv) * inv;
+  S.b2 = dot(d, qv) * inv;
+  S.b0 = 1.0f - S.b1 - S.b2;
+  float tt = dot(e2, qv) * inv;
+  S.x = o + d * tt;
+  V3 N0 = v3(a.nrm[t.x]), N1 = v3(a.nrm[t.y]), N2 = v3(a.nrm[t.z]);
+  S.nraw = N0 * S.b0 + N1 * S.b1 + N2 * S.b2;
+  S.inv_nlen = rsqrtf(dot(S.nraw, S.nraw));
+  S.ns = S.nraw * (S.inv_nlen * (float)flip);
+  S.wo = normalize(-d);
+  V3 A0 = v3(a.alb[t.x]), A1 = v3(a.alb[t.y]), A2 = v3(a.alb[t.z]);
+  S.rho = A0 * S.b0 + A1 * S.b1 + A2 * S.b2;
+  float2 u0 = a.uv[t.x], u1 = a.uv[t.y], u2 = a.uv[t.z];
+  S.u = S.b0 * u0.x + S.b1 * u1.x + S.b2 * u2.x;
+  S.v = S.b0 * u0.y + S.b1 * u1.y + S.b2 * u2.y;
+  S.flip = flip;
+  return S;
+}
+
+FR_DEV V3 light_rgb(const RenderArgs& a, int j) {
+  const float* l = a.lights_dev + 3 * j;
+  return V3{__ldg(l), __ldg(l + 1), __ldg(l + 2)};
+}
+// A light is off when all three channels are exactly zero.
+FR_DEV bool light_on(const RenderArgs& a, int j) {
+  V3 l = light_rgb(a, j);
+  return l.x != 0.0f || l.y != 0.0f || l.z != 0.0f;
+}
+
+// One-sample radiance along a camera ray, lights that are on only.
+FR_DEV V3 radiance(const RenderArgs& a, V3 o, V3 d, int tag, uint32_t c0, uint32_t c1, unsigned long long* cnt) {
+  float t;
+  int f = closest_hit(a.mesh, o, d, t, a.err, cnt);
+  if (f < 0) return V3{0, 0, 0};
+  int flip = face_flip(a.mesh, f, d);
+  V3 x32 = hit_point(o, d, t);
+  Surf S = surface(a, f, o, d, flip);
+  int idx[4];
+  float w[4], fu, fv;
+  float cs = cspec_lookup(a.cspec, S.u, S.v, idx, w, fu, fv);
+  V3 L{0, 0, 0};
+  const float area = a.side * a.side;
+  for (int j = 0; j < a.n_lights; ++j) {
+    if (!light_on(a, j)) continue;
+    U4 q = philox(a.seed, a.iter, c0, c1, (uint32_t)(tag << 8 | j), 0);
+    V3 y = light_point(a.lights[j], a.side, unitf(q.x), unitf(q.y));
+    if (!visible(a.mesh, x32, y, f, flip, a.tmin, a.err, cnt)) continue;
+    ShadeOut sh = shade_light(S, cs, light_rgb(a, j), y, a.lights[j].dl, a.m);
+    L += sh.h * area;
+  }
+  return L;
+}
+
+// Camera ray of sample s of pixel (px, py).
+FR_DEV V3 sample_dir(const RenderArgs& a, int px, int py, int s, uint32_t& pix) {
+  pix = (uint32_t)(py * a.W + px);
+  U4 q = philox(a.seed, a.iter, pix, (uint32_t)s, (uint32_t)(TAG_CAMERA << 8), 0);
+  float sx = __fadd_rn((float)px, unitf(q.x));
+  float sy = __fadd_rn((float)py, unitf(q.y));
+  return camera_dir(a.cam, sx, sy);
+}
+
+__global__ void __launch_bounds__(256) k_render_fwd(RenderArgs a, float* __restrict__ image) {
+  const int spp = a.spp;
+  long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long total = (long long)tiled_pixel_count(a.W, a.H) * spp;
+  int ip = (int)(tid / spp), s = (int)(tid - (long long)ip * spp);
+  int px = 0, py = 0;
+  bool valid = tid < total && tile_pixel(ip, a.W, a.H, px, py);
+  unsigned long long* cnt = a.counters;
+  V3 L{0, 0, 0};
+  uint32_t pix = 0;
+  if (valid) {
+    V3 d = sample_dir(a, px, py, s, pix);
+    L = radiance(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt);
+  }
+  const float inv = 1.0f / (float)spp;
+  if (spp <= 32 && (32 % spp) == 0) {
+    for (int off = spp >> 1; off > 0; off >>= 1) {
+      L.x += __shfl_xor_sync(0xffffffffu, L.x, off);
+      L.y += __shfl_xor_sync(0xffffffffu, L.y, off);
+      L.z += __shfl_xor_sync(0xffffffffu, L.z, off);
+    }
+    if (valid && s == 0) {
+      image[3 * pix] = L.x * inv; image[3 * pix + 1] = L.y * inv; image[3 * pix + 2] = L.z * inv;
+    }
+  } else if (valid) {
+    atomicAdd(&image[3 * pix], L.x * inv);
+    atomicAdd(&image[3 * pix + 1], L.y * inv);
+    atomicAdd(&image[3 * pix + 2], L.z * inv);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Interior adjoint
+
+// Reverse-mode of shade_light for one light.  G = adjoint RGB times area/spp.
+FR_DEV void shade_light_bwd(const Surf& S, float cs, V3 l, V3 y, V3 dl, float m, V3 G, V3& g_x, V3& g_ns,
+                            V3& g_rho, float& g_cs, V3& g_l) {
+  V3 w = y - S.x;
+  float d2 = dot(w, w);
+  float ir = rsqrtf(d2);
+  V3 wi = w * ir;
+  float ci = dot(S.ns, wi);
+  if (!(ci > 0.0f)) return;
+  float cy = dot(dl, wi);
+  if (!(cy > 0.0f)) return;
+  float co = dot(S.ns, S.wo);
+  float spec = 0.0f, D = 0.0f, Gf = 0.0f, ch = 0.0f, oh = 0.0f, g1 = 0.0f, g2 = 0.0f, hlen = 1.0f;
+  int branch = 0;
+  V3 h{0, 0, 0};
+  if (co > 0.0f) {
+    V3 hv = wi + S.wo;
+    hlen = len(hv);
+    h = hv * (1.0f / hlen);
+    ch = dot(S.ns, h);
+    oh = dot(S.wo, h);
+    float ch2 = ch * ch;
+    float tan2 = (1.0f - ch2) / ch2;
+    D = __expf(-tan2 / (m * m)) / (PI_F * m * m * ch2 * ch2);
+    g1 = 2.0f * ch * co / oh;
+    g2 = 2.0f * ch * ci / oh;
+    float inner = g1 <= g2 ? g1 : g2;
+    if (1.0f <= inner) { Gf = 1.0f; branch = 0; }
+    else { Gf = inner; branch = g1 <= g2 ? 1 : 2; }
+    spec = D * Gf / (4.0f * ci * co);
+  }
+  float geo = ci * cy / d2;
+  const float ip = 1.0f / PI_F;
+  V3 F{S.rho.x * ip + cs * spec, S.rho.y * ip + cs * spec, S.rho.z * ip + cs * spec};
+  g_l += V3{G.x * F.x * geo, G.y * F.y * geo, G.z * F.z * geo};
+  V3 s{G.x * l.x, G.y * l.y, G.z * l.z};
+  g_rho += s * (geo * ip);
+  float Ssum = (s.x + s.y + s.z) * geo;
+  g_cs += Ssum * spec;
+  float d_spec = Ssum * cs;
+  float d_geo = s.x * F.x + s.y * F.y + s.z * F.z;
+  float d_ci = d_geo * cy / d2;
+  float d_cy = d_geo * ci / d2;
+  float d_d2 = -d_geo * geo / d2;
+  float d_co = 0.0f;
+  V3 d_ns{0, 0, 0}, d_wi{0, 0, 0};
+  if (co > 0.0f && d_spec != 0.0f) {
+    float k4 = 4.0f * ci * co;
+    float d_D = d_spec * Gf / k4, d_G = d_spec * D / k4;
+    d_ci -= d_spec * spec / ci;
+    d_co -= d_spec * spec / co;
+    float d_ch = 0.0f, d_oh = 0.0f;
+    if (branch == 1) { d_ch += d_G * 2.0f * co / oh; d_co += d_G * 2.0f * ch / oh; d_oh -= d_G * g1 / oh; }
+    else if (branch == 2) { d_ch += d_G * 2.0f * ci / oh; d_ci += d_G * 2.0f * ch / oh; d_oh -= d_G * g2 / oh; }
+    d_ch += d_D * D * (2.0f / (m * m * ch * ch * ch) - 4.0f / ch);
+    d_ns += h * d_ch;
+    V3 d_h = S.ns * d_ch + S.wo * d_oh;
+    d_wi += (d_h - h * dot(d_h, h)) * (1.0f / hlen);
+  }
+  d_ns += wi * d_ci + S.wo * d_co;
+  d_wi += S.ns * d_ci + dl * d_cy;
+  V3 d_w = (d_wi - wi * dot(d_wi, wi)) * ir + w * (2.0f * d_d2);
+  g_x -= d_w;
+  g_ns += d_ns;
+}
+
+FR_DEV void atomic_add3(float4* p, V3 v) {
+  atomicAdd(p, make_float4(v.x, v.y, v.z, 0.0f));
+}
+
+// Adjoint of the hit point x = o + t d with respect to the hit triangle's
+// vertices (ray fixed), plus barycentric adjoints g_b1, g_b2 (b0 = 1-b1-b2
+// already folded in).  Scatters b_k * lambda into dX.
+FR_DEV void hit_adjoint(const RenderArgs& a, int f, V3 d, const Surf& S, V3 g_x, float g_b1, float g_b2,
+                        float4* dX) {
+  int4 t = a.mesh.tris[f];
+  V3 P0 = v3(a.mesh.X[t.x]), P1 = v3(a.mesh.X[t.y]), P2 = v3(a.mesh.X[t.z]);
+  V3 e1 = P1 - P0, e2 = P2 - P0;
+  V3 n = cross(e1, e2);
+  float det = dot(d, n);
+  float g_t = dot(g_x, d);
+  V3 lam = (n * g_t + cross(d, e2) * g_b1 + cross(e1, d) * g_b2) * (1.0f / det);
+  atomic_add3(dX + t.x, lam * S.b0);
+  atomic_add3(dX + t.y, lam * S.b1);
+  atomic_add3(dX + t.z, lam * S.b2);
+}
+
+__global__ void __launch_bounds__(256) k_bwd_interior(RenderArgs a, GradBufs gb) {
+  __shared__ float sC[CS * CS];
+  __shared__ float sL[3 * MAX_LIGHTS];
+  for (int i = threadIdx.x; i < CS * CS; i += blockDim.x) sC[i] = 0.0f;
+  for (int i = threadIdx.x; i < 3 * MAX_LIGHTS; i += blockDim.x) sL[i] = 0.0f;
+  __syncthreads();
+  const int spp = a.spp;
+  long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long total = (long long)tiled_pixel_count(a.W, a.H) * spp;
+  int ip = (int)(tid / spp), s = (int)(tid - (long long)ip * spp);
+  int px = 0, py = 0;
+  unsigned long long* cnt = a.counters ? a.counters + 4 : nullptr;
+  if (tid < total && tile_pixel(ip, a.W, a.H, px, py)) {
+    uint32_t pix;
+    V3 d = sample_dir(a, px, py, s, pix);
+    const float* dI = gb.d_image + 3 * (size_t)pix;
+    V3 dimg{dI[0], dI[1], dI[2]};
+    float t;
+    int f = (dimg.x != 0.0f || dimg.y != 0.0f || dimg.z != 0.0f) ? closest_hit(a.mesh, a.cam.o, d, t, a.err, cnt) : -1;
+    if (f >= 0) {
+      int flip = face_flip(a.mesh, f, d);
+      V3 x32 = hit_point(a.cam.o, d, t);
+      Surf S = surface(a, f, a.cam.o, d, flip);
+      int idx[4];
+      float w[4], fu, fv;
+      float cs = cspec_lookup(a.cspec, S.u, S.v, idx, w, fu, fv);
+      const float scale = a.side * a.side / (float)spp;
+      V3 G = dimg * scale;
+      V3 g_x{0, 0, 0}, g_ns{0, 0, 0}, g_rho{0, 0, 0};
+      float g_cs = 0.0f;
+      for (int j = 0; j < a.n_lights; ++j) {
+        U4 q = philox(a.seed, a.iter, pix, (uint32_t)s, (uint32_t)(TAG_LIGHT << 8 | j), 0);
+        V3 y = light_point(a.lights[j], a.side, unitf(q.x), unitf(q.y));
+        if (!visible(a.mesh, x32, y, f, flip, a.tmin, a.err, cnt)) continue;
+        V3 g_l{0, 0, 0};
+        shade_light_bwd(S, cs, light_rgb(a, j), y, a.lights[j].dl, a.m, G, g_x, g_ns, g_rho, g_cs, g_l);
+        atomicAdd(&sL[3 * j], g_l.x);
+        atomicAdd(&sL[3 * j + 1], g_l.y);
+        atomicAdd(&sL[3 * j + 2], g_l.z);
+      }
+      int4 tri = a.mesh.tris[f];
+      // shading normal: ns = flip * n / |n|
+      V3 nh = S.nraw * S.inv_nlen;
+      V3 dnh = g_ns * (float)flip;
+      V3 g_n = (dnh - nh * dot(nh, dnh)) * S.inv_nlen;
+      V3 N0 = v3(a.nrm[tri.x]), N1 = v3(a.nrm[tri.y]), N2 = v3(a.nrm[tri.z]);
+      V3 A0 = v3(a.alb[tri.x]), A1 = v3(a.alb[tri.y]), A2 = v3(a.alb[tri.z]);
+      atomic_add3(gb.dN + tri.x, g_n * S.b0);
+      atomic_add3(gb.dN + tri.y, g_n * S.b1);
+      atomic_add3(gb.dN + tri.z, g_n * S.b2);
+      atomic_add3(gb.dA + tri.x, g_rho * S.b0);
+      atomic_add3(gb.dA + tri.y, g_rho * S.b1);
+      atomic_add3(gb.dA + tri.z, g_rho * S.b2);
+      float gb0 = dot(N0, g_n) + dot(A0, g_rho);
+      float gb1 = dot(N1, g_n) + dot(A1, g_rho);
+      float gb2 = dot(N2, g_n) + dot(A2, g_rho);
+      // specular map
+      if (g_cs != 0.0f) {
+        for (int k = 0; k < 4; ++k) atomicAdd(&sC[idx[k]], w[k] * g_cs);
+        const float* C = a.cspec;
+        float C0 = C[idx[0]], C1 = C[idx[1]], C2 = C[idx[2]], C3 = C[idx[3]];
+        float dfu = g_cs * (-(1.0f - fv) * C0 + (1.0f - fv) * C1 - fv * C2 + fv * C3);
+        float dfv = g_cs * (-(1.0f - fu) * C0 - fu * C1 + (1.0f - fu) * C2 + fu * C3);
+        float du = dfu * (float)CS, dv = dfv * (float)CS;
+        float2 u0 = a.uv[tri.x], u1 = a.uv[tri.y], u2 = a.uv[tri.z];
+        gb0 += u0.x * du + u0.y * dv;
+        gb1 += u1.x * du + u1.y * dv;
+        gb2 += u2.x * du + u2.y * dv;
+      }
+      hit_adjoint(a, f, d, S, g_x, gb1 - gb0, gb2 - gb0, gb.dX);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < CS * CS; i += blockDim.x)
+    if (sC[i] != 0.0f) atomicAdd(&gb.dC[i], sC[i]);
+  for (int i = threadIdx.x; i < 3 * a.n_lights; i += blockDim.x)
+    if (sL[i] != 0.0f) atomicAdd(&gb.dL[i], sL[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Primary-visibility edges
+
+__global__ void __launch_bounds__(256) k_bwd_pedge(RenderArgs a, GradBufs gb) {
+  long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long total = (long long)a.W * a.H * a.spp;
+  if (tid >= total) return;
+  const int nS = *a.n_sil;
+  if (nS <= 0) return;
+  uint32_t pix = (uint32_t)(tid / a.spp);
+  int s = (int)(tid - (long long)pix * a.spp);
+  U4 q = philox(a.seed, a.iter, pix, (uint32_t)s, (uint32_t)(TAG_PEDGE << 8), 0);
+  int k = (int)(((unsigned long long)q.x * (unsigned long long)nS) >> 32);
+  float u = unitf(q.y);
+  int4 E = a.edges_canon[a.sil[k]];
+  V3 A = v3(a.mesh.X[E.x]), B = v3(a.mesh.X[E.y]);
+  float ax, ay, bx, by;
+  project(a.cam, A, ax, ay);
+  project(a.cam, B, bx, by);
+  float ex = __fsub_rn(bx, ax), ey = __fsub_rn(by, ay);
+  float mx = __fadd_rn(ax, __fmul_rn(u, ex)), my = __fadd_rn(ay, __fmul_rn(u, ey));
+  float fx = floorf(mx), fy = floorf(my);
+  if (!(fx >= 0.0f && fx < (float)a.W && fy >= 0.0f && fy < (float)a.H)) return;
+  int ipx = (int)fx, ipy = (int)fy;
+  const float* dI = gb.d_image + 3 * ((size_t)ipy * a.W + ipx);
+  V3 dimg{dI[0], dI[1], dI[2]};
+  if (dimg.x == 0.0f && dimg.y == 0.0f && dimg.z == 0.0f) return;
+  float L2 = __fmul_rn(ex, ex);
+  L2 = __fadd_rn(L2, __fmul_rn(ey, ey));
+  float Ln = __fsqrt_rn(L2);
+  if (Ln == 0.0f) return;
+  float nx = __fdiv_rn(-ey, Ln), ny = __fdiv_rn(ex, Ln);
+  float e = a.eps_pedge;
+  V3 dp = camera_dir(a.cam, __fadd_rn(mx, __fmul_rn(e, nx)), __fadd_rn(my, __fmul_rn(e, ny)));
+  V3 dm = camera_dir(a.cam, __fsub_rn(mx, __fmul_rn(e, nx)), __fsub_rn(my, __fmul_rn(e, ny)));
+  unsigned long long* cnt = a.counters ? a.counters + 4 : nullptr;
+  V3 fp = radiance(a, a.cam.o, dp, TAG_PEDGE_LIGHT, pix, (uint32_t)s, cnt);
+  V3 fm = radiance(a, a.cam.o, dm, TAG_PEDGE_LIGHT, pix, (uint32_t)s, cnt);
+  float delta = dot(dimg, fm - fp);
+  if (delta == 0.0f) return;
+  float w = delta * (float)nS / ((float)a.W * (float)a.H * (float)a.spp);
+  float gmx = -ey * w, gmy = ex * w;       // w * R90(e)
+  const float kc = a.cam.k;
+  // adjoint of the screen projection for each endpoint
+  {
+    float qa = a.cam.dcam - A.z, c = 1.0f - u;
+    float gx = gmx * c, gy = gmy * c;
+    atomic_add3(gb.dX + E.x, V3{gx / (kc * qa), -gy / (kc * qa), (gx * A.x - gy * A.y) / (kc * qa * qa)});
+  }
+  {
+    float qb = a.cam.dcam - B.z;
+    float gx = gmx * u, gy = gmy * u;
+    atomic_add3(gb.dX + E.y, V3{gx / (kc * qb), -gy / (kc * qb), (gx * B.x - gy * B.y) / (kc * qb * qb)});
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Shadow-boundary edges
+
+// Clip the edge parameter interval to the part whose central projection from
+// x lands in the light square (decision form).
+FR_DEV bool shadow_clip(V3 A, V3 B, V3 x, const Light& L, float hs, float kappa, float& t0, float& t1) {
+  V3 xc = sub3r(x, L.c);
+  float al1 = dot3r(xc, L.e1), al2 = dot3r(xc, L.e2);
+  float D = -dot3r(xc, L.dl);
+  float ca[5], cb[5];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    V3 q = sub3r(e == 0 ? A : B, x);
+    float h = dot3r(q, L.dl), s1 = dot3r(q, L.e1), s2 = dot3r(q, L.e2);
+    float n1 = __fadd_rn(__fmul_rn(al1, h), __fmul_rn(s1, D));
+    float n2 = __fadd_rn(__fmul_rn(al2, h), __fmul_rn(s2, D));
+    float hh = __fmul_rn(hs, h);
+    float* cc = e == 0 ? ca : cb;
+    cc[0] = __fsub_rn(h, kappa);
+    cc[1] = __fsub_rn(hh, n1);
+    cc[2] = __fadd_rn(hh, n1);
+    cc[3] = __fsub_rn(hh, n2);
+    cc[4] = __fadd_rn(hh, n2);
+  }
+  float lo = 0.0f, hi = 1.0f;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    float p = ca[k], r = cb[k];
+    if (p < 0.0f && r < 0.0f) return false;
+    if (p < 0.0f) { float rr = __fdiv_rn(p, __fsub_rn(p, r)); if (rr > lo) lo = rr; }
+    else if (r < 0.0f) { float rr = __fdiv_rn(p, __fsub_rn(p, r)); if (rr < hi) hi = rr; }
+  }
+  t0 = lo; t1 = hi;
+  return lo < hi;
+}
+
+FR_DEV V3 edge_proj(V3 A, V3 B, V3 x, const Light& L, float D, float tau) {
+  V3 p{__fadd_rn(A.x, __fmul_rn(tau, __fsub_rn(B.x, A.x))), __fadd_rn(A.y, __fmul_rn(tau, __fsub_rn(B.y, A.y))),
+       __fadd_rn(A.z, __fmul_rn(tau, __fsub_rn(B.z, A.z)))};
+  V3 q = sub3r(p, x);
+  float h = dot3r(q, L.dl);
+  float f = __fdiv_rn(D, h);
+  return V3{__fadd_rn(x.x, __fmul_rn(f, q.x)), __fadd_rn(x.y, __fmul_rn(f, q.y)), __fadd_rn(x.z, __fmul_rn(f, q.z))};
+}
+
+FR_DEV bool silhouette_from(const Mesh& m, int4 E, V3 x) {
+  float4 n0 = m.ng[E.z];
+  float s0 = dot3r(v3(n0), sub3r(x, v3(m.X[m.tris[E.z].x])));
+  if (E.w < 0) return s0 != 0.0f;
+  float4 n1 = m.ng[E.w];
+  float s1 = dot3r(v3(n1), sub3r(x, v3(m.X[m.tris[E.w].x])));
+  return (s0 > 0.0f && s1 < 0.0f) || (s0 < 0.0f && s1 > 0.0f);
+}
+
+struct Pick {
+  int n;          // number of candidate edges
+  int edge;       // canonical id of the pick
+  int4 E;         // its (v0, v1, f0, f1)
+  float t0, t1;   // clipped parameter interval
+};
+
+// Enumerate candidate edges with the edge BVH (pyramid culling is
+// conservative; the leaf test decides) and keep the minimum (key, id).
+FR_DEV Pick shadow_pick(const RenderArgs& a, V3 x, int hitf, int j, uint32_t pix, int s, unsigned long long* cnt) {
+  const Light& L = a.lights[j];
+  const float hs = __fmul_rn(0.5f, a.side);
+  Pick P;
+  P.n = 0; P.edge = -1; P.t0 = P.t1 = 0.0f;
+  uint32_t bestkey = 0xffffffffu;
+  // side planes of the pyramid from x through the light square, inward normals
+  V3 Q[4];
+  const float sg[4][2] = {{-1, -1}, {1, -1}, {1, 1}, {-1, 1}};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) Q[k] = L.c + L.e1 * (sg[k][0] * hs) + L.e2 * (sg[k][1] * hs);
+  V3 pn[4];
+  float pm[4];
+  V3 cx = L.c - x;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    V3 n = cross(Q[k] - x, Q[(k + 1) & 3] - x);
+    if (dot(n, cx) < 0.0f) n = -n;
+    pn[k] = n;
+    pm[k] = 1e-4f * len(n);
+  }
+  const float fm = 1e-4f;
+  int stack[STACK];
+  int sp = 0, node = 0, steps = 0;
+  unsigned long long nvis = 0, nedge = 0;
+  if (a.ebvh.bvh.n_nodes == 0) return P;
+  while (true) {
+    if (++steps > MAX_STEPS) { atomicOr(a.err, ERR_STEPS); break; }
+    ++nvis;
+    const float4* N = a.ebvh.bvh.nodes + 4 * node;
+    float4 b0 = N[0], b1 = N[1], b2 = N[2];
+    int4 ch = *reinterpret_cast<const int4*>(N + 3);
+    V3 lo[2] = {V3{b0.x, b0.y, b0.z}, V3{b1.z, b1.w, b2.x}};
+    V3 hi[2] = {V3{b0.w, b1.x, b1.y}, V3{b2.y, b2.z, b2.w}};
+    int todo[2];
+    int nt = 0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      // front plane: some point with (p - x).dl >= kappa
+      V3 pp{L.dl.x > 0 ? hi[c].x : lo[c].x, L.dl.y > 0 ? hi[c].y : lo[c].y, L.dl.z > 0 ? hi[c].z : lo[c].z};
+      bool keep = dot(pp - x, L.dl) >= a.kappa - fm;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        V3 n = pn[k];
+        V3 p{n.x > 0 ? hi[c].x : lo[c].x, n.y > 0 ? hi[c].y : lo[c].y, n.z > 0 ? hi[c].z : lo[c].z};
+        keep = keep && dot(n, p - x) >= -pm[k];
+      }
+      if (keep) todo[nt++] = c == 0 ? ch.x : ch.y;
+    }
+    int next = -1;
+    for (int k = 0; k < nt; ++k) {
+      int c2 = todo[k];
+      if (c2 == EMPTY_CHILD) continue;
+      if (leaf_child(c2)) {
+        int f0 = leaf_first(c2), n = leaf_count(c2);
+        for (int i = 0; i < n; ++i) {
+          int4 E = a.ebvh.edges[f0 + i];
+          ++nedge;
+          if (E.z == hitf || E.w == hitf) continue;
+          if (!silhouette_from(a.mesh, E, x)) continue;
+          float t0, t1;
+          if (!shadow_clip(v3(a.mesh.X[E.x]), v3(a.mesh.X[E.y]), x, L, hs, a.kappa, t0, t1)) continue;
+          int id = a.ebvh.edge_id[f0 + i];
+          uint32_t key = philox(a.seed, a.iter, pix, (uint32_t)s, (uint32_t)(TAG_SEDGE_PICK << 8 | j), (uint32_t)id).x;
+          ++P.n;
+          if (P.edge < 0 || key < bestkey || (key == bestkey && id < P.edge)) {
+            bestkey = key; P.edge = id; P.E = E; P.t0 = t0; P.t1 = t1;
+          }
+        }
+      } else if (next < 0) {
+        next = c2;
+      } else {
+        if (sp >= STACK) { atomicOr(a.err, ERR_STACK); goto done; }
+        stack[sp++] = c2;
+      }
+    }
+    if (next >= 0) { node = next; continue; }
+    if (sp == 0) break;
+    node = stack[--sp];
+  }
+done:
+  if (cnt) { atomicAdd(cnt + 2, nvis); atomicAdd(cnt + 3, nedge); }
+  return P;
+}
+
+__global__ void __launch_bounds__(256) k_bwd_sedge(RenderArgs a, GradBufs gb) {
+  const int spp = a.spp;
+  long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long total = (long long)tiled_pixel_count(a.W, a.H) * spp;
+  int ip = (int)(tid / spp), s = (int)(tid - (long long)ip * spp);
+  int px = 0, py = 0;
+  if (!(tid < total && tile_pixel(ip, a.W, a.H, px, py))) return;
+  uint32_t pix;
+  V3 d = sample_dir(a, px, py, s, pix);
+  const float* dI = gb.d_image + 3 * (size_t)pix;
+  V3 wrgb = V3{dI[0], dI[1], dI[2]} * (1.0f / (float)spp);
+  if (wrgb.x == 0.0f && wrgb.y == 0.0f && wrgb.z == 0.0f) return;
+  unsigned long long* cnt = a.counters ? a.counters + 4 : nullptr;
+  float t;
+  int f = closest_hit(a.mesh, a.cam.o, d, t, a.err, cnt);
+  if (f < 0) return;
+  int flip = face_flip(a.mesh, f, d);
+  V3 x32 = hit_point(a.cam.o, d, t);
+  bool have_surf = false;
+  Surf S;
+  float cs = 0.0f;
+  for (int j = 0; j < a.n_lights; ++j) {
+    if (!light_on(a, j)) continue;
+    Pick P = shadow_pick(a, x32, f, j, pix, s, cnt);
+    if (P.n == 0) continue;
+    const Light& L = a.lights[j];
+    V3 A = v3(a.mesh.X[P.E.x]), B = v3(a.mesh.X[P.E.y]);
+    U4 q = philox(a.seed, a.iter, pix, (uint32_t)s, (uint32_t)(TAG_SEDGE_POINT << 8 | j), 0);
+    float u = unitf(q.x);
+    float tau = __fadd_rn(P.t0, __fmul_rn(u, __fsub_rn(P.t1, P.t0)));
+    float Dd = -dot3r(sub3r(x32, L.c), L.dl);
+    V3 y = edge_proj(A, B, x32, L, Dd, tau);
+    V3 y0 = edge_proj(A, B, x32, L, Dd, P.t0);
+    V3 y1 = edge_proj(A, B, x32, L, Dd, P.t1);
+    V3 nv = cross3r(L.dl, sub3r(y1, y0));
+    float nl = __fsqrt_rn(dot3r(nv, nv));
+    if (nl == 0.0f) continue;
+    nv = V3{__fdiv_rn(nv.x, nl), __fdiv_rn(nv.y, nl), __fdiv_rn(nv.z, nl)};
+    const float e = a.eps_sedge;
+    V3 yp{__fadd_rn(y.x, __fmul_rn(e, nv.x)), __fadd_rn(y.y, __fmul_rn(e, nv.y)), __fadd_rn(y.z, __fmul_rn(e, nv.z))};
+    V3 ym{__fsub_rn(y.x, __fmul_rn(e, nv.x)), __fsub_rn(y.y, __fmul_rn(e, nv.y)), __fsub_rn(y.z, __fmul_rn(e, nv.z))};
+    bool vp = visible(a.mesh, x32, yp, f, flip, a.tmin, a.err, cnt);
+    bool vm = visible(a.mesh, x32, ym, f, flip, a.tmin, a.err, cnt);
+    if (vp == vm) continue;
+    if (!have_surf) {
+      S = surface(a, f, a.cam.o, d, flip);
+      int idx[4];
+      float w[4], fu, fv;
+      cs = cspec_lookup(a.cspec, S.u, S.v, idx, w, fu, fv);
+      have_surf = true;
+    }
+    V3 l = light_rgb(a, j);
+    V3 gp{0, 0, 0}, gm{0, 0, 0};
+    if (vp) gp = shade_light(S, cs, l, yp, L.dl, a.m).h;
+    if (vm) gm = shade_light(S, cs, l, ym, L.dl, a.m).h;
+    float delta = dot(wrgb, gm - gp);
+    if (delta == 0.0f) continue;
+    float w = delta * (float)P.n * (P.t1 - P.t0);
+    // adjoint of y(tau) = x + q D/h, q = p - x, p = A + tau (B - A)
+    V3 BA = B - A;
+    V3 p = A + BA * tau;
+    V3 qv = p - S.x;
+    float h = dot(qv, L.dl);
+    float D = dot(L.c - S.x, L.dl);
+    float fct = D / h;
+    float Dh2 = D / (h * h);
+    V3 dYdt = BA * fct - qv * (Dh2 * dot(BA, L.dl));
+    V3 gY = cross(L.dl, dYdt) * w;
+    float gYq = dot(gY, qv);
+    V3 gq = gY * fct - L.dl * (gYq * Dh2);
+    V3 gx = gY - L.dl * (gYq / h) - gq;
+    atomic_add3(gb.dX + P.E.x, gq * (1.0f - tau));
+    atomic_add3(gb.dX + P.E.y, gq * tau);
+    hit_adjoint(a, f, d, S, gx, 0.0f, 0.0f, gb.dX);
+  }
+}
+
+}  // namespace fr

@@ -1,0 +1,234 @@
+"""Python binding of libfacert (include/facert.h): argument marshalling only.
+
+Every step of the render and its gradient runs in the library's CUDA kernels;
+PyTorch supplies device memory and the stream.  There is no CPU fallback: if
+the compiled library is missing, loading fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+_LIB = None
+
+FR_ERRORS = {-1: "invalid argument", -2: "inconsistent shapes", -3: "CUDA error", -4: "out of device memory",
+             -5: "device traversal limit reached", -6: "mesh or bases not uploaded"}
+
+
+class FrConfig(C.Structure):
+    _fields_ = [("tan_half_fov", C.c_float), ("d_cam", C.c_float), ("light_radius", C.c_float),
+                ("light_side", C.c_float), ("beckmann_m", C.c_float), ("eps_pedge", C.c_float),
+                ("eps_sedge", C.c_float), ("shadow_tmin", C.c_float), ("clip_kappa", C.c_float),
+                ("n_lights", C.c_int32)]
+
+
+class FrRenderOpts(C.Structure):
+    _fields_ = [("W", C.c_int32), ("H", C.c_int32), ("spp", C.c_int32), ("seed", C.c_uint32),
+                ("iter", C.c_uint32), ("terms", C.c_int32)]
+
+
+EXPORTS = ["fr_default_config", "fr_create", "fr_destroy", "fr_set_stream", "fr_last_error", "fr_strerror",
+           "fr_upload_mesh", "fr_upload_bases", "fr_n_params", "fr_render", "fr_render_backward", "fr_loss",
+           "fr_geometry", "fr_light_stage", "fr_sync", "fr_set_counters", "fr_get_counters",
+           "fr_launch_count"]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libfacert.so (built by build.build()); raises if it is missing."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    p = path or lib_path()
+    if not os.path.exists(p):
+        raise RuntimeError(f"libfacert.so not found at {p}: run __graft_entry__.build() first")
+    L = C.CDLL(p)
+    vp, i32, f32 = C.c_void_p, C.c_int32, C.c_float
+    L.fr_default_config.argtypes = [vp]
+    L.fr_default_config.restype = None
+    L.fr_create.argtypes = [C.POINTER(vp), vp, i32]
+    L.fr_destroy.argtypes = [vp]
+    L.fr_destroy.restype = None
+    L.fr_set_stream.argtypes = [vp, vp]
+    L.fr_last_error.argtypes = [vp]
+    L.fr_last_error.restype = C.c_char_p
+    L.fr_strerror.argtypes = [i32]
+    L.fr_strerror.restype = C.c_char_p
+    L.fr_upload_mesh.argtypes = [vp, vp, i32, vp, i32, vp]
+    L.fr_upload_bases.argtypes = [vp, vp, i32, vp, i32, vp, vp, i32]
+    L.fr_n_params.argtypes = [vp]
+    L.fr_render.argtypes = [vp, vp, vp, vp]
+    L.fr_render_backward.argtypes = [vp, vp, vp, vp, vp, i32]
+    L.fr_loss.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, f32, f32, vp, vp, vp]
+    L.fr_geometry.argtypes = [vp, vp, vp, vp, vp]
+    L.fr_light_stage.argtypes = [vp, vp]
+    L.fr_sync.argtypes = [vp]
+    L.fr_set_counters.argtypes = [vp, i32]
+    L.fr_get_counters.argtypes = [vp, vp]
+    L.fr_launch_count.argtypes = [vp]
+    L.fr_launch_count.restype = C.c_uint64
+    _LIB = L
+    return L
+
+
+def default_config(**kw) -> FrConfig:
+    c = FrConfig()
+    load().fr_default_config(C.byref(c))
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _hptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class Renderer:
+    """One library context on one CUDA device."""
+
+    def __init__(self, scene=None, device: int = 0, config: FrConfig | None = None):
+        self.lib = load()
+        self.device = torch.device("cuda", device)
+        self.cfg = config or default_config()
+        h = C.c_void_p()
+        rc = self.lib.fr_create(C.byref(h), C.byref(self.cfg), device)
+        if rc:
+            raise RuntimeError(f"fr_create failed: {FR_ERRORS.get(rc, rc)}")
+        self.ctx = h
+        self.P = 0
+        if scene is not None:
+            self.upload(scene)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.fr_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc < 0:
+            msg = self.lib.fr_last_error(self.ctx).decode()
+            raise RuntimeError(f"{what} failed ({FR_ERRORS.get(rc, rc)}): {msg}")
+        return rc
+
+    def _stream(self):
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        self.lib.fr_set_stream(self.ctx, C.c_void_p(s))
+
+    def upload(self, scene):
+        mean = np.ascontiguousarray(scene.mean, np.float32)
+        tris = np.ascontiguousarray(scene.tris, np.int32)
+        uv = np.ascontiguousarray(scene.uv, np.float32)
+        self._stream()
+        self._check(self.lib.fr_upload_mesh(self.ctx, _hptr(mean), mean.shape[0], _hptr(tris), tris.shape[0],
+                                            _hptr(uv)), "fr_upload_mesh")
+        B = [np.ascontiguousarray(b, np.float32) for b in (scene.B_id, scene.B_exp, scene.alb_mean, scene.B_alb)]
+        self._check(self.lib.fr_upload_bases(self.ctx, _hptr(B[0]), B[0].shape[1], _hptr(B[1]), B[1].shape[1],
+                                             _hptr(B[2]), _hptr(B[3]), B[3].shape[1]), "fr_upload_bases")
+        self.P = self.lib.fr_n_params(self.ctx)
+        self.V = mean.shape[0]
+
+    @staticmethod
+    def opts(W, H, spp, seed=0, iter=0, terms=0) -> FrRenderOpts:
+        return FrRenderOpts(W=W, H=H, spp=spp, seed=seed, iter=iter, terms=terms)
+
+    def _theta(self, theta):
+        assert theta.device == self.device and theta.dtype == torch.float32 and theta.is_contiguous()
+        assert theta.numel() == self.P, (theta.numel(), self.P)
+        return theta
+
+    def render(self, theta, W, H, spp, seed=0, iter=0, out=None):
+        theta = self._theta(theta)
+        img = out if out is not None else torch.empty((H, W, 3), device=self.device, dtype=torch.float32)
+        o = self.opts(W, H, spp, seed, iter)
+        self._stream()
+        self._check(self.lib.fr_render(self.ctx, _ptr(theta), C.byref(o), _ptr(img)), "fr_render")
+        return img
+
+    def backward(self, theta, d_image, W, H, spp, seed=0, iter=0, terms=0, grad=None, accumulate=False):
+        theta = self._theta(theta)
+        d_image = d_image.contiguous()
+        assert d_image.dtype == torch.float32 and d_image.numel() == W * H * 3
+        g = grad if grad is not None else torch.empty(self.P, device=self.device, dtype=torch.float64)
+        o = self.opts(W, H, spp, seed, iter, terms)
+        self._stream()
+        self._check(self.lib.fr_render_backward(self.ctx, _ptr(theta), C.byref(o), _ptr(d_image), _ptr(g),
+                                                1 if accumulate else 0), "fr_render_backward")
+        return g
+
+    def loss(self, theta, image, target, mask=None, m=None, w1=0.0, w2=0.0, d_image=None, grad=None):
+        theta = self._theta(theta)
+        H, W = image.shape[0], image.shape[1]
+        loss = torch.empty(1, device=self.device, dtype=torch.float64)
+        self._stream()
+        self._check(self.lib.fr_loss(self.ctx, _ptr(theta), W, H, _ptr(image), _ptr(target), _ptr(mask), _ptr(m),
+                                     float(w1), float(w2), _ptr(loss), _ptr(d_image), _ptr(grad)), "fr_loss")
+        return loss
+
+    def geometry(self, theta):
+        theta = self._theta(theta)
+        X = torch.empty((self.V, 3), device=self.device)
+        N = torch.empty_like(X)
+        A = torch.empty_like(X)
+        self._stream()
+        n_sil = self._check(self.lib.fr_geometry(self.ctx, _ptr(theta), _ptr(X), _ptr(N), _ptr(A)), "fr_geometry")
+        return dict(X=X, normals=N, albedo=A, n_silhouette=n_sil)
+
+    def light_stage(self):
+        out = np.zeros((self.cfg.n_lights, 12), np.float32)
+        self._check(self.lib.fr_light_stage(self.ctx, _hptr(out)), "fr_light_stage")
+        return out
+
+    def sync(self):
+        return self._check(self.lib.fr_sync(self.ctx), "fr_sync")
+
+    def set_counters(self, on=True):
+        self.lib.fr_set_counters(self.ctx, 1 if on else 0)
+
+    def launches(self) -> int:
+        return int(self.lib.fr_launch_count(self.ctx))
+
+    def counters(self):
+        out = np.zeros(8, np.uint64)
+        self._check(self.lib.fr_get_counters(self.ctx, _hptr(out)), "fr_get_counters")
+        return out
+
+
+class FaceRender(torch.autograd.Function):
+    """image = F(theta): forward renders, backward re-traces with the same samples."""
+
+    @staticmethod
+    def forward(ctx, theta, renderer: Renderer, W: int, H: int, spp: int, seed: int = 0, iter: int = 0):
+        ctx.renderer = renderer
+        ctx.args = (W, H, spp, seed, iter)
+        ctx.save_for_backward(theta)
+        return renderer.render(theta.detach().contiguous(), W, H, spp, seed, iter)
+
+    @staticmethod
+    def backward(ctx, d_image):
+        (theta,) = ctx.saved_tensors
+        W, H, spp, seed, iter = ctx.args
+        g = ctx.renderer.backward(theta.detach().contiguous(), d_image.float().contiguous(), W, H, spp, seed, iter)
+        return g.to(torch.float32), None, None, None, None, None, None
+
+
+def render(theta, renderer: Renderer, W: int, H: int, spp: int, seed: int = 0, iter: int = 0):
+    """Differentiable render (autograd entry point)."""
+    return FaceRender.apply(theta, renderer, W, H, spp, seed, iter)

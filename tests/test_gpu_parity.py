@@ -1,0 +1,226 @@
+"""GPU path against the CPU oracle, element by element, on identical seeded inputs.
+
+Tolerances (written here, from the target accuracy of the method):
+* image: |g - o| <= 1e-4 * max(|o|, 1e-4 * mean|o|) per pixel and channel;
+  at most 0.01 % of pixels may differ by a flipped discrete decision
+* gradient: |g - o| <= 1e-3 * max(|o|, 1e-3 * max|o| over the parameter group)
+The GPU takes every discrete decision in FP32 with the oracle's order of
+operations, so flips are not expected; values differ by FP32 rounding.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import default_config
+from paper_1910_05200_gb300 import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+GROUPS = ["alpha", "beta", "delta", "cspec", "pose", "lights"]
+
+
+@pytest.fixture(scope="module")
+def fr():
+    from paper_1910_05200_gb300 import build, facert
+    build.build()
+    return facert
+
+
+@pytest.fixture(scope="module")
+def tiny_r(fr, tiny):
+    scene, theta, _ = tiny
+    return fr.Renderer(scene, device=0)
+
+
+@pytest.fixture(scope="module")
+def full():
+    scene, theta, c = S.make_workload("full", seed=1)
+    return scene, theta, c
+
+
+@pytest.fixture(scope="module")
+def full_r(fr, full):
+    return fr.Renderer(full[0], device=0)
+
+
+def image_errors(got, ref):
+    scale = np.maximum(np.abs(ref), 1e-4 * np.abs(ref).mean() + 1e-30)
+    rel = np.abs(got - ref) / scale
+    bad_px = np.any(rel > 1e-4, axis=-1)
+    return rel, bad_px
+
+
+def assert_image(got, ref):
+    rel, bad = image_errors(got, ref)
+    n = bad.size
+    allowed = int(1e-4 * n)
+    assert bad.sum() <= allowed, f"{bad.sum()} of {n} pixels off (max rel {rel.max():.3e}, allowed {allowed})"
+
+
+def group_slices(K=(80, 90, 80)):
+    o = S.param_offsets(*K)
+    return {"alpha": slice(o["alpha"], o["beta"]), "beta": slice(o["beta"], o["delta"]),
+            "delta": slice(o["delta"], o["cspec"]), "cspec": slice(o["cspec"], o["pose"]),
+            "pose": slice(o["pose"], o["lights"]), "lights": slice(o["lights"], o["total"])}
+
+
+def assert_grad(got, ref, K=(80, 90, 80), what=""):
+    report = []
+    for name, sl in group_slices(K).items():
+        o, g = ref[sl], got[sl]
+        floor = 1e-3 * np.abs(o).max()
+        if floor == 0:
+            assert np.all(np.abs(g) <= 1e-9), (what, name, np.abs(g).max())
+            continue
+        err = np.abs(g - o) / np.maximum(np.abs(o), floor)
+        report.append((name, float(err.max())))
+        assert err.max() <= 1e-3, f"{what} {name}: max rel err {err.max():.3e} at {int(err.argmax())} " \
+                                  f"(got {g[err.argmax()]:.6e}, oracle {o[err.argmax()]:.6e})"
+    return report
+
+
+def test_geometry_matches_oracle(oracle, tiny, tiny_r):
+    scene, theta, _ = tiny
+    geo = tiny_r.geometry(torch.tensor(theta, device="cuda:0"))
+    ref = oracle.geometry(default_config(), scene, theta)
+    X = geo["X"].cpu().numpy()
+    # FP64 accumulation then rounding: bitwise equal up to rare rounding-boundary ties
+    assert (X != ref["X32"]).mean() < 1e-3
+    assert np.abs(X - ref["X"]).max() < 1e-6
+    assert np.abs(geo["normals"].cpu().numpy() - ref["normals"]).max() < 2e-5
+    assert np.abs(geo["albedo"].cpu().numpy() - ref["albedo"]).max() < 2e-5
+    assert geo["n_silhouette"] == ref["n_silhouette"]
+
+
+@pytest.mark.parametrize("W,H,spp,seed", [(64, 64, 4, 0), (37, 29, 3, 7), (8, 8, 32, 3), (1, 1, 1, 5)])
+def test_forward_matches_oracle(oracle, tiny, tiny_r, W, H, spp, seed):
+    scene, theta, _ = tiny
+    img = tiny_r.render(torch.tensor(theta, device="cuda:0"), W, H, spp, seed=seed)
+    tiny_r.sync()
+    ref = oracle.render(default_config(W=W, H=H, spp=spp, seed=seed), scene, theta)
+    if W * H > 1:
+        assert ref.max() > 0
+    assert_image(img.cpu().numpy().astype(np.float64), ref)
+
+
+@pytest.mark.parametrize("terms", [1, 2, 4])
+def test_backward_terms_match_oracle(oracle, tiny, tiny_r, terms):
+    scene, theta, _ = tiny
+    W = H = 64
+    spp = 4
+    rng = np.random.default_rng(terms)
+    dI = rng.normal(size=(H, W, 3)).astype(np.float32)
+    g = tiny_r.backward(torch.tensor(theta, device="cuda:0"), torch.tensor(dI, device="cuda:0"), W, H, spp,
+                        seed=2, terms=terms)
+    tiny_r.sync()
+    cfg = default_config(W=W, H=H, spp=spp, seed=2, terms=terms)
+    ref = oracle.render_backward(cfg, scene, theta, dI.astype(np.float64))
+    got = g.cpu().numpy()
+    if terms == 1:
+        assert np.abs(ref).max() > 0
+    assert_grad(got, ref, what=f"terms={terms}")
+
+
+def test_backward_total_and_ragged(oracle, tiny, tiny_r):
+    scene, theta, _ = tiny
+    W, H, spp = 37, 29, 3
+    rng = np.random.default_rng(9)
+    dI = rng.normal(size=(H, W, 3)).astype(np.float32)
+    g = tiny_r.backward(torch.tensor(theta, device="cuda:0"), torch.tensor(dI, device="cuda:0"), W, H, spp, seed=4)
+    tiny_r.sync()
+    ref = oracle.render_backward(default_config(W=W, H=H, spp=spp, seed=4), scene, theta, dI.astype(np.float64))
+    assert_grad(g.cpu().numpy(), ref, what="all terms, ragged")
+
+
+def test_autograd_function(fr, tiny_r, tiny):
+    scene, theta, _ = tiny
+    th = torch.tensor(theta, device="cuda:0", requires_grad=True)
+    img = fr.render(th, tiny_r, 32, 32, 2, 11)
+    w = torch.randn(32, 32, 3, device="cuda:0", generator=torch.Generator("cuda:0").manual_seed(0))
+    (img * w).sum().backward()
+    direct = tiny_r.backward(th.detach(), w, 32, 32, 2, 11)
+    assert torch.allclose(th.grad.double(), direct, rtol=1e-6, atol=1e-9)
+
+
+def test_loss_matches_oracle(oracle, tiny, tiny_r):
+    scene, theta, _ = tiny
+    W, H = 40, 30
+    rng = np.random.default_rng(3)
+    img = rng.uniform(size=(H, W, 3)).astype(np.float32)
+    tgt = rng.uniform(size=(H, W, 3)).astype(np.float32)
+    mask = (rng.uniform(size=(H, W)) > 0.3).astype(np.uint8)
+    m = rng.uniform(size=60).astype(np.float32)
+    dev = lambda a: torch.tensor(a, device="cuda:0")
+    d_image = torch.empty(H, W, 3, device="cuda:0")
+    grad = torch.zeros(len(theta), device="cuda:0", dtype=torch.float64)
+    loss = tiny_r.loss(dev(theta), dev(img), dev(tgt), dev(mask), dev(m), 0.3, 0.7, d_image, grad)
+    val, dref, gref = oracle.loss(default_config(W=W, H=H), scene, theta, img, tgt, mask, m, 0.3, 0.7)
+    assert abs(loss.item() - val) <= 1e-12 * abs(val)
+    assert np.allclose(d_image.cpu().numpy(), dref, rtol=0, atol=1e-6)
+    assert np.allclose(grad.cpu().numpy(), gref, rtol=1e-12, atol=1e-12)
+
+
+def test_all_lights_off_is_black(oracle, tiny, tiny_r):
+    scene, theta, _ = tiny
+    th = theta.copy()
+    o = S.param_offsets()
+    th[o["lights"]:] = 0
+    t = torch.tensor(th, device="cuda:0")
+    img = tiny_r.render(t, 16, 16, 2)
+    assert img.abs().max().item() == 0
+    dI = torch.ones(16, 16, 3, device="cuda:0")
+    g = tiny_r.backward(t, dI, 16, 16, 2).cpu().numpy()
+    ref = oracle.render_backward(default_config(W=16, H=16, spp=2), scene, th, np.ones((16, 16, 3)))
+    assert np.all(g[:o["lights"]] == 0)         # nothing lit: no geometry, albedo or texture gradient
+    assert np.abs(ref[o["lights"]:]).max() > 0   # but the lights still get their gradient
+    assert_grad(g, ref, what="lights off")
+
+
+def test_errors_are_reported(fr, tiny):
+    scene, theta, _ = tiny
+    r = fr.Renderer(None, device=0)
+    with pytest.raises(RuntimeError, match="not uploaded|upload"):
+        r.P = len(theta)
+        r.render(torch.tensor(theta, device="cuda:0"), 8, 8, 1)
+    r2 = fr.Renderer(scene, device=0)
+    with pytest.raises(RuntimeError, match="invalid argument"):
+        r2.render(torch.tensor(theta, device="cuda:0"), 0, 8, 1)
+    bad = S.Scene(scene.mean, np.concatenate([scene.tris, scene.tris[:1]]), scene.uv, scene.B_id, scene.B_exp,
+                  scene.alb_mean, scene.B_alb)
+    with pytest.raises(RuntimeError, match="shape"):
+        fr.Renderer(bad, device=0)
+
+
+# ---------------------------------------------------------------------------
+# Full size (35,709 vertices, 256 x 256, 16 spp): sampled outputs
+
+def test_full_size_forward_sampled_pixels(oracle, full, full_r):
+    scene, theta, c = full
+    W, H, spp = c["W"], c["H"], c["spp"]
+    img = full_r.render(torch.tensor(theta, device="cuda:0"), W, H, spp, seed=3)
+    full_r.sync()
+    pix = S.random_pixels(W, H, 48, seed=5)
+    # include pixels on the face and its silhouette
+    got = img.cpu().numpy().reshape(-1, 3)
+    lit = np.nonzero(got.sum(1) > 0)[0]
+    pix = np.unique(np.concatenate([pix, lit[:: max(1, len(lit) // 48)][:48]])).astype(np.int32)
+    ref = oracle.render(default_config(W=W, H=H, spp=spp, seed=3), scene, theta, pixels=pix)
+    assert_image(got[pix], ref)
+
+
+def test_full_size_backward_masked_adjoint(oracle, full, full_r):
+    """Gradient of <d_image, image> with d_image supported on a few pixels."""
+    scene, theta, c = full
+    W, H, spp = c["W"], c["H"], c["spp"]
+    th = torch.tensor(theta, device="cuda:0")
+    img = full_r.render(th, W, H, spp, seed=3).cpu().numpy().reshape(-1, 3)
+    lit = np.nonzero(img.sum(1) > 0)[0]
+    rng = np.random.default_rng(0)
+    pix = rng.choice(lit, size=12, replace=False)
+    dI = np.zeros((H * W, 3), np.float32)
+    dI[pix] = rng.normal(size=(len(pix), 3))
+    dI = dI.reshape(H, W, 3)
+    g = full_r.backward(th, torch.tensor(dI, device="cuda:0"), W, H, spp, seed=3).cpu().numpy()
+    full_r.sync()
+    ref = oracle.render_backward(default_config(W=W, H=H, spp=spp, seed=3), scene, theta, dI.astype(np.float64))
+    assert_grad(g, ref, what="full size, masked adjoint")
