@@ -286,7 +286,7 @@ def run_ours(args):
     cnt = r.counters()
     r.set_counters(False)
     from paper_1910_05200_gb300 import roofline as RF
-    flops_bwd = RF.backward_flops(cnt, samples, c["n_on"])
+    flops_bwd = float(RF.backward_flops([int(x) for x in cnt], samples, c["n_on"]))
     t_bwd = float(np.mean(ms_bwd)) * 1e-3
     clk = clocks.summary()
     peak = RF.fp32_peak_tflops(clk.get("sm_mhz"))

@@ -158,6 +158,11 @@ int fr_loss(fr_ctx* ctx, const float* theta, int32_t W, int32_t H, const float* 
  * silhouette edges (>= 0) or an error. */
 int fr_geometry(fr_ctx* ctx, const float* theta, float* X, float* N, float* A);
 
+/* Per-vertex position gradient of the last fr_render_backward on this
+ * context (after the normals adjoint, before the pose and basis
+ * contractions): dX[V*3] FP32 device.  For inspection and tests. */
+int fr_vertex_grad(fr_ctx* ctx, float* dX);
+
 /* Light stage frames (host, out[n_lights*12]: centre, e1, e2, direction). */
 int fr_light_stage(const fr_ctx* ctx, float* out);
 

@@ -131,6 +131,7 @@ struct OracleConfig {
   float tan_half_fov, d_cam, light_radius, light_side, beckmann_m;
   float eps_pedge, eps_sedge, shadow_tmin, clip_kappa;
   int32_t n_lights, shade_mode, n_threads, terms;
+  int32_t value_mesh;   // 0: values on the FP64 posed mesh; 1: on the posed mesh rounded to FP32
 };
 struct OracleScene {
   int32_t V, F, K_id, K_exp, K_alb;
@@ -254,7 +255,8 @@ struct Render {
   Layout lay;
   int V, F, NL;
   std::vector<double> Xm;      // model-space vertices [V*3]
-  std::vector<double> X;       // posed vertices [V*3] (FP64 values)
+  std::vector<double> X;       // posed vertices used for values [V*3]
+  std::vector<double> X64;     // posed vertices in FP64, before any rounding
   std::vector<float> X32;      // posed vertices rounded to FP32 (decisions)
   std::vector<double> alb;     // albedo [V*3]
   std::vector<double> nrm;     // unit vertex normals [V*3]
@@ -325,7 +327,7 @@ int prepare(Render& r) {
   const float* be = r.theta + r.lay.beta;
   const float* de = r.theta + r.lay.delta;
   const float* po = r.theta + r.lay.pose;
-  r.Xm.assign(n3, 0.0); r.X.assign(n3, 0.0); r.X32.assign(n3, 0.0f); r.alb.assign(n3, 0.0);
+  r.Xm.assign(n3, 0.0); r.X.assign(n3, 0.0); r.X64.assign(n3, 0.0); r.X32.assign(n3, 0.0f); r.alb.assign(n3, 0.0);
   for (int i = 0; i < n3; ++i) {
     double x = s.mean[i];
     for (int k = 0; k < s.K_id; ++k) x += (double)s.B_id[(size_t)i * s.K_id + k] * al[k];
@@ -339,8 +341,9 @@ int prepare(Render& r) {
   for (int v = 0; v < V; ++v)
     for (int c = 0; c < 3; ++c) {
       double x = r.R[3 * c] * r.Xm[3 * v] + r.R[3 * c + 1] * r.Xm[3 * v + 1] + r.R[3 * c + 2] * r.Xm[3 * v + 2] + po[3 + c];
-      r.X[3 * v + c] = x;
+      r.X64[3 * v + c] = x;
       r.X32[3 * v + c] = (float)x;
+      r.X[3 * v + c] = r.cfg->value_mesh ? (double)(float)x : x;
     }
   // FP32 face normals for decisions; FP64 area-weighted vertex normals for values.
   r.ng32.assign(3 * r.F, 0.0f);
@@ -606,15 +609,27 @@ int nthreads(const OracleConfig* c) {
 // ---------------------------------------------------------------------------
 // Backward.
 
-struct Grad {            // per-thread FP64 accumulators
+// Per-thread FP64 accumulators.  Next to every sum the oracle keeps its L1
+// mass (the sum of the absolute values of the contributions, propagated
+// through the adjoints with absolute Jacobians): the size against which the
+// rounding error of any other evaluation order or precision is measured.
+struct Grad {
   std::vector<double> dX, dN, dA, dC, dL;
-  void init(int V, int NL) { dX.assign(3 * V, 0); dN.assign(3 * V, 0); dA.assign(3 * V, 0); dC.assign(CS * CS, 0); dL.assign(3 * NL, 0); }
+  std::vector<double> aX, aN, aA, aC, aL;   // L1 masses
+  void init(int V, int NL) {
+    dX.assign(3 * V, 0); dN.assign(3 * V, 0); dA.assign(3 * V, 0); dC.assign(CS * CS, 0); dL.assign(3 * NL, 0);
+    aX.assign(3 * V, 0); aN.assign(3 * V, 0); aA.assign(3 * V, 0); aC.assign(CS * CS, 0); aL.assign(3 * NL, 0);
+  }
   void add(const Grad& g) {
-    for (size_t i = 0; i < dX.size(); ++i) { dX[i] += g.dX[i]; dN[i] += g.dN[i]; dA[i] += g.dA[i]; }
-    for (size_t i = 0; i < dC.size(); ++i) dC[i] += g.dC[i];
-    for (size_t i = 0; i < dL.size(); ++i) dL[i] += g.dL[i];
+    for (size_t i = 0; i < dX.size(); ++i) {
+      dX[i] += g.dX[i]; dN[i] += g.dN[i]; dA[i] += g.dA[i];
+      aX[i] += g.aX[i]; aN[i] += g.aN[i]; aA[i] += g.aA[i];
+    }
+    for (size_t i = 0; i < dC.size(); ++i) { dC[i] += g.dC[i]; aC[i] += g.aC[i]; }
+    for (size_t i = 0; i < dL.size(); ++i) { dL[i] += g.dL[i]; aL[i] += g.aL[i]; }
   }
 };
+inline void acc(std::vector<double>& d, std::vector<double>& a, size_t i, double v) { d[i] += v; a[i] += std::fabs(v); }
 
 // Interior derivative of one camera sample: the exact derivative of the
 // per-sample estimator with its samples and decisions held fixed.
@@ -655,12 +670,12 @@ void interior_sample(const Render& r, const float* o, const float* d, const Hit&
     for (int k = 0; k < NI; ++k) gin[k] = w[0] * hv.x.d[k] + w[1] * hv.y.d[k] + w[2] * hv.z.d[k];
     for (int k = 0; k < 3; ++k)
       for (int c = 0; c < 3; ++c) {
-        g.dX[3 * t[k] + c] += gin[3 * k + c];
-        g.dN[3 * t[k] + c] += gin[9 + 3 * k + c];
-        g.dA[3 * t[k] + c] += gin[18 + 3 * k + c];
+        acc(g.dX, g.aX, 3 * t[k] + c, gin[3 * k + c]);
+        acc(g.dN, g.aN, 3 * t[k] + c, gin[9 + 3 * k + c]);
+        acc(g.dA, g.aA, 3 * t[k] + c, gin[18 + 3 * k + c]);
       }
-    for (int k = 0; k < 4; ++k) g.dC[tex[k]] += gin[27 + k];
-    for (int c = 0; c < 3; ++c) g.dL[3 * j + c] += gin[31 + c];
+    for (int k = 0; k < 4; ++k) acc(g.dC, g.aC, tex[k], gin[27 + k]);
+    for (int c = 0; c < 3; ++c) acc(g.dL, g.aL, 3 * j + c, gin[31 + c]);
   }
 }
 
@@ -712,8 +727,13 @@ void primary_edge_sample(const Render& r, uint32_t pix, int s, const double* dim
   V3<double> fm = radiance(r, r.cam_o, dm, TAG_PEDGE_LIGHT, pix, (uint32_t)s, nullptr);
   double delta = dI[0] * (fm.x - fp.x) + dI[1] * (fm.y - fp.y) + dI[2] * (fm.z - fp.z);
   if (delta == 0.0) return;
+  // the sample is a difference of two estimates: its mass counts both
+  double dmass = std::fabs(dI[0]) * (std::fabs(fm.x) + std::fabs(fp.x)) +
+                 std::fabs(dI[1]) * (std::fabs(fm.y) + std::fabs(fp.y)) +
+                 std::fabs(dI[2]) * (std::fabs(fm.z) + std::fabs(fp.z));
   const double N_es = (double)c.W * c.H * c.spp;
   double w = delta * nS / N_es;
+  double wm = dmass * nS / N_es;
   typedef Dual<6> D6;
   V3<double> a = r.v64(E.v0), b = r.v64(E.v1);
   V3<D6> A(D6::var(a.x, 0), D6::var(a.y, 1), D6::var(a.z, 2));
@@ -729,6 +749,7 @@ void primary_edge_sample(const Render& r, uint32_t pix, int s, const double* dim
     double vn = -evy * mdx + evx * mdy;          // R90(e) . dm/dtheta
     int v = i < 3 ? E.v0 : E.v1;
     g.dX[3 * v + (i % 3)] += w * vn;
+    g.aX[3 * v + (i % 3)] += std::fabs(wm * vn);
   }
 }
 
@@ -851,7 +872,11 @@ void shadow_edge_sample(const Render& r, const float* o, const float* d, const H
   if (vm) gm = light_integrand<double>(S.x, S.ns, S.wo, S.rho, cs, lv, widen(ym), widen(L.dl), c.beckmann_m);
   double delta = wrgb[0] * (gm.x - gp.x) + wrgb[1] * (gm.y - gp.y) + wrgb[2] * (gm.z - gp.z);
   if (delta == 0.0) return;
+  double dmass = std::fabs(wrgb[0]) * (std::fabs(gm.x) + std::fabs(gp.x)) +
+                 std::fabs(wrgb[1]) * (std::fabs(gm.y) + std::fabs(gp.y)) +
+                 std::fabs(wrgb[2]) * (std::fabs(gm.z) + std::fabs(gp.z));
   double w = delta * (double)n * ((double)bestclip.t1 - (double)bestclip.t0);
+  double wm = dmass * (double)n * ((double)bestclip.t1 - (double)bestclip.t0);
   // y(tau) as a function of the edge endpoints, the hit triangle and tau.
   typedef Dual<16> D16;
   const int32_t* t = &r.sc->tris[3 * h.f];
@@ -881,20 +906,25 @@ void shadow_edge_sample(const Render& r, const float* o, const float* d, const H
     double vn = Rn.x * Y.x.d[k] + Rn.y * Y.y.d[k] + Rn.z * Y.z.d[k];
     int v = k < 3 ? E.v0 : (k < 6 ? E.v1 : t[(k - 6) / 3]);
     g.dX[3 * v + (k % 3)] += w * vn;
+    g.aX[3 * v + (k % 3)] += std::fabs(wm * vn);
   }
 }
 
 // dN (unit vertex normals) -> dX through normalisation and face cross products.
-void normals_adjoint(const Render& r, const std::vector<double>& dN, std::vector<double>& dX) {
+void normals_adjoint(const Render& r, const std::vector<double>& dN, std::vector<double>& dX,
+                     const std::vector<double>& aN, std::vector<double>& aX) {
   const int V = r.V;
-  std::vector<double> gs(3 * V, 0.0);
+  std::vector<double> gs(3 * V, 0.0), as(3 * V, 0.0);
   typedef Dual<3> D3;
   for (int v = 0; v < V; ++v) {
     V3<D3> s(D3::var(r.nsum[3 * v], 0), D3::var(r.nsum[3 * v + 1], 1), D3::var(r.nsum[3 * v + 2], 2));
     if (dot(s, s).v == 0.0) continue;
     V3<D3> n = normalize(s);
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < 3; ++k) {
       gs[3 * v + k] = dN[3 * v] * n.x.d[k] + dN[3 * v + 1] * n.y.d[k] + dN[3 * v + 2] * n.z.d[k];
+      as[3 * v + k] = aN[3 * v] * std::fabs(n.x.d[k]) + aN[3 * v + 1] * std::fabs(n.y.d[k]) +
+                      aN[3 * v + 2] * std::fabs(n.z.d[k]);
+    }
   }
   typedef Dual<9> D9;
   for (int f = 0; f < r.F; ++f) {
@@ -905,57 +935,78 @@ void normals_adjoint(const Render& r, const std::vector<double>& dN, std::vector
       P[k] = V3<D9>(D9::var(p.x, 3 * k), D9::var(p.y, 3 * k + 1), D9::var(p.z, 3 * k + 2));
     }
     V3<D9> cr = cross(P[1] - P[0], P[2] - P[0]);
-    double gc[3] = {0, 0, 0};
+    double gc[3] = {0, 0, 0}, ac[3] = {0, 0, 0};
     for (int k = 0; k < 3; ++k)
-      for (int cc = 0; cc < 3; ++cc) gc[cc] += gs[3 * t[k] + cc];
-    for (int i = 0; i < 9; ++i)
+      for (int cc = 0; cc < 3; ++cc) { gc[cc] += gs[3 * t[k] + cc]; ac[cc] += as[3 * t[k] + cc]; }
+    for (int i = 0; i < 9; ++i) {
       dX[3 * t[i / 3] + i % 3] += gc[0] * cr.x.d[i] + gc[1] * cr.y.d[i] + gc[2] * cr.z.d[i];
+      aX[3 * t[i / 3] + i % 3] += ac[0] * std::fabs(cr.x.d[i]) + ac[1] * std::fabs(cr.y.d[i]) +
+                                  ac[2] * std::fabs(cr.z.d[i]);
+    }
   }
 }
 
 // dX, dA -> parameter gradient (alpha, beta, delta, pose) ; dC, dL copied.
-void geometry_adjoint(const Render& r, const Grad& G, const std::vector<double>& dX, double* out) {
+void geometry_adjoint(const Render& r, const Grad& G, const std::vector<double>& dX, const std::vector<double>& aX,
+                      double* out, double* mass) {
   const OracleScene& s = *r.sc;
   const Layout& lay = r.lay;
   const int V = r.V;
-  for (int i = 0; i < lay.total; ++i) out[i] = 0.0;
+  for (int i = 0; i < lay.total; ++i) { out[i] = 0.0; mass[i] = 0.0; }
   // dXm = R^T dX
-  std::vector<double> dXm(3 * V);
+  std::vector<double> dXm(3 * V), aXm(3 * V);
   for (int v = 0; v < V; ++v)
-    for (int c = 0; c < 3; ++c)
+    for (int c = 0; c < 3; ++c) {
       dXm[3 * v + c] = r.R[c] * dX[3 * v] + r.R[3 + c] * dX[3 * v + 1] + r.R[6 + c] * dX[3 * v + 2];
+      aXm[3 * v + c] = std::fabs(r.R[c]) * aX[3 * v] + std::fabs(r.R[3 + c]) * aX[3 * v + 1] +
+                       std::fabs(r.R[6 + c]) * aX[3 * v + 2];
+    }
   for (int k = 0; k < s.K_id; ++k) {
-    double a = 0;
-    for (int i = 0; i < 3 * V; ++i) a += (double)s.B_id[(size_t)i * s.K_id + k] * dXm[i];
-    out[lay.alpha + k] = a;
+    double a = 0, m = 0;
+    for (int i = 0; i < 3 * V; ++i) {
+      double b = s.B_id[(size_t)i * s.K_id + k];
+      a += b * dXm[i]; m += std::fabs(b) * aXm[i];
+    }
+    out[lay.alpha + k] = a; mass[lay.alpha + k] = m;
   }
   for (int k = 0; k < s.K_exp; ++k) {
-    double a = 0;
-    for (int i = 0; i < 3 * V; ++i) a += (double)s.B_exp[(size_t)i * s.K_exp + k] * dXm[i];
-    out[lay.beta + k] = a;
+    double a = 0, m = 0;
+    for (int i = 0; i < 3 * V; ++i) {
+      double b = s.B_exp[(size_t)i * s.K_exp + k];
+      a += b * dXm[i]; m += std::fabs(b) * aXm[i];
+    }
+    out[lay.beta + k] = a; mass[lay.beta + k] = m;
   }
   for (int k = 0; k < s.K_alb; ++k) {
-    double a = 0;
-    for (int i = 0; i < 3 * V; ++i) a += (double)s.B_alb[(size_t)i * s.K_alb + k] * G.dA[i];
-    out[lay.delta + k] = a;
+    double a = 0, m = 0;
+    for (int i = 0; i < 3 * V; ++i) {
+      double b = s.B_alb[(size_t)i * s.K_alb + k];
+      a += b * G.dA[i]; m += std::fabs(b) * G.aA[i];
+    }
+    out[lay.delta + k] = a; mass[lay.delta + k] = m;
   }
-  for (int i = 0; i < CS * CS; ++i) out[lay.cspec + i] = G.dC[i];
+  for (int i = 0; i < CS * CS; ++i) { out[lay.cspec + i] = G.dC[i]; mass[lay.cspec + i] = G.aC[i]; }
   // pose: rotation angles by dual numbers, translation = sum of dX
   typedef Dual<3> D3;
   const float* po = r.theta + lay.pose;
   D3 Rd[9];
   rotation_dual<3>(D3::var(po[0], 0), D3::var(po[1], 1), D3::var(po[2], 2), Rd);
-  double dr[3] = {0, 0, 0}, dt[3] = {0, 0, 0};
+  double dr[3] = {0, 0, 0}, dt[3] = {0, 0, 0}, mr[3] = {0, 0, 0}, mt[3] = {0, 0, 0};
   for (int v = 0; v < V; ++v)
     for (int c = 0; c < 3; ++c) {
       dt[c] += dX[3 * v + c];
+      mt[c] += aX[3 * v + c];
       for (int m = 0; m < 3; ++m) {
         double dRx = Rd[3 * c].d[m] * r.Xm[3 * v] + Rd[3 * c + 1].d[m] * r.Xm[3 * v + 1] + Rd[3 * c + 2].d[m] * r.Xm[3 * v + 2];
         dr[m] += dX[3 * v + c] * dRx;
+        mr[m] += aX[3 * v + c] * std::fabs(dRx);
       }
     }
-  for (int m = 0; m < 3; ++m) { out[lay.pose + m] = dr[m]; out[lay.pose + 3 + m] = dt[m]; }
-  for (int i = 0; i < 3 * r.NL; ++i) out[lay.lights + i] = G.dL[i];
+  for (int m = 0; m < 3; ++m) {
+    out[lay.pose + m] = dr[m]; out[lay.pose + 3 + m] = dt[m];
+    mass[lay.pose + m] = mr[m]; mass[lay.pose + 3 + m] = mt[m];
+  }
+  for (int i = 0; i < 3 * r.NL; ++i) { out[lay.lights + i] = G.dL[i]; mass[lay.lights + i] = G.aL[i]; }
 }
 
 }  // namespace
@@ -997,7 +1048,7 @@ int oracle_geometry(const OracleConfig* cfg, const OracleScene* sc, const float*
   int rc = prepare(r);
   if (rc) return rc;
   size_t n = 3 * (size_t)sc->V;
-  if (X) std::memcpy(X, r.X.data(), n * sizeof(double));
+  if (X) std::memcpy(X, r.X64.data(), n * sizeof(double));
   if (X32) std::memcpy(X32, r.X32.data(), n * sizeof(float));
   if (albedo) std::memcpy(albedo, r.alb.data(), n * sizeof(double));
   if (normals) std::memcpy(normals, r.nrm.data(), n * sizeof(double));
@@ -1041,7 +1092,8 @@ int oracle_render(const OracleConfig* cfg, const OracleScene* sc, const float* t
 // parts as three consecutive P-vectors.  cfg->terms selects the terms
 // (bitmask 1 | 2 | 4; 0 means all).  Pixels whose adjoint is zero are skipped.
 int oracle_render_backward(const OracleConfig* cfg, const OracleScene* sc, const float* theta,
-                           const double* d_image, double* grad, double* grad_terms, double* dX_out) {
+                           const double* d_image, double* grad, double* grad_terms, double* dX_out,
+                           double* grad_mass, double* dX_mass) {
   Render r(cfg, sc, theta);
   int rc = prepare(r);
   if (rc) return rc;
@@ -1049,9 +1101,9 @@ int oracle_render_backward(const OracleConfig* cfg, const OracleScene* sc, const
   const int terms = cfg->terms ? cfg->terms : 7;
   const int npx = cfg->W * cfg->H;
   const int P = r.lay.total;
-  std::vector<double> total(P, 0.0);
+  std::vector<double> total(P, 0.0), tmass(P, 0.0);
   if (grad_terms) std::fill(grad_terms, grad_terms + 3 * P, 0.0);
-  std::vector<double> dXtot(3 * r.V, 0.0);
+  std::vector<double> dXtot(3 * r.V, 0.0), aXtot(3 * r.V, 0.0);
   for (int term = 0; term < 3; ++term) {
     int bit = 1 << term;
     if (!(terms & bit)) continue;
@@ -1079,19 +1131,21 @@ int oracle_render_backward(const OracleConfig* cfg, const OracleScene* sc, const
         }
       }
     });
-    Grad acc;
-    acc.init(r.V, r.NL);
-    for (auto& g : G) acc.add(g);
-    std::vector<double> dX = acc.dX;
-    normals_adjoint(r, acc.dN, dX);
-    for (int i = 0; i < 3 * r.V; ++i) dXtot[i] += dX[i];
-    std::vector<double> part(P);
-    geometry_adjoint(r, acc, dX, part.data());
-    for (int i = 0; i < P; ++i) total[i] += part[i];
+    Grad tot;
+    tot.init(r.V, r.NL);
+    for (auto& gg : G) tot.add(gg);
+    std::vector<double> dX = tot.dX, aX = tot.aX;
+    normals_adjoint(r, tot.dN, dX, tot.aN, aX);
+    for (int i = 0; i < 3 * r.V; ++i) { dXtot[i] += dX[i]; aXtot[i] += aX[i]; }
+    std::vector<double> part(P), pmass(P);
+    geometry_adjoint(r, tot, dX, aX, part.data(), pmass.data());
+    for (int i = 0; i < P; ++i) { total[i] += part[i]; tmass[i] += pmass[i]; }
     if (grad_terms) std::memcpy(grad_terms + term * P, part.data(), P * sizeof(double));
   }
   std::memcpy(grad, total.data(), P * sizeof(double));
   if (dX_out) std::memcpy(dX_out, dXtot.data(), 3 * r.V * sizeof(double));
+  if (grad_mass) std::memcpy(grad_mass, tmass.data(), P * sizeof(double));
+  if (dX_mass) std::memcpy(dX_mass, aXtot.data(), 3 * r.V * sizeof(double));
   return 0;
 }
 

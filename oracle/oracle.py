@@ -41,7 +41,7 @@ class OracleConfig(C.Structure):
                 ("eps_sedge", C.c_float), ("shadow_tmin", C.c_float),
                 ("clip_kappa", C.c_float),
                 ("n_lights", C.c_int32), ("shade_mode", C.c_int32),
-                ("n_threads", C.c_int32), ("terms", C.c_int32)]
+                ("n_threads", C.c_int32), ("terms", C.c_int32), ("value_mesh", C.c_int32)]
 
 
 class OracleScene(C.Structure):
@@ -59,11 +59,14 @@ DEFAULTS = dict(tan_half_fov=0.275, d_cam=4.0, light_radius=3.0, light_side=0.6,
 
 
 def default_config(W=64, H=64, spp=4, seed=0, iter=0, shade_mode=0, n_threads=0, terms=0,
-                   **kw) -> OracleConfig:
+                   value_mesh=1, **kw) -> OracleConfig:
+    """value_mesh = 1 (default) evaluates the estimator on the posed mesh rounded
+    to FP32, the mesh the renderer consumes; 0 keeps the FP64 posed mesh (used by
+    finite-difference pins, where rounding steps would swamp small differences)."""
     d = dict(DEFAULTS)
     d.update(kw)
     return OracleConfig(W=W, H=H, spp=spp, seed=seed, iter=iter, shade_mode=shade_mode,
-                        n_threads=n_threads, terms=terms, **d)
+                        n_threads=n_threads, terms=terms, value_mesh=value_mesh, **d)
 
 
 def _ptr(a):
@@ -82,7 +85,7 @@ class Oracle:
         L.oracle_light_stage.argtypes = [C.c_int32, C.c_float, vp]
         L.oracle_geometry.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.oracle_render.argtypes = [vp, vp, vp, vp, C.c_int32, vp, vp]
-        L.oracle_render_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.oracle_render_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.oracle_loss.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.c_float, C.c_float, vp, vp]
         L.oracle_loss.restype = C.c_double
         L.oracle_light_estimate.argtypes = [vp, vp, vp, vp, vp, C.c_double, vp, C.c_int32,
@@ -155,7 +158,10 @@ class Oracle:
             raise RuntimeError(f"oracle_render failed: {rc}")
         return (img, int(sig[0])) if signature else img
 
-    def render_backward(self, cfg, scene, theta, d_image, terms=False, dX=False):
+    def render_backward(self, cfg, scene, theta, d_image, terms=False, dX=False, mass=False):
+        """Gradient [P]; optionally the per-term parts [3, P], the per-vertex
+        position gradient [V, 3], the L1 mass [P] of each component and (with
+        dX and mass) the L1 mass [V, 3] of the per-vertex gradient."""
         s = self._scene(scene)
         th = np.ascontiguousarray(theta, np.float32)
         dI = np.ascontiguousarray(d_image, np.float64).reshape(cfg.H, cfg.W, 3)
@@ -163,8 +169,10 @@ class Oracle:
         g = np.zeros(P)
         gt = np.zeros((3, P))
         dXo = np.zeros((s.V, 3))
+        gm = np.zeros(P)
+        dXm = np.zeros((s.V, 3))
         rc = self.lib.oracle_render_backward(C.byref(cfg), C.byref(s), _ptr(th), _ptr(dI), _ptr(g),
-                                             _ptr(gt), _ptr(dXo))
+                                             _ptr(gt), _ptr(dXo), _ptr(gm), _ptr(dXm))
         if rc:
             raise RuntimeError(f"oracle_render_backward failed: {rc}")
         out = [g]
@@ -172,6 +180,10 @@ class Oracle:
             out.append(gt)
         if dX:
             out.append(dXo)
+        if mass:
+            out.append(gm)
+            if dX:
+                out.append(dXm)
         return out[0] if len(out) == 1 else tuple(out)
 
     def loss(self, cfg, scene, theta, image, target, mask=None, m=None, w1=0.0, w2=0.0):

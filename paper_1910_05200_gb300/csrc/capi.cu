@@ -669,6 +669,15 @@ int fr_geometry(fr_ctx* ctx, const float* theta, float* X, float* N, float* A) {
   return nsil;
 }
 
+int fr_vertex_grad(fr_ctx* ctx, float* dX) {
+  if (!ctx || !dX) return FR_ERR_INVALID_ARG;
+  if (!ctx->have_mesh) return fail(ctx, FR_ERR_NOT_READY, "mesh not uploaded");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaMemcpy2DAsync(dX, 3 * sizeof(float), ctx->dX.p, sizeof(float4), 3 * sizeof(float), ctx->V,
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+  return FR_OK;
+}
+
 int fr_light_stage(const fr_ctx* ctx, float* out) {
   if (!ctx || !out) return FR_ERR_INVALID_ARG;
   for (int k = 0; k < ctx->cfg.n_lights; ++k) {

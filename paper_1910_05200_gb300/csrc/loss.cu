@@ -13,9 +13,9 @@ __global__ void k_loss_data(int n_pix, const float* __restrict__ image, const fl
     bool in = mask ? mask[p] != 0 : true;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      float diff = image[3 * p + c] - target[3 * p + c];
-      if (in) acc += (double)diff * (double)diff;
-      if (d_image) d_image[3 * p + c] = in ? 2.0f * diff : 0.0f;
+      double diff = (double)image[3 * p + c] - (double)target[3 * p + c];
+      if (in) acc += diff * diff;
+      if (d_image) d_image[3 * p + c] = in ? (float)(2.0 * diff) : 0.0f;
     }
   }
   for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);

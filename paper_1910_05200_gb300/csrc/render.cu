@@ -33,8 +33,9 @@ FR_DEV Surf surface(const RenderArgs& a, int f, V3 o, V3 d, int flip) {
   S.b1 = dot(s, pv) * inv;
   S.b2 = dot(d, qv) * inv;
   S.b0 = 1.0f - S.b1 - S.b2;
-  float tt = dot(e2, qv) * inv;
-  S.x = o + d * tt;
+  // hit point from the barycentrics: its error is relative to the triangle,
+  // not to the camera distance
+  S.x = P0 + e1 * S.b1 + e2 * S.b2;
   V3 N0 = v3(a.nrm[t.x]), N1 = v3(a.nrm[t.y]), N2 = v3(a.nrm[t.z]);
   S.nraw = N0 * S.b0 + N1 * S.b1 + N2 * S.b2;
   S.inv_nlen = rsqrtf(dot(S.nraw, S.nraw));
@@ -199,15 +200,51 @@ FR_DEV void atomic_add3(float4* p, V3 v) {
 // Adjoint of the hit point x = o + t d with respect to the hit triangle's
 // vertices (ray fixed), plus barycentric adjoints g_b1, g_b2 (b0 = 1-b1-b2
 // already folded in).  Scatters b_k * lambda into dX.
+FR_DEV void cross64(const double* a, const double* b, double* r) {
+  r[0] = a[1] * b[2] - a[2] * b[1];
+  r[1] = a[2] * b[0] - a[0] * b[2];
+  r[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Hit point of the ray (o, d) on face f in FP64 (Moller-Trumbore on the FP32
+// vertices): accurate along the surface even for grazing rays.
+FR_DEV void hit_point64(const RenderArgs& a, int f, V3 o, V3 d, double* x) {
+  int4 t = a.mesh.tris[f];
+  float4 p0 = a.mesh.X[t.x], p1 = a.mesh.X[t.y], p2 = a.mesh.X[t.z];
+  double e1[3] = {(double)p1.x - p0.x, (double)p1.y - p0.y, (double)p1.z - p0.z};
+  double e2[3] = {(double)p2.x - p0.x, (double)p2.y - p0.y, (double)p2.z - p0.z};
+  double dd[3] = {d.x, d.y, d.z};
+  double s[3] = {(double)o.x - p0.x, (double)o.y - p0.y, (double)o.z - p0.z};
+  double pv[3], qv[3];
+  cross64(dd, e2, pv);
+  cross64(s, e1, qv);
+  double inv = 1.0 / (e1[0] * pv[0] + e1[1] * pv[1] + e1[2] * pv[2]);
+  double b1 = (s[0] * pv[0] + s[1] * pv[1] + s[2] * pv[2]) * inv;
+  double b2 = (dd[0] * qv[0] + dd[1] * qv[1] + dd[2] * qv[2]) * inv;
+  x[0] = (double)p0.x + b1 * e1[0] + b2 * e2[0];
+  x[1] = (double)p0.y + b1 * e1[1] + b2 * e2[1];
+  x[2] = (double)p0.z + b1 * e1[2] + b2 * e2[2];
+}
+
+// The 3x3 solve is ill-conditioned for grazing hits (det -> 0), so it runs in
+// FP64 (a few dozen operations per sample).
 FR_DEV void hit_adjoint(const RenderArgs& a, int f, V3 d, const Surf& S, V3 g_x, float g_b1, float g_b2,
                         float4* dX) {
   int4 t = a.mesh.tris[f];
-  V3 P0 = v3(a.mesh.X[t.x]), P1 = v3(a.mesh.X[t.y]), P2 = v3(a.mesh.X[t.z]);
-  V3 e1 = P1 - P0, e2 = P2 - P0;
-  V3 n = cross(e1, e2);
-  float det = dot(d, n);
-  float g_t = dot(g_x, d);
-  V3 lam = (n * g_t + cross(d, e2) * g_b1 + cross(e1, d) * g_b2) * (1.0f / det);
+  float4 p0 = a.mesh.X[t.x], p1 = a.mesh.X[t.y], p2 = a.mesh.X[t.z];
+  double e1x = (double)p1.x - p0.x, e1y = (double)p1.y - p0.y, e1z = (double)p1.z - p0.z;
+  double e2x = (double)p2.x - p0.x, e2y = (double)p2.y - p0.y, e2z = (double)p2.z - p0.z;
+  double dx = d.x, dy = d.y, dz = d.z;
+  double nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+  double det = dx * nx + dy * ny + dz * nz;
+  double gt = (double)g_x.x * dx + (double)g_x.y * dy + (double)g_x.z * dz;
+  double b1 = g_b1, b2 = g_b2;
+  // lambda = (n g_t + (d x e2) g_b1 + (e1 x d) g_b2) / det
+  double lx = nx * gt + (dy * e2z - dz * e2y) * b1 + (e1y * dz - e1z * dy) * b2;
+  double ly = ny * gt + (dz * e2x - dx * e2z) * b1 + (e1z * dx - e1x * dz) * b2;
+  double lz = nz * gt + (dx * e2y - dy * e2x) * b1 + (e1x * dy - e1y * dx) * b2;
+  double inv = 1.0 / det;
+  V3 lam{(float)(lx * inv), (float)(ly * inv), (float)(lz * inv)};
   atomic_add3(dX + t.x, lam * S.b0);
   atomic_add3(dX + t.y, lam * S.b1);
   atomic_add3(dX + t.z, lam * S.b2);
@@ -333,16 +370,21 @@ __global__ void __launch_bounds__(256) k_bwd_pedge(RenderArgs a, GradBufs gb) {
   float delta = dot(dimg, fm - fp);
   if (delta == 0.0f) return;
   float w = delta * (float)nS / ((float)a.W * (float)a.H * (float)a.spp);
-  float gmx = -ey * w, gmy = ex * w;       // w * R90(e)
   const float kc = a.cam.k;
+  // screen edge vector from 3D differences (accurate for short edges)
+  float qa = a.cam.dcam - A.z, qb = a.cam.dcam - B.z;
+  V3 BA = B - A;
+  float iq = 1.0f / (qa * qb * kc);
+  float evx = (BA.x * qa + A.x * BA.z) * iq;
+  float evy = -(BA.y * qa + A.y * BA.z) * iq;
+  float gmx = -evy * w, gmy = evx * w;     // w * R90(e)
   // adjoint of the screen projection for each endpoint
   {
-    float qa = a.cam.dcam - A.z, c = 1.0f - u;
+    float c = 1.0f - u;
     float gx = gmx * c, gy = gmy * c;
     atomic_add3(gb.dX + E.x, V3{gx / (kc * qa), -gy / (kc * qa), (gx * A.x - gy * A.y) / (kc * qa * qa)});
   }
   {
-    float qb = a.cam.dcam - B.z;
     float gx = gmx * u, gy = gmy * u;
     atomic_add3(gb.dX + E.y, V3{gx / (kc * qb), -gy / (kc * qb), (gx * B.x - gy * B.y) / (kc * qb * qb)});
   }
@@ -554,21 +596,32 @@ __global__ void __launch_bounds__(256) k_bwd_sedge(RenderArgs a, GradBufs gb) {
     float delta = dot(wrgb, gm - gp);
     if (delta == 0.0f) continue;
     float w = delta * (float)P.n * (P.t1 - P.t0);
-    // adjoint of y(tau) = x + q D/h, q = p - x, p = A + tau (B - A)
-    V3 BA = B - A;
-    V3 p = A + BA * tau;
-    V3 qv = p - S.x;
-    float h = dot(qv, L.dl);
-    float D = dot(L.c - S.x, L.dl);
-    float fct = D / h;
-    float Dh2 = D / (h * h);
-    V3 dYdt = BA * fct - qv * (Dh2 * dot(BA, L.dl));
-    V3 gY = cross(L.dl, dYdt) * w;
-    float gYq = dot(gY, qv);
-    V3 gq = gY * fct - L.dl * (gYq * Dh2);
-    V3 gx = gY - L.dl * (gYq / h) - gq;
-    atomic_add3(gb.dX + P.E.x, gq * (1.0f - tau));
-    atomic_add3(gb.dX + P.E.y, gq * tau);
+    // Adjoint of the boundary point y(tau) = x + q D/h on the light plane,
+    // q = p - x, p = A + tau (B - A), h = q.dl, D = (c - x).dl.  With
+    // u = B - A and K = (dl x (q x u)) x q, the normal velocity of the
+    // boundary times its length element gives
+    //   dE/dp = w (D/h^2)^2 K,   dE/dx = w (1 - D/h) (D/h^3) K.
+    // For an occluder close to the shading point these factors amplify any
+    // error in x, and x itself is ill-conditioned at grazing hits, so this
+    // (rare: only where the two sides differ) step runs in FP64.
+    double x64[3];
+    hit_point64(a, f, a.cam.o, d, x64);
+    double ue[3] = {(double)B.x - A.x, (double)B.y - A.y, (double)B.z - A.z};
+    double qv[3] = {((double)A.x - x64[0]) + ue[0] * tau, ((double)A.y - x64[1]) + ue[1] * tau,
+                    ((double)A.z - x64[2]) + ue[2] * tau};
+    double dl[3] = {L.dl.x, L.dl.y, L.dl.z};
+    double h = qv[0] * dl[0] + qv[1] * dl[1] + qv[2] * dl[2];
+    double D = ((double)L.c.x - x64[0]) * dl[0] + ((double)L.c.y - x64[1]) * dl[1] + ((double)L.c.z - x64[2]) * dl[2];
+    double Dh2 = D / (h * h);
+    double t1[3], t2[3], K[3];
+    cross64(qv, ue, t1);
+    cross64(dl, t1, t2);
+    cross64(t2, qv, K);
+    double sp = (double)w * Dh2 * Dh2, sx = (double)w * (1.0 - D / h) * (Dh2 / h);
+    V3 g_p{(float)(K[0] * sp), (float)(K[1] * sp), (float)(K[2] * sp)};
+    V3 gx{(float)(K[0] * sx), (float)(K[1] * sx), (float)(K[2] * sx)};
+    atomic_add3(gb.dX + P.E.x, g_p * (1.0f - tau));
+    atomic_add3(gb.dX + P.E.y, g_p * tau);
     hit_adjoint(a, f, d, S, gx, 0.0f, 0.0f, gb.dX);
   }
 }

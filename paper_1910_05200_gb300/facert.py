@@ -34,7 +34,7 @@ class FrRenderOpts(C.Structure):
 
 EXPORTS = ["fr_default_config", "fr_create", "fr_destroy", "fr_set_stream", "fr_last_error", "fr_strerror",
            "fr_upload_mesh", "fr_upload_bases", "fr_n_params", "fr_render", "fr_render_backward", "fr_loss",
-           "fr_geometry", "fr_light_stage", "fr_sync", "fr_set_counters", "fr_get_counters",
+           "fr_geometry", "fr_vertex_grad", "fr_light_stage", "fr_sync", "fr_set_counters", "fr_get_counters",
            "fr_launch_count"]
 
 
@@ -70,6 +70,7 @@ def load(path: str | None = None):
     L.fr_loss.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, f32, f32, vp, vp, vp]
     L.fr_geometry.argtypes = [vp, vp, vp, vp, vp]
     L.fr_light_stage.argtypes = [vp, vp]
+    L.fr_vertex_grad.argtypes = [vp, vp]
     L.fr_sync.argtypes = [vp]
     L.fr_set_counters.argtypes = [vp, i32]
     L.fr_get_counters.argtypes = [vp, vp]
@@ -190,6 +191,12 @@ class Renderer:
         self._stream()
         n_sil = self._check(self.lib.fr_geometry(self.ctx, _ptr(theta), _ptr(X), _ptr(N), _ptr(A)), "fr_geometry")
         return dict(X=X, normals=N, albedo=A, n_silhouette=n_sil)
+
+    def vertex_grad(self):
+        dX = torch.empty((self.V, 3), device=self.device)
+        self._stream()
+        self._check(self.lib.fr_vertex_grad(self.ctx, _ptr(dX)), "fr_vertex_grad")
+        return dX
 
     def light_stage(self):
         out = np.zeros((self.cfg.n_lights, 12), np.float32)

@@ -259,7 +259,7 @@ def test_loss_hand_case(oracle):
 
 def _grad_setup():
     scene, theta, _ = S.make_workload("tiny", seed=3)
-    cfg = default_config(W=24, H=24, spp=2, seed=5)
+    cfg = default_config(W=24, H=24, spp=2, seed=5, value_mesh=0)
     rng = np.random.default_rng(11)
     dI = rng.normal(size=(24, 24, 3))
     return scene, theta, cfg, dI
