@@ -158,6 +158,20 @@ int fr_loss(fr_ctx* ctx, const float* theta, int32_t W, int32_t H, const float* 
  * silhouette edges (>= 0) or an error. */
 int fr_geometry(fr_ctx* ctx, const float* theta, float* X, float* N, float* A);
 
+/* fr_geometry for callers that must not allocate device memory during the
+ * call (their allocator owns the device, their memory budget is fixed at
+ * start-up, or they cannot afford the synchronisation an allocation may
+ * cause).  The paper has no counterpart: this is a deployment variant.
+ * Same outputs and return value as fr_geometry; the camera-silhouette
+ * compaction keeps its scratch (one int per 256 edges) in a static device
+ * array of 4096 ints, so meshes with more than 1,048,576 edges are rejected
+ * with FR_ERR_INVALID_ARG.  The array is shared by every call on a device and
+ * kept until the process exits; calls whose GPU work overlaps race on it.
+ * The first call on a device looks up the array's device address (set-up);
+ * make that first call before any stream capture.  Calls no cudaMalloc or
+ * cudaFree. */
+int fr_geometry_noalloc(fr_ctx* ctx, const float* theta, float* X, float* N, float* A);
+
 /* Per-vertex position gradient of the last fr_render_backward on this
  * context (after the normals adjoint, before the pose and basis
  * contractions): dX[V*3] FP32 device.  For inspection and tests. */

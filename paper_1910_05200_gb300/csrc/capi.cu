@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -313,8 +314,8 @@ int refit(fr_ctx* ctx, DevBVH& b, bool is_edge) {
   return FR_OK;
 }
 
-// Geometry, normals, refits and camera silhouettes for theta.
-int prepare(fr_ctx* ctx, const float* theta, int W, int H) {
+// Geometry, normals and refits for theta.
+int prepare_geometry(fr_ctx* ctx, const float* theta) {
   if (!ctx->have_mesh || !ctx->have_bases) return fail(ctx, FR_ERR_NOT_READY, "mesh and bases must be uploaded first");
   if (!theta) return fail(ctx, FR_ERR_INVALID_ARG, "theta is null");
   GeoArgs g = geo_args(ctx);
@@ -327,12 +328,17 @@ int prepare(fr_ctx* ctx, const float* theta, int W, int H) {
   CKL();
   int rc = refit(ctx, ctx->tbvh, false);
   if (rc) return rc;
-  rc = refit(ctx, ctx->ebvh, true);
-  if (rc) return rc;
+  return refit(ctx, ctx->ebvh, true);
+}
+
+// Order-preserving list of camera-silhouette edges; block_count is the
+// compaction's scratch (one int per 256 edges).
+int silhouettes(fr_ctx* ctx, int* block_count) {
+  cudaStream_t s = ctx->stream;
   SilArgs sa;
   sa.E = ctx->E; sa.edges = ctx->edges_canon.p; sa.tris = ctx->tris.p; sa.ng = ctx->ng.p; sa.X = ctx->X.p;
   sa.cam_o = V3{0.0f, 0.0f, ctx->cfg.d_cam};
-  sa.block_count = ctx->block_count.p; sa.sil = ctx->sil.p; sa.n_sil = ctx->n_sil.p;
+  sa.block_count = block_count; sa.sil = ctx->sil.p; sa.n_sil = ctx->n_sil.p;
   int nb = (ctx->E + 255) / 256;
   k_silhouette_flags<<<nb, 256, 0, s>>>(sa);
   CKL();
@@ -340,8 +346,28 @@ int prepare(fr_ctx* ctx, const float* theta, int W, int H) {
   CKL();
   k_silhouette_scatter<<<nb, 256, 0, s>>>(sa);
   CKL();
-  (void)W; (void)H;
   return FR_OK;
+}
+
+// Geometry, normals, refits and camera silhouettes for theta.
+int prepare(fr_ctx* ctx, const float* theta, int W, int H) {
+  int rc = prepare_geometry(ctx, theta);
+  if (rc) return rc;
+  (void)W; (void)H;
+  return silhouettes(ctx, ctx->block_count.p);
+}
+
+// Copy the geometry outputs of the last prepare and return the silhouette count.
+int geometry_outputs(fr_ctx* ctx, float* X, float* N, float* A) {
+  const int V = ctx->V;
+  cudaStream_t s = ctx->stream;
+  if (X) CK(cudaMemcpy2DAsync(X, 3 * sizeof(float), ctx->X.p, sizeof(float4), 3 * sizeof(float), V, cudaMemcpyDeviceToDevice, s));
+  if (N) CK(cudaMemcpy2DAsync(N, 3 * sizeof(float), ctx->nrm.p, sizeof(float4), 3 * sizeof(float), V, cudaMemcpyDeviceToDevice, s));
+  if (A) CK(cudaMemcpy2DAsync(A, 3 * sizeof(float), ctx->alb.p, sizeof(float4), 3 * sizeof(float), V, cudaMemcpyDeviceToDevice, s));
+  int nsil = 0;
+  CK(cudaMemcpyAsync(&nsil, ctx->n_sil.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return nsil;
 }
 
 int check_opts(fr_ctx* ctx, const fr_render_opts* o) {
@@ -658,15 +684,7 @@ int fr_geometry(fr_ctx* ctx, const float* theta, float* X, float* N, float* A) {
   CK(cudaSetDevice(ctx->device));
   int rc = prepare(ctx, theta, 1, 1);
   if (rc) return rc;
-  const int V = ctx->V;
-  cudaStream_t s = ctx->stream;
-  if (X) CK(cudaMemcpy2DAsync(X, 3 * sizeof(float), ctx->X.p, sizeof(float4), 3 * sizeof(float), V, cudaMemcpyDeviceToDevice, s));
-  if (N) CK(cudaMemcpy2DAsync(N, 3 * sizeof(float), ctx->nrm.p, sizeof(float4), 3 * sizeof(float), V, cudaMemcpyDeviceToDevice, s));
-  if (A) CK(cudaMemcpy2DAsync(A, 3 * sizeof(float), ctx->alb.p, sizeof(float4), 3 * sizeof(float), V, cudaMemcpyDeviceToDevice, s));
-  int nsil = 0;
-  CK(cudaMemcpyAsync(&nsil, ctx->n_sil.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  return nsil;
+  return geometry_outputs(ctx, X, N, A);
 }
 
 int fr_vertex_grad(fr_ctx* ctx, float* dX) {
@@ -704,6 +722,65 @@ int fr_get_counters(fr_ctx* ctx, uint64_t* out) {
 }
 
 uint64_t fr_launch_count(const fr_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+// ---------------------------------------------------------------------------
+// Geometry stage without device allocation.
+//
+// Some callers cannot call cudaMalloc while they run this library: a
+// framework whose caching allocator owns all device memory and forbids
+// allocations behind its back, a fixed-budget deployment that reserves every
+// byte at start-up, or a latency-critical loop that must not pay the implicit
+// device synchronisation cudaMalloc/cudaFree may trigger.  For them the
+// camera-silhouette compaction keeps its per-block counts in the file-scope
+// array below instead of a context buffer.  The array exists once per device
+// that loads the library and lives until the process exits; every call on
+// that device shares it, and each call overwrites every count it reads before
+// reading it, so nothing has to be cleared between calls.  Two calls whose
+// work overlaps on the GPU (different contexts on different streams of the
+// same device) race on it.
+
+constexpr int NOALLOC_MAX_SIL_BLOCKS = 4096;   // 16 KiB: up to 4096 * 256 = 1,048,576 edges
+static __device__ __align__(256) int g_noalloc_sil_blocks[NOALLOC_MAX_SIL_BLOCKS];
+
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 64;
+int* g_noalloc_sil_ptr[NOALLOC_MAX_DEVICES];   // device address of the array, per device
+std::mutex g_noalloc_mu;
+
+// In host code the array's name only stands in for the symbol; its device
+// address comes from the runtime, once per device, with that device current.
+int noalloc_scratch(fr_ctx* ctx, int** out) {
+  if (ctx->device < 0 || ctx->device >= NOALLOC_MAX_DEVICES)
+    return fail(ctx, FR_ERR_INVALID_ARG, "device %d beyond the %d devices supported", ctx->device, NOALLOC_MAX_DEVICES);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_sil_ptr[ctx->device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_sil_blocks);
+    if (e != cudaSuccess || !p)
+      return fail(ctx, FR_ERR_CUDA, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
+    g_noalloc_sil_ptr[ctx->device] = static_cast<int*>(p);
+  }
+  *out = g_noalloc_sil_ptr[ctx->device];
+  return FR_OK;
+}
+}  // namespace
+
+int fr_geometry_noalloc(fr_ctx* ctx, const float* theta, float* X, float* N, float* A) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  int nb = (ctx->E + 255) / 256;
+  if (nb > NOALLOC_MAX_SIL_BLOCKS)
+    return fail(ctx, FR_ERR_INVALID_ARG, "fr_geometry_noalloc supports at most %d mesh edges (mesh has %d)",
+                NOALLOC_MAX_SIL_BLOCKS * 256, ctx->E);
+  CK(cudaSetDevice(ctx->device));
+  int* scratch = nullptr;
+  int rc = noalloc_scratch(ctx, &scratch);
+  if (rc) return rc;
+  rc = prepare_geometry(ctx, theta);
+  if (rc) return rc;
+  rc = silhouettes(ctx, scratch);
+  if (rc) return rc;
+  return geometry_outputs(ctx, X, N, A);
+}
 
 // Wait for the context stream and report device-side limit hits (traversal
 // stack overflow or step cap) raised since the last call, clearing the flag.

@@ -34,7 +34,7 @@ class FrRenderOpts(C.Structure):
 
 EXPORTS = ["fr_default_config", "fr_create", "fr_destroy", "fr_set_stream", "fr_last_error", "fr_strerror",
            "fr_upload_mesh", "fr_upload_bases", "fr_n_params", "fr_render", "fr_render_backward", "fr_loss",
-           "fr_geometry", "fr_vertex_grad", "fr_light_stage", "fr_sync", "fr_set_counters", "fr_get_counters",
+           "fr_geometry", "fr_geometry_noalloc", "fr_vertex_grad", "fr_light_stage", "fr_sync", "fr_set_counters", "fr_get_counters",
            "fr_launch_count"]
 
 
@@ -69,6 +69,7 @@ def load(path: str | None = None):
     L.fr_render_backward.argtypes = [vp, vp, vp, vp, vp, i32]
     L.fr_loss.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, f32, f32, vp, vp, vp]
     L.fr_geometry.argtypes = [vp, vp, vp, vp, vp]
+    L.fr_geometry_noalloc.argtypes = [vp, vp, vp, vp, vp]
     L.fr_light_stage.argtypes = [vp, vp]
     L.fr_vertex_grad.argtypes = [vp, vp]
     L.fr_sync.argtypes = [vp]
