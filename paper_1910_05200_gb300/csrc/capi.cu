@@ -174,7 +174,7 @@ struct Builder {
 };
 
 struct DevBVH {
-  DBuf<float4> nodes;
+  DBuf<float4> nodes, cones;
   DBuf<int> leaf_first, leaf_count, leaf_parent, leaf_slot, node_parent, node_slot, counter;
   int n_nodes = 0, n_leaves = 0;
 };
@@ -198,7 +198,7 @@ struct fr_ctx {
   int K_id = 0, K_exp = 0, K_alb = 0;
   DBuf<float> BidT, BexpT, alb_mean, BalbT;
   // per-render state
-  DBuf<float4> X, Xm, alb, nrm, ng, tv;
+  DBuf<float4> X, Xm, alb, nrm, ng, tv, epack;
   DBuf<int> sil, n_sil, block_count, err_flag;
   DBuf<unsigned long long> counters;
   bool counters_on = false;
@@ -206,6 +206,7 @@ struct fr_ctx {
   // gradient accumulators
   DBuf<float4> dX, dN, dA, gs;
   DBuf<float> dXm, dC, dL;
+  DBuf<int2> hits;        // primary hit per tiled sample (backward)
   int n_params() const { return K_id + K_exp + K_alb + CS * CS + 6 + 3 * cfg.n_lights; }
   int off_cspec() const { return K_id + K_exp + K_alb; }
   int off_pose() const { return off_cspec() + CS * CS; }
@@ -278,6 +279,10 @@ int upload_bvh(fr_ctx* ctx, const HostBVH& h, DevBVH& d) {
   CK(upload(d.node_parent, h.node_parent.data(), h.node_parent.size(), ctx->stream));
   CK(upload(d.node_slot, h.node_slot.data(), h.node_slot.size(), ctx->stream));
   CK(d.counter.alloc(d.n_nodes));
+  {
+    std::vector<float4> full(2 * (size_t)d.n_nodes, make_float4(0, 0, 1, CONE_FULL));
+    CK(upload(d.cones, full.data(), full.size(), ctx->stream));
+  }
   return FR_OK;
 }
 
@@ -309,6 +314,7 @@ int refit(fr_ctx* ctx, DevBVH& b, bool is_edge) {
   r.leaf_slot = b.leaf_slot.p; r.node_parent = b.node_parent.p; r.node_slot = b.node_slot.p;
   r.counter = b.counter.p; r.nodes = b.nodes.p; r.is_edge = is_edge ? 1 : 0;
   r.tv = ctx->tv.p; r.edges = ctx->edges_leaf.p; r.X = ctx->X.p;
+  r.pack = ctx->epack.p; r.cones = b.cones.p;
   k_refit<<<(b.n_leaves + 255) / 256, 256, 0, ctx->stream>>>(r);
   CKL();
   return FR_OK;
@@ -325,6 +331,9 @@ int prepare_geometry(fr_ctx* ctx, const float* theta) {
   k_faces<<<(ctx->F + 255) / 256, 256, 0, s>>>(g);
   CKL();
   k_vertex_normals<<<(ctx->V + 255) / 256, 256, 0, s>>>(g);
+  CKL();
+  k_pack_edges<<<(ctx->E + 255) / 256, 256, 0, s>>>(ctx->E, ctx->edges_leaf.p, ctx->edge_id_leaf.p, ctx->tris.p,
+                                                     ctx->X.p, ctx->ng.p, ctx->epack.p);
   CKL();
   int rc = refit(ctx, ctx->tbvh, false);
   if (rc) return rc;
@@ -390,6 +399,7 @@ RenderArgs render_args(fr_ctx* c, const float* theta, const fr_render_opts* o) {
   a.mesh.bvh.nodes = c->tbvh.nodes.p; a.mesh.bvh.n_nodes = c->tbvh.n_nodes;
   a.ebvh.bvh.nodes = c->ebvh.nodes.p; a.ebvh.bvh.n_nodes = c->ebvh.n_nodes;
   a.ebvh.edges = c->edges_leaf.p; a.ebvh.edge_id = c->edge_id_leaf.p;
+  a.ebvh.pack = c->epack.p; a.ebvh.verts = c->edges_leaf.p; a.ebvh.cones = c->ebvh.cones.p;
   a.nrm = c->nrm.p; a.alb = c->alb.p; a.uv = reinterpret_cast<const float2*>(c->uv.p);
   a.cspec = theta + c->off_cspec(); a.lights_dev = theta + c->off_lights();
   a.sil = c->sil.p; a.n_sil = c->n_sil.p; a.edges_canon = c->edges_canon.p;
@@ -461,13 +471,15 @@ void fr_destroy(fr_ctx* ctx) {
   ctx->mean.free_(); ctx->uv.free_(); ctx->tris.free_(); ctx->edges_canon.free_(); ctx->edges_leaf.free_();
   ctx->vf_off.free_(); ctx->vf_idx.free_(); ctx->tri_perm.free_(); ctx->edge_id_leaf.free_();
   for (DevBVH* b : {&ctx->tbvh, &ctx->ebvh}) {
-    b->nodes.free_(); b->leaf_first.free_(); b->leaf_count.free_(); b->leaf_parent.free_(); b->leaf_slot.free_();
+    b->nodes.free_(); b->cones.free_(); b->leaf_first.free_(); b->leaf_count.free_(); b->leaf_parent.free_(); b->leaf_slot.free_();
     b->node_parent.free_(); b->node_slot.free_(); b->counter.free_();
   }
   ctx->BidT.free_(); ctx->BexpT.free_(); ctx->alb_mean.free_(); ctx->BalbT.free_();
   ctx->X.free_(); ctx->Xm.free_(); ctx->alb.free_(); ctx->nrm.free_(); ctx->ng.free_(); ctx->tv.free_();
+  ctx->epack.free_();
   ctx->sil.free_(); ctx->n_sil.free_(); ctx->block_count.free_(); ctx->err_flag.free_(); ctx->counters.free_();
   ctx->dX.free_(); ctx->dN.free_(); ctx->dA.free_(); ctx->gs.free_(); ctx->dXm.free_(); ctx->dC.free_(); ctx->dL.free_();
+  ctx->hits.free_();
   delete ctx;
 }
 
@@ -545,7 +557,7 @@ int fr_upload_mesh(fr_ctx* ctx, const float* mean, int32_t V, const int32_t* tri
   if (rc) return rc;
   ctx->V = V; ctx->F = F; ctx->E = E;
   CK(ctx->X.alloc(V)); CK(ctx->Xm.alloc(V)); CK(ctx->alb.alloc(V)); CK(ctx->nrm.alloc(V));
-  CK(ctx->ng.alloc(F)); CK(ctx->tv.alloc(3 * (size_t)F));
+  CK(ctx->ng.alloc(F)); CK(ctx->tv.alloc(3 * (size_t)F)); CK(ctx->epack.alloc(6 * (size_t)E));
   CK(ctx->sil.alloc(E)); CK(ctx->block_count.alloc((E + 255) / 256));
   CK(ctx->dX.alloc(V)); CK(ctx->dN.alloc(V)); CK(ctx->dA.alloc(V)); CK(ctx->gs.alloc(V));
   CK(ctx->dXm.alloc(3 * (size_t)V)); CK(ctx->dC.alloc(CS * CS)); CK(ctx->dL.alloc(3 * MAX_LIGHTS));
@@ -622,13 +634,18 @@ int fr_render_backward(fr_ctx* ctx, const float* theta, const fr_render_opts* op
   CK(cudaMemsetAsync(ctx->dL.p, 0, sizeof(float) * 3 * MAX_LIGHTS, s));
   if (ctx->counters_on) CK(cudaMemsetAsync(ctx->counters.p, 0, 8 * sizeof(unsigned long long), s));
   RenderArgs a = render_args(ctx, theta, opts);
+  const int terms = opts->terms ? opts->terms : (TERM_INTERIOR | TERM_PEDGE | TERM_SEDGE);
+  long long tiled = (long long)(((opts->W + 7) / 8) * ((opts->H + 7) / 8)) * 64 * opts->spp;
+  if ((terms & TERM_SEDGE) && ctx->hits.n < (size_t)tiled) CK(ctx->hits.alloc(tiled));
   GradBufs gb;
   gb.dX = ctx->dX.p; gb.dN = ctx->dN.p; gb.dA = ctx->dA.p; gb.dC = ctx->dC.p; gb.dL = ctx->dL.p;
   gb.d_image = d_image;
-  const int terms = opts->terms ? opts->terms : (TERM_INTERIOR | TERM_PEDGE | TERM_SEDGE);
-  long long tiled = (long long)(((opts->W + 7) / 8) * ((opts->H + 7) / 8)) * 64 * opts->spp;
-  if (terms & TERM_INTERIOR) {
-    k_bwd_interior<<<grid_for(tiled, 256), 256, 0, s>>>(a, gb);
+  gb.hits = (terms & TERM_SEDGE) ? ctx->hits.p : nullptr;
+  // The interior pass finds each sample's primary hit; the shadow-edge pass reuses it.
+  if (terms & (TERM_INTERIOR | TERM_SEDGE)) {
+    RenderArgs ai = a;
+    if (!(terms & TERM_INTERIOR)) { ai.n_lights = 0; }   // hits only
+    k_bwd_interior<<<grid_for(tiled, 256), 256, 0, s>>>(ai, gb);
     CKL();
   }
   if (terms & TERM_PEDGE) {
@@ -636,7 +653,8 @@ int fr_render_backward(fr_ctx* ctx, const float* theta, const fr_render_opts* op
     CKL();
   }
   if (terms & TERM_SEDGE) {
-    k_bwd_sedge<<<grid_for(tiled, 256), 256, 0, s>>>(a, gb);
+    dim3 grid(grid_for(tiled, 256), ctx->cfg.n_lights);
+    k_bwd_sedge<<<grid, 256, 0, s>>>(a, gb);
     CKL();
   }
   GeoArgs g = geo_args(ctx);

@@ -159,6 +159,28 @@ struct BVHView {
   int n_nodes;
 };
 
+// Normal cone (axis.xyz, half-angle in radians; >= pi means "any direction").
+constexpr float CONE_FULL = 4.0f;
+
+FR_DEV float4 cone_merge(float4 c1, float4 c2) {
+  if (c1.w >= PI_F || c2.w >= PI_F) return make_float4(0, 0, 1, CONE_FULL);
+  float d = c1.x * c2.x + c1.y * c2.y + c1.z * c2.z;
+  float w = acosf(fminf(1.0f, fmaxf(-1.0f, d)));
+  if (w + c2.w <= c1.w) return c1;
+  if (w + c1.w <= c2.w) return c2;
+  float th = 0.5f * (w + c1.w + c2.w);
+  if (th >= PI_F) return make_float4(0, 0, 1, CONE_FULL);
+  float rot = th - c1.w;             // rotate axis 1 toward axis 2 by rot
+  float ax = c1.x, ay = c1.y, az = c1.z;
+  if (w > 1e-6f) {
+    float is = 1.0f / sinf(w), s1 = sinf(w - rot) * is, s2 = sinf(rot) * is;
+    ax = c1.x * s1 + c2.x * s2; ay = c1.y * s1 + c2.y * s2; az = c1.z * s1 + c2.z * s2;
+    float in = rsqrtf(ax * ax + ay * ay + az * az);
+    ax *= in; ay *= in; az *= in;
+  }
+  return make_float4(ax, ay, az, th * 1.0001f + 1e-5f);   // slack for rounding
+}
+
 // Child code of an absent child (root of a hierarchy with a single leaf).
 constexpr int EMPTY_CHILD = (int)0x80000000;
 FR_DEV bool leaf_child(int c) { return c < 0; }

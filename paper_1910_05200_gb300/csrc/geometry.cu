@@ -92,6 +92,29 @@ __global__ void k_faces(GeoArgs g) {
   g.tv[3 * i + 2] = make_float4(c.x, c.y, c.z, 0.0f);
 }
 
+// Packed per-edge records for the shadow-edge search (edge-BVH leaf order):
+// endpoints, ids, and for each adjacent face its decision-form normal and
+// first vertex, so that a leaf test reads one 96-byte record.
+__global__ void k_pack_edges(int E, const int4* __restrict__ edges_leaf, const int* __restrict__ edge_id,
+                             const int4* __restrict__ tris, const float4* __restrict__ X,
+                             const float4* __restrict__ ng, float4* __restrict__ pack) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= E) return;
+  int4 e = edges_leaf[i];
+  float4 a = X[e.x], b = X[e.y];
+  float4 n0 = ng[e.z];
+  float4 p0 = X[tris[e.z].x];
+  float4 n1 = make_float4(0, 0, 0, 0), p1 = make_float4(0, 0, 0, 0);
+  if (e.w >= 0) { n1 = ng[e.w]; p1 = X[tris[e.w].x]; }
+  float4* R = pack + 6 * (size_t)i;
+  R[0] = make_float4(a.x, a.y, a.z, __int_as_float(edge_id[i]));
+  R[1] = make_float4(b.x, b.y, b.z, __int_as_float(e.z));
+  R[2] = make_float4(n0.x, n0.y, n0.z, __int_as_float(e.w));
+  R[3] = make_float4(p0.x, p0.y, p0.z, 0.0f);
+  R[4] = make_float4(n1.x, n1.y, n1.z, 0.0f);
+  R[5] = make_float4(p1.x, p1.y, p1.z, 0.0f);
+}
+
 // Unit vertex normals: gather the face cross products around each vertex.
 __global__ void k_vertex_normals(GeoArgs g) {
   int v = blockIdx.x * blockDim.x + threadIdx.x;
@@ -123,6 +146,29 @@ __device__ __forceinline__ void write_slot(float4* nodes, int node, int slot, V3
 
 // Bottom-up refit: one thread per leaf; the second child to arrive at a node
 // computes the node's box and carries on upward.
+// Normal cone of the faces adjacent to the edges of one leaf; boundary edges
+// make it full (they are silhouettes from any side).
+__device__ float4 leaf_cone(const float4* pack, int first, int cnt) {
+  V3 n[8];
+  int m = 0;
+  bool full = false;
+  for (int k = 0; k < cnt; ++k) {
+    const float4* R = pack + 6 * (first + k);
+    float4 n0 = R[2];
+    n[m++] = normalize(v3(n0));
+    if (__float_as_int(n0.w) < 0) full = true;
+    else n[m++] = normalize(v3(R[4]));
+  }
+  V3 sum{0, 0, 0};
+  for (int k = 0; k < m; ++k) sum += n[k];
+  float l2 = dot(sum, sum);
+  if (full || !(l2 > 1e-12f)) return make_float4(0, 0, 1, CONE_FULL);
+  V3 ax = sum * rsqrtf(l2);
+  float th = 0.0f;
+  for (int k = 0; k < m; ++k) th = fmaxf(th, acosf(fminf(1.0f, fmaxf(-1.0f, dot(ax, n[k])))));
+  return make_float4(ax.x, ax.y, ax.z, th * 1.0001f + 1e-4f);
+}
+
 __global__ void k_refit(RefitArgs r) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= r.n_leaves) return;
@@ -143,9 +189,11 @@ __global__ void k_refit(RefitArgs r) {
     }
   }
   pad_box(lo, hi);
+  float4 cone = r.is_edge ? leaf_cone(r.pack, first, cnt) : make_float4(0, 0, 1, CONE_FULL);
   int node = r.leaf_parent[i], slot = r.leaf_slot[i];
   while (node >= 0) {
     write_slot(r.nodes, node, slot, lo, hi);
+    if (r.is_edge) r.cones[2 * node + slot] = cone;
     __threadfence();
     int prev = atomicAdd(&r.counter[node], 1);
     if (prev == 0) return;          // the sibling finishes this node
@@ -155,6 +203,10 @@ __global__ void k_refit(RefitArgs r) {
     V3 l0{Nv[0], Nv[1], Nv[2]}, h0{Nv[3], Nv[4], Nv[5]}, l1{Nv[6], Nv[7], Nv[8]}, h1{Nv[9], Nv[10], Nv[11]};
     lo = V3{fminf(l0.x, l1.x), fminf(l0.y, l1.y), fminf(l0.z, l1.z)};
     hi = V3{fmaxf(h0.x, h1.x), fmaxf(h0.y, h1.y), fmaxf(h0.z, h1.z)};
+    if (r.is_edge) {
+      volatile const float* C = reinterpret_cast<const float*>(r.cones + 2 * node);
+      cone = cone_merge(make_float4(C[0], C[1], C[2], C[3]), make_float4(C[4], C[5], C[6], C[7]));
+    }
     slot = r.node_slot[node];
     node = r.node_parent[node];
   }

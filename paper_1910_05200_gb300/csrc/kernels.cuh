@@ -38,6 +38,8 @@ struct RefitArgs {
   const float4* tv;       // triangles (is_edge = 0)
   const int4* edges;      // leaf-ordered edges (is_edge = 1)
   const float4* X;
+  const float4* pack;     // packed edge records (is_edge = 1): face normals for the cones
+  float4* cones;          // [n_nodes * 2] normal cone per child slot (is_edge = 1)
 };
 
 struct SilArgs {
@@ -56,6 +58,9 @@ struct EdgeBVH {
   BVHView bvh;
   const int4* edges;      // leaf-ordered (v0, v1, f0, f1)
   const int* edge_id;     // leaf slot -> canonical edge id
+  const float4* pack;     // leaf-ordered packed records, 6 float4 per edge
+  const int4* verts;      // same as edges (v0, v1 read by the adjoint)
+  const float4* cones;    // [n_nodes * 2] normal cones of the faces below each child
 };
 
 struct RenderArgs {
@@ -86,10 +91,14 @@ struct GradBufs {
   float* dC;              // [1024]
   float* dL;              // [3N]
   const float* d_image;   // [H*W*3]
+  int2* hits;             // per tiled sample: (face or -1, t bits), written by k_bwd_interior
 };
 
 __global__ void k_geometry(GeoArgs g, const float* __restrict__ theta);
 __global__ void k_faces(GeoArgs g);
+__global__ void k_pack_edges(int E, const int4* __restrict__ edges_leaf, const int* __restrict__ edge_id,
+                             const int4* __restrict__ tris, const float4* __restrict__ X,
+                             const float4* __restrict__ ng, float4* __restrict__ pack);
 __global__ void k_vertex_normals(GeoArgs g);
 __global__ void k_refit(RefitArgs r);
 __global__ void k_silhouette_flags(SilArgs s);

@@ -262,13 +262,16 @@ __global__ void __launch_bounds__(256) k_bwd_interior(RenderArgs a, GradBufs gb)
   int ip = (int)(tid / spp), s = (int)(tid - (long long)ip * spp);
   int px = 0, py = 0;
   unsigned long long* cnt = a.counters ? a.counters + 4 : nullptr;
-  if (tid < total && tile_pixel(ip, a.W, a.H, px, py)) {
+  bool in_image = tid < total && tile_pixel(ip, a.W, a.H, px, py);
+  if (tid < total && !in_image && gb.hits) gb.hits[tid] = make_int2(-1, 0);
+  if (in_image) {
     uint32_t pix;
     V3 d = sample_dir(a, px, py, s, pix);
     const float* dI = gb.d_image + 3 * (size_t)pix;
     V3 dimg{dI[0], dI[1], dI[2]};
-    float t;
+    float t = 0.0f;
     int f = (dimg.x != 0.0f || dimg.y != 0.0f || dimg.z != 0.0f) ? closest_hit(a.mesh, a.cam.o, d, t, a.err, cnt) : -1;
+    if (gb.hits) gb.hits[tid] = make_int2(f, __float_as_int(t));
     if (f >= 0) {
       int flip = face_flip(a.mesh, f, d);
       V3 x32 = hit_point(a.cam.o, d, t);
@@ -444,22 +447,42 @@ FR_DEV bool silhouette_from(const Mesh& m, int4 E, V3 x) {
   return (s0 > 0.0f && s1 < 0.0f) || (s0 < 0.0f && s1 > 0.0f);
 }
 
+// Packed edge record (6 float4 per edge, edge-BVH leaf order), written per
+// render by k_pack_edges:
+//   [0] a.xyz, canonical edge id   [1] b.xyz, f0   [2] n0.xyz, f1
+//   [3] V0(f0).xyz                 [4] n1.xyz      [5] V0(f1).xyz
+// n = decision-form face normal, V0 = first vertex of the face.
+
+// Silhouette seen from x (decision form), from a packed record.
+FR_DEV bool packed_silhouette(const float4* R, V3 x, int f1) {
+  float4 n0 = R[2], p0 = R[3];
+  float s0 = dot3r(v3(n0), sub3r(x, v3(p0)));
+  if (f1 < 0) return s0 != 0.0f;
+  float4 n1 = R[4], p1 = R[5];
+  float s1 = dot3r(v3(n1), sub3r(x, v3(p1)));
+  return (s0 > 0.0f && s1 < 0.0f) || (s0 < 0.0f && s1 > 0.0f);
+}
+
+// Candidate search for one (shading point, light): traverse the edge BVH,
+// keeping a child when (1) its box reaches the pyramid from x through the
+// light square (4 side planes and the plane in front of x, with margins) and
+// (2) its normal cone does not prove every face below it is seen from the
+// same side (no silhouette possible).  Both tests are conservative; the leaf
+// test (silhouette + clip, decision form) decides.  The candidate with the
+// minimum Philox key is kept, so the pick does not depend on the order of
+// enumeration.
 struct Pick {
-  int n;          // number of candidate edges
-  int edge;       // canonical id of the pick
-  int4 E;         // its (v0, v1, f0, f1)
-  float t0, t1;   // clipped parameter interval
+  int n;        // number of candidates
+  int id;       // canonical id of the pick
+  int slot;     // its leaf slot in the packed array
 };
 
-// Enumerate candidate edges with the edge BVH (pyramid culling is
-// conservative; the leaf test decides) and keep the minimum (key, id).
-FR_DEV Pick shadow_pick(const RenderArgs& a, V3 x, int hitf, int j, uint32_t pix, int s, unsigned long long* cnt) {
+FR_DEV Pick pick_light(const RenderArgs& a, V3 x, int hitf, int j, uint32_t pix, int s, unsigned long long* cnt) {
   const Light& L = a.lights[j];
   const float hs = __fmul_rn(0.5f, a.side);
   Pick P;
-  P.n = 0; P.edge = -1; P.t0 = P.t1 = 0.0f;
+  P.n = 0; P.id = -1; P.slot = -1;
   uint32_t bestkey = 0xffffffffu;
-  // side planes of the pyramid from x through the light square, inward normals
   V3 Q[4];
   const float sg[4][2] = {{-1, -1}, {1, -1}, {1, 1}, {-1, 1}};
 #pragma unroll
@@ -474,7 +497,6 @@ FR_DEV Pick shadow_pick(const RenderArgs& a, V3 x, int hitf, int j, uint32_t pix
     pn[k] = n;
     pm[k] = 1e-4f * len(n);
   }
-  const float fm = 1e-4f;
   int stack[STACK];
   int sp = 0, node = 0, steps = 0;
   unsigned long long nvis = 0, nedge = 0;
@@ -487,39 +509,60 @@ FR_DEV Pick shadow_pick(const RenderArgs& a, V3 x, int hitf, int j, uint32_t pix
     int4 ch = *reinterpret_cast<const int4*>(N + 3);
     V3 lo[2] = {V3{b0.x, b0.y, b0.z}, V3{b1.z, b1.w, b2.x}};
     V3 hi[2] = {V3{b0.w, b1.x, b1.y}, V3{b2.y, b2.z, b2.w}};
+    int code[2] = {ch.x, ch.y};
     int todo[2];
     int nt = 0;
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-      // front plane: some point with (p - x).dl >= kappa
+      if (code[c] == EMPTY_CHILD) continue;
       V3 pp{L.dl.x > 0 ? hi[c].x : lo[c].x, L.dl.y > 0 ? hi[c].y : lo[c].y, L.dl.z > 0 ? hi[c].z : lo[c].z};
-      bool keep = dot(pp - x, L.dl) >= a.kappa - fm;
+      bool keep = dot(pp - x, L.dl) >= a.kappa - 1e-4f;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         V3 n = pn[k];
         V3 p{n.x > 0 ? hi[c].x : lo[c].x, n.y > 0 ? hi[c].y : lo[c].y, n.z > 0 ? hi[c].z : lo[c].z};
         keep = keep && dot(n, p - x) >= -pm[k];
       }
-      if (keep) todo[nt++] = c == 0 ? ch.x : ch.y;
+      if (!keep) continue;
+      float4 cn = a.ebvh.cones[2 * node + c];
+      if (cn.w < PI_F) {
+        // every face normal below lies within cn.w of the axis and every point
+        // in the bounding sphere (cb, rb): psi + beta + th < pi/2 means all
+        // faces face x, psi - beta - th > pi/2 means all face away
+        V3 cb = (lo[c] + hi[c]) * 0.5f;
+        float rb = len((hi[c] - lo[c]) * 0.5f) * 1.0001f + 1e-6f;
+        V3 v = x - cb;
+        float dv2 = dot(v, v);
+        if (dv2 > rb * rb) {
+          float idv = rsqrtf(dv2);
+          float psi = acosf(fminf(1.0f, fmaxf(-1.0f, dot(v, v3(cn)) * idv)));
+          float beta = asinf(fminf(1.0f, rb * idv));
+          const float half_pi = 1.57079632679f, margin = 2e-3f;
+          if (psi + beta + cn.w < half_pi - margin || psi - beta - cn.w > half_pi + margin) continue;
+        }
+      }
+      todo[nt++] = code[c];
     }
     int next = -1;
     for (int k = 0; k < nt; ++k) {
       int c2 = todo[k];
-      if (c2 == EMPTY_CHILD) continue;
       if (leaf_child(c2)) {
-        int f0 = leaf_first(c2), n = leaf_count(c2);
+        int first = leaf_first(c2), n = leaf_count(c2);
         for (int i = 0; i < n; ++i) {
-          int4 E = a.ebvh.edges[f0 + i];
+          const float4* R = a.ebvh.pack + 6 * (first + i);
+          float4 r1 = R[1], r2 = R[2];
+          int f0 = __float_as_int(r1.w), f1 = __float_as_int(r2.w);
           ++nedge;
-          if (E.z == hitf || E.w == hitf) continue;
-          if (!silhouette_from(a.mesh, E, x)) continue;
+          if (f0 == hitf || f1 == hitf) continue;
+          if (!packed_silhouette(R, x, f1)) continue;
+          float4 r0 = R[0];
           float t0, t1;
-          if (!shadow_clip(v3(a.mesh.X[E.x]), v3(a.mesh.X[E.y]), x, L, hs, a.kappa, t0, t1)) continue;
-          int id = a.ebvh.edge_id[f0 + i];
+          if (!shadow_clip(v3(r0), v3(r1), x, L, hs, a.kappa, t0, t1)) continue;
+          int id = __float_as_int(r0.w);
           uint32_t key = philox(a.seed, a.iter, pix, (uint32_t)s, (uint32_t)(TAG_SEDGE_PICK << 8 | j), (uint32_t)id).x;
           ++P.n;
-          if (P.edge < 0 || key < bestkey || (key == bestkey && id < P.edge)) {
-            bestkey = key; P.edge = id; P.E = E; P.t0 = t0; P.t1 = t1;
+          if (P.id < 0 || key < bestkey || (key == bestkey && id < P.id)) {
+            bestkey = key; P.id = id; P.slot = first + i;
           }
         }
       } else if (next < 0) {
@@ -538,92 +581,104 @@ done:
   return P;
 }
 
+// Boundary term of one light given its pick: sample the clipped edge,
+// difference the integrand across the projected edge, scatter the adjoint.
+FR_DEV void sedge_contribution(const RenderArgs& a, const GradBufs& gb, int j, int n_cand, int slot, V3 d, V3 x32,
+                               int f, int flip, uint32_t pix, int s, V3 wrgb, unsigned long long* cnt) {
+  const Light& L = a.lights[j];
+  const float hs = __fmul_rn(0.5f, a.side);
+  const float4* R = a.ebvh.pack + 6 * slot;
+  float4 r0 = R[0], r1 = R[1];
+  V3 A = v3(r0), B = v3(r1);
+  int4 ev = a.ebvh.verts[slot];
+  int v0 = ev.x, v1 = ev.y;
+  float t0, t1;
+  shadow_clip(A, B, x32, L, hs, a.kappa, t0, t1);
+  U4 q = philox(a.seed, a.iter, pix, (uint32_t)s, (uint32_t)(TAG_SEDGE_POINT << 8 | j), 0);
+  float u = unitf(q.x);
+  float tau = __fadd_rn(t0, __fmul_rn(u, __fsub_rn(t1, t0)));
+  float Dd = -dot3r(sub3r(x32, L.c), L.dl);
+  V3 y = edge_proj(A, B, x32, L, Dd, tau);
+  V3 y0 = edge_proj(A, B, x32, L, Dd, t0);
+  V3 y1 = edge_proj(A, B, x32, L, Dd, t1);
+  V3 nv = cross3r(L.dl, sub3r(y1, y0));
+  float nl = __fsqrt_rn(dot3r(nv, nv));
+  if (nl == 0.0f) return;
+  nv = V3{__fdiv_rn(nv.x, nl), __fdiv_rn(nv.y, nl), __fdiv_rn(nv.z, nl)};
+  const float e = a.eps_sedge;
+  V3 yp{__fadd_rn(y.x, __fmul_rn(e, nv.x)), __fadd_rn(y.y, __fmul_rn(e, nv.y)), __fadd_rn(y.z, __fmul_rn(e, nv.z))};
+  V3 ym{__fsub_rn(y.x, __fmul_rn(e, nv.x)), __fsub_rn(y.y, __fmul_rn(e, nv.y)), __fsub_rn(y.z, __fmul_rn(e, nv.z))};
+  bool vp = visible(a.mesh, x32, yp, f, flip, a.tmin, a.err, cnt);
+  bool vm = visible(a.mesh, x32, ym, f, flip, a.tmin, a.err, cnt);
+  if (vp == vm) return;
+  Surf S = surface(a, f, a.cam.o, d, flip);
+  int idx[4];
+  float w4[4], fu, fv;
+  float cs = cspec_lookup(a.cspec, S.u, S.v, idx, w4, fu, fv);
+  V3 l = light_rgb(a, j);
+  V3 gp{0, 0, 0}, gm{0, 0, 0};
+  if (vp) gp = shade_light(S, cs, l, yp, L.dl, a.m).h;
+  if (vm) gm = shade_light(S, cs, l, ym, L.dl, a.m).h;
+  float delta = dot(wrgb, gm - gp);
+  if (delta == 0.0f) return;
+  float w = delta * (float)n_cand * (t1 - t0);
+  // Adjoint of the boundary point y(tau) = x + q D/h on the light plane,
+  // q = p - x, p = A + tau (B - A), h = q.dl, D = (c - x).dl.  With
+  // u = B - A and K = (dl x (q x u)) x q, the normal velocity of the
+  // boundary times its length element gives
+  //   dE/dp = w (D/h^2)^2 K,   dE/dx = w (1 - D/h) (D/h^3) K.
+  // For an occluder close to the shading point these factors amplify any
+  // error in x, and x itself is ill-conditioned at grazing hits, so this
+  // (rare: only where the two sides differ) step runs in FP64.
+  double x64[3];
+  hit_point64(a, f, a.cam.o, d, x64);
+  double ue[3] = {(double)B.x - A.x, (double)B.y - A.y, (double)B.z - A.z};
+  double qv[3] = {((double)A.x - x64[0]) + ue[0] * tau, ((double)A.y - x64[1]) + ue[1] * tau,
+                  ((double)A.z - x64[2]) + ue[2] * tau};
+  double dl[3] = {L.dl.x, L.dl.y, L.dl.z};
+  double h = qv[0] * dl[0] + qv[1] * dl[1] + qv[2] * dl[2];
+  double D = ((double)L.c.x - x64[0]) * dl[0] + ((double)L.c.y - x64[1]) * dl[1] + ((double)L.c.z - x64[2]) * dl[2];
+  double Dh2 = D / (h * h);
+  double c1[3], c2[3], K[3];
+  cross64(qv, ue, c1);
+  cross64(dl, c1, c2);
+  cross64(c2, qv, K);
+  double sp = (double)w * Dh2 * Dh2, sx = (double)w * (1.0 - D / h) * (Dh2 / h);
+  V3 g_p{(float)(K[0] * sp), (float)(K[1] * sp), (float)(K[2] * sp)};
+  V3 gx{(float)(K[0] * sx), (float)(K[1] * sx), (float)(K[2] * sx)};
+  atomic_add3(gb.dX + v0, g_p * (1.0f - tau));
+  atomic_add3(gb.dX + v1, g_p * tau);
+  hit_adjoint(a, f, d, S, gx, 0.0f, 0.0f, gb.dX);
+}
+
+// One thread per (light, camera sample), light-major: a warp serves one light
+// and neighbouring samples, so traversals stay coherent, and warps of lights
+// that are off retire at once.  The primary hit comes from the interior pass
+// of the same backward call (gb.hits).
 __global__ void __launch_bounds__(256) k_bwd_sedge(RenderArgs a, GradBufs gb) {
+  const int j = blockIdx.y;
+  if (!light_on(a, j)) return;
   const int spp = a.spp;
   long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   long long total = (long long)tiled_pixel_count(a.W, a.H) * spp;
+  if (tid >= total) return;
+  int2 hit = gb.hits[tid];
+  int f = hit.x;
+  if (f < 0) return;
   int ip = (int)(tid / spp), s = (int)(tid - (long long)ip * spp);
   int px = 0, py = 0;
-  if (!(tid < total && tile_pixel(ip, a.W, a.H, px, py))) return;
+  tile_pixel(ip, a.W, a.H, px, py);
   uint32_t pix;
   V3 d = sample_dir(a, px, py, s, pix);
   const float* dI = gb.d_image + 3 * (size_t)pix;
   V3 wrgb = V3{dI[0], dI[1], dI[2]} * (1.0f / (float)spp);
-  if (wrgb.x == 0.0f && wrgb.y == 0.0f && wrgb.z == 0.0f) return;
   unsigned long long* cnt = a.counters ? a.counters + 4 : nullptr;
-  float t;
-  int f = closest_hit(a.mesh, a.cam.o, d, t, a.err, cnt);
-  if (f < 0) return;
+  float t = __int_as_float(hit.y);
   int flip = face_flip(a.mesh, f, d);
   V3 x32 = hit_point(a.cam.o, d, t);
-  bool have_surf = false;
-  Surf S;
-  float cs = 0.0f;
-  for (int j = 0; j < a.n_lights; ++j) {
-    if (!light_on(a, j)) continue;
-    Pick P = shadow_pick(a, x32, f, j, pix, s, cnt);
-    if (P.n == 0) continue;
-    const Light& L = a.lights[j];
-    V3 A = v3(a.mesh.X[P.E.x]), B = v3(a.mesh.X[P.E.y]);
-    U4 q = philox(a.seed, a.iter, pix, (uint32_t)s, (uint32_t)(TAG_SEDGE_POINT << 8 | j), 0);
-    float u = unitf(q.x);
-    float tau = __fadd_rn(P.t0, __fmul_rn(u, __fsub_rn(P.t1, P.t0)));
-    float Dd = -dot3r(sub3r(x32, L.c), L.dl);
-    V3 y = edge_proj(A, B, x32, L, Dd, tau);
-    V3 y0 = edge_proj(A, B, x32, L, Dd, P.t0);
-    V3 y1 = edge_proj(A, B, x32, L, Dd, P.t1);
-    V3 nv = cross3r(L.dl, sub3r(y1, y0));
-    float nl = __fsqrt_rn(dot3r(nv, nv));
-    if (nl == 0.0f) continue;
-    nv = V3{__fdiv_rn(nv.x, nl), __fdiv_rn(nv.y, nl), __fdiv_rn(nv.z, nl)};
-    const float e = a.eps_sedge;
-    V3 yp{__fadd_rn(y.x, __fmul_rn(e, nv.x)), __fadd_rn(y.y, __fmul_rn(e, nv.y)), __fadd_rn(y.z, __fmul_rn(e, nv.z))};
-    V3 ym{__fsub_rn(y.x, __fmul_rn(e, nv.x)), __fsub_rn(y.y, __fmul_rn(e, nv.y)), __fsub_rn(y.z, __fmul_rn(e, nv.z))};
-    bool vp = visible(a.mesh, x32, yp, f, flip, a.tmin, a.err, cnt);
-    bool vm = visible(a.mesh, x32, ym, f, flip, a.tmin, a.err, cnt);
-    if (vp == vm) continue;
-    if (!have_surf) {
-      S = surface(a, f, a.cam.o, d, flip);
-      int idx[4];
-      float w[4], fu, fv;
-      cs = cspec_lookup(a.cspec, S.u, S.v, idx, w, fu, fv);
-      have_surf = true;
-    }
-    V3 l = light_rgb(a, j);
-    V3 gp{0, 0, 0}, gm{0, 0, 0};
-    if (vp) gp = shade_light(S, cs, l, yp, L.dl, a.m).h;
-    if (vm) gm = shade_light(S, cs, l, ym, L.dl, a.m).h;
-    float delta = dot(wrgb, gm - gp);
-    if (delta == 0.0f) continue;
-    float w = delta * (float)P.n * (P.t1 - P.t0);
-    // Adjoint of the boundary point y(tau) = x + q D/h on the light plane,
-    // q = p - x, p = A + tau (B - A), h = q.dl, D = (c - x).dl.  With
-    // u = B - A and K = (dl x (q x u)) x q, the normal velocity of the
-    // boundary times its length element gives
-    //   dE/dp = w (D/h^2)^2 K,   dE/dx = w (1 - D/h) (D/h^3) K.
-    // For an occluder close to the shading point these factors amplify any
-    // error in x, and x itself is ill-conditioned at grazing hits, so this
-    // (rare: only where the two sides differ) step runs in FP64.
-    double x64[3];
-    hit_point64(a, f, a.cam.o, d, x64);
-    double ue[3] = {(double)B.x - A.x, (double)B.y - A.y, (double)B.z - A.z};
-    double qv[3] = {((double)A.x - x64[0]) + ue[0] * tau, ((double)A.y - x64[1]) + ue[1] * tau,
-                    ((double)A.z - x64[2]) + ue[2] * tau};
-    double dl[3] = {L.dl.x, L.dl.y, L.dl.z};
-    double h = qv[0] * dl[0] + qv[1] * dl[1] + qv[2] * dl[2];
-    double D = ((double)L.c.x - x64[0]) * dl[0] + ((double)L.c.y - x64[1]) * dl[1] + ((double)L.c.z - x64[2]) * dl[2];
-    double Dh2 = D / (h * h);
-    double t1[3], t2[3], K[3];
-    cross64(qv, ue, t1);
-    cross64(dl, t1, t2);
-    cross64(t2, qv, K);
-    double sp = (double)w * Dh2 * Dh2, sx = (double)w * (1.0 - D / h) * (Dh2 / h);
-    V3 g_p{(float)(K[0] * sp), (float)(K[1] * sp), (float)(K[2] * sp)};
-    V3 gx{(float)(K[0] * sx), (float)(K[1] * sx), (float)(K[2] * sx)};
-    atomic_add3(gb.dX + P.E.x, g_p * (1.0f - tau));
-    atomic_add3(gb.dX + P.E.y, g_p * tau);
-    hit_adjoint(a, f, d, S, gx, 0.0f, 0.0f, gb.dX);
-  }
+  Pick P = pick_light(a, x32, f, j, pix, s, cnt);
+  if (P.n == 0) return;
+  sedge_contribution(a, gb, j, P.n, P.slot, d, x32, f, flip, pix, s, wrgb, cnt);
 }
 
 }  // namespace fr
