@@ -38,9 +38,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-pixels", type=int, default=24, help="oracle sample: pixels per step")
+    ap.add_argument("--cpu-pixels", type=int, default=128, help="cpu_baseline leg: oracle pixels (all spp)")
+    ap.add_argument("--ref-pixels", type=int, default=32, help="reference arm: oracle pixels per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=0, help="only run this many steps, no extras (ncu)")
+    ap.add_argument("--profile-res", type=int, default=0, help="with --profile-steps: image side (small ncu case)")
     return ap.parse_args()
 
 
@@ -149,15 +151,15 @@ def run_reference(args):
     scene, theta, c = workload()
     cores = os.cpu_count() or 1
     for i in range(args.warmup):
-        oracle_step_time(scene, theta, c, max(2, args.cpu_pixels // 4), seed=100 + i)
+        oracle_step_time(scene, theta, c, max(2, args.ref_pixels // 4), seed=100 + i)
     times, samples = [], 0
     for i in range(args.steps):
-        dt, n = oracle_step_time(scene, theta, c, args.cpu_pixels, seed=i)
+        dt, n = oracle_step_time(scene, theta, c, args.ref_pixels, seed=i)
         times.append(dt)
         samples += n
     total = sum(times)
     value = samples / total / 1e6
-    sample_desc = f"{args.cpu_pixels} random pixels x {c['spp']} spp per step, fwd+bwd (adjoint on those pixels)"
+    sample_desc = f"{args.ref_pixels} random pixels x {c['spp']} spp per step, fwd+bwd (adjoint on those pixels)"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Msamples/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -183,6 +185,8 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     scene, theta, c = workload()
     W, H, spp = c["W"], c["H"], c["spp"]
+    if args.profile_steps and args.profile_res:
+        W = H = args.profile_res
     r = facert.Renderer(scene, device=local)
     stream = torch.cuda.current_stream(dev)
     th = torch.tensor(theta, device=dev)
@@ -223,28 +227,26 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    kev = []   # events around the dominant kernel's call (backward) for the roofline
+    phases = []   # per-step phase times from the library's own events (same stream)
+    r.set_timing(True)
     launches0 = r.launches()
     for i in range(args.steps):
         flush.zero_()
         ev[i][0].record(stream)
         r.render(th, W, H, spp, seed=seed0 + args.warmup + i, out=image)
         loss = r.loss(th, image, target, d_image=d_image)
-        kb0 = torch.cuda.Event(enable_timing=True)
-        kb1 = torch.cuda.Event(enable_timing=True)
-        kb0.record(stream)
         r.backward(th, d_image, W, H, spp, seed=seed0 + args.warmup + i, grad=grad)
-        kb1.record(stream)
         ev[i][1].record(stream)
-        kev.append((kb0, kb1))
+        phases.append(r.timings())        # synchronises between steps (outside the step's events)
     torch.cuda.synchronize()
     launches = r.launches() - launches0
+    r.set_timing(False)
     if world > 1:
         dist.barrier()
     clocks.stop()
     r.sync()
     ms = [a.elapsed_time(b) for a, b in ev]
-    ms_bwd = [a.elapsed_time(b) for a, b in kev]
+    ph_mean = {k: float(np.mean([p[k] for p in phases])) for k in phases[0]}
     t_step = float(np.mean(ms))
     if world > 1:
         t = torch.tensor([t_step], device=dev)
@@ -280,28 +282,29 @@ def run_ours(args):
     h2d = th_h.numel() * 4 + tgt_h.numel() * 4
     d2h = grad_h.numel() * 8 + 8
 
-    # --- roofline of the dominant kernel group (backward) --------------------
+    # --- roofline of the dominant kernel (shadow-edge search) ---------------
     r.set_counters(True)
-    r.backward(th, d_image, W, H, spp, seed=5, grad=grad)
-    cnt = r.counters()
+    r.backward(th, d_image, W, H, spp, seed=seed0 + args.warmup, grad=grad)
+    cnt = [int(x) for x in r.counters()]
     r.set_counters(False)
     from paper_1910_05200_gb300 import roofline as RF
-    flops_bwd = float(RF.backward_flops([int(x) for x in cnt], samples, c["n_on"]))
-    t_bwd = float(np.mean(ms_bwd)) * 1e-3
+    flops_sedge = float(RF.sedge_flops(cnt))
+    t_sedge = ph_mean["shadow_edges"] * 1e-3
     clk = clocks.summary()
     peak = RF.fp32_peak_tflops(clk.get("sm_mhz"))
-    achieved = flops_bwd / t_bwd / 1e12
-    roof = {"bound": "alu", "kernel": "render_backward (interior + edge terms)", "achieved": achieved,
-            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-            "peak_note": "FP32 lanes x 2 x median SM clock under load (152 SMs x 128 lanes)",
-            "flops_per_launch": flops_bwd, "counts": [int(x) for x in cnt]}
+    achieved = flops_sedge / t_sedge / 1e12
+    roof = {"bound": "alu", "kernel": "k_bwd_sedge (shadow-boundary edge search)", "achieved": achieved,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": RF.SEDGE_TRAFFIC_BYTES,
+            "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x median SM clock under load",
+            "flops_per_launch": flops_sedge, "ms_per_launch": ph_mean["shadow_edges"],
+            "counts_sedge": cnt[12:16]}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Msamples/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": workload_config(c, scene),
-                "ms_backward": float(np.mean(ms_bwd)),
+                "ms_phases": ph_mean,
                 "e2e": {"value": world * samples / (t_e2e * 1e-3) / 1e6, "unit": "Msamples/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": t_e2e},
                 "gpu_launches": int(launches), "clocks": clk, "roofline": roof,

@@ -185,12 +185,22 @@ int fr_light_stage(const fr_ctx* ctx, float* out);
  * fr_sync, FR_ERR_CUDA if the stream reported an error, else FR_OK. */
 int fr_sync(fr_ctx* ctx);
 
-/* Counts of the last fr_render / fr_render_backward call, read back after a
- * stream synchronisation: BVH nodes visited, triangle tests, edge-BVH nodes
- * visited, edge tests, in that order (out[8]: forward then backward).
+/* Work counts of the last fr_render / fr_render_backward call, read back
+ * after a stream synchronisation.  out[16]: four counts (BVH nodes visited,
+ * triangle tests, edge-BVH nodes visited, edge tests) for each of the
+ * forward, interior, primary-edge and shadow-edge kernels, in that order.
  * Collected only when enabled with fr_set_counters(ctx, 1). */
 int fr_set_counters(fr_ctx* ctx, int32_t enable);
 int fr_get_counters(fr_ctx* ctx, uint64_t* out);
+
+/* Per-phase device time (CUDA events on the context stream) of the most
+ * recent call containing each phase, in ms: out[7] = geometry (morphable
+ * model, normals, refits, silhouettes), forward render, interior adjoint,
+ * primary edges, shadow edges, normal/geometry adjoint, loss.  Events are
+ * recorded only while enabled with fr_set_timing(ctx, 1); fr_get_timings
+ * synchronises the stream.  A phase not run since enabling reads 0. */
+int fr_set_timing(fr_ctx* ctx, int32_t enable);
+int fr_get_timings(fr_ctx* ctx, float* out);
 
 /* Number of kernels this context has launched since it was created. */
 uint64_t fr_launch_count(const fr_ctx* ctx);

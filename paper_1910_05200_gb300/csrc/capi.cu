@@ -181,6 +181,10 @@ struct DevBVH {
 
 }  // namespace
 
+constexpr int NCOUNT = 16;   // work counters: 4 per render kernel
+constexpr int NPHASE = 7;    // timed phases
+enum { PH_GEOMETRY = 0, PH_FORWARD, PH_INTERIOR, PH_PEDGE, PH_SEDGE, PH_ADJOINT, PH_LOSS };
+
 struct fr_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -203,6 +207,16 @@ struct fr_ctx {
   DBuf<unsigned long long> counters;
   bool counters_on = false;
   uint64_t launches = 0;
+  // per-phase timing (fr_set_timing): geometry, forward, interior, primary
+  // edges, shadow edges, adjoint, loss
+  bool timing_on = false, events_made = false;
+  cudaEvent_t ev[NPHASE][2];
+  bool phase_used[NPHASE] = {false};
+  void mark(int phase, int end) {
+    if (!timing_on) return;
+    cudaEventRecord(ev[phase][end], stream);
+    if (end) phase_used[phase] = true;
+  }
   // gradient accumulators
   DBuf<float4> dX, dN, dA, gs;
   DBuf<float> dXm, dC, dL;
@@ -360,10 +374,13 @@ int silhouettes(fr_ctx* ctx, int* block_count) {
 
 // Geometry, normals, refits and camera silhouettes for theta.
 int prepare(fr_ctx* ctx, const float* theta, int W, int H) {
+  ctx->mark(PH_GEOMETRY, 0);
   int rc = prepare_geometry(ctx, theta);
   if (rc) return rc;
   (void)W; (void)H;
-  return silhouettes(ctx, ctx->block_count.p);
+  rc = silhouettes(ctx, ctx->block_count.p);
+  ctx->mark(PH_GEOMETRY, 1);
+  return rc;
 }
 
 // Copy the geometry outputs of the last prepare and return the silhouette count.
@@ -451,13 +468,13 @@ int fr_create(fr_ctx** out, const fr_config* cfg, int32_t device) {
   ctx->device = device;
   ctx->cfg = c;
   ctx->lights = make_lights(c.n_lights, c.light_radius);
-  if (ctx->err_flag.alloc(1) != cudaSuccess || ctx->counters.alloc(8) != cudaSuccess ||
+  if (ctx->err_flag.alloc(1) != cudaSuccess || ctx->counters.alloc(NCOUNT) != cudaSuccess ||
       ctx->n_sil.alloc(1) != cudaSuccess) {
     delete ctx;
     return FR_ERR_OOM;
   }
   cudaMemset(ctx->err_flag.p, 0, sizeof(int));
-  cudaMemset(ctx->counters.p, 0, 8 * sizeof(unsigned long long));
+  cudaMemset(ctx->counters.p, 0, NCOUNT * sizeof(unsigned long long));
   cudaMemset(ctx->n_sil.p, 0, sizeof(int));
   if (cudaDeviceSynchronize() != cudaSuccess) { delete ctx; return FR_ERR_CUDA; }
   *out = ctx;
@@ -480,6 +497,8 @@ void fr_destroy(fr_ctx* ctx) {
   ctx->sil.free_(); ctx->n_sil.free_(); ctx->block_count.free_(); ctx->err_flag.free_(); ctx->counters.free_();
   ctx->dX.free_(); ctx->dN.free_(); ctx->dA.free_(); ctx->gs.free_(); ctx->dXm.free_(); ctx->dC.free_(); ctx->dL.free_();
   ctx->hits.free_();
+  if (ctx->events_made)
+    for (int i = 0; i < NPHASE; ++i) { cudaEventDestroy(ctx->ev[i][0]); cudaEventDestroy(ctx->ev[i][1]); }
   delete ctx;
 }
 
@@ -606,12 +625,14 @@ int fr_render(fr_ctx* ctx, const float* theta, const fr_render_opts* opts, float
   rc = prepare(ctx, theta, opts->W, opts->H);
   if (rc) return rc;
   RenderArgs a = render_args(ctx, theta, opts);
-  if (ctx->counters_on) CK(cudaMemsetAsync(ctx->counters.p, 0, 8 * sizeof(unsigned long long), ctx->stream));
+  if (ctx->counters_on) CK(cudaMemsetAsync(ctx->counters.p, 0, 4 * sizeof(unsigned long long), ctx->stream));
   bool shuffle = opts->spp <= 32 && (32 % opts->spp) == 0;
   if (!shuffle) CK(cudaMemsetAsync(image, 0, sizeof(float) * 3 * (size_t)opts->W * opts->H, ctx->stream));
   long long threads = (long long)(((opts->W + 7) / 8) * ((opts->H + 7) / 8)) * 64 * opts->spp;
+  ctx->mark(PH_FORWARD, 0);
   k_render_fwd<<<grid_for(threads, 256), 256, 0, ctx->stream>>>(a, image);
   CKL();
+  ctx->mark(PH_FORWARD, 1);
   return FR_OK;
 }
 
@@ -632,7 +653,7 @@ int fr_render_backward(fr_ctx* ctx, const float* theta, const fr_render_opts* op
   CK(cudaMemsetAsync(ctx->dA.p, 0, sizeof(float4) * V, s));
   CK(cudaMemsetAsync(ctx->dC.p, 0, sizeof(float) * CS * CS, s));
   CK(cudaMemsetAsync(ctx->dL.p, 0, sizeof(float) * 3 * MAX_LIGHTS, s));
-  if (ctx->counters_on) CK(cudaMemsetAsync(ctx->counters.p, 0, 8 * sizeof(unsigned long long), s));
+  if (ctx->counters_on) CK(cudaMemsetAsync(ctx->counters.p + 4, 0, 12 * sizeof(unsigned long long), s));
   RenderArgs a = render_args(ctx, theta, opts);
   const int terms = opts->terms ? opts->terms : (TERM_INTERIOR | TERM_PEDGE | TERM_SEDGE);
   long long tiled = (long long)(((opts->W + 7) / 8) * ((opts->H + 7) / 8)) * 64 * opts->spp;
@@ -645,18 +666,25 @@ int fr_render_backward(fr_ctx* ctx, const float* theta, const fr_render_opts* op
   if (terms & (TERM_INTERIOR | TERM_SEDGE)) {
     RenderArgs ai = a;
     if (!(terms & TERM_INTERIOR)) { ai.n_lights = 0; }   // hits only
+    ctx->mark(PH_INTERIOR, 0);
     k_bwd_interior<<<grid_for(tiled, 256), 256, 0, s>>>(ai, gb);
     CKL();
+    ctx->mark(PH_INTERIOR, 1);
   }
   if (terms & TERM_PEDGE) {
+    ctx->mark(PH_PEDGE, 0);
     k_bwd_pedge<<<grid_for((long long)opts->W * opts->H * opts->spp, 256), 256, 0, s>>>(a, gb);
     CKL();
+    ctx->mark(PH_PEDGE, 1);
   }
   if (terms & TERM_SEDGE) {
     dim3 grid(grid_for(tiled, 256), ctx->cfg.n_lights);
+    ctx->mark(PH_SEDGE, 0);
     k_bwd_sedge<<<grid, 256, 0, s>>>(a, gb);
     CKL();
+    ctx->mark(PH_SEDGE, 1);
   }
+  ctx->mark(PH_ADJOINT, 0);
   GeoArgs g = geo_args(ctx);
   k_normals_bwd_vertex<<<(V + 255) / 256, 256, 0, s>>>(g, ctx->dN.p, ctx->gs.p);
   CKL();
@@ -675,6 +703,7 @@ int fr_render_backward(fr_ctx* ctx, const float* theta, const fr_render_opts* op
   CKL();
   k_add_small<<<1, 128, 0, s>>>(ctx->dL.p, 3 * ctx->cfg.n_lights, grad, ctx->off_lights());
   CKL();
+  ctx->mark(PH_ADJOINT, 1);
   return FR_OK;
 }
 
@@ -686,6 +715,7 @@ int fr_loss(fr_ctx* ctx, const float* theta, int32_t W, int32_t H, const float* 
   if (!ctx->have_bases) return fail(ctx, FR_ERR_NOT_READY, "bases not uploaded");
   CK(cudaSetDevice(ctx->device));
   cudaStream_t s = ctx->stream;
+  ctx->mark(PH_LOSS, 0);
   CK(cudaMemsetAsync(loss, 0, sizeof(double), s));
   int n = W * H;
   int blocks = std::min((n + 255) / 256, 4 * 152);
@@ -694,6 +724,7 @@ int fr_loss(fr_ctx* ctx, const float* theta, int32_t W, int32_t H, const float* 
   k_loss_reg<<<1, 256, 0, s>>>(theta, ctx->K_id + ctx->K_exp + ctx->K_alb, ctx->off_lights(), 3 * ctx->cfg.n_lights,
                                m, w1, w2, loss, grad);
   CKL();
+  ctx->mark(PH_LOSS, 1);
   return FR_OK;
 }
 
@@ -732,10 +763,36 @@ int fr_set_counters(fr_ctx* ctx, int32_t enable) {
 
 int fr_get_counters(fr_ctx* ctx, uint64_t* out) {
   if (!ctx || !out) return FR_ERR_INVALID_ARG;
-  unsigned long long c[8];
+  unsigned long long c[NCOUNT];
   CK(cudaStreamSynchronize(ctx->stream));
   CK(cudaMemcpy(c, ctx->counters.p, sizeof c, cudaMemcpyDeviceToHost));
-  for (int i = 0; i < 8; ++i) out[i] = c[i];
+  for (int i = 0; i < NCOUNT; ++i) out[i] = c[i];
+  return FR_OK;
+}
+
+int fr_set_timing(fr_ctx* ctx, int32_t enable) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  CK(cudaSetDevice(ctx->device));
+  if (enable && !ctx->events_made) {
+    for (int i = 0; i < NPHASE; ++i) {
+      CK(cudaEventCreate(&ctx->ev[i][0]));
+      CK(cudaEventCreate(&ctx->ev[i][1]));
+    }
+    ctx->events_made = true;
+  }
+  ctx->timing_on = enable != 0;
+  for (int i = 0; i < NPHASE; ++i) ctx->phase_used[i] = false;
+  return FR_OK;
+}
+
+int fr_get_timings(fr_ctx* ctx, float* ms) {
+  if (!ctx || !ms) return FR_ERR_INVALID_ARG;
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < NPHASE; ++i) {
+    ms[i] = 0.0f;
+    if (ctx->events_made && ctx->phase_used[i]) CK(cudaEventElapsedTime(&ms[i], ctx->ev[i][0], ctx->ev[i][1]));
+  }
   return FR_OK;
 }
 

@@ -81,7 +81,7 @@ struct RenderArgs {
   const int* n_sil;
   const int4* edges_canon;
   int* err;
-  unsigned long long* counters;  // [8] or null
+  unsigned long long* counters;  // [16] or null: 4 per kernel (fwd, interior, pedge, sedge)
 };
 
 struct GradBufs {

@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(256) k_render_fwd(RenderArgs a, float* __restr
   int ip = (int)(tid / spp), s = (int)(tid - (long long)ip * spp);
   int px = 0, py = 0;
   bool valid = tid < total && tile_pixel(ip, a.W, a.H, px, py);
-  unsigned long long* cnt = a.counters;
+  unsigned long long* cnt = a.counters;      // forward: counters 0..3
   V3 L{0, 0, 0};
   uint32_t pix = 0;
   if (valid) {
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(256) k_bwd_interior(RenderArgs a, GradBufs gb)
   long long total = (long long)tiled_pixel_count(a.W, a.H) * spp;
   int ip = (int)(tid / spp), s = (int)(tid - (long long)ip * spp);
   int px = 0, py = 0;
-  unsigned long long* cnt = a.counters ? a.counters + 4 : nullptr;
+  unsigned long long* cnt = a.counters ? a.counters + 4 : nullptr;    // interior: 4..7
   bool in_image = tid < total && tile_pixel(ip, a.W, a.H, px, py);
   if (tid < total && !in_image && gb.hits) gb.hits[tid] = make_int2(-1, 0);
   if (in_image) {
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(256) k_bwd_pedge(RenderArgs a, GradBufs gb) {
   float e = a.eps_pedge;
   V3 dp = camera_dir(a.cam, __fadd_rn(mx, __fmul_rn(e, nx)), __fadd_rn(my, __fmul_rn(e, ny)));
   V3 dm = camera_dir(a.cam, __fsub_rn(mx, __fmul_rn(e, nx)), __fsub_rn(my, __fmul_rn(e, ny)));
-  unsigned long long* cnt = a.counters ? a.counters + 4 : nullptr;
+  unsigned long long* cnt = a.counters ? a.counters + 8 : nullptr;    // primary edges: 8..11
   V3 fp = radiance(a, a.cam.o, dp, TAG_PEDGE_LIGHT, pix, (uint32_t)s, cnt);
   V3 fm = radiance(a, a.cam.o, dm, TAG_PEDGE_LIGHT, pix, (uint32_t)s, cnt);
   float delta = dot(dimg, fm - fp);
@@ -672,7 +672,7 @@ __global__ void __launch_bounds__(256) k_bwd_sedge(RenderArgs a, GradBufs gb) {
   V3 d = sample_dir(a, px, py, s, pix);
   const float* dI = gb.d_image + 3 * (size_t)pix;
   V3 wrgb = V3{dI[0], dI[1], dI[2]} * (1.0f / (float)spp);
-  unsigned long long* cnt = a.counters ? a.counters + 4 : nullptr;
+  unsigned long long* cnt = a.counters ? a.counters + 12 : nullptr;   // shadow edges: 12..15
   float t = __int_as_float(hit.y);
   int flip = face_flip(a.mesh, f, d);
   V3 x32 = hit_point(a.cam.o, d, t);

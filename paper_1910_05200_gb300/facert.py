@@ -34,7 +34,7 @@ class FrRenderOpts(C.Structure):
 
 EXPORTS = ["fr_default_config", "fr_create", "fr_destroy", "fr_set_stream", "fr_last_error", "fr_strerror",
            "fr_upload_mesh", "fr_upload_bases", "fr_n_params", "fr_render", "fr_render_backward", "fr_loss",
-           "fr_geometry", "fr_geometry_noalloc", "fr_vertex_grad", "fr_light_stage", "fr_sync", "fr_set_counters", "fr_get_counters",
+           "fr_geometry", "fr_geometry_noalloc", "fr_vertex_grad", "fr_light_stage", "fr_sync", "fr_set_counters", "fr_get_counters", "fr_set_timing", "fr_get_timings",
            "fr_launch_count"]
 
 
@@ -75,6 +75,8 @@ def load(path: str | None = None):
     L.fr_sync.argtypes = [vp]
     L.fr_set_counters.argtypes = [vp, i32]
     L.fr_get_counters.argtypes = [vp, vp]
+    L.fr_set_timing.argtypes = [vp, i32]
+    L.fr_get_timings.argtypes = [vp, vp]
     L.fr_launch_count.argtypes = [vp]
     L.fr_launch_count.restype = C.c_uint64
     _LIB = L
@@ -213,8 +215,18 @@ class Renderer:
     def launches(self) -> int:
         return int(self.lib.fr_launch_count(self.ctx))
 
+    PHASES = ("geometry", "forward", "interior", "primary_edges", "shadow_edges", "adjoint", "loss")
+
+    def set_timing(self, on=True):
+        self._check(self.lib.fr_set_timing(self.ctx, 1 if on else 0), "fr_set_timing")
+
+    def timings(self) -> dict:
+        out = np.zeros(len(self.PHASES), np.float32)
+        self._check(self.lib.fr_get_timings(self.ctx, _hptr(out)), "fr_get_timings")
+        return dict(zip(self.PHASES, out.tolist()))
+
     def counters(self):
-        out = np.zeros(8, np.uint64)
+        out = np.zeros(16, np.uint64)
         self._check(self.lib.fr_get_counters(self.ctx, _hptr(out)), "fr_get_counters")
         return out
 

@@ -12,8 +12,13 @@ from __future__ import annotations
 # FLOPs per operation
 NODE_VISIT = 40        # two child slab tests: 6 sub, 6 mul, 10 min/max, 2 cmp each
 TRI_TEST = 40          # watertight test: 9 sub, 6 mul + 6 sub (shear), 9 edge-fn ops, 3+6 for T, div
-EDGE_NODE_VISIT = 80   # two child boxes against 5 pyramid planes (3 sub + 5 for a dot each)
-EDGE_TEST = 100        # 2 silhouette dots (16) + clip of 2 endpoints against 5 planes (~84)
+EDGE_NODE_VISIT = 200  # two children: box vs 5 pyramid planes (~55) + normal-cone test (~45) each
+EDGE_TEST = 110        # 2 silhouette tests (16) + clip of 2 endpoints against 5 planes (~94)
+
+# DRAM bytes of one k_bwd_sedge launch at 256x256x16 spp (ncu, full-size capture);
+# dram__bytes_read.sum + dram__bytes_write.sum, one 1-pass capture of the
+# current kernel (the working set is L2-resident: ~34 MB per 26 ms launch).
+SEDGE_TRAFFIC_BYTES = 33.75e6 + 0.70e6
 SHADE_FWD = 150        # one light sample shaded (BRDF + geometry term)
 SHADE_BWD = 420        # one light sample: forward recompute + adjoint
 N_LIGHTS = 20
@@ -27,8 +32,17 @@ def forward_flops(cnt, samples: int, n_on: int) -> float:
 
 
 def backward_flops(cnt, samples: int, n_on: int) -> float:
+    """All backward kernels: counters 4..15."""
     shading = samples * (N_LIGHTS * SHADE_BWD + 2 * n_on * SHADE_FWD)
-    return (cnt[4] * NODE_VISIT + cnt[5] * TRI_TEST + cnt[6] * EDGE_NODE_VISIT + cnt[7] * EDGE_TEST + shading)
+    trav = 0
+    for k in (4, 8, 12):
+        trav += cnt[k] * NODE_VISIT + cnt[k + 1] * TRI_TEST + cnt[k + 2] * EDGE_NODE_VISIT + cnt[k + 3] * EDGE_TEST
+    return trav + shading
+
+
+def sedge_flops(cnt) -> float:
+    """Shadow-edge kernel: counters 12..15 (its shadow rays, its edge search)."""
+    return cnt[12] * NODE_VISIT + cnt[13] * TRI_TEST + cnt[14] * EDGE_NODE_VISIT + cnt[15] * EDGE_TEST
 
 
 def fp32_peak_tflops(sm_mhz: float | None) -> float:
