@@ -125,8 +125,14 @@ int32_t fr_n_params(const fr_ctx* ctx);
  * device, overwritten with the mean over spp of the per-sample radiance:
  * one jittered camera ray per sample, one uniform point per light that is
  * on, a shadow ray for self-shadows, Cook-Torrance shading.  Lights with
- * l_j = 0 are skipped.  Returns FR_ERR_NOT_READY before both uploads. */
-int fr_render(fr_ctx* ctx, const float* theta, const fr_render_opts* opts, float* image);
+ * l_j = 0 are skipped.  aov[H*W*14] device or NULL: per-pixel denoiser
+ * features (means over the pixel's samples, misses counting as zero):
+ * 0-2 noisy RGB, 3-5 shading normal, 6-8 diffuse albedo, 9 specular albedo,
+ * 10 distance to the camera / d_cam, 11 fraction of the lit lights that are
+ * visible, 12 variance over samples of the luminance (r+g+b)/3, 13 fraction
+ * of samples that hit the face.  Returns FR_ERR_NOT_READY before both
+ * uploads. */
+int fr_render(fr_ctx* ctx, const float* theta, const fr_render_opts* opts, float* image, float* aov);
 
 /* Gradient of <d_image, image(theta)> with respect to theta (Face Modeling
  * paragraph: backpropagation through the differentiable ray tracer).  Uses
@@ -201,6 +207,34 @@ int fr_get_counters(fr_ctx* ctx, uint64_t* out);
  * synchronises the stream.  A phase not run since enabling reads 0. */
 int fr_set_timing(fr_ctx* ctx, int32_t enable);
 int fr_get_timings(fr_ctx* ctx, float* out);
+
+/* Per-pixel MLP denoiser (motivated by the Results and Conclusion paragraph:
+ * few samples give a noisy render, many samples a slow optimisation).
+ * y = rgb + cov s_out (W4 h3 + b4), h_l = relu(W_l h_{l-1} + b_l),
+ * h_0 = (t(x) - mu) * is, 14 -> 64 -> 64 -> 64 -> 3 over the fr_render
+ * features (t: feature 12 enters as its square root; mu, is, s_out fixed
+ * standardisation constants that training leaves unchanged; cov = feature
+ * 13, so pixels the face does not cover pass through); FP16 weights
+ * and activations on the tensor cores, FP32 accumulation.  Master weights
+ * are FP32, packed W1[64][14] b1[64] W2[64][64] b2[64] W3[64][64] b3[64]
+ * W4[3][64] b4[3] mu[14] is[14] s_out (fr_denoiser_n_weights() = 9504). */
+int32_t fr_denoiser_n_weights(void);
+/* Copy weights in (host w[n]); resets the Adam state.  Allocates the
+ * denoiser's buffers on first use. */
+int fr_denoiser_set_weights(fr_ctx* ctx, const float* w, int32_t n);
+int fr_denoiser_get_weights(fr_ctx* ctx, float* w, int32_t n);
+/* Inference on n_pix pixels: aov[n_pix*14] device features, out[n_pix*3]
+ * device.  With d_out[n_pix*3] (device, the adjoint of out), also writes
+ * d_rgb[n_pix*3] = J^T d_out, J = dy/d(noisy rgb), the image-space adjoint
+ * to hand to fr_render_backward (other features are held constant). */
+int fr_denoise(fr_ctx* ctx, const float* aov, int32_t n_pix, float* out, const float* d_out, float* d_rgb);
+/* One Adam step (lr, beta 0.9/0.999, eps 1e-8) on the mean over pixels of
+ * |y - target|^2; target[n_pix*3] device; loss: one FP64 device scalar
+ * (the loss before the step). */
+int fr_denoiser_train_step(fr_ctx* ctx, const float* aov, const float* target, int32_t n_pix, float lr,
+                           double* loss);
+/* Gradient of the last training step (host g[n]), for tests. */
+int fr_denoiser_get_grad(fr_ctx* ctx, float* g, int32_t n);
 
 /* Number of kernels this context has launched since it was created. */
 uint64_t fr_launch_count(const fr_ctx* ctx);

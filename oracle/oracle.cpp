@@ -544,11 +544,15 @@ double cspec_value(const Render& r, double u, double v) {
   return w[0] * C[idx[0]] + w[1] * C[idx[1]] + w[2] * C[idx[2]] + w[3] * C[idx[3]];
 }
 
+// Auxiliary per-sample features (denoiser inputs): shading normal, diffuse
+// albedo, specular albedo, distance / d_cam, fraction of lit lights visible.
+struct Aux { double n[3], rho[3], cs, depth, vis, hit; };
+
 // One-sample radiance along a camera ray (all lights that are on), using
 // light samples from stream `tag` keyed by (c0, c1).  Also returns a decision
-// signature.
+// signature and, optionally, the auxiliary features.
 V3<double> radiance(const Render& r, const float* o, const float* d, int tag, uint32_t c0, uint32_t c1,
-                    uint64_t* sig) {
+                    uint64_t* sig, Aux* aux = nullptr) {
   Hit h = closest_hit(r, o, d);
   if (sig) *sig = *sig * 1000003u + (uint64_t)(h.f + 1);
   if (h.f < 0) return V3<double>();
@@ -560,18 +564,30 @@ V3<double> radiance(const Render& r, const float* o, const float* d, int tag, ui
   double cs = cspec_value(r, S.u, S.v);
   V3<double> L;
   const double area = (double)r.cfg->light_side * (double)r.cfg->light_side;
+  int n_on = 0, n_vis = 0;
   for (int j = 0; j < r.NL; ++j) {
     if (!r.light_on(j)) continue;
+    ++n_on;
     U4 q = philox(r.cfg->seed, r.cfg->iter, c0, c1, (uint32_t)(tag << 8 | j), 0);
     float y32[3];
     light_point32(r.lights[j], r.cfg->light_side, unitf(q.v[0]), unitf(q.v[1]), y32);
     bool vis = visible(r, x32, y32, h.f, flip);
     if (sig) *sig = *sig * 31u + (vis ? 1u : 0u);
     if (!vis) continue;
+    ++n_vis;
     const float* l = r.lightrgb(j);
     V3<double> hv = light_integrand<double>(S.x, S.ns, S.wo, S.rho, cs, V3<double>(l[0], l[1], l[2]),
                                             widen(y32), widen(r.lights[j].dl), r.cfg->beckmann_m);
     L = L + hv * area;
+  }
+  if (aux) {
+    aux->n[0] = S.ns.x; aux->n[1] = S.ns.y; aux->n[2] = S.ns.z;
+    aux->rho[0] = S.rho.x; aux->rho[1] = S.rho.y; aux->rho[2] = S.rho.z;
+    aux->cs = cs;
+    V3<double> dd = widen(d);
+    aux->depth = (double)h.t * std::sqrt(dot(dd, dd)) / (double)r.cfg->d_cam;
+    aux->vis = n_on ? (double)n_vis / n_on : 0.0;
+    aux->hit = 1.0;
   }
   return L;
 }
@@ -1058,7 +1074,7 @@ int oracle_geometry(const OracleConfig* cfg, const OracleScene* sc, const float*
 // Forward render.  pix == NULL renders all W*H pixels into image[H*W*3];
 // otherwise the n_pix listed pixel indices (py*W+px) into image[n_pix*3].
 int oracle_render(const OracleConfig* cfg, const OracleScene* sc, const float* theta,
-                  const int32_t* pix, int32_t n_pix, double* image, uint64_t* signature) {
+                  const int32_t* pix, int32_t n_pix, double* image, uint64_t* signature, double* aov) {
   Render r(cfg, sc, theta);
   int rc = prepare(r);
   if (rc) return rc;
@@ -1069,14 +1085,30 @@ int oracle_render(const OracleConfig* cfg, const OracleScene* sc, const float* t
     int px = p % cfg->W, py = p / cfg->W;
     V3<double> acc;
     uint64_t sg = 0;
+    double f[15] = {0};   // feature sums: n, rho, cs, depth, vis, Y^2, hit, Y
     for (int s = 0; s < cfg->spp; ++s) {
       float d[3];
       uint32_t pp;
       sample_ray(r, px, py, s, d, &pp);
-      acc = acc + radiance(r, r.cam_o, d, TAG_LIGHT, pp, (uint32_t)s, &sg);
+      Aux ax{{0, 0, 0}, {0, 0, 0}, 0, 0, 0, 0};
+      V3<double> L = radiance(r, r.cam_o, d, TAG_LIGHT, pp, (uint32_t)s, &sg, aov ? &ax : nullptr);
+      acc = acc + L;
+      if (aov) {
+        double Y = (L.x + L.y + L.z) / 3.0;
+        for (int k = 0; k < 3; ++k) { f[3 + k] += ax.n[k]; f[6 + k] += ax.rho[k]; }
+        f[9] += ax.cs; f[10] += ax.depth; f[11] += ax.vis; f[12] += Y * Y; f[13] += ax.hit; f[14] += Y;
+      }
     }
     acc = acc / (double)cfg->spp;
     image[3 * i] = acc.x; image[3 * i + 1] = acc.y; image[3 * i + 2] = acc.z;
+    if (aov) {
+      double* o = aov + 14 * (size_t)i;
+      o[0] = acc.x; o[1] = acc.y; o[2] = acc.z;
+      for (int k = 3; k < 12; ++k) o[k] = f[k] / cfg->spp;
+      double mY = f[14] / cfg->spp;
+      o[12] = std::max(0.0, f[12] / cfg->spp - mY * mY);
+      o[13] = f[13] / cfg->spp;
+    }
     sig[i] = sg * 2654435761u + (uint64_t)p;
   });
   if (signature) {

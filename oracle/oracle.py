@@ -84,7 +84,7 @@ class Oracle:
         L.oracle_n_edges.argtypes = [vp, vp, vp, vp]
         L.oracle_light_stage.argtypes = [C.c_int32, C.c_float, vp]
         L.oracle_geometry.argtypes = [vp, vp, vp, vp, vp, vp, vp]
-        L.oracle_render.argtypes = [vp, vp, vp, vp, C.c_int32, vp, vp]
+        L.oracle_render.argtypes = [vp, vp, vp, vp, C.c_int32, vp, vp, vp]
         L.oracle_render_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.oracle_loss.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.c_float, C.c_float, vp, vp]
         L.oracle_loss.restype = C.c_double
@@ -142,7 +142,9 @@ class Oracle:
             raise RuntimeError(f"oracle_geometry failed: {n_sil}")
         return dict(X=X, X32=X32, albedo=A, normals=N, n_silhouette=n_sil)
 
-    def render(self, cfg, scene, theta, pixels=None, signature=False):
+    def render(self, cfg, scene, theta, pixels=None, signature=False, aov=False):
+        """Image [H, W, 3] (or [n_pix, 3]); optionally the decision signature and
+        the 14 denoiser features per pixel."""
         s = self._scene(scene)
         th = np.ascontiguousarray(theta, np.float32)
         if pixels is None:
@@ -153,10 +155,17 @@ class Oracle:
             img = np.zeros((len(pixels), 3))
             pp, n = _ptr(pixels), len(pixels)
         sig = np.zeros(1, np.uint64)
-        rc = self.lib.oracle_render(C.byref(cfg), C.byref(s), _ptr(th), pp, n, _ptr(img), _ptr(sig))
+        feats = np.zeros(img.shape[:-1] + (14,)) if aov else None
+        rc = self.lib.oracle_render(C.byref(cfg), C.byref(s), _ptr(th), pp, n, _ptr(img), _ptr(sig),
+                                    None if feats is None else _ptr(feats))
         if rc:
             raise RuntimeError(f"oracle_render failed: {rc}")
-        return (img, int(sig[0])) if signature else img
+        out = [img]
+        if signature:
+            out.append(int(sig[0]))
+        if aov:
+            out.append(feats)
+        return out[0] if len(out) == 1 else tuple(out)
 
     def render_backward(self, cfg, scene, theta, d_image, terms=False, dX=False, mass=False):
         """Gradient [P]; optionally the per-term parts [3, P], the per-vertex

@@ -221,6 +221,11 @@ struct fr_ctx {
   DBuf<float4> dX, dN, dA, gs;
   DBuf<float> dXm, dC, dL;
   DBuf<int2> hits;        // primary hit per tiled sample (backward)
+  DBuf<float> aov_scratch;  // mean luminance per pixel (feature output, atomic path)
+  // denoiser: FP32 master weights, Adam moments, gradients, training scratch
+  DBuf<float> mlp_w, mlp_m, mlp_v, mlp_g, mlp_scratch;
+  bool have_mlp = false;
+  int mlp_steps = 0;
   int n_params() const { return K_id + K_exp + K_alb + CS * CS + 6 + 3 * cfg.n_lights; }
   int off_cspec() const { return K_id + K_exp + K_alb; }
   int off_pose() const { return off_cspec() + CS * CS; }
@@ -421,6 +426,7 @@ RenderArgs render_args(fr_ctx* c, const float* theta, const fr_render_opts* o) {
   a.cspec = theta + c->off_cspec(); a.lights_dev = theta + c->off_lights();
   a.sil = c->sil.p; a.n_sil = c->n_sil.p; a.edges_canon = c->edges_canon.p;
   a.err = c->err_flag.p;
+  a.aov_scratch = nullptr;
   a.counters = c->counters_on ? c->counters.p : nullptr;
   return a;
 }
@@ -496,7 +502,8 @@ void fr_destroy(fr_ctx* ctx) {
   ctx->epack.free_();
   ctx->sil.free_(); ctx->n_sil.free_(); ctx->block_count.free_(); ctx->err_flag.free_(); ctx->counters.free_();
   ctx->dX.free_(); ctx->dN.free_(); ctx->dA.free_(); ctx->gs.free_(); ctx->dXm.free_(); ctx->dC.free_(); ctx->dL.free_();
-  ctx->hits.free_();
+  ctx->hits.free_(); ctx->aov_scratch.free_();
+  ctx->mlp_w.free_(); ctx->mlp_m.free_(); ctx->mlp_v.free_(); ctx->mlp_g.free_(); ctx->mlp_scratch.free_();
   if (ctx->events_made)
     for (int i = 0; i < NPHASE; ++i) { cudaEventDestroy(ctx->ev[i][0]); cudaEventDestroy(ctx->ev[i][1]); }
   delete ctx;
@@ -616,7 +623,7 @@ int fr_upload_bases(fr_ctx* ctx, const float* B_id, int32_t K_id, const float* B
 
 int32_t fr_n_params(const fr_ctx* ctx) { return ctx ? ctx->n_params() : FR_ERR_INVALID_ARG; }
 
-int fr_render(fr_ctx* ctx, const float* theta, const fr_render_opts* opts, float* image) {
+int fr_render(fr_ctx* ctx, const float* theta, const fr_render_opts* opts, float* image, float* aov) {
   if (!ctx) return FR_ERR_INVALID_ARG;
   int rc = check_opts(ctx, opts);
   if (rc) return rc;
@@ -627,11 +634,23 @@ int fr_render(fr_ctx* ctx, const float* theta, const fr_render_opts* opts, float
   RenderArgs a = render_args(ctx, theta, opts);
   if (ctx->counters_on) CK(cudaMemsetAsync(ctx->counters.p, 0, 4 * sizeof(unsigned long long), ctx->stream));
   bool shuffle = opts->spp <= 32 && (32 % opts->spp) == 0;
-  if (!shuffle) CK(cudaMemsetAsync(image, 0, sizeof(float) * 3 * (size_t)opts->W * opts->H, ctx->stream));
+  const size_t npix = (size_t)opts->W * opts->H;
+  if (!shuffle) CK(cudaMemsetAsync(image, 0, sizeof(float) * 3 * npix, ctx->stream));
+  if (aov && !shuffle) {
+    if (ctx->aov_scratch.n < npix) CK(ctx->aov_scratch.alloc(npix));
+    CK(cudaMemsetAsync(aov, 0, sizeof(float) * 14 * npix, ctx->stream));
+    CK(cudaMemsetAsync(ctx->aov_scratch.p, 0, sizeof(float) * npix, ctx->stream));
+    a.aov_scratch = ctx->aov_scratch.p;
+  }
   long long threads = (long long)(((opts->W + 7) / 8) * ((opts->H + 7) / 8)) * 64 * opts->spp;
   ctx->mark(PH_FORWARD, 0);
-  k_render_fwd<<<grid_for(threads, 256), 256, 0, ctx->stream>>>(a, image);
+  if (aov) k_render_fwd_aov<<<grid_for(threads, 256), 256, 0, ctx->stream>>>(a, image, aov);
+  else k_render_fwd<<<grid_for(threads, 256), 256, 0, ctx->stream>>>(a, image);
   CKL();
+  if (aov && !shuffle) {
+    k_aov_finish<<<grid_for((long long)npix, 256), 256, 0, ctx->stream>>>((int)npix, aov, ctx->aov_scratch.p);
+    CKL();
+  }
   ctx->mark(PH_FORWARD, 1);
   return FR_OK;
 }
@@ -797,6 +816,103 @@ int fr_get_timings(fr_ctx* ctx, float* ms) {
 }
 
 uint64_t fr_launch_count(const fr_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+// ---------------------------------------------------------------------------
+// Denoiser
+
+int32_t fr_denoiser_n_weights(void) { return mlp_n_weights(); }
+
+int fr_denoiser_set_weights(fr_ctx* ctx, const float* w, int32_t n) {
+  if (!ctx || !w) return FR_ERR_INVALID_ARG;
+  if (n != mlp_n_weights()) return fail(ctx, FR_ERR_SHAPE, "denoiser has %d weights, got %d", mlp_n_weights(), n);
+  CK(cudaSetDevice(ctx->device));
+  if (!ctx->have_mlp) {
+    CK(ctx->mlp_w.alloc(n)); CK(ctx->mlp_m.alloc(n)); CK(ctx->mlp_v.alloc(n)); CK(ctx->mlp_g.alloc(n));
+    static bool attr_done[64] = {false};
+    if (ctx->device < 64 && !attr_done[ctx->device]) {
+      CK(cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_smem_bytes()));
+      CK(cudaFuncSetAttribute(k_mlp_train_fwdbwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_smem_bytes()));
+      CK(cudaFuncSetAttribute(k_mlp_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 4));
+      attr_done[ctx->device] = true;
+    }
+  }
+  CK(cudaMemcpyAsync(ctx->mlp_w.p, w, sizeof(float) * n, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemsetAsync(ctx->mlp_m.p, 0, sizeof(float) * n, ctx->stream));
+  CK(cudaMemsetAsync(ctx->mlp_v.p, 0, sizeof(float) * n, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->have_mlp = true;
+  ctx->mlp_steps = 0;
+  return FR_OK;
+}
+
+int fr_denoiser_get_weights(fr_ctx* ctx, float* w, int32_t n) {
+  if (!ctx || !w) return FR_ERR_INVALID_ARG;
+  if (!ctx->have_mlp) return fail(ctx, FR_ERR_NOT_READY, "denoiser weights not set");
+  if (n != mlp_n_weights()) return fail(ctx, FR_ERR_SHAPE, "denoiser has %d weights, got %d", mlp_n_weights(), n);
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaMemcpyAsync(w, ctx->mlp_w.p, sizeof(float) * n, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FR_OK;
+}
+
+int fr_denoise(fr_ctx* ctx, const float* aov, int32_t n_pix, float* out, const float* d_out, float* d_rgb) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  if (!ctx->have_mlp) return fail(ctx, FR_ERR_NOT_READY, "denoiser weights not set");
+  if (!aov || !out || n_pix < 1 || (d_out && !d_rgb)) return fail(ctx, FR_ERR_INVALID_ARG, "fr_denoise arguments");
+  CK(cudaSetDevice(ctx->device));
+  int blocks = (n_pix + 127) / 128;
+  k_mlp_infer<<<blocks, 256, mlp_smem_bytes(), ctx->stream>>>(n_pix, ctx->mlp_w.p, aov, out, d_out, d_rgb);
+  CKL();
+  return FR_OK;
+}
+
+int fr_denoiser_train_step(fr_ctx* ctx, const float* aov, const float* target, int32_t n_pix, float lr,
+                           double* loss) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  if (!ctx->have_mlp) return fail(ctx, FR_ERR_NOT_READY, "denoiser weights not set");
+  if (!aov || !target || !loss || n_pix < 1 || !(lr > 0)) return fail(ctx, FR_ERR_INVALID_ARG, "train_step arguments");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  const int stride = mlp_train_stride();
+  if (ctx->mlp_scratch.n < (size_t)n_pix * stride) CK(ctx->mlp_scratch.alloc((size_t)n_pix * stride));
+  const int NW = mlp_n_weights();
+  CK(cudaMemsetAsync(ctx->mlp_g.p, 0, sizeof(float) * NW, s));
+  CK(cudaMemsetAsync(loss, 0, sizeof(double), s));
+  k_mlp_train_fwdbwd<<<(n_pix + 127) / 128, 128, mlp_smem_bytes(), s>>>(n_pix, ctx->mlp_w.p, aov, target,
+                                                                        ctx->mlp_scratch.p, loss);
+  CKL();
+  int off[8];
+  mlp_layer_offsets(off);
+  // scratch offsets: h0 0, h1 16, h2 80, h3 144, g1 208, g2 272, g3 336, g4 400
+  const int chunk = 128;
+  const int nb = (n_pix + chunk - 1) / chunk;
+  struct L { int g, h, N, K, Kw, w, b; } layers[4] = {
+      {208, 0, 64, 16, 14, off[0], off[1]}, {272, 16, 64, 64, 64, off[2], off[3]},
+      {336, 80, 64, 64, 64, off[4], off[5]}, {400, 144, 3, 64, 64, off[6], off[7]}};
+  for (const L& l : layers) {
+    size_t sm = sizeof(float) * chunk * (l.N + l.K);
+    k_mlp_wgrad<<<nb, 256, sm, s>>>(n_pix, ctx->mlp_scratch.p, l.g, l.h, l.N, l.K, l.Kw, ctx->mlp_g.p + l.w,
+                                    ctx->mlp_g.p + l.b, chunk);
+    CKL();
+  }
+  ctx->mlp_steps++;
+  const float b1 = 0.9f, b2 = 0.999f;
+  float c1 = 1.0f - std::pow(b1, (float)ctx->mlp_steps), c2 = 1.0f - std::pow(b2, (float)ctx->mlp_steps);
+  k_adam<<<(NW + 255) / 256, 256, 0, s>>>(NW, ctx->mlp_w.p, ctx->mlp_g.p, ctx->mlp_m.p, ctx->mlp_v.p, lr, b1, b2,
+                                          1e-8f, c1, c2);
+  CKL();
+  return FR_OK;
+}
+
+// Gradient of the last training step (for tests), host copy.
+int fr_denoiser_get_grad(fr_ctx* ctx, float* g, int32_t n) {
+  if (!ctx || !g) return FR_ERR_INVALID_ARG;
+  if (!ctx->have_mlp || n != mlp_n_weights()) return fail(ctx, FR_ERR_SHAPE, "denoiser gradient size");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaMemcpyAsync(g, ctx->mlp_g.p, sizeof(float) * n, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FR_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Geometry stage without device allocation.

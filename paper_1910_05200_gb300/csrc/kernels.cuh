@@ -81,6 +81,7 @@ struct RenderArgs {
   const int* n_sil;
   const int4* edges_canon;
   int* err;
+  float* aov_scratch;     // [W*H] mean luminance for the atomic AOV path
   unsigned long long* counters;  // [16] or null: 4 per kernel (fwd, interior, pedge, sedge)
 };
 
@@ -113,6 +114,8 @@ __global__ void k_basis_T(const float* __restrict__ BT, int K, int n, const floa
 __global__ void k_add_small(const float* __restrict__ src, int n, double* __restrict__ grad, int off);
 
 __global__ void k_render_fwd(RenderArgs a, float* __restrict__ image);
+__global__ void k_render_fwd_aov(RenderArgs a, float* __restrict__ image, float* __restrict__ aov);
+__global__ void k_aov_finish(int n_pix, float* __restrict__ aov, const float* __restrict__ meanY);
 __global__ void k_bwd_interior(RenderArgs a, GradBufs gb);
 __global__ void k_bwd_pedge(RenderArgs a, GradBufs gb);
 __global__ void k_bwd_sedge(RenderArgs a, GradBufs gb);
@@ -122,6 +125,21 @@ __global__ void k_loss_data(int n_pix, const float* __restrict__ image, const fl
 __global__ void k_loss_reg(const float* __restrict__ theta, int n_prior, int off_lights, int n_light_vals,
                            const float* __restrict__ m, float w1, float w2, double* __restrict__ loss,
                            double* __restrict__ grad);
+
+// denoiser (denoise.cu)
+__global__ void k_mlp_infer(int n_pix, const float* __restrict__ w, const float* __restrict__ aov,
+                            float* __restrict__ out, const float* __restrict__ d_out, float* __restrict__ d_rgb);
+__global__ void k_mlp_train_fwdbwd(int n_pix, const float* __restrict__ w, const float* __restrict__ aov,
+                                   const float* __restrict__ target, float* __restrict__ scratch,
+                                   double* __restrict__ loss);
+__global__ void k_mlp_wgrad(int n_pix, const float* __restrict__ scratch, int g_off, int h_off, int N, int K, int Kw,
+                            float* __restrict__ dW, float* __restrict__ db, int chunk);
+__global__ void k_adam(int n, float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2);
+int mlp_n_weights();
+size_t mlp_smem_bytes();
+int mlp_train_stride();
+void mlp_layer_offsets(int* off);
 
 // Pixel order: 8x8 tiles, row-major tiles; returns false for pixels outside the image.
 FR_DEV bool tile_pixel(int idx, int W, int H, int& px, int& py) {

@@ -60,8 +60,17 @@ FR_DEV bool light_on(const RenderArgs& a, int j) {
   return l.x != 0.0f || l.y != 0.0f || l.z != 0.0f;
 }
 
+// Per-sample auxiliary features for the denoiser (means over spp are taken
+// by the caller): shading normal, diffuse albedo, specular albedo, distance
+// to the camera / d_cam, fraction of lit lights that are visible, hit flag.
+struct SampleAux {
+  V3 n, rho;
+  float cs, depth, vis, hit;
+};
+
 // One-sample radiance along a camera ray, lights that are on only.
-FR_DEV V3 radiance(const RenderArgs& a, V3 o, V3 d, int tag, uint32_t c0, uint32_t c1, unsigned long long* cnt) {
+FR_DEV V3 radiance(const RenderArgs& a, V3 o, V3 d, int tag, uint32_t c0, uint32_t c1, unsigned long long* cnt,
+                   SampleAux* aux = nullptr) {
   float t;
   int f = closest_hit(a.mesh, o, d, t, a.err, cnt);
   if (f < 0) return V3{0, 0, 0};
@@ -73,13 +82,22 @@ FR_DEV V3 radiance(const RenderArgs& a, V3 o, V3 d, int tag, uint32_t c0, uint32
   float cs = cspec_lookup(a.cspec, S.u, S.v, idx, w, fu, fv);
   V3 L{0, 0, 0};
   const float area = a.side * a.side;
+  int n_on = 0, n_vis = 0;
   for (int j = 0; j < a.n_lights; ++j) {
     if (!light_on(a, j)) continue;
+    ++n_on;
     U4 q = philox(a.seed, a.iter, c0, c1, (uint32_t)(tag << 8 | j), 0);
     V3 y = light_point(a.lights[j], a.side, unitf(q.x), unitf(q.y));
     if (!visible(a.mesh, x32, y, f, flip, a.tmin, a.err, cnt)) continue;
+    ++n_vis;
     ShadeOut sh = shade_light(S, cs, light_rgb(a, j), y, a.lights[j].dl, a.m);
     L += sh.h * area;
+  }
+  if (aux) {
+    aux->n = S.ns; aux->rho = S.rho; aux->cs = cs;
+    aux->depth = t * len(d) / a.cam.dcam;
+    aux->vis = n_on ? (float)n_vis / (float)n_on : 0.0f;
+    aux->hit = 1.0f;
   }
   return L;
 }
@@ -93,7 +111,13 @@ FR_DEV V3 sample_dir(const RenderArgs& a, int px, int py, int s, uint32_t& pix) 
   return camera_dir(a.cam, sx, sy);
 }
 
-__global__ void __launch_bounds__(256) k_render_fwd(RenderArgs a, float* __restrict__ image) {
+// AOV = true also writes the denoiser features aov[14 * pixel + k]:
+// 0-2 noisy RGB, 3-5 shading normal, 6-8 diffuse albedo, 9 specular albedo,
+// 10 depth, 11 visible-light fraction, 12 variance over spp of the
+// luminance (r+g+b)/3, 13 coverage (fraction of samples that hit), all means
+// over the pixel's samples (misses count as zero).
+template <bool AOV>
+FR_DEV void render_fwd_body(const RenderArgs& a, float* __restrict__ image, float* __restrict__ aov) {
   const int spp = a.spp;
   long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   long long total = (long long)tiled_pixel_count(a.W, a.H) * spp;
@@ -101,27 +125,73 @@ __global__ void __launch_bounds__(256) k_render_fwd(RenderArgs a, float* __restr
   int px = 0, py = 0;
   bool valid = tid < total && tile_pixel(ip, a.W, a.H, px, py);
   unsigned long long* cnt = a.counters;      // forward: counters 0..3
-  V3 L{0, 0, 0};
+  constexpr int NV = AOV ? 15 : 3;           // RGB (+ 11 features + squared luminance)
+  float v[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = 0.0f;
   uint32_t pix = 0;
   if (valid) {
     V3 d = sample_dir(a, px, py, s, pix);
-    L = radiance(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt);
+    SampleAux aux{V3{0, 0, 0}, V3{0, 0, 0}, 0.0f, 0.0f, 0.0f, 0.0f};
+    V3 L = radiance(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt, AOV ? &aux : nullptr);
+    v[0] = L.x; v[1] = L.y; v[2] = L.z;
+    if (AOV) {
+      v[3] = aux.n.x; v[4] = aux.n.y; v[5] = aux.n.z;
+      v[6] = aux.rho.x; v[7] = aux.rho.y; v[8] = aux.rho.z;
+      v[9] = aux.cs; v[10] = aux.depth; v[11] = aux.vis;
+      float Y = (L.x + L.y + L.z) * (1.0f / 3.0f);
+      v[12] = Y * Y;
+      v[13] = aux.hit;
+      v[14] = Y;
+    }
   }
   const float inv = 1.0f / (float)spp;
-  if (spp <= 32 && (32 % spp) == 0) {
+  bool shuffle = spp <= 32 && (32 % spp) == 0;
+  if (shuffle) {
     for (int off = spp >> 1; off > 0; off >>= 1) {
-      L.x += __shfl_xor_sync(0xffffffffu, L.x, off);
-      L.y += __shfl_xor_sync(0xffffffffu, L.y, off);
-      L.z += __shfl_xor_sync(0xffffffffu, L.z, off);
+#pragma unroll
+      for (int k = 0; k < NV; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
     }
-    if (valid && s == 0) {
-      image[3 * pix] = L.x * inv; image[3 * pix + 1] = L.y * inv; image[3 * pix + 2] = L.z * inv;
+    if (!(valid && s == 0)) return;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) image[3 * pix + k] = v[k] * inv;
+    if (AOV) {
+      float* o = aov + 14 * (size_t)pix;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) o[k] = v[k] * inv;
+      float mY = v[14] * inv;
+      o[12] = fmaxf(0.0f, v[12] * inv - mY * mY);
+      o[13] = v[13] * inv;
     }
   } else if (valid) {
-    atomicAdd(&image[3 * pix], L.x * inv);
-    atomicAdd(&image[3 * pix + 1], L.y * inv);
-    atomicAdd(&image[3 * pix + 2], L.z * inv);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) atomicAdd(&image[3 * pix + k], v[k] * inv);
+    if (AOV) {
+      // the caller finishes the variance (aux[12] holds E[Y^2], scratch E[Y]) in k_aov_finish
+      float* o = aov + 14 * (size_t)pix;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) atomicAdd(&o[k], v[k] * inv);
+      atomicAdd(&o[12], v[12] * inv);
+      atomicAdd(&o[13], v[13] * inv);
+      atomicAdd(&a.aov_scratch[pix], v[14] * inv);
+    }
   }
+}
+
+__global__ void __launch_bounds__(256) k_render_fwd(RenderArgs a, float* __restrict__ image) {
+  render_fwd_body<false>(a, image, nullptr);
+}
+__global__ void __launch_bounds__(256) k_render_fwd_aov(RenderArgs a, float* __restrict__ image,
+                                                        float* __restrict__ aov) {
+  render_fwd_body<true>(a, image, aov);
+}
+
+// Variance of the luminance for the atomic path: E[Y^2] - E[Y]^2.
+__global__ void k_aov_finish(int n_pix, float* __restrict__ aov, const float* __restrict__ meanY) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_pix) return;
+  float m = meanY[p];
+  aov[14 * (size_t)p + 12] = fmaxf(0.0f, aov[14 * (size_t)p + 12] - m * m);
 }
 
 // ---------------------------------------------------------------------------

@@ -35,7 +35,8 @@ class FrRenderOpts(C.Structure):
 EXPORTS = ["fr_default_config", "fr_create", "fr_destroy", "fr_set_stream", "fr_last_error", "fr_strerror",
            "fr_upload_mesh", "fr_upload_bases", "fr_n_params", "fr_render", "fr_render_backward", "fr_loss",
            "fr_geometry", "fr_geometry_noalloc", "fr_vertex_grad", "fr_light_stage", "fr_sync", "fr_set_counters", "fr_get_counters", "fr_set_timing", "fr_get_timings",
-           "fr_launch_count"]
+           "fr_launch_count", "fr_denoiser_n_weights", "fr_denoiser_set_weights", "fr_denoiser_get_weights",
+           "fr_denoise", "fr_denoiser_train_step", "fr_denoiser_get_grad"]
 
 
 def lib_path() -> str:
@@ -65,7 +66,7 @@ def load(path: str | None = None):
     L.fr_upload_mesh.argtypes = [vp, vp, i32, vp, i32, vp]
     L.fr_upload_bases.argtypes = [vp, vp, i32, vp, i32, vp, vp, i32]
     L.fr_n_params.argtypes = [vp]
-    L.fr_render.argtypes = [vp, vp, vp, vp]
+    L.fr_render.argtypes = [vp, vp, vp, vp, vp]
     L.fr_render_backward.argtypes = [vp, vp, vp, vp, vp, i32]
     L.fr_loss.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, f32, f32, vp, vp, vp]
     L.fr_geometry.argtypes = [vp, vp, vp, vp, vp]
@@ -79,6 +80,12 @@ def load(path: str | None = None):
     L.fr_get_timings.argtypes = [vp, vp]
     L.fr_launch_count.argtypes = [vp]
     L.fr_launch_count.restype = C.c_uint64
+    L.fr_denoiser_n_weights.argtypes = []
+    L.fr_denoiser_set_weights.argtypes = [vp, vp, i32]
+    L.fr_denoiser_get_weights.argtypes = [vp, vp, i32]
+    L.fr_denoise.argtypes = [vp, vp, i32, vp, vp, vp]
+    L.fr_denoiser_train_step.argtypes = [vp, vp, vp, i32, f32, vp]
+    L.fr_denoiser_get_grad.argtypes = [vp, vp, i32]
     _LIB = L
     return L
 
@@ -158,13 +165,17 @@ class Renderer:
         assert theta.numel() == self.P, (theta.numel(), self.P)
         return theta
 
-    def render(self, theta, W, H, spp, seed=0, iter=0, out=None):
+    def render(self, theta, W, H, spp, seed=0, iter=0, out=None, aov=None):
+        """Render; with aov (an [H, W, 14] float32 tensor, or True to allocate
+        one) also writes the per-pixel denoiser features and returns (image, aov)."""
         theta = self._theta(theta)
         img = out if out is not None else torch.empty((H, W, 3), device=self.device, dtype=torch.float32)
+        if aov is True:
+            aov = torch.empty((H, W, 14), device=self.device, dtype=torch.float32)
         o = self.opts(W, H, spp, seed, iter)
         self._stream()
-        self._check(self.lib.fr_render(self.ctx, _ptr(theta), C.byref(o), _ptr(img)), "fr_render")
-        return img
+        self._check(self.lib.fr_render(self.ctx, _ptr(theta), C.byref(o), _ptr(img), _ptr(aov)), "fr_render")
+        return img if aov is None else (img, aov)
 
     def backward(self, theta, d_image, W, H, spp, seed=0, iter=0, terms=0, grad=None, accumulate=False):
         theta = self._theta(theta)
@@ -211,6 +222,42 @@ class Renderer:
 
     def set_counters(self, on=True):
         self.lib.fr_set_counters(self.ctx, 1 if on else 0)
+
+    # -- denoiser -----------------------------------------------------------------
+    def set_denoiser(self, w):
+        w = np.ascontiguousarray(w, np.float32)
+        self._check(self.lib.fr_denoiser_set_weights(self.ctx, _hptr(w), w.size), "fr_denoiser_set_weights")
+
+    def denoiser_weights(self):
+        w = np.zeros(self.lib.fr_denoiser_n_weights(), np.float32)
+        self._check(self.lib.fr_denoiser_get_weights(self.ctx, _hptr(w), w.size), "fr_denoiser_get_weights")
+        return w
+
+    def denoiser_grad(self):
+        g = np.zeros(self.lib.fr_denoiser_n_weights(), np.float32)
+        self._check(self.lib.fr_denoiser_get_grad(self.ctx, _hptr(g), g.size), "fr_denoiser_get_grad")
+        return g
+
+    def denoise(self, aov, d_out=None):
+        """aov [..., 14] -> denoised RGB [..., 3]; with d_out also returns J^T d_out."""
+        aov = aov.contiguous()
+        n = aov.numel() // 14
+        out = torch.empty(aov.shape[:-1] + (3,), device=self.device, dtype=torch.float32)
+        d_rgb = None if d_out is None else torch.empty_like(out)
+        self._stream()
+        self._check(self.lib.fr_denoise(self.ctx, _ptr(aov), n, _ptr(out),
+                                        _ptr(None if d_out is None else d_out.contiguous()), _ptr(d_rgb)),
+                    "fr_denoise")
+        return out if d_out is None else (out, d_rgb)
+
+    def denoiser_train_step(self, aov, target, lr):
+        aov = aov.contiguous()
+        target = target.contiguous()
+        loss = torch.empty(1, device=self.device, dtype=torch.float64)
+        self._stream()
+        self._check(self.lib.fr_denoiser_train_step(self.ctx, _ptr(aov), _ptr(target), aov.numel() // 14,
+                                                    float(lr), _ptr(loss)), "fr_denoiser_train_step")
+        return loss
 
     def launches(self) -> int:
         return int(self.lib.fr_launch_count(self.ctx))
