@@ -111,6 +111,18 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def aggregate(t_step_ms: float, samples_per_rank: int, world: int, device=None):
+    """Whole-job throughput of replicas: the slowest rank's step time (max over
+    ranks) and the samples of all ranks.  Returns (t_step_ms, Msamples/s)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([t_step_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step_ms = float(t.item())
+    return t_step_ms, world * samples_per_rank / (t_step_ms * 1e-3) / 1e6
+
+
 def workload():
     from paper_1910_05200_gb300 import synthetic as S
     scene, theta, c = S.make_workload("full", seed=1)
@@ -247,13 +259,8 @@ def run_ours(args):
     r.sync()
     ms = [a.elapsed_time(b) for a, b in ev]
     ph_mean = {k: float(np.mean([p[k] for p in phases])) for k in phases[0]}
-    t_step = float(np.mean(ms))
-    if world > 1:
-        t = torch.tensor([t_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_step = float(t.item())
     samples = W * H * spp
-    value = world * samples / (t_step * 1e-3) / 1e6
+    t_step, value = aggregate(float(np.mean(ms)), samples, world, dev)
 
     # --- end to end through the public API, host buffers ---------------------
     th_h = torch.tensor(theta).pin_memory()

@@ -236,6 +236,15 @@ int fr_denoiser_train_step(fr_ctx* ctx, const float* aov, const float* target, i
 /* Gradient of the last training step (host g[n]), for tests. */
 int fr_denoiser_get_grad(fr_ctx* ctx, float* g, int32_t n);
 
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected with step >= 1)
+ * on theta[P] (FP32, device) from grad[P] (FP64, device), with moment
+ * buffers m[P], v[P] (FP32, device, zero before the first step) and
+ * per-parameter learning rates lr[P] (FP32, device; 0 freezes a parameter,
+ * which is how the staged schedule of the Optimization paragraph selects
+ * the groups it optimises).  Afterwards lights are clamped to >= 0 and
+ * specular texels to [0, 1]. */
+int fr_adam_step(fr_ctx* ctx, float* theta, const double* grad, float* m, float* v, const float* lr, int32_t step);
+
 /* Number of kernels this context has launched since it was created. */
 uint64_t fr_launch_count(const fr_ctx* ctx);
 

@@ -897,9 +897,23 @@ int fr_denoiser_train_step(fr_ctx* ctx, const float* aov, const float* target, i
   }
   ctx->mlp_steps++;
   const float b1 = 0.9f, b2 = 0.999f;
-  float c1 = 1.0f - std::pow(b1, (float)ctx->mlp_steps), c2 = 1.0f - std::pow(b2, (float)ctx->mlp_steps);
+  float c1 = (float)(1.0 - std::pow((double)b1, (double)ctx->mlp_steps));
+  float c2 = (float)(1.0 - std::pow((double)b2, (double)ctx->mlp_steps));
   k_adam<<<(NW + 255) / 256, 256, 0, s>>>(NW, ctx->mlp_w.p, ctx->mlp_g.p, ctx->mlp_m.p, ctx->mlp_v.p, lr, b1, b2,
                                           1e-8f, c1, c2);
+  CKL();
+  return FR_OK;
+}
+
+int fr_adam_step(fr_ctx* ctx, float* theta, const double* grad, float* m, float* v, const float* lr, int32_t step) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  if (!ctx->have_bases) return fail(ctx, FR_ERR_NOT_READY, "bases not uploaded");
+  if (!theta || !grad || !m || !v || !lr || step < 1) return fail(ctx, FR_ERR_INVALID_ARG, "fr_adam_step arguments");
+  CK(cudaSetDevice(ctx->device));
+  const int P = ctx->n_params();
+  float c1 = (float)(1.0 - std::pow(0.9, (double)step)), c2 = (float)(1.0 - std::pow(0.999, (double)step));
+  k_adam_theta<<<(P + 255) / 256, 256, 0, ctx->stream>>>(P, theta, grad, m, v, lr, c1, c2, ctx->off_cspec(), CS * CS,
+                                                         ctx->off_lights());
   CKL();
   return FR_OK;
 }

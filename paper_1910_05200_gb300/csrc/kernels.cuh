@@ -136,6 +136,9 @@ __global__ void k_mlp_wgrad(int n_pix, const float* __restrict__ scratch, int g_
                             float* __restrict__ dW, float* __restrict__ db, int chunk);
 __global__ void k_adam(int n, float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
                        float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2);
+__global__ void k_adam_theta(int n, float* __restrict__ theta, const double* __restrict__ grad,
+                             float* __restrict__ m, float* __restrict__ v, const float* __restrict__ lr, float c1,
+                             float c2, int off_cspec, int n_cspec, int off_lights);
 int mlp_n_weights();
 size_t mlp_smem_bytes();
 int mlp_train_stride();

@@ -163,6 +163,7 @@ def run(quick=False, device=0):
         xs = sorted(t_plain)
         return float(np.interp(spp, xs, [t_plain[x] for x in xs]))
 
+    r.weights_trained = r.denoiser_weights()
     out = {
         "workload": f"full face, {W}x{H}, {c['n_on']} of 20 lights on (fixed), train {n_train} faces, "
                     f"test {n_test} faces",
@@ -177,11 +178,17 @@ def run(quick=False, device=0):
         "speedup_at_equal_gradient_error": t_at(eq_grad) / t_den,
         "reaches_1024spp_image_error": e_den_img <= e_img.get(1024, float("nan")),
     }
+    out["_weights"] = r.weights_trained
     return out
 
 
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--quick", action="store_true")
+    ap.add_argument("--save-weights", default="")
     a = ap.parse_args()
-    print(json.dumps(run(a.quick), indent=1))
+    res = run(a.quick)
+    w = res.pop("_weights")
+    if a.save_weights:
+        np.save(a.save_weights, w)
+    print(json.dumps(res, indent=1))

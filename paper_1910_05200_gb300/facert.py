@@ -36,7 +36,7 @@ EXPORTS = ["fr_default_config", "fr_create", "fr_destroy", "fr_set_stream", "fr_
            "fr_upload_mesh", "fr_upload_bases", "fr_n_params", "fr_render", "fr_render_backward", "fr_loss",
            "fr_geometry", "fr_geometry_noalloc", "fr_vertex_grad", "fr_light_stage", "fr_sync", "fr_set_counters", "fr_get_counters", "fr_set_timing", "fr_get_timings",
            "fr_launch_count", "fr_denoiser_n_weights", "fr_denoiser_set_weights", "fr_denoiser_get_weights",
-           "fr_denoise", "fr_denoiser_train_step", "fr_denoiser_get_grad"]
+           "fr_denoise", "fr_denoiser_train_step", "fr_denoiser_get_grad", "fr_adam_step"]
 
 
 def lib_path() -> str:
@@ -86,6 +86,7 @@ def load(path: str | None = None):
     L.fr_denoise.argtypes = [vp, vp, i32, vp, vp, vp]
     L.fr_denoiser_train_step.argtypes = [vp, vp, vp, i32, f32, vp]
     L.fr_denoiser_get_grad.argtypes = [vp, vp, i32]
+    L.fr_adam_step.argtypes = [vp, vp, vp, vp, vp, vp, i32]
     _LIB = L
     return L
 
@@ -258,6 +259,12 @@ class Renderer:
         self._check(self.lib.fr_denoiser_train_step(self.ctx, _ptr(aov), _ptr(target), aov.numel() // 14,
                                                     float(lr), _ptr(loss)), "fr_denoiser_train_step")
         return loss
+
+    def adam_step(self, theta, grad, m, v, lr, step):
+        """In-place Adam step on theta (see fr_adam_step)."""
+        self._stream()
+        self._check(self.lib.fr_adam_step(self.ctx, _ptr(theta), _ptr(grad), _ptr(m), _ptr(v), _ptr(lr), int(step)),
+                    "fr_adam_step")
 
     def launches(self) -> int:
         return int(self.lib.fr_launch_count(self.ctx))
