@@ -320,7 +320,7 @@ FR_DEV void hit_adjoint(const RenderArgs& a, int f, V3 d, const Surf& S, V3 g_x,
   atomic_add3(dX + t.z, lam * S.b2);
 }
 
-__global__ void __launch_bounds__(256) k_bwd_interior(RenderArgs a, GradBufs gb) {
+__global__ void __launch_bounds__(256, 3) k_bwd_interior(RenderArgs a, GradBufs gb) {
   __shared__ float sC[CS * CS];
   __shared__ float sL[3 * MAX_LIGHTS];
   for (int i = threadIdx.x; i < CS * CS; i += blockDim.x) sC[i] = 0.0f;
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(256) k_bwd_interior(RenderArgs a, GradBufs gb)
 // ---------------------------------------------------------------------------
 // Primary-visibility edges
 
-__global__ void __launch_bounds__(256) k_bwd_pedge(RenderArgs a, GradBufs gb) {
+__global__ void __launch_bounds__(256, 4) k_bwd_pedge(RenderArgs a, GradBufs gb) {
   long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   long long total = (long long)a.W * a.H * a.spp;
   if (tid >= total) return;
@@ -585,6 +585,31 @@ FR_DEV Pick pick_light(const RenderArgs& a, V3 x, int hitf, int j, uint32_t pix,
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       if (code[c] == EMPTY_CHILD) continue;
+      float4 cn = a.ebvh.cones[2 * node + c];
+      if (cn.w < PI_F) {
+        // Every face normal below lies within th = cn.w of the axis and every
+        // point in the bounding sphere (cb, rb), seen from x, within beta of
+        // the direction to the centre.  With psi the angle between the axis
+        // and x - cb and T = th + margin: psi + beta + T < pi/2 (all faces
+        // face x) or psi - beta - T > pi/2 (all face away) rules out any
+        // silhouette below.  In sines and cosines, when beta + T < pi/2:
+        // cos psi > sin(beta + T) or cos psi < -sin(beta + T).
+        V3 cb = (lo[c] + hi[c]) * 0.5f;
+        float rb = len((hi[c] - lo[c]) * 0.5f) * 1.0001f + 1e-6f;
+        V3 v = x - cb;
+        float dv2 = dot(v, v);
+        if (dv2 > rb * rb) {
+          float idv = rsqrtf(dv2);
+          float sb = rb * idv, cb2 = sqrtf(fmaxf(0.0f, 1.0f - sb * sb));
+          float sT, cT;
+          __sincosf(cn.w + 2e-3f, &sT, &cT);
+          if (cb2 * cT - sb * sT > 0.0f) {
+            float S = sb * cT + cb2 * sT;
+            float cpsi = dot(v, v3(cn)) * idv;
+            if (cpsi > S || cpsi < -S) continue;
+          }
+        }
+      }
       V3 pp{L.dl.x > 0 ? hi[c].x : lo[c].x, L.dl.y > 0 ? hi[c].y : lo[c].y, L.dl.z > 0 ? hi[c].z : lo[c].z};
       bool keep = dot(pp - x, L.dl) >= a.kappa - 1e-4f;
 #pragma unroll
@@ -594,23 +619,6 @@ FR_DEV Pick pick_light(const RenderArgs& a, V3 x, int hitf, int j, uint32_t pix,
         keep = keep && dot(n, p - x) >= -pm[k];
       }
       if (!keep) continue;
-      float4 cn = a.ebvh.cones[2 * node + c];
-      if (cn.w < PI_F) {
-        // every face normal below lies within cn.w of the axis and every point
-        // in the bounding sphere (cb, rb): psi + beta + th < pi/2 means all
-        // faces face x, psi - beta - th > pi/2 means all face away
-        V3 cb = (lo[c] + hi[c]) * 0.5f;
-        float rb = len((hi[c] - lo[c]) * 0.5f) * 1.0001f + 1e-6f;
-        V3 v = x - cb;
-        float dv2 = dot(v, v);
-        if (dv2 > rb * rb) {
-          float idv = rsqrtf(dv2);
-          float psi = acosf(fminf(1.0f, fmaxf(-1.0f, dot(v, v3(cn)) * idv)));
-          float beta = asinf(fminf(1.0f, rb * idv));
-          const float half_pi = 1.57079632679f, margin = 2e-3f;
-          if (psi + beta + cn.w < half_pi - margin || psi - beta - cn.w > half_pi + margin) continue;
-        }
-      }
       todo[nt++] = code[c];
     }
     int next = -1;
@@ -648,6 +656,138 @@ FR_DEV Pick pick_light(const RenderArgs& a, V3 x, int hitf, int j, uint32_t pix,
   }
 done:
   if (cnt) { atomicAdd(cnt + 2, nvis); atomicAdd(cnt + 3, nedge); }
+  return P;
+}
+
+// Warp-cooperative version of pick_light: the 32 lanes of a warp share one
+// light and (light-major launch) neighbouring shading points, so the warp
+// walks the edge BVH once with tests that hold for every point of the
+// group's bounding sphere (centre rc, radius rr): the pyramid from any x in
+// the sphere lies in the pyramid from rc dilated by rr, and a face seen from
+// any x in the sphere is judged with the node's sphere grown by rr.  Control
+// flow is uniform across the warp; each lane with a valid shading point runs
+// the exact leaf test (decision form) on its own x.  Lanes without one
+// (valid = false) still take part in the walk.
+FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int j, uint32_t pix, int s,
+                            unsigned long long* cnt) {
+  const Light& L = a.lights[j];
+  const float hs = __fmul_rn(0.5f, a.side);
+  Pick P;
+  P.n = 0; P.id = -1; P.slot = -1;
+  uint32_t bestkey = 0xffffffffu;
+  // group bounding box -> sphere
+  V3 lo_x = valid ? x : V3{3e38f, 3e38f, 3e38f};
+  V3 hi_x = valid ? x : V3{-3e38f, -3e38f, -3e38f};
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    lo_x.x = fminf(lo_x.x, __shfl_xor_sync(0xffffffffu, lo_x.x, off));
+    lo_x.y = fminf(lo_x.y, __shfl_xor_sync(0xffffffffu, lo_x.y, off));
+    lo_x.z = fminf(lo_x.z, __shfl_xor_sync(0xffffffffu, lo_x.z, off));
+    hi_x.x = fmaxf(hi_x.x, __shfl_xor_sync(0xffffffffu, hi_x.x, off));
+    hi_x.y = fmaxf(hi_x.y, __shfl_xor_sync(0xffffffffu, hi_x.y, off));
+    hi_x.z = fmaxf(hi_x.z, __shfl_xor_sync(0xffffffffu, hi_x.z, off));
+  }
+  if (!(lo_x.x <= hi_x.x) || a.ebvh.bvh.n_nodes == 0) return P;   // no valid lane
+  const V3 rc = (lo_x + hi_x) * 0.5f;
+  const float rr = len((hi_x - lo_x) * 0.5f) * 1.0001f + 1e-6f;
+  V3 Q[4];
+  const float sg[4][2] = {{-1, -1}, {1, -1}, {1, 1}, {-1, 1}};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) Q[k] = L.c + L.e1 * (sg[k][0] * hs) + L.e2 * (sg[k][1] * hs);
+  V3 pn[4];
+  float pm[4];
+  V3 cx = L.c - rc;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    V3 n = cross(Q[k] - rc, Q[(k + 1) & 3] - rc);
+    if (dot(n, cx) < 0.0f) n = -n;
+    float ln = len(n);
+    pn[k] = n;
+    pm[k] = (1e-4f + rr) * ln;     // margin + dilation by the group radius
+  }
+  int stack[STACK];
+  int sp = 0, node = 0, steps = 0;
+  unsigned long long nvis = 0, nedge = 0;
+  while (true) {
+    if (++steps > MAX_STEPS) { atomicOr(a.err, ERR_STEPS); break; }
+    ++nvis;
+    const float4* N = a.ebvh.bvh.nodes + 4 * node;
+    float4 b0 = N[0], b1 = N[1], b2 = N[2];
+    int4 ch = *reinterpret_cast<const int4*>(N + 3);
+    V3 lo[2] = {V3{b0.x, b0.y, b0.z}, V3{b1.z, b1.w, b2.x}};
+    V3 hi[2] = {V3{b0.w, b1.x, b1.y}, V3{b2.y, b2.z, b2.w}};
+    int code[2] = {ch.x, ch.y};
+    int todo[2];
+    int nt = 0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      if (code[c] == EMPTY_CHILD) continue;
+      float4 cn = a.ebvh.cones[2 * node + c];
+      if (cn.w < PI_F) {
+        V3 cb = (lo[c] + hi[c]) * 0.5f;
+        float rb = len((hi[c] - lo[c]) * 0.5f) * 1.0001f + 1e-6f + rr;
+        V3 v = rc - cb;
+        float dv2 = dot(v, v);
+        if (dv2 > rb * rb) {
+          float idv = rsqrtf(dv2);
+          float sb = rb * idv, cb2 = sqrtf(fmaxf(0.0f, 1.0f - sb * sb));
+          float sT, cT;
+          __sincosf(cn.w + 2e-3f, &sT, &cT);
+          if (cb2 * cT - sb * sT > 0.0f) {
+            float S = sb * cT + cb2 * sT;
+            float cpsi = dot(v, v3(cn)) * idv;
+            if (cpsi > S || cpsi < -S) continue;
+          }
+        }
+      }
+      V3 pp{L.dl.x > 0 ? hi[c].x : lo[c].x, L.dl.y > 0 ? hi[c].y : lo[c].y, L.dl.z > 0 ? hi[c].z : lo[c].z};
+      bool keep = dot(pp - rc, L.dl) >= a.kappa - 1e-4f - rr;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        V3 n = pn[k];
+        V3 p{n.x > 0 ? hi[c].x : lo[c].x, n.y > 0 ? hi[c].y : lo[c].y, n.z > 0 ? hi[c].z : lo[c].z};
+        keep = keep && dot(n, p - rc) >= -pm[k];
+      }
+      if (!keep) continue;
+      todo[nt++] = code[c];
+    }
+    int next = -1;
+    for (int k = 0; k < nt; ++k) {
+      int c2 = todo[k];
+      if (leaf_child(c2)) {
+        int first = leaf_first(c2), n = leaf_count(c2);
+        for (int i = 0; i < n; ++i) {
+          if (!valid) continue;
+          const float4* R = a.ebvh.pack + 6 * (first + i);
+          float4 r1 = R[1], r2 = R[2];
+          int f0 = __float_as_int(r1.w), f1 = __float_as_int(r2.w);
+          ++nedge;
+          if (f0 == hitf || f1 == hitf) continue;
+          if (!packed_silhouette(R, x, f1)) continue;
+          float4 r0 = R[0];
+          float t0, t1;
+          if (!shadow_clip(v3(r0), v3(r1), x, L, hs, a.kappa, t0, t1)) continue;
+          int id = __float_as_int(r0.w);
+          uint32_t key = philox(a.seed, a.iter, pix, (uint32_t)s, (uint32_t)(TAG_SEDGE_PICK << 8 | j), (uint32_t)id).x;
+          ++P.n;
+          if (P.id < 0 || key < bestkey || (key == bestkey && id < P.id)) {
+            bestkey = key; P.id = id; P.slot = first + i;
+          }
+        }
+      } else if (next < 0) {
+        next = c2;
+      } else {
+        if (sp >= STACK) { atomicOr(a.err, ERR_STACK); goto done; }
+        stack[sp++] = c2;
+      }
+    }
+    if (next >= 0) { node = next; continue; }
+    if (sp == 0) break;
+    node = stack[--sp];
+  }
+done:
+  if (cnt && (threadIdx.x & 31) == 0) { atomicAdd(cnt + 2, nvis); }
+  if (cnt) atomicAdd(cnt + 3, nedge);
   return P;
 }
 
@@ -725,29 +865,35 @@ FR_DEV void sedge_contribution(const RenderArgs& a, const GradBufs& gb, int j, i
 // and neighbouring samples, so traversals stay coherent, and warps of lights
 // that are off retire at once.  The primary hit comes from the interior pass
 // of the same backward call (gb.hits).
-__global__ void __launch_bounds__(256) k_bwd_sedge(RenderArgs a, GradBufs gb) {
+__global__ void __launch_bounds__(256, 4) k_bwd_sedge(RenderArgs a, GradBufs gb) {
   const int j = blockIdx.y;
-  if (!light_on(a, j)) return;
+  if (!light_on(a, j)) return;                 // uniform over the block
   const int spp = a.spp;
   long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   long long total = (long long)tiled_pixel_count(a.W, a.H) * spp;
-  if (tid >= total) return;
-  int2 hit = gb.hits[tid];
+  // every lane reaches the warp-cooperative pick; lanes without a shading point
+  // take part with valid = false
+  bool valid = tid < total;
+  int2 hit = valid ? gb.hits[tid] : make_int2(-1, 0);
   int f = hit.x;
-  if (f < 0) return;
+  valid = valid && f >= 0;
   int ip = (int)(tid / spp), s = (int)(tid - (long long)ip * spp);
   int px = 0, py = 0;
-  tile_pixel(ip, a.W, a.H, px, py);
-  uint32_t pix;
-  V3 d = sample_dir(a, px, py, s, pix);
-  const float* dI = gb.d_image + 3 * (size_t)pix;
-  V3 wrgb = V3{dI[0], dI[1], dI[2]} * (1.0f / (float)spp);
+  uint32_t pix = 0;
+  V3 d{0, 0, -1}, x32{0, 0, 0}, wrgb{0, 0, 0};
+  int flip = 1;
+  if (valid) {
+    tile_pixel(ip, a.W, a.H, px, py);
+    d = sample_dir(a, px, py, s, pix);
+    const float* dI = gb.d_image + 3 * (size_t)pix;
+    wrgb = V3{dI[0], dI[1], dI[2]} * (1.0f / (float)spp);
+    float t = __int_as_float(hit.y);
+    flip = face_flip(a.mesh, f, d);
+    x32 = hit_point(a.cam.o, d, t);
+  }
   unsigned long long* cnt = a.counters ? a.counters + 12 : nullptr;   // shadow edges: 12..15
-  float t = __int_as_float(hit.y);
-  int flip = face_flip(a.mesh, f, d);
-  V3 x32 = hit_point(a.cam.o, d, t);
-  Pick P = pick_light(a, x32, f, j, pix, s, cnt);
-  if (P.n == 0) return;
+  Pick P = pick_light_warp(a, valid, x32, f, j, pix, s, cnt);
+  if (!valid || P.n == 0) return;
   sedge_contribution(a, gb, j, P.n, P.slot, d, x32, f, flip, pix, s, wrgb, cnt);
 }
 

@@ -15,10 +15,14 @@ TRI_TEST = 40          # watertight test: 9 sub, 6 mul + 6 sub (shear), 9 edge-f
 EDGE_NODE_VISIT = 200  # two children: box vs 5 pyramid planes (~55) + normal-cone test (~45) each
 EDGE_TEST = 110        # 2 silhouette tests (16) + clip of 2 endpoints against 5 planes (~94)
 
-# DRAM bytes of one k_bwd_sedge launch at 256x256x16 spp (ncu, full-size capture);
-# dram__bytes_read.sum + dram__bytes_write.sum, one 1-pass capture of the
-# current kernel (the working set is L2-resident: ~34 MB per 26 ms launch).
-SEDGE_TRAFFIC_BYTES = 33.75e6 + 0.70e6
+# Counting in k_bwd_sedge: the edge-BVH descent is shared by the 32 lanes of
+# a warp (one traversal of the warp's bounding sphere), so an edge-BVH visit
+# is counted once per warp; edge tests are per lane.
+
+# DRAM bytes of one k_bwd_sedge launch at 256x256x16 spp from a 1-pass ncu
+# capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum);
+# None until the kernel as it stands has been captured.
+SEDGE_TRAFFIC_BYTES = None
 SHADE_FWD = 150        # one light sample shaded (BRDF + geometry term)
 SHADE_BWD = 420        # one light sample: forward recompute + adjoint
 N_LIGHTS = 20
