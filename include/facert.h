@@ -245,8 +245,103 @@ int fr_denoiser_get_grad(fr_ctx* ctx, float* g, int32_t n);
  * specular texels to [0, 1]. */
 int fr_adam_step(fr_ctx* ctx, float* theta, const double* grad, float* m, float* v, const float* lr, int32_t step);
 
-/* Number of kernels this context has launched since it was created. */
+/* Number of kernels this context has launched since it was created (a
+ * replayed batch graph counts its kernel nodes on every replay). */
 uint64_t fr_launch_count(const fr_ctx* ctx);
+
+/* ---------------------------------------------------------------------------
+ * Batched frames.  Several frames of one face (a video, or crops of uneven
+ * size) fitted together: Eq. 1 of the Optimization paragraph summed over
+ * frames, with identity alpha, albedo delta and specular map c_spec shared
+ * and expression beta, pose and lights per frame.  One step renders every
+ * frame, takes the loss and its gradient with respect to all parameters:
+ *   loss = sum_f E_data,f + w1 (|alpha|^2 + |delta|^2 + sum_f |beta_f|^2)
+ *          + w2 sum_f sum_j |l_fj - m_j|^2.
+ * The paper fits single images; batching is this library's extension (the
+ * per-frame arithmetic is that of fr_render / fr_loss / fr_render_backward,
+ * with the same samples for equal (seed, iter)).
+ *
+ * A step is one CUDA graph: per-frame geometry and refits, the render +
+ * loss + backward of all frames (three launches over all frames, or one
+ * persistent launch: fr_tile_config), and the per-frame geometry adjoints.
+ * The launch configuration comes from fr_batch_autotune or
+ * fr_batch_set_config.
+ *
+ * Layouts (all device, FP32 unless stated):
+ *   theta_shared[Ps] = alpha[K_id] | delta[K_alb] | c_spec[32*32],
+ *   theta_frames[F][Pf] = beta[K_exp] | pose[6] | lights[3N],
+ *   Ps = fr_batch_n_shared(ctx), Pf = fr_batch_n_frame(ctx);
+ *   images, targets: the frames' H_f x W_f x 3 images one after another in
+ *   frame order (frame f starts at pixel sum_{g<f} W_g H_g);
+ *   masks: the same packing of H_f x W_f uint8.
+ * ------------------------------------------------------------------------- */
+typedef struct fr_batch fr_batch;
+
+/* One frame: crop size and the seed of its samples. */
+typedef struct fr_frame {
+  int32_t W, H;
+  uint32_t seed;
+} fr_frame;
+
+/* Launch configuration of a step's render + loss + backward.
+ *   fused = 0 (phased, the default): three launches, each over all frames
+ *     in frame order -- forward + loss + interior adjoint, shadow edges
+ *     (light-major within a frame), primary edges; blocks of 256 threads;
+ *     min_blocks 3 or 4 is the register budget of the shadow-edge kernel
+ *     (65536 / (256 * min_blocks) registers per thread); tile_w, tile_h and
+ *     block are ignored (8x8 tiles).  Needs spp dividing 32.
+ *   fused = 1: one persistent launch whose warps take work items from a
+ *     queue: tiles of tile_w x tile_h pixels (sides 1..64) that run forward,
+ *     loss, interior and shadow-edge terms together, then chunks of
+ *     primary-edge samples; block threads (a multiple of 32 up to 256);
+ *     min_blocks 2, 3 or 4 is the kernel's register budget.
+ * ms is the time of one step measured by fr_batch_autotune (0 otherwise). */
+typedef struct fr_tile_config {
+  int32_t tile_w, tile_h, block, min_blocks, fused;
+  float ms;
+} fr_tile_config;
+
+int32_t fr_batch_n_shared(const fr_ctx* ctx);
+int32_t fr_batch_n_frame(const fr_ctx* ctx);
+
+/* Create a batch of n_frames frames (frames: host array) at spp samples per
+ * pixel on a context with mesh and bases uploaded.  Allocates every buffer
+ * the steps use (about 30 MB per frame for a 35,709-vertex mesh plus the
+ * images).  *out receives the batch; it must be destroyed before its
+ * context.  FR_ERR_INVALID_ARG for n_frames < 1, a frame with W, H < 1,
+ * more than 2^31 - 1 samples in a frame, or spp that neither divides 32 nor
+ * is a multiple of 32. */
+int fr_batch_create(fr_ctx* ctx, const fr_frame* frames, int32_t n_frames, int32_t spp, fr_batch** out);
+void fr_batch_destroy(fr_batch* b);
+
+/* Targets (packed images), masks (packed uint8, or NULL for all pixels) and
+ * the light prior m[3N] (or NULL for zero): copied into the batch (device to
+ * device, on the context stream) and used by every later step. */
+int fr_batch_set_targets(fr_batch* b, const float* targets, const uint8_t* masks, const float* m);
+
+/* One step for parameters (theta_shared, theta_frames) and sample stream
+ * iter.  Outputs (device, each may be NULL): loss (one FP64), grad_shared[Ps]
+ * and grad_frames[F][Pf] (FP64, overwritten), images (packed, FP32).
+ * Enqueued on the context stream; the first step with a configuration or
+ * weights (w1, w2) not seen before captures the graph.  A device-side
+ * traversal limit or a primary-edge wait that expired is reported by the
+ * next fr_sync (FR_ERR_DEVICE_LIMIT). */
+int fr_batch_step(fr_batch* b, const float* theta_shared, const float* theta_frames, float w1, float w2,
+                  uint32_t iter, double* loss, double* grad_shared, double* grad_frames, float* images);
+
+/* Autotuner: time one step (mean of `reps` graph replays after one warm-up
+ * replay, CUDA events on the context stream) for every candidate launch
+ * configuration that fits the device and the batch, keep the fastest, and
+ * return the table (host, up to cap entries; *n_out receives the count).
+ * Candidates: phased with min_blocks 3 and 4; fused with tiles 2x2 and 4x4,
+ * blocks of 256 and min_blocks 2 and 4.  Results do not depend on the
+ * configuration beyond the order of floating-point atomic additions (and,
+ * for spp a multiple of 32, the order of the pixel sums). */
+int fr_batch_autotune(fr_batch* b, const float* theta_shared, const float* theta_frames, int32_t reps,
+                      fr_tile_config* table, int32_t cap, int32_t* n_out);
+int fr_batch_get_config(const fr_batch* b, fr_tile_config* out);
+/* Set the configuration by hand (FR_ERR_INVALID_ARG if it does not fit). */
+int fr_batch_set_config(fr_batch* b, const fr_tile_config* cfg);
 
 #ifdef __cplusplus
 }

@@ -13,8 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfacert.so")
-SOURCES = ["geometry.cu", "render.cu", "loss.cu", "denoise.cu", "optim.cu", "capi.cu"]
-HEADERS = ["common.cuh", "kernels.cuh"]
+SOURCES = ["geometry.cu", "render.cu", "batch.cu", "loss.cu", "denoise.cu", "optim.cu", "capi.cu", "batch_api.cu"]
+HEADERS = ["common.cuh", "kernels.cuh", "render_device.cuh", "context.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-rdc=false",
               "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]

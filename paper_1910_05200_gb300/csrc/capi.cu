@@ -12,27 +12,11 @@
 #include <string>
 #include <vector>
 
-#include "../../include/facert.h"
-#include "kernels.cuh"
+#include "context.cuh"
 
 using namespace fr;
 
 namespace {
-
-// ---------------------------------------------------------------------------
-// Device buffer owned by the context.
-template <class T> struct DBuf {
-  T* p = nullptr;
-  size_t n = 0;
-  void free_() { if (p) cudaFree(p); p = nullptr; n = 0; }
-  cudaError_t alloc(size_t count) {
-    free_();
-    if (count == 0) return cudaSuccess;
-    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
-    if (e == cudaSuccess) n = count;
-    return e;
-  }
-};
 
 // Binary BVH in the device layout of common.cuh plus the refit topology.
 struct HostBVH {
@@ -173,66 +157,9 @@ struct Builder {
   }
 };
 
-struct DevBVH {
-  DBuf<float4> nodes, cones;
-  DBuf<int> leaf_first, leaf_count, leaf_parent, leaf_slot, node_parent, node_slot, counter;
-  int n_nodes = 0, n_leaves = 0;
-};
-
 }  // namespace
 
-constexpr int NCOUNT = 16;   // work counters: 4 per render kernel
-constexpr int NPHASE = 7;    // timed phases
-enum { PH_GEOMETRY = 0, PH_FORWARD, PH_INTERIOR, PH_PEDGE, PH_SEDGE, PH_ADJOINT, PH_LOSS };
-
-struct fr_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  fr_config cfg;
-  std::string err;
-  std::vector<Light> lights;
-  // mesh
-  int V = 0, F = 0, E = 0;
-  bool have_mesh = false, have_bases = false;
-  DBuf<float> mean, uv;
-  DBuf<int4> tris, edges_canon, edges_leaf;
-  DBuf<int> vf_off, vf_idx, tri_perm, edge_id_leaf;
-  DevBVH tbvh, ebvh;
-  // bases
-  int K_id = 0, K_exp = 0, K_alb = 0;
-  DBuf<float> BidT, BexpT, alb_mean, BalbT;
-  // per-render state
-  DBuf<float4> X, Xm, alb, nrm, ng, tv, epack;
-  DBuf<int> sil, n_sil, block_count, err_flag;
-  DBuf<unsigned long long> counters;
-  bool counters_on = false;
-  uint64_t launches = 0;
-  // per-phase timing (fr_set_timing): geometry, forward, interior, primary
-  // edges, shadow edges, adjoint, loss
-  bool timing_on = false, events_made = false;
-  cudaEvent_t ev[NPHASE][2];
-  bool phase_used[NPHASE] = {false};
-  void mark(int phase, int end) {
-    if (!timing_on) return;
-    cudaEventRecord(ev[phase][end], stream);
-    if (end) phase_used[phase] = true;
-  }
-  // gradient accumulators
-  DBuf<float4> dX, dN, dA, gs;
-  DBuf<float> dXm, dC, dL;
-  DBuf<int2> hits;        // primary hit per tiled sample (backward)
-  DBuf<float> aov_scratch;  // mean luminance per pixel (feature output, atomic path)
-  // denoiser: FP32 master weights, Adam moments, gradients, training scratch
-  DBuf<float> mlp_w, mlp_m, mlp_v, mlp_g, mlp_scratch;
-  bool have_mlp = false;
-  int mlp_steps = 0;
-  int n_params() const { return K_id + K_exp + K_alb + CS * CS + 6 + 3 * cfg.n_lights; }
-  int off_cspec() const { return K_id + K_exp + K_alb; }
-  int off_pose() const { return off_cspec() + CS * CS; }
-  int off_lights() const { return off_pose() + 6; }
-};
-
-namespace {
+namespace fr {
 
 int fail(fr_ctx* c, int code, const char* fmt, ...) {
   char buf[512];
@@ -244,21 +171,9 @@ int fail(fr_ctx* c, int code, const char* fmt, ...) {
   return code;
 }
 
-#define CK(call)                                                                              \
-  do {                                                                                        \
-    cudaError_t e_ = (call);                                                                  \
-    if (e_ != cudaSuccess)                                                                    \
-      return fail(ctx, e_ == cudaErrorMemoryAllocation ? FR_ERR_OOM : FR_ERR_CUDA, "%s: %s (%s:%d)", \
-                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                          \
-  } while (0)
+}  // namespace fr
 
-#define CKL()                                                                                 \
-  do {                                                                                        \
-    ++ctx->launches;                                                                          \
-    cudaError_t e_ = cudaGetLastError();                                                      \
-    if (e_ != cudaSuccess)                                                                    \
-      return fail(ctx, FR_ERR_CUDA, "kernel launch: %s (%s:%d)", cudaGetErrorString(e_), __FILE__, __LINE__); \
-  } while (0)
+namespace {
 
 template <class T> cudaError_t upload(DBuf<T>& b, const T* h, size_t n, cudaStream_t s) {
   cudaError_t e = b.alloc(n);
@@ -305,12 +220,28 @@ int upload_bvh(fr_ctx* ctx, const HostBVH& h, DevBVH& d) {
   return FR_OK;
 }
 
-GeoArgs geo_args(fr_ctx* c) {
+}  // namespace
+
+namespace fr {
+
+FrameView main_view(fr_ctx* c) {
+  FrameView v;
+  v.X = c->X.p; v.Xm = c->Xm.p; v.alb = c->alb.p; v.nrm = c->nrm.p; v.ng = c->ng.p; v.tv = c->tv.p;
+  v.epack = c->epack.p;
+  v.tnodes = c->tbvh.nodes.p; v.tcones = c->tbvh.cones.p; v.tcounter = c->tbvh.counter.p;
+  v.enodes = c->ebvh.nodes.p; v.econes = c->ebvh.cones.p; v.ecounter = c->ebvh.counter.p;
+  v.sil = c->sil.p; v.n_sil = c->n_sil.p; v.block_count = c->block_count.p;
+  v.dX = c->dX.p; v.dN = c->dN.p; v.dA = c->dA.p; v.gs = c->gs.p;
+  v.dXm = c->dXm.p; v.dC = c->dC.p; v.dL = c->dL.p;
+  return v;
+}
+
+GeoArgs geo_args(fr_ctx* c, const FrameView& v) {
   GeoArgs g;
   g.V = c->V; g.F = c->F; g.K_id = c->K_id; g.K_exp = c->K_exp; g.K_alb = c->K_alb; g.off_pose = c->off_pose();
   g.mean = c->mean.p; g.BidT = c->BidT.p; g.BexpT = c->BexpT.p; g.alb_mean = c->alb_mean.p; g.BalbT = c->BalbT.p;
   g.tris = c->tris.p; g.tri_perm = c->tri_perm.p; g.vf_off = c->vf_off.p; g.vf_idx = c->vf_idx.p;
-  g.X = c->X.p; g.Xm = c->Xm.p; g.alb = c->alb.p; g.nrm = c->nrm.p; g.ng = c->ng.p; g.tv = c->tv.p;
+  g.X = v.X; g.Xm = v.Xm; g.alb = v.alb; g.nrm = v.nrm; g.ng = v.ng; g.tv = v.tv;
   return g;
 }
 
@@ -324,26 +255,28 @@ Cam make_cam(const fr_ctx* c, int W, int H) {
   return cam;
 }
 
-int refit(fr_ctx* ctx, DevBVH& b, bool is_edge) {
+// Bottom-up refit of one BVH's boxes (topology b, boxes in nodes / cones).
+static int refit(fr_ctx* ctx, const DevBVH& b, float4* nodes, float4* cones, int* counter, bool is_edge,
+                 const FrameView& v) {
   if (b.n_leaves == 0) return FR_OK;
-  CK(cudaMemsetAsync(b.counter.p, 0, sizeof(int) * b.n_nodes, ctx->stream));
+  CK(cudaMemsetAsync(counter, 0, sizeof(int) * b.n_nodes, ctx->stream));
   RefitArgs r;
   r.n_leaves = b.n_leaves;
   r.leaf_first = b.leaf_first.p; r.leaf_count = b.leaf_count.p; r.leaf_parent = b.leaf_parent.p;
   r.leaf_slot = b.leaf_slot.p; r.node_parent = b.node_parent.p; r.node_slot = b.node_slot.p;
-  r.counter = b.counter.p; r.nodes = b.nodes.p; r.is_edge = is_edge ? 1 : 0;
-  r.tv = ctx->tv.p; r.edges = ctx->edges_leaf.p; r.X = ctx->X.p;
-  r.pack = ctx->epack.p; r.cones = b.cones.p;
+  r.counter = counter; r.nodes = nodes; r.is_edge = is_edge ? 1 : 0;
+  r.tv = v.tv; r.edges = ctx->edges_leaf.p; r.X = v.X;
+  r.pack = v.epack; r.cones = cones;
   k_refit<<<(b.n_leaves + 255) / 256, 256, 0, ctx->stream>>>(r);
   CKL();
   return FR_OK;
 }
 
-// Geometry, normals and refits for theta.
-int prepare_geometry(fr_ctx* ctx, const float* theta) {
+// Geometry, normals, packed edges and refits for theta.
+int prepare_geometry(fr_ctx* ctx, const float* theta, const FrameView& v) {
   if (!ctx->have_mesh || !ctx->have_bases) return fail(ctx, FR_ERR_NOT_READY, "mesh and bases must be uploaded first");
   if (!theta) return fail(ctx, FR_ERR_INVALID_ARG, "theta is null");
-  GeoArgs g = geo_args(ctx);
+  GeoArgs g = geo_args(ctx, v);
   cudaStream_t s = ctx->stream;
   k_geometry<<<(ctx->V + 127) / 128, 128, 0, s>>>(g, theta);
   CKL();
@@ -352,21 +285,21 @@ int prepare_geometry(fr_ctx* ctx, const float* theta) {
   k_vertex_normals<<<(ctx->V + 255) / 256, 256, 0, s>>>(g);
   CKL();
   k_pack_edges<<<(ctx->E + 255) / 256, 256, 0, s>>>(ctx->E, ctx->edges_leaf.p, ctx->edge_id_leaf.p, ctx->tris.p,
-                                                     ctx->X.p, ctx->ng.p, ctx->epack.p);
+                                                     v.X, v.ng, v.epack);
   CKL();
-  int rc = refit(ctx, ctx->tbvh, false);
+  int rc = refit(ctx, ctx->tbvh, v.tnodes, v.tcones, v.tcounter, false, v);
   if (rc) return rc;
-  return refit(ctx, ctx->ebvh, true);
+  return refit(ctx, ctx->ebvh, v.enodes, v.econes, v.ecounter, true, v);
 }
 
 // Order-preserving list of camera-silhouette edges; block_count is the
 // compaction's scratch (one int per 256 edges).
-int silhouettes(fr_ctx* ctx, int* block_count) {
+int silhouettes(fr_ctx* ctx, const FrameView& v) {
   cudaStream_t s = ctx->stream;
   SilArgs sa;
-  sa.E = ctx->E; sa.edges = ctx->edges_canon.p; sa.tris = ctx->tris.p; sa.ng = ctx->ng.p; sa.X = ctx->X.p;
+  sa.E = ctx->E; sa.edges = ctx->edges_canon.p; sa.tris = ctx->tris.p; sa.ng = v.ng; sa.X = v.X;
   sa.cam_o = V3{0.0f, 0.0f, ctx->cfg.d_cam};
-  sa.block_count = block_count; sa.sil = ctx->sil.p; sa.n_sil = ctx->n_sil.p;
+  sa.block_count = v.block_count; sa.sil = v.sil; sa.n_sil = v.n_sil;
   int nb = (ctx->E + 255) / 256;
   k_silhouette_flags<<<nb, 256, 0, s>>>(sa);
   CKL();
@@ -377,13 +310,66 @@ int silhouettes(fr_ctx* ctx, int* block_count) {
   return FR_OK;
 }
 
-// Geometry, normals, refits and camera silhouettes for theta.
+RenderArgs render_args(fr_ctx* c, const float* theta, const fr_render_opts* o, const FrameView& v) {
+  RenderArgs a;
+  a.W = o->W; a.H = o->H; a.spp = o->spp; a.seed = o->seed; a.iter = o->iter;
+  a.n_lights = c->cfg.n_lights;
+  a.side = c->cfg.light_side; a.m = c->cfg.beckmann_m; a.eps_pedge = c->cfg.eps_pedge;
+  a.eps_sedge = c->cfg.eps_sedge; a.tmin = c->cfg.shadow_tmin; a.kappa = c->cfg.clip_kappa;
+  a.cam = make_cam(c, o->W, o->H);
+  for (int j = 0; j < c->cfg.n_lights; ++j) a.lights[j] = c->lights[j];
+  a.mesh.X = v.X; a.mesh.ng = v.ng; a.mesh.tris = c->tris.p; a.mesh.tv = v.tv;
+  a.mesh.bvh.nodes = v.tnodes; a.mesh.bvh.n_nodes = c->tbvh.n_nodes;
+  a.ebvh.bvh.nodes = v.enodes; a.ebvh.bvh.n_nodes = c->ebvh.n_nodes;
+  a.ebvh.edges = c->edges_leaf.p; a.ebvh.edge_id = c->edge_id_leaf.p;
+  a.ebvh.pack = v.epack; a.ebvh.verts = c->edges_leaf.p; a.ebvh.cones = v.econes;
+  a.nrm = v.nrm; a.alb = v.alb; a.uv = reinterpret_cast<const float2*>(c->uv.p);
+  a.cspec = theta + c->off_cspec(); a.lights_dev = theta + c->off_lights();
+  a.sil = v.sil; a.n_sil = v.n_sil; a.edges_canon = c->edges_canon.p;
+  a.err = c->err_flag.p;
+  a.aov_scratch = nullptr;
+  a.counters = c->counters_on ? c->counters.p : nullptr;
+  return a;
+}
+
+int adjoint(fr_ctx* ctx, const float* theta, const FrameView& v, double* grad, bool with_alb) {
+  cudaStream_t s = ctx->stream;
+  const int V = ctx->V;
+  GeoArgs g = geo_args(ctx, v);
+  k_normals_bwd_vertex<<<(V + 255) / 256, 256, 0, s>>>(g, v.dN, v.gs);
+  CKL();
+  k_normals_bwd_gather<<<(V + 255) / 256, 256, 0, s>>>(g, v.gs, v.dX);
+  CKL();
+  k_pose_bwd<<<152, 256, 0, s>>>(g, theta, v.dX, v.dXm, grad);
+  CKL();
+  const int n3 = 3 * V;
+  if (ctx->K_id) { k_basis_T<<<ctx->K_id, 256, 0, s>>>(ctx->BidT.p, ctx->K_id, n3, v.dXm, nullptr, grad, 0); CKL(); }
+  if (ctx->K_exp) { k_basis_T<<<ctx->K_exp, 256, 0, s>>>(ctx->BexpT.p, ctx->K_exp, n3, v.dXm, nullptr, grad, ctx->K_id); CKL(); }
+  if (ctx->K_alb && with_alb) {
+    k_basis_T<<<ctx->K_alb, 256, 0, s>>>(ctx->BalbT.p, ctx->K_alb, n3, nullptr, v.dA, grad, ctx->K_id + ctx->K_exp);
+    CKL();
+  }
+  if (v.dC) {
+    k_add_small<<<(CS * CS + 255) / 256, 256, 0, s>>>(v.dC, CS * CS, grad, ctx->off_cspec());
+    CKL();
+  }
+  k_add_small<<<1, 128, 0, s>>>(v.dL, 3 * ctx->cfg.n_lights, grad, ctx->off_lights());
+  CKL();
+  return FR_OK;
+}
+
+}  // namespace fr
+
+namespace {
+
+// Geometry, normals, refits and camera silhouettes for theta (context buffers).
 int prepare(fr_ctx* ctx, const float* theta, int W, int H) {
   ctx->mark(PH_GEOMETRY, 0);
-  int rc = prepare_geometry(ctx, theta);
+  FrameView v = main_view(ctx);
+  int rc = prepare_geometry(ctx, theta, v);
   if (rc) return rc;
   (void)W; (void)H;
-  rc = silhouettes(ctx, ctx->block_count.p);
+  rc = silhouettes(ctx, v);
   ctx->mark(PH_GEOMETRY, 1);
   return rc;
 }
@@ -408,30 +394,6 @@ int check_opts(fr_ctx* ctx, const fr_render_opts* o) {
     return fail(ctx, FR_ERR_INVALID_ARG, "image or sample count too large");
   return FR_OK;
 }
-
-RenderArgs render_args(fr_ctx* c, const float* theta, const fr_render_opts* o) {
-  RenderArgs a;
-  a.W = o->W; a.H = o->H; a.spp = o->spp; a.seed = o->seed; a.iter = o->iter;
-  a.n_lights = c->cfg.n_lights;
-  a.side = c->cfg.light_side; a.m = c->cfg.beckmann_m; a.eps_pedge = c->cfg.eps_pedge;
-  a.eps_sedge = c->cfg.eps_sedge; a.tmin = c->cfg.shadow_tmin; a.kappa = c->cfg.clip_kappa;
-  a.cam = make_cam(c, o->W, o->H);
-  for (int j = 0; j < c->cfg.n_lights; ++j) a.lights[j] = c->lights[j];
-  a.mesh.X = c->X.p; a.mesh.ng = c->ng.p; a.mesh.tris = c->tris.p; a.mesh.tv = c->tv.p;
-  a.mesh.bvh.nodes = c->tbvh.nodes.p; a.mesh.bvh.n_nodes = c->tbvh.n_nodes;
-  a.ebvh.bvh.nodes = c->ebvh.nodes.p; a.ebvh.bvh.n_nodes = c->ebvh.n_nodes;
-  a.ebvh.edges = c->edges_leaf.p; a.ebvh.edge_id = c->edge_id_leaf.p;
-  a.ebvh.pack = c->epack.p; a.ebvh.verts = c->edges_leaf.p; a.ebvh.cones = c->ebvh.cones.p;
-  a.nrm = c->nrm.p; a.alb = c->alb.p; a.uv = reinterpret_cast<const float2*>(c->uv.p);
-  a.cspec = theta + c->off_cspec(); a.lights_dev = theta + c->off_lights();
-  a.sil = c->sil.p; a.n_sil = c->n_sil.p; a.edges_canon = c->edges_canon.p;
-  a.err = c->err_flag.p;
-  a.aov_scratch = nullptr;
-  a.counters = c->counters_on ? c->counters.p : nullptr;
-  return a;
-}
-
-unsigned grid_for(long long threads, int block) { return (unsigned)((threads + block - 1) / block); }
 
 }  // namespace
 
@@ -631,7 +593,7 @@ int fr_render(fr_ctx* ctx, const float* theta, const fr_render_opts* opts, float
   CK(cudaSetDevice(ctx->device));
   rc = prepare(ctx, theta, opts->W, opts->H);
   if (rc) return rc;
-  RenderArgs a = render_args(ctx, theta, opts);
+  RenderArgs a = render_args(ctx, theta, opts, main_view(ctx));
   if (ctx->counters_on) CK(cudaMemsetAsync(ctx->counters.p, 0, 4 * sizeof(unsigned long long), ctx->stream));
   bool shuffle = opts->spp <= 32 && (32 % opts->spp) == 0;
   const size_t npix = (size_t)opts->W * opts->H;
@@ -673,7 +635,7 @@ int fr_render_backward(fr_ctx* ctx, const float* theta, const fr_render_opts* op
   CK(cudaMemsetAsync(ctx->dC.p, 0, sizeof(float) * CS * CS, s));
   CK(cudaMemsetAsync(ctx->dL.p, 0, sizeof(float) * 3 * MAX_LIGHTS, s));
   if (ctx->counters_on) CK(cudaMemsetAsync(ctx->counters.p + 4, 0, 12 * sizeof(unsigned long long), s));
-  RenderArgs a = render_args(ctx, theta, opts);
+  RenderArgs a = render_args(ctx, theta, opts, main_view(ctx));
   const int terms = opts->terms ? opts->terms : (TERM_INTERIOR | TERM_PEDGE | TERM_SEDGE);
   long long tiled = (long long)(((opts->W + 7) / 8) * ((opts->H + 7) / 8)) * 64 * opts->spp;
   if ((terms & TERM_SEDGE) && ctx->hits.n < (size_t)tiled) CK(ctx->hits.alloc(tiled));
@@ -704,24 +666,8 @@ int fr_render_backward(fr_ctx* ctx, const float* theta, const fr_render_opts* op
     ctx->mark(PH_SEDGE, 1);
   }
   ctx->mark(PH_ADJOINT, 0);
-  GeoArgs g = geo_args(ctx);
-  k_normals_bwd_vertex<<<(V + 255) / 256, 256, 0, s>>>(g, ctx->dN.p, ctx->gs.p);
-  CKL();
-  k_normals_bwd_gather<<<(V + 255) / 256, 256, 0, s>>>(g, ctx->gs.p, ctx->dX.p);
-  CKL();
-  k_pose_bwd<<<152, 256, 0, s>>>(g, theta, ctx->dX.p, ctx->dXm.p, grad);
-  CKL();
-  const int n3 = 3 * V;
-  if (ctx->K_id) { k_basis_T<<<ctx->K_id, 256, 0, s>>>(ctx->BidT.p, ctx->K_id, n3, ctx->dXm.p, nullptr, grad, 0); CKL(); }
-  if (ctx->K_exp) { k_basis_T<<<ctx->K_exp, 256, 0, s>>>(ctx->BexpT.p, ctx->K_exp, n3, ctx->dXm.p, nullptr, grad, ctx->K_id); CKL(); }
-  if (ctx->K_alb) {
-    k_basis_T<<<ctx->K_alb, 256, 0, s>>>(ctx->BalbT.p, ctx->K_alb, n3, nullptr, ctx->dA.p, grad, ctx->K_id + ctx->K_exp);
-    CKL();
-  }
-  k_add_small<<<(CS * CS + 255) / 256, 256, 0, s>>>(ctx->dC.p, CS * CS, grad, ctx->off_cspec());
-  CKL();
-  k_add_small<<<1, 128, 0, s>>>(ctx->dL.p, 3 * ctx->cfg.n_lights, grad, ctx->off_lights());
-  CKL();
+  rc = adjoint(ctx, theta, main_view(ctx), grad, true);
+  if (rc) return rc;
   ctx->mark(PH_ADJOINT, 1);
   return FR_OK;
 }
@@ -980,9 +926,11 @@ int fr_geometry_noalloc(fr_ctx* ctx, const float* theta, float* X, float* N, flo
   int* scratch = nullptr;
   int rc = noalloc_scratch(ctx, &scratch);
   if (rc) return rc;
-  rc = prepare_geometry(ctx, theta);
+  FrameView v = main_view(ctx);
+  rc = prepare_geometry(ctx, theta, v);
   if (rc) return rc;
-  rc = silhouettes(ctx, scratch);
+  v.block_count = scratch;
+  rc = silhouettes(ctx, v);
   if (rc) return rc;
   return geometry_outputs(ctx, X, N, A);
 }

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #define FR_DEV __device__ __forceinline__
+#define FR_HOST_DEV __host__ __device__
 
 namespace fr {
 
@@ -25,7 +26,7 @@ constexpr float PI_F = 3.14159265358979323846f;
 enum { TAG_CAMERA = 0, TAG_LIGHT = 1, TAG_PEDGE = 2, TAG_PEDGE_LIGHT = 3, TAG_SEDGE_POINT = 4,
        TAG_SEDGE_PICK = 5 };
 enum { TERM_INTERIOR = 1, TERM_PEDGE = 2, TERM_SEDGE = 4 };
-enum { ERR_STACK = 1, ERR_STEPS = 2 };
+enum { ERR_STACK = 1, ERR_STEPS = 2, ERR_WAIT = 4 };   // device error flags
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).

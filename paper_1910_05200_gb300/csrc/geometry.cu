@@ -61,8 +61,11 @@ __global__ void k_geometry(GeoArgs g, const float* __restrict__ theta) {
     for (int k = 0; k < K1; ++k) x += (double)g.BidT[(size_t)k * n3 + i] * (double)coef[k];
     for (int k = 0; k < K2; ++k) x += (double)g.BexpT[(size_t)k * n3 + i] * (double)coef[K1 + k];
     xm[c] = x;
-    float al = g.alb_mean[i];
-    for (int k = 0; k < K3; ++k) al += g.BalbT[(size_t)k * n3 + i] * coef[K1 + K2 + k];
+    float al = 0.0f;
+    if (g.alb) {             // null: albedo kept from another frame of a batch
+      al = g.alb_mean[i];
+      for (int k = 0; k < K3; ++k) al += g.BalbT[(size_t)k * n3 + i] * coef[K1 + K2 + k];
+    }
     a[c] = al;
   }
   const float* t = theta + g.off_pose + 3;
@@ -74,7 +77,7 @@ __global__ void k_geometry(GeoArgs g, const float* __restrict__ theta) {
   }
   g.X[v] = make_float4(X[0], X[1], X[2], 0.0f);
   g.Xm[v] = make_float4((float)xm[0], (float)xm[1], (float)xm[2], 0.0f);
-  g.alb[v] = make_float4(a[0], a[1], a[2], 0.0f);
+  if (g.alb) g.alb[v] = make_float4(a[0], a[1], a[2], 0.0f);
 }
 
 // Face normals in decision form and the leaf-ordered triangle array.

@@ -95,6 +95,88 @@ struct GradBufs {
   int2* hits;             // per tiled sample: (face or -1, t bits), written by k_bwd_interior
 };
 
+// One frame of a batch: the render arguments and gradient buffers of that
+// frame plus its image, adjoint, target and loss slots (device table).
+struct BatchFrame {
+  RenderArgs a;           // a.iter is replaced by *BatchArgs::iter
+  GradBufs gb;            // gb.d_image is this frame's adjoint; gb.hits unused
+  float* image;           // [H*W*3]
+  float* d_image;         // [H*W*3], written by the frame's tile items
+  const float* target;    // [H*W*3]
+  const uint8_t* mask;    // [H*W] or null
+  double* loss;           // E_data of the frame (added)
+  int tiles_x, n_tiles;
+  long long n_pedge;      // primary-edge samples: W*H*spp
+};
+
+// Work items of the persistent kernel: tile items (frame, tile) first, then
+// primary-edge items (frame | PEDGE_ITEM, chunk), each group in frame order.
+constexpr int PEDGE_ITEM = 1 << 30;
+// Spin limit of a primary-edge item waiting for its frame's tiles
+// (__nanosleep(256) per try: about a second).
+constexpr int BATCH_WAIT_LIMIT = 1 << 22;
+
+struct BatchArgs {
+  const BatchFrame* frames;
+  const int2* items;
+  int n_items;
+  int tile_w, tile_h;     // pixels per tile item
+  int pedge_chunk;        // edge samples per primary-edge item
+  int* queue;             // next item, zeroed before the launch
+  int* tiles_done;        // [n_frames], zeroed before the launch
+  const uint32_t* iter;
+  int* err;
+  unsigned long long* counters;  // [16] or null, same layout as the single-image kernels
+};
+
+// Phase kernels of a batch (one launch per phase for all frames): block b of
+// the launch belongs to the frame f with block_start[f] <= b <
+// block_start[f + 1]; frames are laid out one after another so that the
+// blocks of one frame run together and its structures stay in L2.
+struct PhaseArgs {
+  const BatchFrame* frames;
+  const int* block_start;   // [n_frames + 1]
+  int n_frames;
+  const uint32_t* iter;
+  int* err;
+  unsigned long long* counters;  // [16] or null
+};
+
+// Per-warp slice of k_batch_step's dynamic shared memory: the arguments of
+// the frame the warp works on and its light-gradient accumulator.
+struct BatchWarpState {
+  RenderArgs a;
+  GradBufs g;
+  float sL[3 * MAX_LIGHTS];
+};
+// Dynamic shared memory of k_batch_step: the block's specular-map
+// accumulator, then one BatchWarpState per warp.
+FR_HOST_DEV inline size_t batch_smem_head() { return (sizeof(float) * CS * CS + 15) & ~(size_t)15; }
+FR_HOST_DEV inline size_t batch_smem_bytes(int block) {
+  return batch_smem_head() + (size_t)(block / 32) * sizeof(BatchWarpState);
+}
+
+// forward + loss + interior adjoint (spp dividing 32), blocks of 256 threads
+// over each frame's samples in 8x8-tile order; writes gb.hits for the
+// shadow-edge phase
+__global__ void k_batch_fwd(PhaseArgs p);
+// shadow edges: per frame n_lights x (that frame's forward blocks), light-major
+__global__ void k_batch_sedge3(PhaseArgs p);
+__global__ void k_batch_sedge4(PhaseArgs p);
+// primary edges: blocks of 256 over each frame's W*H*spp edge samples
+__global__ void k_batch_pedge(PhaseArgs p);
+__global__ void k_batch_step2(BatchArgs b);
+__global__ void k_batch_step3(BatchArgs b);
+__global__ void k_batch_step4(BatchArgs b);
+__global__ void k_batch_gather_theta(int n_frames, int P, int K_id, int K_exp, int K_alb, int n_light_vals,
+                                     const float* __restrict__ ts, const float* __restrict__ tf,
+                                     float* __restrict__ theta);
+__global__ void k_batch_reduce(int n_frames, int P, int K_id, int K_exp, int K_alb, int n_light_vals,
+                               const float* __restrict__ theta, const double* __restrict__ grad_full,
+                               const double* __restrict__ loss_frames, const float* __restrict__ m, float w1,
+                               float w2, double* __restrict__ grad_s, double* __restrict__ grad_f,
+                               double* __restrict__ loss);
+
 __global__ void k_geometry(GeoArgs g, const float* __restrict__ theta);
 __global__ void k_faces(GeoArgs g);
 __global__ void k_pack_edges(int E, const int4* __restrict__ edges_leaf, const int* __restrict__ edge_id,

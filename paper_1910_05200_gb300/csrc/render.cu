@@ -18,98 +18,9 @@
 //                   that is on, one edge picked uniformly (minimum Philox key)
 //                   among the edges that are silhouettes seen from the shading
 //                   point and whose central projection crosses the light square.
-#include "kernels.cuh"
+#include "render_device.cuh"
 
 namespace fr {
-
-FR_DEV Surf surface(const RenderArgs& a, int f, V3 o, V3 d, int flip) {
-  int4 t = a.mesh.tris[f];
-  V3 P0 = v3(a.mesh.X[t.x]), P1 = v3(a.mesh.X[t.y]), P2 = v3(a.mesh.X[t.z]);
-  V3 e1 = P1 - P0, e2 = P2 - P0, s = o - P0;
-  V3 pv = cross(d, e2);
-  float inv = 1.0f / dot(e1, pv);
-  V3 qv = cross(s, e1);
-  Surf S;
-  S.b1 = dot(s, pv) * inv;
-  S.b2 = dot(d, qv) * inv;
-  S.b0 = 1.0f - S.b1 - S.b2;
-  // hit point from the barycentrics: its error is relative to the triangle,
-  // not to the camera distance
-  S.x = P0 + e1 * S.b1 + e2 * S.b2;
-  V3 N0 = v3(a.nrm[t.x]), N1 = v3(a.nrm[t.y]), N2 = v3(a.nrm[t.z]);
-  S.nraw = N0 * S.b0 + N1 * S.b1 + N2 * S.b2;
-  S.inv_nlen = rsqrtf(dot(S.nraw, S.nraw));
-  S.ns = S.nraw * (S.inv_nlen * (float)flip);
-  S.wo = normalize(-d);
-  V3 A0 = v3(a.alb[t.x]), A1 = v3(a.alb[t.y]), A2 = v3(a.alb[t.z]);
-  S.rho = A0 * S.b0 + A1 * S.b1 + A2 * S.b2;
-  float2 u0 = a.uv[t.x], u1 = a.uv[t.y], u2 = a.uv[t.z];
-  S.u = S.b0 * u0.x + S.b1 * u1.x + S.b2 * u2.x;
-  S.v = S.b0 * u0.y + S.b1 * u1.y + S.b2 * u2.y;
-  S.flip = flip;
-  return S;
-}
-
-FR_DEV V3 light_rgb(const RenderArgs& a, int j) {
-  const float* l = a.lights_dev + 3 * j;
-  return V3{__ldg(l), __ldg(l + 1), __ldg(l + 2)};
-}
-// A light is off when all three channels are exactly zero.
-FR_DEV bool light_on(const RenderArgs& a, int j) {
-  V3 l = light_rgb(a, j);
-  return l.x != 0.0f || l.y != 0.0f || l.z != 0.0f;
-}
-
-// Per-sample auxiliary features for the denoiser (means over spp are taken
-// by the caller): shading normal, diffuse albedo, specular albedo, distance
-// to the camera / d_cam, fraction of lit lights that are visible, hit flag.
-struct SampleAux {
-  V3 n, rho;
-  float cs, depth, vis, hit;
-};
-
-// One-sample radiance along a camera ray, lights that are on only.
-FR_DEV V3 radiance(const RenderArgs& a, V3 o, V3 d, int tag, uint32_t c0, uint32_t c1, unsigned long long* cnt,
-                   SampleAux* aux = nullptr) {
-  float t;
-  int f = closest_hit(a.mesh, o, d, t, a.err, cnt);
-  if (f < 0) return V3{0, 0, 0};
-  int flip = face_flip(a.mesh, f, d);
-  V3 x32 = hit_point(o, d, t);
-  Surf S = surface(a, f, o, d, flip);
-  int idx[4];
-  float w[4], fu, fv;
-  float cs = cspec_lookup(a.cspec, S.u, S.v, idx, w, fu, fv);
-  V3 L{0, 0, 0};
-  const float area = a.side * a.side;
-  int n_on = 0, n_vis = 0;
-  for (int j = 0; j < a.n_lights; ++j) {
-    if (!light_on(a, j)) continue;
-    ++n_on;
-    U4 q = philox(a.seed, a.iter, c0, c1, (uint32_t)(tag << 8 | j), 0);
-    V3 y = light_point(a.lights[j], a.side, unitf(q.x), unitf(q.y));
-    if (!visible(a.mesh, x32, y, f, flip, a.tmin, a.err, cnt)) continue;
-    ++n_vis;
-    ShadeOut sh = shade_light(S, cs, light_rgb(a, j), y, a.lights[j].dl, a.m);
-    L += sh.h * area;
-  }
-  if (aux) {
-    aux->n = S.ns; aux->rho = S.rho; aux->cs = cs;
-    aux->depth = t * len(d) / a.cam.dcam;
-    aux->vis = n_on ? (float)n_vis / (float)n_on : 0.0f;
-    aux->hit = 1.0f;
-  }
-  return L;
-}
-
-// Camera ray of sample s of pixel (px, py).
-FR_DEV V3 sample_dir(const RenderArgs& a, int px, int py, int s, uint32_t& pix) {
-  pix = (uint32_t)(py * a.W + px);
-  U4 q = philox(a.seed, a.iter, pix, (uint32_t)s, (uint32_t)(TAG_CAMERA << 8), 0);
-  float sx = __fadd_rn((float)px, unitf(q.x));
-  float sy = __fadd_rn((float)py, unitf(q.y));
-  return camera_dir(a.cam, sx, sy);
-}
 
 // AOV = true also writes the denoiser features aov[14 * pixel + k]:
 // 0-2 noisy RGB, 3-5 shading normal, 6-8 diffuse albedo, 9 specular albedo,
@@ -181,6 +92,7 @@ FR_DEV void render_fwd_body(const RenderArgs& a, float* __restrict__ image, floa
 __global__ void __launch_bounds__(256) k_render_fwd(RenderArgs a, float* __restrict__ image) {
   render_fwd_body<false>(a, image, nullptr);
 }
+
 __global__ void __launch_bounds__(256) k_render_fwd_aov(RenderArgs a, float* __restrict__ image,
                                                         float* __restrict__ aov) {
   render_fwd_body<true>(a, image, aov);
@@ -192,132 +104,6 @@ __global__ void k_aov_finish(int n_pix, float* __restrict__ aov, const float* __
   if (p >= n_pix) return;
   float m = meanY[p];
   aov[14 * (size_t)p + 12] = fmaxf(0.0f, aov[14 * (size_t)p + 12] - m * m);
-}
-
-// ---------------------------------------------------------------------------
-// Interior adjoint
-
-// Reverse-mode of shade_light for one light.  G = adjoint RGB times area/spp.
-FR_DEV void shade_light_bwd(const Surf& S, float cs, V3 l, V3 y, V3 dl, float m, V3 G, V3& g_x, V3& g_ns,
-                            V3& g_rho, float& g_cs, V3& g_l) {
-  V3 w = y - S.x;
-  float d2 = dot(w, w);
-  float ir = rsqrtf(d2);
-  V3 wi = w * ir;
-  float ci = dot(S.ns, wi);
-  if (!(ci > 0.0f)) return;
-  float cy = dot(dl, wi);
-  if (!(cy > 0.0f)) return;
-  float co = dot(S.ns, S.wo);
-  float spec = 0.0f, D = 0.0f, Gf = 0.0f, ch = 0.0f, oh = 0.0f, g1 = 0.0f, g2 = 0.0f, hlen = 1.0f;
-  int branch = 0;
-  V3 h{0, 0, 0};
-  if (co > 0.0f) {
-    V3 hv = wi + S.wo;
-    hlen = len(hv);
-    h = hv * (1.0f / hlen);
-    ch = dot(S.ns, h);
-    oh = dot(S.wo, h);
-    float ch2 = ch * ch;
-    float tan2 = (1.0f - ch2) / ch2;
-    D = __expf(-tan2 / (m * m)) / (PI_F * m * m * ch2 * ch2);
-    g1 = 2.0f * ch * co / oh;
-    g2 = 2.0f * ch * ci / oh;
-    float inner = g1 <= g2 ? g1 : g2;
-    if (1.0f <= inner) { Gf = 1.0f; branch = 0; }
-    else { Gf = inner; branch = g1 <= g2 ? 1 : 2; }
-    spec = D * Gf / (4.0f * ci * co);
-  }
-  float geo = ci * cy / d2;
-  const float ip = 1.0f / PI_F;
-  V3 F{S.rho.x * ip + cs * spec, S.rho.y * ip + cs * spec, S.rho.z * ip + cs * spec};
-  g_l += V3{G.x * F.x * geo, G.y * F.y * geo, G.z * F.z * geo};
-  V3 s{G.x * l.x, G.y * l.y, G.z * l.z};
-  g_rho += s * (geo * ip);
-  float Ssum = (s.x + s.y + s.z) * geo;
-  g_cs += Ssum * spec;
-  float d_spec = Ssum * cs;
-  float d_geo = s.x * F.x + s.y * F.y + s.z * F.z;
-  float d_ci = d_geo * cy / d2;
-  float d_cy = d_geo * ci / d2;
-  float d_d2 = -d_geo * geo / d2;
-  float d_co = 0.0f;
-  V3 d_ns{0, 0, 0}, d_wi{0, 0, 0};
-  if (co > 0.0f && d_spec != 0.0f) {
-    float k4 = 4.0f * ci * co;
-    float d_D = d_spec * Gf / k4, d_G = d_spec * D / k4;
-    d_ci -= d_spec * spec / ci;
-    d_co -= d_spec * spec / co;
-    float d_ch = 0.0f, d_oh = 0.0f;
-    if (branch == 1) { d_ch += d_G * 2.0f * co / oh; d_co += d_G * 2.0f * ch / oh; d_oh -= d_G * g1 / oh; }
-    else if (branch == 2) { d_ch += d_G * 2.0f * ci / oh; d_ci += d_G * 2.0f * ch / oh; d_oh -= d_G * g2 / oh; }
-    d_ch += d_D * D * (2.0f / (m * m * ch * ch * ch) - 4.0f / ch);
-    d_ns += h * d_ch;
-    V3 d_h = S.ns * d_ch + S.wo * d_oh;
-    d_wi += (d_h - h * dot(d_h, h)) * (1.0f / hlen);
-  }
-  d_ns += wi * d_ci + S.wo * d_co;
-  d_wi += S.ns * d_ci + dl * d_cy;
-  V3 d_w = (d_wi - wi * dot(d_wi, wi)) * ir + w * (2.0f * d_d2);
-  g_x -= d_w;
-  g_ns += d_ns;
-}
-
-FR_DEV void atomic_add3(float4* p, V3 v) {
-  atomicAdd(p, make_float4(v.x, v.y, v.z, 0.0f));
-}
-
-// Adjoint of the hit point x = o + t d with respect to the hit triangle's
-// vertices (ray fixed), plus barycentric adjoints g_b1, g_b2 (b0 = 1-b1-b2
-// already folded in).  Scatters b_k * lambda into dX.
-FR_DEV void cross64(const double* a, const double* b, double* r) {
-  r[0] = a[1] * b[2] - a[2] * b[1];
-  r[1] = a[2] * b[0] - a[0] * b[2];
-  r[2] = a[0] * b[1] - a[1] * b[0];
-}
-
-// Hit point of the ray (o, d) on face f in FP64 (Moller-Trumbore on the FP32
-// vertices): accurate along the surface even for grazing rays.
-FR_DEV void hit_point64(const RenderArgs& a, int f, V3 o, V3 d, double* x) {
-  int4 t = a.mesh.tris[f];
-  float4 p0 = a.mesh.X[t.x], p1 = a.mesh.X[t.y], p2 = a.mesh.X[t.z];
-  double e1[3] = {(double)p1.x - p0.x, (double)p1.y - p0.y, (double)p1.z - p0.z};
-  double e2[3] = {(double)p2.x - p0.x, (double)p2.y - p0.y, (double)p2.z - p0.z};
-  double dd[3] = {d.x, d.y, d.z};
-  double s[3] = {(double)o.x - p0.x, (double)o.y - p0.y, (double)o.z - p0.z};
-  double pv[3], qv[3];
-  cross64(dd, e2, pv);
-  cross64(s, e1, qv);
-  double inv = 1.0 / (e1[0] * pv[0] + e1[1] * pv[1] + e1[2] * pv[2]);
-  double b1 = (s[0] * pv[0] + s[1] * pv[1] + s[2] * pv[2]) * inv;
-  double b2 = (dd[0] * qv[0] + dd[1] * qv[1] + dd[2] * qv[2]) * inv;
-  x[0] = (double)p0.x + b1 * e1[0] + b2 * e2[0];
-  x[1] = (double)p0.y + b1 * e1[1] + b2 * e2[1];
-  x[2] = (double)p0.z + b1 * e1[2] + b2 * e2[2];
-}
-
-// The 3x3 solve is ill-conditioned for grazing hits (det -> 0), so it runs in
-// FP64 (a few dozen operations per sample).
-FR_DEV void hit_adjoint(const RenderArgs& a, int f, V3 d, const Surf& S, V3 g_x, float g_b1, float g_b2,
-                        float4* dX) {
-  int4 t = a.mesh.tris[f];
-  float4 p0 = a.mesh.X[t.x], p1 = a.mesh.X[t.y], p2 = a.mesh.X[t.z];
-  double e1x = (double)p1.x - p0.x, e1y = (double)p1.y - p0.y, e1z = (double)p1.z - p0.z;
-  double e2x = (double)p2.x - p0.x, e2y = (double)p2.y - p0.y, e2z = (double)p2.z - p0.z;
-  double dx = d.x, dy = d.y, dz = d.z;
-  double nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
-  double det = dx * nx + dy * ny + dz * nz;
-  double gt = (double)g_x.x * dx + (double)g_x.y * dy + (double)g_x.z * dz;
-  double b1 = g_b1, b2 = g_b2;
-  // lambda = (n g_t + (d x e2) g_b1 + (e1 x d) g_b2) / det
-  double lx = nx * gt + (dy * e2z - dz * e2y) * b1 + (e1y * dz - e1z * dy) * b2;
-  double ly = ny * gt + (dz * e2x - dx * e2z) * b1 + (e1z * dx - e1x * dz) * b2;
-  double lz = nz * gt + (dx * e2y - dy * e2x) * b1 + (e1x * dy - e1y * dx) * b2;
-  double inv = 1.0 / det;
-  V3 lam{(float)(lx * inv), (float)(ly * inv), (float)(lz * inv)};
-  atomic_add3(dX + t.x, lam * S.b0);
-  atomic_add3(dX + t.y, lam * S.b1);
-  atomic_add3(dX + t.z, lam * S.b2);
 }
 
 __global__ void __launch_bounds__(256, 3) k_bwd_interior(RenderArgs a, GradBufs gb) {
@@ -342,58 +128,7 @@ __global__ void __launch_bounds__(256, 3) k_bwd_interior(RenderArgs a, GradBufs 
     float t = 0.0f;
     int f = (dimg.x != 0.0f || dimg.y != 0.0f || dimg.z != 0.0f) ? closest_hit(a.mesh, a.cam.o, d, t, a.err, cnt) : -1;
     if (gb.hits) gb.hits[tid] = make_int2(f, __float_as_int(t));
-    if (f >= 0) {
-      int flip = face_flip(a.mesh, f, d);
-      V3 x32 = hit_point(a.cam.o, d, t);
-      Surf S = surface(a, f, a.cam.o, d, flip);
-      int idx[4];
-      float w[4], fu, fv;
-      float cs = cspec_lookup(a.cspec, S.u, S.v, idx, w, fu, fv);
-      const float scale = a.side * a.side / (float)spp;
-      V3 G = dimg * scale;
-      V3 g_x{0, 0, 0}, g_ns{0, 0, 0}, g_rho{0, 0, 0};
-      float g_cs = 0.0f;
-      for (int j = 0; j < a.n_lights; ++j) {
-        U4 q = philox(a.seed, a.iter, pix, (uint32_t)s, (uint32_t)(TAG_LIGHT << 8 | j), 0);
-        V3 y = light_point(a.lights[j], a.side, unitf(q.x), unitf(q.y));
-        if (!visible(a.mesh, x32, y, f, flip, a.tmin, a.err, cnt)) continue;
-        V3 g_l{0, 0, 0};
-        shade_light_bwd(S, cs, light_rgb(a, j), y, a.lights[j].dl, a.m, G, g_x, g_ns, g_rho, g_cs, g_l);
-        atomicAdd(&sL[3 * j], g_l.x);
-        atomicAdd(&sL[3 * j + 1], g_l.y);
-        atomicAdd(&sL[3 * j + 2], g_l.z);
-      }
-      int4 tri = a.mesh.tris[f];
-      // shading normal: ns = flip * n / |n|
-      V3 nh = S.nraw * S.inv_nlen;
-      V3 dnh = g_ns * (float)flip;
-      V3 g_n = (dnh - nh * dot(nh, dnh)) * S.inv_nlen;
-      V3 N0 = v3(a.nrm[tri.x]), N1 = v3(a.nrm[tri.y]), N2 = v3(a.nrm[tri.z]);
-      V3 A0 = v3(a.alb[tri.x]), A1 = v3(a.alb[tri.y]), A2 = v3(a.alb[tri.z]);
-      atomic_add3(gb.dN + tri.x, g_n * S.b0);
-      atomic_add3(gb.dN + tri.y, g_n * S.b1);
-      atomic_add3(gb.dN + tri.z, g_n * S.b2);
-      atomic_add3(gb.dA + tri.x, g_rho * S.b0);
-      atomic_add3(gb.dA + tri.y, g_rho * S.b1);
-      atomic_add3(gb.dA + tri.z, g_rho * S.b2);
-      float gb0 = dot(N0, g_n) + dot(A0, g_rho);
-      float gb1 = dot(N1, g_n) + dot(A1, g_rho);
-      float gb2 = dot(N2, g_n) + dot(A2, g_rho);
-      // specular map
-      if (g_cs != 0.0f) {
-        for (int k = 0; k < 4; ++k) atomicAdd(&sC[idx[k]], w[k] * g_cs);
-        const float* C = a.cspec;
-        float C0 = C[idx[0]], C1 = C[idx[1]], C2 = C[idx[2]], C3 = C[idx[3]];
-        float dfu = g_cs * (-(1.0f - fv) * C0 + (1.0f - fv) * C1 - fv * C2 + fv * C3);
-        float dfv = g_cs * (-(1.0f - fu) * C0 - fu * C1 + (1.0f - fu) * C2 + fu * C3);
-        float du = dfu * (float)CS, dv = dfv * (float)CS;
-        float2 u0 = a.uv[tri.x], u1 = a.uv[tri.y], u2 = a.uv[tri.z];
-        gb0 += u0.x * du + u0.y * dv;
-        gb1 += u1.x * du + u1.y * dv;
-        gb2 += u2.x * du + u2.y * dv;
-      }
-      hit_adjoint(a, f, d, S, g_x, gb1 - gb0, gb2 - gb0, gb.dX);
-    }
+    if (f >= 0) interior_sample(a, gb, sC, sL, pix, s, d, f, t, dimg, cnt);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < CS * CS; i += blockDim.x)
@@ -402,463 +137,10 @@ __global__ void __launch_bounds__(256, 3) k_bwd_interior(RenderArgs a, GradBufs 
     if (sL[i] != 0.0f) atomicAdd(&gb.dL[i], sL[i]);
 }
 
-// ---------------------------------------------------------------------------
-// Primary-visibility edges
-
 __global__ void __launch_bounds__(256, 4) k_bwd_pedge(RenderArgs a, GradBufs gb) {
   long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  long long total = (long long)a.W * a.H * a.spp;
-  if (tid >= total) return;
-  const int nS = *a.n_sil;
-  if (nS <= 0) return;
-  uint32_t pix = (uint32_t)(tid / a.spp);
-  int s = (int)(tid - (long long)pix * a.spp);
-  U4 q = philox(a.seed, a.iter, pix, (uint32_t)s, (uint32_t)(TAG_PEDGE << 8), 0);
-  int k = (int)(((unsigned long long)q.x * (unsigned long long)nS) >> 32);
-  float u = unitf(q.y);
-  int4 E = a.edges_canon[a.sil[k]];
-  V3 A = v3(a.mesh.X[E.x]), B = v3(a.mesh.X[E.y]);
-  float ax, ay, bx, by;
-  project(a.cam, A, ax, ay);
-  project(a.cam, B, bx, by);
-  float ex = __fsub_rn(bx, ax), ey = __fsub_rn(by, ay);
-  float mx = __fadd_rn(ax, __fmul_rn(u, ex)), my = __fadd_rn(ay, __fmul_rn(u, ey));
-  float fx = floorf(mx), fy = floorf(my);
-  if (!(fx >= 0.0f && fx < (float)a.W && fy >= 0.0f && fy < (float)a.H)) return;
-  int ipx = (int)fx, ipy = (int)fy;
-  const float* dI = gb.d_image + 3 * ((size_t)ipy * a.W + ipx);
-  V3 dimg{dI[0], dI[1], dI[2]};
-  if (dimg.x == 0.0f && dimg.y == 0.0f && dimg.z == 0.0f) return;
-  float L2 = __fmul_rn(ex, ex);
-  L2 = __fadd_rn(L2, __fmul_rn(ey, ey));
-  float Ln = __fsqrt_rn(L2);
-  if (Ln == 0.0f) return;
-  float nx = __fdiv_rn(-ey, Ln), ny = __fdiv_rn(ex, Ln);
-  float e = a.eps_pedge;
-  V3 dp = camera_dir(a.cam, __fadd_rn(mx, __fmul_rn(e, nx)), __fadd_rn(my, __fmul_rn(e, ny)));
-  V3 dm = camera_dir(a.cam, __fsub_rn(mx, __fmul_rn(e, nx)), __fsub_rn(my, __fmul_rn(e, ny)));
-  unsigned long long* cnt = a.counters ? a.counters + 8 : nullptr;    // primary edges: 8..11
-  V3 fp = radiance(a, a.cam.o, dp, TAG_PEDGE_LIGHT, pix, (uint32_t)s, cnt);
-  V3 fm = radiance(a, a.cam.o, dm, TAG_PEDGE_LIGHT, pix, (uint32_t)s, cnt);
-  float delta = dot(dimg, fm - fp);
-  if (delta == 0.0f) return;
-  float w = delta * (float)nS / ((float)a.W * (float)a.H * (float)a.spp);
-  const float kc = a.cam.k;
-  // screen edge vector from 3D differences (accurate for short edges)
-  float qa = a.cam.dcam - A.z, qb = a.cam.dcam - B.z;
-  V3 BA = B - A;
-  float iq = 1.0f / (qa * qb * kc);
-  float evx = (BA.x * qa + A.x * BA.z) * iq;
-  float evy = -(BA.y * qa + A.y * BA.z) * iq;
-  float gmx = -evy * w, gmy = evx * w;     // w * R90(e)
-  // adjoint of the screen projection for each endpoint
-  {
-    float c = 1.0f - u;
-    float gx = gmx * c, gy = gmy * c;
-    atomic_add3(gb.dX + E.x, V3{gx / (kc * qa), -gy / (kc * qa), (gx * A.x - gy * A.y) / (kc * qa * qa)});
-  }
-  {
-    float gx = gmx * u, gy = gmy * u;
-    atomic_add3(gb.dX + E.y, V3{gx / (kc * qb), -gy / (kc * qb), (gx * B.x - gy * B.y) / (kc * qb * qb)});
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Shadow-boundary edges
-
-// Clip the edge parameter interval to the part whose central projection from
-// x lands in the light square (decision form).
-FR_DEV bool shadow_clip(V3 A, V3 B, V3 x, const Light& L, float hs, float kappa, float& t0, float& t1) {
-  V3 xc = sub3r(x, L.c);
-  float al1 = dot3r(xc, L.e1), al2 = dot3r(xc, L.e2);
-  float D = -dot3r(xc, L.dl);
-  float ca[5], cb[5];
-#pragma unroll
-  for (int e = 0; e < 2; ++e) {
-    V3 q = sub3r(e == 0 ? A : B, x);
-    float h = dot3r(q, L.dl), s1 = dot3r(q, L.e1), s2 = dot3r(q, L.e2);
-    float n1 = __fadd_rn(__fmul_rn(al1, h), __fmul_rn(s1, D));
-    float n2 = __fadd_rn(__fmul_rn(al2, h), __fmul_rn(s2, D));
-    float hh = __fmul_rn(hs, h);
-    float* cc = e == 0 ? ca : cb;
-    cc[0] = __fsub_rn(h, kappa);
-    cc[1] = __fsub_rn(hh, n1);
-    cc[2] = __fadd_rn(hh, n1);
-    cc[3] = __fsub_rn(hh, n2);
-    cc[4] = __fadd_rn(hh, n2);
-  }
-  float lo = 0.0f, hi = 1.0f;
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    float p = ca[k], r = cb[k];
-    if (p < 0.0f && r < 0.0f) return false;
-    if (p < 0.0f) { float rr = __fdiv_rn(p, __fsub_rn(p, r)); if (rr > lo) lo = rr; }
-    else if (r < 0.0f) { float rr = __fdiv_rn(p, __fsub_rn(p, r)); if (rr < hi) hi = rr; }
-  }
-  t0 = lo; t1 = hi;
-  return lo < hi;
-}
-
-FR_DEV V3 edge_proj(V3 A, V3 B, V3 x, const Light& L, float D, float tau) {
-  V3 p{__fadd_rn(A.x, __fmul_rn(tau, __fsub_rn(B.x, A.x))), __fadd_rn(A.y, __fmul_rn(tau, __fsub_rn(B.y, A.y))),
-       __fadd_rn(A.z, __fmul_rn(tau, __fsub_rn(B.z, A.z)))};
-  V3 q = sub3r(p, x);
-  float h = dot3r(q, L.dl);
-  float f = __fdiv_rn(D, h);
-  return V3{__fadd_rn(x.x, __fmul_rn(f, q.x)), __fadd_rn(x.y, __fmul_rn(f, q.y)), __fadd_rn(x.z, __fmul_rn(f, q.z))};
-}
-
-FR_DEV bool silhouette_from(const Mesh& m, int4 E, V3 x) {
-  float4 n0 = m.ng[E.z];
-  float s0 = dot3r(v3(n0), sub3r(x, v3(m.X[m.tris[E.z].x])));
-  if (E.w < 0) return s0 != 0.0f;
-  float4 n1 = m.ng[E.w];
-  float s1 = dot3r(v3(n1), sub3r(x, v3(m.X[m.tris[E.w].x])));
-  return (s0 > 0.0f && s1 < 0.0f) || (s0 < 0.0f && s1 > 0.0f);
-}
-
-// Packed edge record (6 float4 per edge, edge-BVH leaf order), written per
-// render by k_pack_edges:
-//   [0] a.xyz, canonical edge id   [1] b.xyz, f0   [2] n0.xyz, f1
-//   [3] V0(f0).xyz                 [4] n1.xyz      [5] V0(f1).xyz
-// n = decision-form face normal, V0 = first vertex of the face.
-
-// Silhouette seen from x (decision form), from a packed record.
-FR_DEV bool packed_silhouette(const float4* R, V3 x, int f1) {
-  float4 n0 = R[2], p0 = R[3];
-  float s0 = dot3r(v3(n0), sub3r(x, v3(p0)));
-  if (f1 < 0) return s0 != 0.0f;
-  float4 n1 = R[4], p1 = R[5];
-  float s1 = dot3r(v3(n1), sub3r(x, v3(p1)));
-  return (s0 > 0.0f && s1 < 0.0f) || (s0 < 0.0f && s1 > 0.0f);
-}
-
-// Candidate search for one (shading point, light): traverse the edge BVH,
-// keeping a child when (1) its box reaches the pyramid from x through the
-// light square (4 side planes and the plane in front of x, with margins) and
-// (2) its normal cone does not prove every face below it is seen from the
-// same side (no silhouette possible).  Both tests are conservative; the leaf
-// test (silhouette + clip, decision form) decides.  The candidate with the
-// minimum Philox key is kept, so the pick does not depend on the order of
-// enumeration.
-struct Pick {
-  int n;        // number of candidates
-  int id;       // canonical id of the pick
-  int slot;     // its leaf slot in the packed array
-};
-
-FR_DEV Pick pick_light(const RenderArgs& a, V3 x, int hitf, int j, uint32_t pix, int s, unsigned long long* cnt) {
-  const Light& L = a.lights[j];
-  const float hs = __fmul_rn(0.5f, a.side);
-  Pick P;
-  P.n = 0; P.id = -1; P.slot = -1;
-  uint32_t bestkey = 0xffffffffu;
-  V3 Q[4];
-  const float sg[4][2] = {{-1, -1}, {1, -1}, {1, 1}, {-1, 1}};
-#pragma unroll
-  for (int k = 0; k < 4; ++k) Q[k] = L.c + L.e1 * (sg[k][0] * hs) + L.e2 * (sg[k][1] * hs);
-  V3 pn[4];
-  float pm[4];
-  V3 cx = L.c - x;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    V3 n = cross(Q[k] - x, Q[(k + 1) & 3] - x);
-    if (dot(n, cx) < 0.0f) n = -n;
-    pn[k] = n;
-    pm[k] = 1e-4f * len(n);
-  }
-  int stack[STACK];
-  int sp = 0, node = 0, steps = 0;
-  unsigned long long nvis = 0, nedge = 0;
-  if (a.ebvh.bvh.n_nodes == 0) return P;
-  while (true) {
-    if (++steps > MAX_STEPS) { atomicOr(a.err, ERR_STEPS); break; }
-    ++nvis;
-    const float4* N = a.ebvh.bvh.nodes + 4 * node;
-    float4 b0 = N[0], b1 = N[1], b2 = N[2];
-    int4 ch = *reinterpret_cast<const int4*>(N + 3);
-    V3 lo[2] = {V3{b0.x, b0.y, b0.z}, V3{b1.z, b1.w, b2.x}};
-    V3 hi[2] = {V3{b0.w, b1.x, b1.y}, V3{b2.y, b2.z, b2.w}};
-    int code[2] = {ch.x, ch.y};
-    int todo[2];
-    int nt = 0;
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      if (code[c] == EMPTY_CHILD) continue;
-      float4 cn = a.ebvh.cones[2 * node + c];
-      if (cn.w < PI_F) {
-        // Every face normal below lies within th = cn.w of the axis and every
-        // point in the bounding sphere (cb, rb), seen from x, within beta of
-        // the direction to the centre.  With psi the angle between the axis
-        // and x - cb and T = th + margin: psi + beta + T < pi/2 (all faces
-        // face x) or psi - beta - T > pi/2 (all face away) rules out any
-        // silhouette below.  In sines and cosines, when beta + T < pi/2:
-        // cos psi > sin(beta + T) or cos psi < -sin(beta + T).
-        V3 cb = (lo[c] + hi[c]) * 0.5f;
-        float rb = len((hi[c] - lo[c]) * 0.5f) * 1.0001f + 1e-6f;
-        V3 v = x - cb;
-        float dv2 = dot(v, v);
-        if (dv2 > rb * rb) {
-          float idv = rsqrtf(dv2);
-          float sb = rb * idv, cb2 = sqrtf(fmaxf(0.0f, 1.0f - sb * sb));
-          float sT, cT;
-          __sincosf(cn.w + 2e-3f, &sT, &cT);
-          if (cb2 * cT - sb * sT > 0.0f) {
-            float S = sb * cT + cb2 * sT;
-            float cpsi = dot(v, v3(cn)) * idv;
-            if (cpsi > S || cpsi < -S) continue;
-          }
-        }
-      }
-      V3 pp{L.dl.x > 0 ? hi[c].x : lo[c].x, L.dl.y > 0 ? hi[c].y : lo[c].y, L.dl.z > 0 ? hi[c].z : lo[c].z};
-      bool keep = dot(pp - x, L.dl) >= a.kappa - 1e-4f;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        V3 n = pn[k];
-        V3 p{n.x > 0 ? hi[c].x : lo[c].x, n.y > 0 ? hi[c].y : lo[c].y, n.z > 0 ? hi[c].z : lo[c].z};
-        keep = keep && dot(n, p - x) >= -pm[k];
-      }
-      if (!keep) continue;
-      todo[nt++] = code[c];
-    }
-    int next = -1;
-    for (int k = 0; k < nt; ++k) {
-      int c2 = todo[k];
-      if (leaf_child(c2)) {
-        int first = leaf_first(c2), n = leaf_count(c2);
-        for (int i = 0; i < n; ++i) {
-          const float4* R = a.ebvh.pack + 6 * (first + i);
-          float4 r1 = R[1], r2 = R[2];
-          int f0 = __float_as_int(r1.w), f1 = __float_as_int(r2.w);
-          ++nedge;
-          if (f0 == hitf || f1 == hitf) continue;
-          if (!packed_silhouette(R, x, f1)) continue;
-          float4 r0 = R[0];
-          float t0, t1;
-          if (!shadow_clip(v3(r0), v3(r1), x, L, hs, a.kappa, t0, t1)) continue;
-          int id = __float_as_int(r0.w);
-          uint32_t key = philox(a.seed, a.iter, pix, (uint32_t)s, (uint32_t)(TAG_SEDGE_PICK << 8 | j), (uint32_t)id).x;
-          ++P.n;
-          if (P.id < 0 || key < bestkey || (key == bestkey && id < P.id)) {
-            bestkey = key; P.id = id; P.slot = first + i;
-          }
-        }
-      } else if (next < 0) {
-        next = c2;
-      } else {
-        if (sp >= STACK) { atomicOr(a.err, ERR_STACK); goto done; }
-        stack[sp++] = c2;
-      }
-    }
-    if (next >= 0) { node = next; continue; }
-    if (sp == 0) break;
-    node = stack[--sp];
-  }
-done:
-  if (cnt) { atomicAdd(cnt + 2, nvis); atomicAdd(cnt + 3, nedge); }
-  return P;
-}
-
-// Warp-cooperative version of pick_light: the 32 lanes of a warp share one
-// light and (light-major launch) neighbouring shading points, so the warp
-// walks the edge BVH once with tests that hold for every point of the
-// group's bounding sphere (centre rc, radius rr): the pyramid from any x in
-// the sphere lies in the pyramid from rc dilated by rr, and a face seen from
-// any x in the sphere is judged with the node's sphere grown by rr.  Control
-// flow is uniform across the warp; each lane with a valid shading point runs
-// the exact leaf test (decision form) on its own x.  Lanes without one
-// (valid = false) still take part in the walk.
-FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int j, uint32_t pix, int s,
-                            unsigned long long* cnt) {
-  const Light& L = a.lights[j];
-  const float hs = __fmul_rn(0.5f, a.side);
-  Pick P;
-  P.n = 0; P.id = -1; P.slot = -1;
-  uint32_t bestkey = 0xffffffffu;
-  // group bounding box -> sphere
-  V3 lo_x = valid ? x : V3{3e38f, 3e38f, 3e38f};
-  V3 hi_x = valid ? x : V3{-3e38f, -3e38f, -3e38f};
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    lo_x.x = fminf(lo_x.x, __shfl_xor_sync(0xffffffffu, lo_x.x, off));
-    lo_x.y = fminf(lo_x.y, __shfl_xor_sync(0xffffffffu, lo_x.y, off));
-    lo_x.z = fminf(lo_x.z, __shfl_xor_sync(0xffffffffu, lo_x.z, off));
-    hi_x.x = fmaxf(hi_x.x, __shfl_xor_sync(0xffffffffu, hi_x.x, off));
-    hi_x.y = fmaxf(hi_x.y, __shfl_xor_sync(0xffffffffu, hi_x.y, off));
-    hi_x.z = fmaxf(hi_x.z, __shfl_xor_sync(0xffffffffu, hi_x.z, off));
-  }
-  if (!(lo_x.x <= hi_x.x) || a.ebvh.bvh.n_nodes == 0) return P;   // no valid lane
-  const V3 rc = (lo_x + hi_x) * 0.5f;
-  const float rr = len((hi_x - lo_x) * 0.5f) * 1.0001f + 1e-6f;
-  V3 Q[4];
-  const float sg[4][2] = {{-1, -1}, {1, -1}, {1, 1}, {-1, 1}};
-#pragma unroll
-  for (int k = 0; k < 4; ++k) Q[k] = L.c + L.e1 * (sg[k][0] * hs) + L.e2 * (sg[k][1] * hs);
-  V3 pn[4];
-  float pm[4];
-  V3 cx = L.c - rc;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    V3 n = cross(Q[k] - rc, Q[(k + 1) & 3] - rc);
-    if (dot(n, cx) < 0.0f) n = -n;
-    float ln = len(n);
-    pn[k] = n;
-    pm[k] = (1e-4f + rr) * ln;     // margin + dilation by the group radius
-  }
-  int stack[STACK];
-  int sp = 0, node = 0, steps = 0;
-  unsigned long long nvis = 0, nedge = 0;
-  while (true) {
-    if (++steps > MAX_STEPS) { atomicOr(a.err, ERR_STEPS); break; }
-    ++nvis;
-    const float4* N = a.ebvh.bvh.nodes + 4 * node;
-    float4 b0 = N[0], b1 = N[1], b2 = N[2];
-    int4 ch = *reinterpret_cast<const int4*>(N + 3);
-    V3 lo[2] = {V3{b0.x, b0.y, b0.z}, V3{b1.z, b1.w, b2.x}};
-    V3 hi[2] = {V3{b0.w, b1.x, b1.y}, V3{b2.y, b2.z, b2.w}};
-    int code[2] = {ch.x, ch.y};
-    int todo[2];
-    int nt = 0;
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      if (code[c] == EMPTY_CHILD) continue;
-      float4 cn = a.ebvh.cones[2 * node + c];
-      if (cn.w < PI_F) {
-        V3 cb = (lo[c] + hi[c]) * 0.5f;
-        float rb = len((hi[c] - lo[c]) * 0.5f) * 1.0001f + 1e-6f + rr;
-        V3 v = rc - cb;
-        float dv2 = dot(v, v);
-        if (dv2 > rb * rb) {
-          float idv = rsqrtf(dv2);
-          float sb = rb * idv, cb2 = sqrtf(fmaxf(0.0f, 1.0f - sb * sb));
-          float sT, cT;
-          __sincosf(cn.w + 2e-3f, &sT, &cT);
-          if (cb2 * cT - sb * sT > 0.0f) {
-            float S = sb * cT + cb2 * sT;
-            float cpsi = dot(v, v3(cn)) * idv;
-            if (cpsi > S || cpsi < -S) continue;
-          }
-        }
-      }
-      V3 pp{L.dl.x > 0 ? hi[c].x : lo[c].x, L.dl.y > 0 ? hi[c].y : lo[c].y, L.dl.z > 0 ? hi[c].z : lo[c].z};
-      bool keep = dot(pp - rc, L.dl) >= a.kappa - 1e-4f - rr;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        V3 n = pn[k];
-        V3 p{n.x > 0 ? hi[c].x : lo[c].x, n.y > 0 ? hi[c].y : lo[c].y, n.z > 0 ? hi[c].z : lo[c].z};
-        keep = keep && dot(n, p - rc) >= -pm[k];
-      }
-      if (!keep) continue;
-      todo[nt++] = code[c];
-    }
-    int next = -1;
-    for (int k = 0; k < nt; ++k) {
-      int c2 = todo[k];
-      if (leaf_child(c2)) {
-        int first = leaf_first(c2), n = leaf_count(c2);
-        for (int i = 0; i < n; ++i) {
-          if (!valid) continue;
-          const float4* R = a.ebvh.pack + 6 * (first + i);
-          float4 r1 = R[1], r2 = R[2];
-          int f0 = __float_as_int(r1.w), f1 = __float_as_int(r2.w);
-          ++nedge;
-          if (f0 == hitf || f1 == hitf) continue;
-          if (!packed_silhouette(R, x, f1)) continue;
-          float4 r0 = R[0];
-          float t0, t1;
-          if (!shadow_clip(v3(r0), v3(r1), x, L, hs, a.kappa, t0, t1)) continue;
-          int id = __float_as_int(r0.w);
-          uint32_t key = philox(a.seed, a.iter, pix, (uint32_t)s, (uint32_t)(TAG_SEDGE_PICK << 8 | j), (uint32_t)id).x;
-          ++P.n;
-          if (P.id < 0 || key < bestkey || (key == bestkey && id < P.id)) {
-            bestkey = key; P.id = id; P.slot = first + i;
-          }
-        }
-      } else if (next < 0) {
-        next = c2;
-      } else {
-        if (sp >= STACK) { atomicOr(a.err, ERR_STACK); goto done; }
-        stack[sp++] = c2;
-      }
-    }
-    if (next >= 0) { node = next; continue; }
-    if (sp == 0) break;
-    node = stack[--sp];
-  }
-done:
-  if (cnt && (threadIdx.x & 31) == 0) { atomicAdd(cnt + 2, nvis); }
-  if (cnt) atomicAdd(cnt + 3, nedge);
-  return P;
-}
-
-// Boundary term of one light given its pick: sample the clipped edge,
-// difference the integrand across the projected edge, scatter the adjoint.
-FR_DEV void sedge_contribution(const RenderArgs& a, const GradBufs& gb, int j, int n_cand, int slot, V3 d, V3 x32,
-                               int f, int flip, uint32_t pix, int s, V3 wrgb, unsigned long long* cnt) {
-  const Light& L = a.lights[j];
-  const float hs = __fmul_rn(0.5f, a.side);
-  const float4* R = a.ebvh.pack + 6 * slot;
-  float4 r0 = R[0], r1 = R[1];
-  V3 A = v3(r0), B = v3(r1);
-  int4 ev = a.ebvh.verts[slot];
-  int v0 = ev.x, v1 = ev.y;
-  float t0, t1;
-  shadow_clip(A, B, x32, L, hs, a.kappa, t0, t1);
-  U4 q = philox(a.seed, a.iter, pix, (uint32_t)s, (uint32_t)(TAG_SEDGE_POINT << 8 | j), 0);
-  float u = unitf(q.x);
-  float tau = __fadd_rn(t0, __fmul_rn(u, __fsub_rn(t1, t0)));
-  float Dd = -dot3r(sub3r(x32, L.c), L.dl);
-  V3 y = edge_proj(A, B, x32, L, Dd, tau);
-  V3 y0 = edge_proj(A, B, x32, L, Dd, t0);
-  V3 y1 = edge_proj(A, B, x32, L, Dd, t1);
-  V3 nv = cross3r(L.dl, sub3r(y1, y0));
-  float nl = __fsqrt_rn(dot3r(nv, nv));
-  if (nl == 0.0f) return;
-  nv = V3{__fdiv_rn(nv.x, nl), __fdiv_rn(nv.y, nl), __fdiv_rn(nv.z, nl)};
-  const float e = a.eps_sedge;
-  V3 yp{__fadd_rn(y.x, __fmul_rn(e, nv.x)), __fadd_rn(y.y, __fmul_rn(e, nv.y)), __fadd_rn(y.z, __fmul_rn(e, nv.z))};
-  V3 ym{__fsub_rn(y.x, __fmul_rn(e, nv.x)), __fsub_rn(y.y, __fmul_rn(e, nv.y)), __fsub_rn(y.z, __fmul_rn(e, nv.z))};
-  bool vp = visible(a.mesh, x32, yp, f, flip, a.tmin, a.err, cnt);
-  bool vm = visible(a.mesh, x32, ym, f, flip, a.tmin, a.err, cnt);
-  if (vp == vm) return;
-  Surf S = surface(a, f, a.cam.o, d, flip);
-  int idx[4];
-  float w4[4], fu, fv;
-  float cs = cspec_lookup(a.cspec, S.u, S.v, idx, w4, fu, fv);
-  V3 l = light_rgb(a, j);
-  V3 gp{0, 0, 0}, gm{0, 0, 0};
-  if (vp) gp = shade_light(S, cs, l, yp, L.dl, a.m).h;
-  if (vm) gm = shade_light(S, cs, l, ym, L.dl, a.m).h;
-  float delta = dot(wrgb, gm - gp);
-  if (delta == 0.0f) return;
-  float w = delta * (float)n_cand * (t1 - t0);
-  // Adjoint of the boundary point y(tau) = x + q D/h on the light plane,
-  // q = p - x, p = A + tau (B - A), h = q.dl, D = (c - x).dl.  With
-  // u = B - A and K = (dl x (q x u)) x q, the normal velocity of the
-  // boundary times its length element gives
-  //   dE/dp = w (D/h^2)^2 K,   dE/dx = w (1 - D/h) (D/h^3) K.
-  // For an occluder close to the shading point these factors amplify any
-  // error in x, and x itself is ill-conditioned at grazing hits, so this
-  // (rare: only where the two sides differ) step runs in FP64.
-  double x64[3];
-  hit_point64(a, f, a.cam.o, d, x64);
-  double ue[3] = {(double)B.x - A.x, (double)B.y - A.y, (double)B.z - A.z};
-  double qv[3] = {((double)A.x - x64[0]) + ue[0] * tau, ((double)A.y - x64[1]) + ue[1] * tau,
-                  ((double)A.z - x64[2]) + ue[2] * tau};
-  double dl[3] = {L.dl.x, L.dl.y, L.dl.z};
-  double h = qv[0] * dl[0] + qv[1] * dl[1] + qv[2] * dl[2];
-  double D = ((double)L.c.x - x64[0]) * dl[0] + ((double)L.c.y - x64[1]) * dl[1] + ((double)L.c.z - x64[2]) * dl[2];
-  double Dh2 = D / (h * h);
-  double c1[3], c2[3], K[3];
-  cross64(qv, ue, c1);
-  cross64(dl, c1, c2);
-  cross64(c2, qv, K);
-  double sp = (double)w * Dh2 * Dh2, sx = (double)w * (1.0 - D / h) * (Dh2 / h);
-  V3 g_p{(float)(K[0] * sp), (float)(K[1] * sp), (float)(K[2] * sp)};
-  V3 gx{(float)(K[0] * sx), (float)(K[1] * sx), (float)(K[2] * sx)};
-  atomic_add3(gb.dX + v0, g_p * (1.0f - tau));
-  atomic_add3(gb.dX + v1, g_p * tau);
-  hit_adjoint(a, f, d, S, gx, 0.0f, 0.0f, gb.dX);
+  if (tid >= (long long)a.W * a.H * a.spp) return;
+  pedge_sample(a, gb, tid, a.counters ? a.counters + 8 : nullptr);    // primary edges: counters 8..11
 }
 
 // One thread per (light, camera sample), light-major: a warp serves one light
@@ -891,10 +173,7 @@ __global__ void __launch_bounds__(256, 4) k_bwd_sedge(RenderArgs a, GradBufs gb)
     flip = face_flip(a.mesh, f, d);
     x32 = hit_point(a.cam.o, d, t);
   }
-  unsigned long long* cnt = a.counters ? a.counters + 12 : nullptr;   // shadow edges: 12..15
-  Pick P = pick_light_warp(a, valid, x32, f, j, pix, s, cnt);
-  if (!valid || P.n == 0) return;
-  sedge_contribution(a, gb, j, P.n, P.slot, d, x32, f, flip, pix, s, wrgb, cnt);
+  sedge_pick_and_add(a, gb, j, valid, d, x32, f, flip, pix, s, wrgb, a.counters ? a.counters + 12 : nullptr);
 }
 
 }  // namespace fr

@@ -32,11 +32,25 @@ class FrRenderOpts(C.Structure):
                 ("iter", C.c_uint32), ("terms", C.c_int32)]
 
 
+class FrFrame(C.Structure):
+    _fields_ = [("W", C.c_int32), ("H", C.c_int32), ("seed", C.c_uint32)]
+
+
+class FrTileConfig(C.Structure):
+    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("block", C.c_int32), ("min_blocks", C.c_int32),
+                ("fused", C.c_int32), ("ms", C.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 EXPORTS = ["fr_default_config", "fr_create", "fr_destroy", "fr_set_stream", "fr_last_error", "fr_strerror",
            "fr_upload_mesh", "fr_upload_bases", "fr_n_params", "fr_render", "fr_render_backward", "fr_loss",
            "fr_geometry", "fr_geometry_noalloc", "fr_vertex_grad", "fr_light_stage", "fr_sync", "fr_set_counters", "fr_get_counters", "fr_set_timing", "fr_get_timings",
            "fr_launch_count", "fr_denoiser_n_weights", "fr_denoiser_set_weights", "fr_denoiser_get_weights",
-           "fr_denoise", "fr_denoiser_train_step", "fr_denoiser_get_grad", "fr_adam_step"]
+           "fr_denoise", "fr_denoiser_train_step", "fr_denoiser_get_grad", "fr_adam_step",
+           "fr_batch_n_shared", "fr_batch_n_frame", "fr_batch_create", "fr_batch_destroy", "fr_batch_set_targets",
+           "fr_batch_step", "fr_batch_autotune", "fr_batch_get_config", "fr_batch_set_config"]
 
 
 def lib_path() -> str:
@@ -87,6 +101,16 @@ def load(path: str | None = None):
     L.fr_denoiser_train_step.argtypes = [vp, vp, vp, i32, f32, vp]
     L.fr_denoiser_get_grad.argtypes = [vp, vp, i32]
     L.fr_adam_step.argtypes = [vp, vp, vp, vp, vp, vp, i32]
+    L.fr_batch_n_shared.argtypes = [vp]
+    L.fr_batch_n_frame.argtypes = [vp]
+    L.fr_batch_create.argtypes = [vp, vp, i32, i32, C.POINTER(vp)]
+    L.fr_batch_destroy.argtypes = [vp]
+    L.fr_batch_destroy.restype = None
+    L.fr_batch_set_targets.argtypes = [vp, vp, vp, vp]
+    L.fr_batch_step.argtypes = [vp, vp, vp, f32, f32, C.c_uint32, vp, vp, vp, vp]
+    L.fr_batch_autotune.argtypes = [vp, vp, vp, i32, vp, i32, C.POINTER(i32)]
+    L.fr_batch_get_config.argtypes = [vp, vp]
+    L.fr_batch_set_config.argtypes = [vp, vp]
     _LIB = L
     return L
 
@@ -306,3 +330,111 @@ class FaceRender(torch.autograd.Function):
 def render(theta, renderer: Renderer, W: int, H: int, spp: int, seed: int = 0, iter: int = 0):
     """Differentiable render (autograd entry point)."""
     return FaceRender.apply(theta, renderer, W, H, spp, seed, iter)
+
+
+class Batch:
+    """Batched frames (fr_batch_*): frames of one face with shared identity,
+    albedo and specular map and per-frame expression, pose and lights, each
+    at its own crop size; one step = one CUDA graph (geometry, the render +
+    loss + backward of all frames, geometry adjoints)."""
+
+    def __init__(self, renderer: Renderer, frames, spp: int):
+        """frames: list of (W, H, seed)."""
+        self.r = renderer
+        self.lib = renderer.lib
+        self.frames = [(int(w), int(h), int(sd)) for w, h, sd in frames]
+        arr = (FrFrame * len(self.frames))(*[FrFrame(w, h, sd) for w, h, sd in self.frames])
+        self.spp = int(spp)
+        self.n_pix = sum(w * h for w, h, _ in self.frames)
+        self.offsets = np.cumsum([0] + [w * h for w, h, _ in self.frames])
+        self.Ps = self.lib.fr_batch_n_shared(renderer.ctx)
+        self.Pf = self.lib.fr_batch_n_frame(renderer.ctx)
+        h = C.c_void_p()
+        renderer._stream()
+        renderer._check(self.lib.fr_batch_create(renderer.ctx, C.cast(arr, C.c_void_p), len(self.frames), self.spp,
+                                                 C.byref(h)), "fr_batch_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fr_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def split(self, packed):
+        """Per-frame [H, W, ...] views of a packed image tensor."""
+        out = []
+        for f, (w, h, _) in enumerate(self.frames):
+            o0, o1 = int(self.offsets[f]), int(self.offsets[f + 1])
+            out.append(packed[o0:o1].reshape(h, w, *packed.shape[1:]))
+        return out
+
+    def set_targets(self, targets, masks=None, m=None):
+        """targets: packed [n_pix, 3] FP32 device; masks packed [n_pix] uint8."""
+        self.r._stream()
+        self.r._check(self.lib.fr_batch_set_targets(self.h, _ptr(targets.contiguous()),
+                                                    _ptr(None if masks is None else masks.contiguous()),
+                                                    _ptr(None if m is None else m.contiguous())),
+                      "fr_batch_set_targets")
+        self._keep = (targets, masks, m)
+
+    def step(self, theta_shared, theta_frames, w1=0.0, w2=0.0, iter=0, images=True):
+        """Returns (loss [1] FP64, grad_shared [Ps] FP64, grad_frames [F, Pf] FP64, images [n_pix, 3] or None)."""
+        dev = self.r.device
+        loss = torch.empty(1, device=dev, dtype=torch.float64)
+        gs = torch.empty(self.Ps, device=dev, dtype=torch.float64)
+        gf = torch.empty(len(self.frames), self.Pf, device=dev, dtype=torch.float64)
+        img = torch.empty(self.n_pix, 3, device=dev) if images else None
+        self.r._stream()
+        self.r._check(self.lib.fr_batch_step(self.h, _ptr(theta_shared.contiguous()), _ptr(theta_frames.contiguous()),
+                                             float(w1), float(w2), int(iter), _ptr(loss), _ptr(gs), _ptr(gf),
+                                             _ptr(img)), "fr_batch_step")
+        return loss, gs, gf, img
+
+    def autotune(self, theta_shared, theta_frames, reps=1):
+        """Time every launch configuration that fits; keep the fastest.  Returns
+        the table (list of dicts) and the chosen configuration."""
+        cap = 64
+        tab = (FrTileConfig * cap)()
+        n = C.c_int32()
+        self.r._stream()
+        self.r._check(self.lib.fr_batch_autotune(self.h, _ptr(theta_shared.contiguous()),
+                                                 _ptr(theta_frames.contiguous()), int(reps), C.cast(tab, C.c_void_p),
+                                                 cap, C.byref(n)), "fr_batch_autotune")
+        return [tab[i].as_dict() for i in range(min(n.value, cap))], self.config()
+
+    def config(self):
+        c = FrTileConfig()
+        self.r._check(self.lib.fr_batch_get_config(self.h, C.byref(c)), "fr_batch_get_config")
+        return c.as_dict()
+
+    def set_config(self, tile_w=8, tile_h=8, block=256, min_blocks=4, fused=0):
+        c = FrTileConfig(int(tile_w), int(tile_h), int(block), int(min_blocks), int(fused), 0.0)
+        self.r._check(self.lib.fr_batch_set_config(self.h, C.byref(c)), "fr_batch_set_config")
+
+
+def split_theta(theta, K=(80, 90, 80), n_lights=20):
+    """Full parameter vector(s) -> (shared, frame) parts: shared = alpha,
+    delta, c_spec; frame = beta, pose, lights.  theta: [..., P] array or tensor."""
+    K_id, K_exp, K_alb = K
+    o_b, o_d = K_id, K_id + K_exp
+    o_c = o_d + K_alb
+    o_p = o_c + 32 * 32
+    lib = torch if isinstance(theta, torch.Tensor) else np
+    cat = (lambda xs: torch.cat(xs, -1)) if lib is torch else (lambda xs: np.concatenate(xs, -1))
+    shared = cat([theta[..., :o_b], theta[..., o_d:o_p]])
+    frame = cat([theta[..., o_b:o_d], theta[..., o_p:]])
+    return shared, frame
+
+
+def join_theta(shared, frame, K=(80, 90, 80)):
+    """Inverse of split_theta for one frame."""
+    K_id, K_exp, K_alb = K
+    lib = torch if isinstance(shared, torch.Tensor) else np
+    cat = (lambda xs: torch.cat(xs, -1)) if lib is torch else (lambda xs: np.concatenate(xs, -1))
+    return cat([shared[..., :K_id], frame[..., :K_exp], shared[..., K_id:], frame[..., K_exp:]])

@@ -264,6 +264,44 @@ def make_workload(name: str = "tiny", seed: int = 0):
     return scene, theta, c
 
 
+# Batched frames: frames of one face with shared identity, albedo and specular
+# map and per-frame expression, pose and lights; square crops of side
+# 128 + 8 floor(25 u), u ~ U[0,1) (128 ... 320 in steps of 8).
+BATCH = dict(kind="full", n_frames=32, spp=16, n_on=14, max_angle_deg=30.0, t_std=0.05, seed=100,
+             side_min=128, side_step=8, side_levels=25)
+
+
+def batch_sides(n_frames: int, seed: int, side_min: int = 128, side_step: int = 8, levels: int = 25):
+    rng = np.random.default_rng(seed)
+    return [int(side_min + side_step * math.floor(levels * u)) for u in rng.uniform(size=n_frames)]
+
+
+def make_batch(scene: Scene, n_frames: int = 32, seed: int = 100, n_on: int = 14, max_angle_deg: float = 30.0,
+               t_std: float = 0.05, sizes=None):
+    """Frames [(W, H, seed_f)] and full parameter vectors [n_frames, P] (FP32)
+    whose alpha, delta and c_spec are the same in every frame.  sizes: list
+    of (W, H); default square crops from batch_sides."""
+    if sizes is None:
+        sizes = [(w, w) for w in batch_sides(n_frames, seed)]
+    kid, kexp, kalb = scene.K
+    o = param_offsets(kid, kexp, kalb)
+    base = make_theta(scene, seed=seed, n_on=n_on, max_angle_deg=max_angle_deg, t_std=t_std)
+    thetas = []
+    for f in range(len(sizes)):
+        th = make_theta(scene, seed=seed * 1000 + 1 + f, n_on=n_on, max_angle_deg=max_angle_deg, t_std=t_std)
+        th[o["alpha"]:o["beta"]] = base[o["alpha"]:o["beta"]]
+        th[o["delta"]:o["pose"]] = base[o["delta"]:o["pose"]]
+        thetas.append(th)
+    frames = [(int(w), int(h), seed * 1000 + f) for f, (w, h) in enumerate(sizes)]
+    return frames, np.stack(thetas)
+
+
+def noise_images(frames, seed: int, lo: float = 0.0, hi: float = 0.5) -> np.ndarray:
+    """Packed [sum W*H, 3] FP32 images, U[lo, hi] per channel."""
+    n = sum(w * h for w, h, _ in frames)
+    return np.random.default_rng(seed).uniform(lo, hi, (n, 3)).astype(np.float32)
+
+
 def random_pixels(W: int, H: int, n: int, seed: int) -> np.ndarray:
     rng = np.random.default_rng(seed)
     return np.sort(rng.choice(W * H, size=min(n, W * H), replace=False)).astype(np.int32)

@@ -1,0 +1,283 @@
+"""Batched frames: the persistent render + loss + backward in a CUDA graph.
+
+Checked frame by frame against the oracle (images, loss, gradients of the
+shared and per-frame parameters), against the single-image path of the same
+library (same samples: images bit-identical when spp divides 32, gradients
+equal up to the order of floating-point atomic additions), across launch
+configurations of the autotuner, and at the full size of 32 frames of the
+35,709-vertex face.
+
+Tolerances: against the oracle, the law of the single-image parity tests
+(1e-3 of each entry with a floor of 1e-3 of the group's largest, or 1e-4 of
+the entry's L1 mass of contributions); between two GPU runs that differ only
+in the order of FP32 atomic additions, 1e-4 of the group's largest plus 1e-3
+of the entry.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import default_config
+from paper_1910_05200_gb300 import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(24, 24), (19, 31), (40, 33)]       # uneven, ragged against every tile shape
+SPP, ITER, W1, W2 = 4, 3, 0.02, 0.002
+KAPPA = 1e-4
+K = (80, 90, 80)
+
+
+def shared_groups():
+    return {"alpha": slice(0, 80), "delta": slice(80, 160), "cspec": slice(160, 1184)}
+
+
+def frame_groups():
+    return {"beta": slice(0, 90), "pose": slice(90, 96), "lights": slice(96, 156)}
+
+
+def assert_groups(got, ref, groups, mass=None, what=""):
+    for name, sl in groups.items():
+        o, g = ref[sl], got[sl]
+        floor = 1e-3 * np.abs(o).max()
+        if floor == 0:
+            assert np.all(np.abs(g) <= 1e-9), (what, name, np.abs(g).max())
+            continue
+        tol = 1e-3 * np.maximum(np.abs(o), floor)
+        if mass is not None:
+            tol = np.maximum(tol, KAPPA * mass[sl])
+        err = np.abs(g - o) / tol
+        assert err.max() <= 1.0, f"{what} {name}: {err.max():.3e} x tolerance at {int(err.argmax())} " \
+                                 f"(got {g[err.argmax()]:.6e}, ref {o[err.argmax()]:.6e})"
+
+
+def assert_atomic_close(got, ref, groups, what=""):
+    for name, sl in groups.items():
+        o, g = ref[sl], got[sl]
+        tol = 1e-4 * np.abs(o).max() + 1e-3 * np.abs(o) + 1e-12
+        err = np.abs(g - o) / tol
+        assert err.max() <= 1.0, f"{what} {name}: {err.max():.3e} x tolerance at {int(err.argmax())}"
+
+
+def combine(fr, per_frame, thetas, m, w1, w2):
+    """Per-frame full gradients (data term) -> batch layout plus the prior and
+    light terms, each parameter counted once (weights as the FP32 values the
+    library receives)."""
+    w1, w2 = float(np.float32(w1)), float(np.float32(w2))
+    shared = sum(fr.split_theta(g)[0] for g in per_frame)
+    frames = np.stack([fr.split_theta(g)[1] for g in per_frame])
+    ts, tf = fr.split_theta(thetas.astype(np.float64))
+    shared[:80] += 2 * w1 * ts[0, :80]
+    shared[80:160] += 2 * w1 * ts[0, 80:160]
+    frames[:, :90] += 2 * w1 * tf[:, :90]
+    frames[:, 96:] += 2 * w2 * (tf[:, 96:] - m.astype(np.float64))
+    reg = w1 * (np.sum(ts[0, :160] ** 2) + np.sum(tf[:, :90] ** 2)) + w2 * np.sum((tf[:, 96:] - m) ** 2)
+    return shared, frames, reg
+
+
+@pytest.fixture(scope="module")
+def fr():
+    from paper_1910_05200_gb300 import build, facert
+    build.build()
+    return facert
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), device="cuda:0")
+
+
+class Case:
+    def __init__(self, fr, scene, sizes, spp, seed=7):
+        self.fr, self.scene, self.spp = fr, scene, spp
+        self.r = fr.Renderer(scene, device=0)
+        self.frames, self.thetas = S.make_batch(scene, seed=seed, n_on=8, max_angle_deg=10.0, t_std=0.02,
+                                                sizes=sizes)
+        self.targets = S.noise_images(self.frames, seed=seed + 1)
+        rng = np.random.default_rng(seed + 2)
+        self.masks = (rng.uniform(size=len(self.targets)) > 0.2).astype(np.uint8)
+        self.m = rng.uniform(0, 1, 60).astype(np.float32)
+        self.b = fr.Batch(self.r, self.frames, spp)
+        self.b.set_targets(dev(self.targets), dev(self.masks), dev(self.m))
+        ts, tf = fr.split_theta(self.thetas)
+        self.ts, self.tf = dev(ts[0]), dev(tf)
+
+    def step(self, it=ITER):
+        loss, gs, gf, img = self.b.step(self.ts, self.tf, W1, W2, iter=it)
+        self.r.sync()
+        return loss.item(), gs.cpu().numpy(), gf.cpu().numpy(), img.cpu().numpy()
+
+    def frame_slices(self, packed):
+        out, o = [], 0
+        for w, h, _ in self.frames:
+            out.append(packed[o:o + w * h].reshape(h, w, *packed.shape[1:]))
+            o += w * h
+        return out
+
+
+@pytest.fixture(scope="module")
+def case(fr, tiny):
+    return Case(fr, tiny[0], SIZES, SPP)
+
+
+@pytest.mark.parametrize("fused", [0, 1])
+def test_batch_matches_oracle(oracle, fr, case, fused):
+    case.b.set_config(4, 4, 256, 4, fused) if fused else case.b.set_config(8, 8, 256, 4, 0)
+    loss, gs, gf, img = case.step()
+    imgs = case.frame_slices(img)
+    tgts = case.frame_slices(case.targets)
+    masks = case.frame_slices(case.masks)
+    per_frame, masses, e_data = [], [], 0.0
+    for f, (w, h, seed) in enumerate(case.frames):
+        cfg = default_config(W=w, H=h, spp=SPP, seed=seed, iter=ITER)
+        ref = oracle.render(cfg, case.scene, case.thetas[f])
+        rel = np.abs(imgs[f] - ref) / np.maximum(np.abs(ref), 1e-4 * np.abs(ref).mean() + 1e-30)
+        assert np.sum(np.any(rel > 1e-4, axis=-1)) <= max(1, int(1e-4 * w * h)), (f, rel.max())
+        d = 2.0 * masks[f][..., None] * (ref - tgts[f])
+        e_data += float(np.sum(masks[f][..., None] * (ref - tgts[f]) ** 2))
+        g, mass = oracle.render_backward(cfg, case.scene, case.thetas[f], d, mass=True)
+        per_frame.append(g)
+        masses.append(mass)
+    gs_ref, gf_ref, reg = combine(fr, per_frame, case.thetas, case.m, W1, W2)
+    ms_ref, mf_ref, _ = combine(fr, masses, case.thetas * 0, case.m * 0, 0.0, 0.0)
+    assert abs(loss - (e_data + reg)) <= 1e-5 * (e_data + reg)
+    assert_groups(gs, gs_ref, shared_groups(), ms_ref, what="shared")
+    for f in range(len(case.frames)):
+        assert_groups(gf[f], gf_ref[f], frame_groups(), mf_ref[f], what=f"frame {f}")
+
+
+@pytest.mark.parametrize("fused", [0, 1])
+def test_batch_equals_single_image_path(fr, case, fused):
+    case.b.set_config(2, 2, 128, 2, fused) if fused else case.b.set_config(8, 8, 256, 3, 0)
+    loss, gs, gf, img = case.step()
+    imgs = case.frame_slices(img)
+    tgts = case.frame_slices(case.targets)
+    masks = case.frame_slices(case.masks)
+    r = case.r
+    per_frame, e_data = [], 0.0
+    for f, (w, h, seed) in enumerate(case.frames):
+        th = dev(case.thetas[f])
+        single = r.render(th, w, h, SPP, seed=seed, iter=ITER)
+        assert np.array_equal(single.cpu().numpy(), imgs[f]), f"frame {f}: image differs from fr_render"
+        d_image = torch.empty(h, w, 3, device="cuda:0")
+        e_data += r.loss(th, single, dev(tgts[f]), dev(masks[f]), None, 0.0, 0.0, d_image).item()
+        per_frame.append(r.backward(th, d_image, w, h, SPP, seed=seed, iter=ITER).cpu().numpy())
+    r.sync()
+    gs_ref, gf_ref, reg = combine(fr, per_frame, case.thetas, case.m, W1, W2)
+    assert abs(loss - (e_data + reg)) <= 1e-12 * abs(e_data + reg)
+    assert_atomic_close(gs, gs_ref, shared_groups(), "shared")
+    for f in range(len(case.frames)):
+        assert_atomic_close(gf[f], gf_ref[f], frame_groups(), f"frame {f}")
+
+
+def test_steps_are_deterministic_and_keyed_by_iter(case):
+    l1, g1, f1, i1 = case.step(ITER)
+    l2, g2, f2, i2 = case.step(ITER)
+    l3, _, _, i3 = case.step(ITER + 1)
+    assert np.array_equal(i1, i2)
+    assert abs(l1 - l2) <= 1e-12 * abs(l1)
+    assert_atomic_close(g2, g1, shared_groups(), "replay")
+    assert not np.array_equal(i1, i3)
+
+
+def test_autotuner_table_and_configuration_invariance(case):
+    _, gs0, gf0, img0 = case.step()
+    table, chosen = case.b.autotune(case.ts, case.tf, reps=1)
+    keys = ("tile_w", "tile_h", "block", "min_blocks", "fused")
+    assert len(table) == 6 and {t["fused"] for t in table} == {0, 1}
+    best = min(table, key=lambda t: t["ms"])
+    assert tuple(chosen[k] for k in keys) == tuple(best[k] for k in keys)
+    for cfg in [(8, 8, 256, 3, 0), (8, 8, 256, 4, 0), (2, 2, 256, 2, 1), (4, 4, 128, 3, 1), (16, 8, 64, 4, 1),
+                (5, 3, 96, 2, 1)]:
+        case.b.set_config(*cfg)
+        _, gs, gf, img = case.step()
+        assert np.array_equal(img, img0), cfg
+        assert_atomic_close(gs, gs0, shared_groups(), f"config {cfg}")
+        for f in range(len(case.frames)):
+            assert_atomic_close(gf[f], gf0[f], frame_groups(), f"config {cfg} frame {f}")
+    case.b.set_config(8, 8, 256, 4, 0)
+
+
+def test_spp_multiple_of_32(fr, tiny):
+    """spp = 64: each pixel in two passes (radiance, then the adjoints with
+    the primary hit traced again); the single-image forward sums such pixels
+    with atomics, so images agree to rounding."""
+    c = Case(fr, tiny[0], [(9, 7), (12, 10)], 64, seed=21)
+    loss, gs, gf, img = c.step()
+    imgs = c.frame_slices(img)
+    tgts, masks = c.frame_slices(c.targets), c.frame_slices(c.masks)
+    per_frame = []
+    for f, (w, h, seed) in enumerate(c.frames):
+        th = dev(c.thetas[f])
+        single = c.r.render(th, w, h, 64, seed=seed, iter=ITER).cpu().numpy()
+        assert np.allclose(imgs[f], single, rtol=1e-5, atol=1e-7)
+        d_image = torch.empty(h, w, 3, device="cuda:0")
+        c.r.loss(th, dev(imgs[f]), dev(tgts[f]), dev(masks[f]), None, 0.0, 0.0, d_image)
+        per_frame.append(c.r.backward(th, d_image, w, h, 64, seed=seed, iter=ITER).cpu().numpy())
+    gs_ref, gf_ref, _ = combine(fr, per_frame, c.thetas, c.m, W1, W2)
+    assert_atomic_close(gs, gs_ref, shared_groups(), "spp 64 shared")
+    for f in range(len(c.frames)):
+        assert_atomic_close(gf[f], gf_ref[f], frame_groups(), f"spp 64 frame {f}")
+
+
+def test_unsupported_spp_is_refused(fr, case):
+    for spp in (3, 48):
+        with pytest.raises(RuntimeError):
+            fr.Batch(case.r, [(8, 8, 0)], spp)
+    b64 = fr.Batch(case.r, [(8, 8, 0)], 64)
+    assert b64.config()["fused"] == 1
+    with pytest.raises(RuntimeError):
+        b64.set_config(8, 8, 256, 4, 0)          # phased launches need spp dividing 32
+
+
+def test_invalid_configurations_are_refused(case):
+    for cfg in [(0, 8, 256, 2, 1), (65, 8, 256, 2, 1), (8, 8, 100, 2, 1), (8, 8, 256, 5, 1), (8, 8, 256, 2, 0),
+                (8, 8, 256, 4, 2)]:
+        with pytest.raises(RuntimeError):
+            case.b.set_config(*cfg)
+
+
+def test_full_size_batch_equals_single_frames(oracle, fr):
+    """32 frames of the 35,709-vertex face, crops 128..320, 16 spp: images of
+    two frames bit-identical to fr_render and sampled pixels against the
+    oracle; the batch gradient equal to the sum of the single-image
+    gradients of all frames."""
+    cfg = S.BATCH
+    scene = S.make_scene(cfg["kind"], seed=0)
+    frames, thetas = S.make_batch(scene, n_frames=cfg["n_frames"], seed=cfg["seed"], n_on=cfg["n_on"],
+                                  max_angle_deg=cfg["max_angle_deg"], t_std=cfg["t_std"])
+    sides = [w for w, _, _ in frames]
+    assert min(sides) >= 128 and max(sides) <= 320 and len(set(sides)) > 8
+    spp = cfg["spp"]
+    r = fr.Renderer(scene, device=0)
+    b = fr.Batch(r, frames, spp)
+    targets = S.noise_images(frames, seed=5, lo=0.0, hi=0.3)
+    b.set_targets(dev(targets))
+    ts, tf = fr.split_theta(thetas)
+    loss, gs, gf, img = b.step(dev(ts[0]), dev(tf), 0.0, 0.0, iter=1)
+    r.sync()
+    gs, gf, img = gs.cpu().numpy(), gf.cpu().numpy(), img.cpu().numpy()
+    assert np.isfinite(loss.item()) and np.all(np.isfinite(gs)) and np.all(np.isfinite(gf))
+    imgs = b.split(img)
+    tg = b.split(targets)
+    per_frame = []
+    for f, (w, h, seed) in enumerate(frames):
+        th = dev(thetas[f])
+        single = r.render(th, w, h, spp, seed=seed, iter=1)
+        d_image = torch.empty(h, w, 3, device="cuda:0")
+        r.loss(th, single, dev(tg[f]), None, None, 0.0, 0.0, d_image)
+        per_frame.append(r.backward(th, d_image, w, h, spp, seed=seed, iter=1).cpu().numpy())
+        if f in (int(np.argmin(sides)), int(np.argmax(sides))):
+            s = single.cpu().numpy()
+            assert np.array_equal(s, imgs[f])
+            lit = np.nonzero(s.reshape(-1, 3).sum(1) > 0)[0]
+            pix = np.unique(np.concatenate([S.random_pixels(w, h, 16, seed=f),
+                                            lit[:: max(1, len(lit) // 16)][:16]])).astype(np.int32)
+            ref = oracle.render(default_config(W=w, H=h, spp=spp, seed=seed, iter=1), scene, thetas[f], pixels=pix)
+            got = s.reshape(-1, 3)[pix]
+            rel = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-4 * np.abs(ref).mean() + 1e-30)
+            assert np.sum(np.any(rel > 1e-4, axis=-1)) <= 1, rel.max()
+    r.sync()
+    gs_ref, gf_ref, _ = combine(fr, per_frame, thetas, np.zeros(60, np.float32), 0.0, 0.0)
+    assert_atomic_close(gs, gs_ref, shared_groups(), "full size shared")
+    for f in range(len(frames)):
+        assert_atomic_close(gf[f], gf_ref[f], frame_groups(), f"full size frame {f}")
