@@ -38,7 +38,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-pixels", type=int, default=128, help="cpu_baseline leg: oracle pixels (all spp)")
+    ap.add_argument("--cpu-pixels", type=int, default=768, help="cpu_baseline leg: oracle pixels (all spp)")
     ap.add_argument("--ref-pixels", type=int, default=32, help="reference arm: oracle pixels per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=0, help="only run this many steps, no extras (ncu)")

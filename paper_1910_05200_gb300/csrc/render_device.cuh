@@ -463,20 +463,30 @@ FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int
   if (!(lo_x.x <= hi_x.x) || a.ebvh.bvh.n_nodes == 0) return P;   // no valid lane
   const V3 rc = (lo_x + hi_x) * 0.5f;
   const float rr = len((hi_x - lo_x) * 0.5f) * 1.0001f + 1e-6f;
-  V3 Q[4];
-  const float sg[4][2] = {{-1, -1}, {1, -1}, {1, 1}, {-1, 1}};
-#pragma unroll
-  for (int k = 0; k < 4; ++k) Q[k] = L.c + L.e1 * (sg[k][0] * hs) + L.e2 * (sg[k][1] * hs);
-  V3 pn[4];
-  float pm[4];
-  V3 cx = L.c - rc;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    V3 n = cross(Q[k] - rc, Q[(k + 1) & 3] - rc);
-    if (dot(n, cx) < 0.0f) n = -n;
-    float ln = len(n);
-    pn[k] = n;
-    pm[k] = (1e-4f + rr) * ln;     // margin + dilation by the group radius
+  // The node test is spread over lanes 0..11: lane 6c + t holds test t of
+  // child c -- t = 0 the normal cone, t = 1 the front plane, t = 2..5 side
+  // plane t - 2 of the pyramid from rc through the light square, each
+  // dilated by the group radius rr.  Every test has the form
+  // dot(n, p - rc) >= -m with p the box corner furthest along n, except the
+  // cone.  A child is kept when its six lanes pass (one ballot).
+  const int lane = threadIdx.x & 31;
+  const int tc = lane < 12 ? lane / 6 : 0, tt = lane < 12 ? lane - 6 * tc : 6;
+  V3 pn{0, 0, 0};
+  float pm = 0.0f;
+  if (tt == 1) {
+    pn = L.dl;
+    pm = rr + 1e-4f - a.kappa;
+  } else if (tt >= 2 && tt <= 5) {
+    // light-square corners in the order (-,-), (+,-), (+,+), (-,+)
+    const int k0 = tt - 2, k1 = (k0 + 1) & 3;
+    const float u0 = (k0 == 1 || k0 == 2) ? hs : -hs, v0 = k0 >= 2 ? hs : -hs;
+    const float u1 = (k1 == 1 || k1 == 2) ? hs : -hs, v1 = k1 >= 2 ? hs : -hs;
+    V3 Qa = L.c + L.e1 * u0 + L.e2 * v0 - rc;
+    V3 Qb = L.c + L.e1 * u1 + L.e2 * v1 - rc;
+    V3 n = cross(Qa, Qb);
+    if (dot(n, L.c - rc) < 0.0f) n = -n;
+    pn = n;
+    pm = (1e-4f + rr) * len(n);     // margin + dilation by the group radius
   }
   int stack[STACK];
   int sp = 0, node = 0, steps = 0;
@@ -487,43 +497,42 @@ FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int
     const float4* N = a.ebvh.bvh.nodes + 4 * node;
     float4 b0 = N[0], b1 = N[1], b2 = N[2];
     int4 ch = *reinterpret_cast<const int4*>(N + 3);
-    V3 lo[2] = {V3{b0.x, b0.y, b0.z}, V3{b1.z, b1.w, b2.x}};
-    V3 hi[2] = {V3{b0.w, b1.x, b1.y}, V3{b2.y, b2.z, b2.w}};
-    int code[2] = {ch.x, ch.y};
-    int todo[2];
-    int nt = 0;
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      if (code[c] == EMPTY_CHILD) continue;
-      float4 cn = a.ebvh.cones[2 * node + c];
-      if (cn.w < PI_F) {
-        V3 cb = (lo[c] + hi[c]) * 0.5f;
-        float rb = len((hi[c] - lo[c]) * 0.5f) * 1.0001f + 1e-6f + rr;
-        V3 v = rc - cb;
-        float dv2 = dot(v, v);
-        if (dv2 > rb * rb) {
-          float idv = rsqrtf(dv2);
-          float sb = rb * idv, cb2 = sqrtf(fmaxf(0.0f, 1.0f - sb * sb));
-          float sT, cT;
-          __sincosf(cn.w + 2e-3f, &sT, &cT);
-          if (cb2 * cT - sb * sT > 0.0f) {
-            float S = sb * cT + cb2 * sT;
-            float cpsi = dot(v, v3(cn)) * idv;
-            if (cpsi > S || cpsi < -S) continue;
+    bool pass = true;
+    if (tt < 6) {
+      const int code_c = tc ? ch.y : ch.x;
+      const V3 lo = tc ? V3{b1.z, b1.w, b2.x} : V3{b0.x, b0.y, b0.z};
+      const V3 hi = tc ? V3{b2.y, b2.z, b2.w} : V3{b0.w, b1.x, b1.y};
+      if (code_c == EMPTY_CHILD) {
+        pass = false;
+      } else if (tt == 0) {
+        float4 cn = a.ebvh.cones[2 * node + tc];
+        if (cn.w < PI_F) {
+          V3 cb = (lo + hi) * 0.5f;
+          float rb = len((hi - lo) * 0.5f) * 1.0001f + 1e-6f + rr;
+          V3 v = rc - cb;
+          float dv2 = dot(v, v);
+          if (dv2 > rb * rb) {
+            float idv = rsqrtf(dv2);
+            float sb = rb * idv, cb2 = sqrtf(fmaxf(0.0f, 1.0f - sb * sb));
+            float sT, cT;
+            __sincosf(cn.w + 2e-3f, &sT, &cT);
+            if (cb2 * cT - sb * sT > 0.0f) {
+              float S = sb * cT + cb2 * sT;
+              float cpsi = dot(v, v3(cn)) * idv;
+              if (cpsi > S || cpsi < -S) pass = false;
+            }
           }
         }
+      } else {
+        V3 p{pn.x > 0 ? hi.x : lo.x, pn.y > 0 ? hi.y : lo.y, pn.z > 0 ? hi.z : lo.z};
+        pass = dot(pn, p - rc) >= -pm;
       }
-      V3 pp{L.dl.x > 0 ? hi[c].x : lo[c].x, L.dl.y > 0 ? hi[c].y : lo[c].y, L.dl.z > 0 ? hi[c].z : lo[c].z};
-      bool keep = dot(pp - rc, L.dl) >= a.kappa - 1e-4f - rr;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        V3 n = pn[k];
-        V3 p{n.x > 0 ? hi[c].x : lo[c].x, n.y > 0 ? hi[c].y : lo[c].y, n.z > 0 ? hi[c].z : lo[c].z};
-        keep = keep && dot(n, p - rc) >= -pm[k];
-      }
-      if (!keep) continue;
-      todo[nt++] = code[c];
     }
+    const unsigned m = __ballot_sync(0xffffffffu, pass);
+    int todo[2];
+    int nt = 0;
+    if ((m & 0x3fu) == 0x3fu) todo[nt++] = ch.x;
+    if (((m >> 6) & 0x3fu) == 0x3fu) todo[nt++] = ch.y;
     int next = -1;
     for (int k = 0; k < nt; ++k) {
       int c2 = todo[k];
