@@ -73,7 +73,7 @@ inline float unitf(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); 
 
 // Stream tags of the third counter word (tag << 8 | light).
 enum { TAG_CAMERA = 0, TAG_LIGHT = 1, TAG_PEDGE = 2, TAG_PEDGE_LIGHT = 3,
-       TAG_SEDGE_POINT = 4, TAG_SEDGE_PICK = 5 };
+       TAG_SEDGE_POINT = 4, TAG_SEDGE_PICK = 5, TAG_PEDGE_OFFSET = 6 };
 
 // ---------------------------------------------------------------------------
 // Dual numbers: value plus N partial derivatives.
@@ -709,15 +709,25 @@ template <class T> void project(const Render& r, const V3<T>& p, T* s) {
   s[1] = ((double)r.cam_cy - Y) / (double)r.cam_k;
 }
 
-// Primary-visibility edge term (Li et al. 2018): one sample per camera
-// sample index, uniform over camera silhouette edges, uniform along the edge.
+// Primary-visibility edge term (Li et al. 2018).  The camera silhouette
+// edges in canonical order form one interval [0, nS): edge k covers
+// [k, k + 1) with parameter u = z - k along it.  The N = W*H*spp samples of a
+// render sample that interval systematically: sample i = pix*spp + s sits at
+// z_i = (i + xi0) nS / N with one uniform offset xi0 per render, so that
+// (nS / N) sum_i f(z_i) estimates sum_k int_0^1 f(k, u) du without bias.  z_i
+// is formed in FP64 (add, multiply, divide in that order).
 void primary_edge_sample(const Render& r, uint32_t pix, int s, const double* dimage, Grad& g) {
   const OracleConfig& c = *r.cfg;
   const int nS = (int)r.sil.size();
   if (nS == 0) return;
-  U4 q = philox(c.seed, c.iter, pix, (uint32_t)s, (uint32_t)(TAG_PEDGE << 8), 0);
-  int k = (int)(((uint64_t)q.v[0] * (uint64_t)nS) >> 32);
-  float u = unitf(q.v[1]);
+  U4 q0 = philox(c.seed, c.iter, 0u, 0u, (uint32_t)(TAG_PEDGE_OFFSET << 8), 0);
+  const double xi0 = (double)q0.v[0] * (1.0 / 4294967296.0);
+  const double i_s = (double)((uint64_t)pix * (uint64_t)c.spp + (uint64_t)s);
+  const double n_s = (double)c.W * c.H * c.spp;
+  double zt = (i_s + xi0) * (double)nS / n_s;
+  int k = (int)std::floor(zt);
+  if (k > nS - 1) k = nS - 1;
+  float u = (float)(zt - (double)k);
   const Edge& E = r.edges[r.sil[k]];
   float a2[2], b2[2];
   project32(r, r.v32(E.v0), a2);

@@ -24,7 +24,7 @@ constexpr float PI_F = 3.14159265358979323846f;
 
 // Stream tags of the Philox counter word 2 (tag << 8 | light).
 enum { TAG_CAMERA = 0, TAG_LIGHT = 1, TAG_PEDGE = 2, TAG_PEDGE_LIGHT = 3, TAG_SEDGE_POINT = 4,
-       TAG_SEDGE_PICK = 5 };
+       TAG_SEDGE_PICK = 5, TAG_PEDGE_OFFSET = 6 };
 enum { TERM_INTERIOR = 1, TERM_PEDGE = 2, TERM_SEDGE = 4 };
 enum { ERR_STACK = 1, ERR_STEPS = 2, ERR_WAIT = 4 };   // device error flags
 

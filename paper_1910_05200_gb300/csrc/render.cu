@@ -11,9 +11,10 @@
 // accumulators:
 //   k_bwd_interior  exact derivative of each sample's estimate with its
 //                   decisions held fixed (all lights, for dL/dl_j);
-//   k_bwd_pedge     primary-visibility edge sampling: one sample per camera
-//                   sample index, uniform over camera-silhouette edges and
-//                   uniform along the edge, radiance differenced across it;
+//   k_bwd_pedge     primary-visibility edge sampling: W*H*spp samples placed
+//                   systematically (one random offset) along the camera
+//                   silhouette edges taken together, radiance differenced
+//                   across the edge;
 //   k_bwd_sedge     shadow-boundary edge sampling: per camera sample and light
 //                   that is on, one edge picked uniformly (minimum Philox key)
 //                   among the edges that are silhouettes seen from the shading

@@ -290,17 +290,26 @@ FR_DEV void interior_sample(const RenderArgs& a, const GradBufs& gb, float* sC, 
 // ---------------------------------------------------------------------------
 // Primary-visibility edges
 
-// Edge sample tid (pixel tid / spp, sample tid % spp) of the primary-visibility
-// term.  d_image is read through L2 (__ldcg): in the batched launch another
+// Edge sample tid (Philox keys: pixel tid / spp, sample tid % spp) of the
+// primary-visibility term.  d_image is read through L2 (__ldcg): in the batched launch another
 // block of the same launch wrote it.
 FR_DEV void pedge_sample(const RenderArgs& a, const GradBufs& gb, long long tid, unsigned long long* cnt) {
   const int nS = *a.n_sil;
   if (nS <= 0) return;
   uint32_t pix = (uint32_t)(tid / a.spp);
   int s = (int)(tid - (long long)pix * a.spp);
-  U4 q = philox(a.seed, a.iter, pix, (uint32_t)s, (uint32_t)(TAG_PEDGE << 8), 0);
-  int k = (int)(((unsigned long long)q.x * (unsigned long long)nS) >> 32);
-  float u = unitf(q.y);
+  // Systematic sampling of the silhouette edges taken as one interval
+  // [0, nS) (edge k = [k, k + 1)): sample tid at z = (tid + xi0) nS / N with
+  // one uniform offset xi0 per launch, formed in FP64 (add, multiply, divide);
+  // (nS / N) sum f(z) is an unbiased estimate of the edge integrals, and
+  // neighbouring threads walk along one edge (coherent rays).
+  U4 q0 = philox(a.seed, a.iter, 0u, 0u, (uint32_t)(TAG_PEDGE_OFFSET << 8), 0);
+  const double xi0 = (double)q0.x * 2.3283064365386963e-10;            // 2^-32
+  const double n_s = (double)((long long)a.W * a.H * a.spp);
+  const double zt = __ddiv_rn(__dmul_rn(__dadd_rn((double)tid, xi0), (double)nS), n_s);
+  int k = (int)floor(zt);
+  if (k > nS - 1) k = nS - 1;
+  float u = __double2float_rn(__dsub_rn(zt, (double)k));
   int4 E = a.edges_canon[a.sil[k]];
   V3 A = v3(a.mesh.X[E.x]), B = v3(a.mesh.X[E.y]);
   float ax, ay, bx, by;
