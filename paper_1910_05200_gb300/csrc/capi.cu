@@ -18,6 +18,12 @@ using namespace fr;
 
 namespace {
 
+// Edges per leaf of the edge hierarchy (the most a leaf code holds).  A node
+// visit of the warp-wide search is a dependent round trip to memory, while
+// the edges of a leaf load independently: measured on the full face,
+// leaves of 8 edges beat 6, 4, 2 and 1.
+constexpr int EDGE_LEAF = 8;
+
 // Binary BVH in the device layout of common.cuh plus the refit topology.
 struct HostBVH {
   std::vector<float4> nodes;          // 4 per node
@@ -38,14 +44,16 @@ struct Box {
   }
 };
 
-// Binned surface-area-heuristic build (12 bins per axis, leaves of <= 4).
+// Binned surface-area-heuristic build (12 bins per axis, leaves of at most
+// `leaf` primitives, 1..8).
 struct Builder {
   const std::vector<Box>& boxes;
   std::vector<float> cen;            // [n*3]
   std::vector<int>& perm;
   HostBVH& out;
-  static constexpr int LEAF = 4, BINS = 12;
-  Builder(const std::vector<Box>& b, HostBVH& o) : boxes(b), perm(o.perm), out(o) {
+  static constexpr int BINS = 12;
+  const int LEAF;
+  Builder(const std::vector<Box>& b, HostBVH& o, int leaf = 4) : boxes(b), perm(o.perm), out(o), LEAF(leaf) {
     size_t n = b.size();
     cen.resize(3 * n);
     perm.resize(n);
@@ -525,7 +533,7 @@ int fr_upload_mesh(fr_ctx* ctx, const float* mean, int32_t V, const int32_t* tri
   }
   HostBVH ht, he2;
   { Builder b(tb, ht); b.run(); }
-  { Builder b(eb, he2); b.run(); }
+  { Builder b(eb, he2, EDGE_LEAF); b.run(); }
   std::vector<int4> tris4(F), edges_leaf(E);
   for (int f = 0; f < F; ++f) tris4[f] = make_int4(tris[3 * f], tris[3 * f + 1], tris[3 * f + 2], 0);
   for (int i = 0; i < E; ++i) edges_leaf[i] = edges[he2.perm[i]];
