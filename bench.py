@@ -304,7 +304,8 @@ def run_ours(args):
             "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": RF.SEDGE_TRAFFIC_BYTES,
             "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x median SM clock under load",
             "flops_per_launch": flops_sedge, "ms_per_launch": ph_mean["shadow_edges"],
-            "counts_sedge": cnt[12:16]}
+            "counts_sedge": dict(zip(("ray_nodes", "tri_tests", "edge_nodes_per_warp", "edge_tests", "clip_tests"),
+                                     cnt[RF.K_SEDGE:RF.K_SEDGE + 5]))}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Msamples/s", "n_gpus": world, "steps": args.steps,

@@ -191,9 +191,11 @@ int fr_light_stage(const fr_ctx* ctx, float* out);
  * fr_sync, FR_ERR_CUDA if the stream reported an error, else FR_OK. */
 int fr_sync(fr_ctx* ctx);
 
-/* Work counts of the last fr_render / fr_render_backward call, read back
- * after a stream synchronisation.  out[16]: four counts (BVH nodes visited,
- * triangle tests, edge-BVH nodes visited, edge tests) for each of the
+/* Work counts of the last fr_render / fr_render_backward call (or batch
+ * step), read back after a stream synchronisation.  out[20]: five counts
+ * (BVH nodes visited by rays, triangle tests, edge-hierarchy nodes visited
+ * -- once per warp, the search being warp-wide --, edge tests per lane,
+ * clip tests of edges that passed the silhouette test) for each of the
  * forward, interior, primary-edge and shadow-edge kernels, in that order.
  * Collected only when enabled with fr_set_counters(ctx, 1). */
 int fr_set_counters(fr_ctx* ctx, int32_t enable);

@@ -49,7 +49,7 @@ FR_DEV void sample_adjoints(const RenderArgs& a, const GradBufs& g, float* sC, f
   valid = valid && hit.x >= 0 && (dv.x != 0.0f || dv.y != 0.0f || dv.z != 0.0f);
   if (valid) {
     d = sample_dir(a, px, py, s, pix);
-    interior_sample(a, g, sC, sL, pix, s, d, hit.x, __int_as_float(hit.y), dv, cnt ? cnt + 4 : nullptr);
+    interior_sample(a, g, sC, sL, pix, s, d, hit.x, __int_as_float(hit.y), dv, cnt ? cnt + CNT_INTERIOR : nullptr);
     wrgb = dv * (1.0f / (float)a.spp);
     flip = face_flip(a.mesh, hit.x, d);
     x32 = hit_point(a.cam.o, d, __int_as_float(hit.y));
@@ -57,7 +57,7 @@ FR_DEV void sample_adjoints(const RenderArgs& a, const GradBufs& g, float* sC, f
   // shadow edges, warp-collective: every lane takes part for every light
   for (int j = 0; j < a.n_lights; ++j) {
     if (!light_on(a, j)) continue;                 // uniform
-    sedge_pick_and_add(a, g, j, valid, d, x32, hit.x, flip, pix, s, wrgb, cnt ? cnt + 12 : nullptr);
+    sedge_pick_and_add(a, g, j, valid, d, x32, hit.x, flip, pix, s, wrgb, cnt ? cnt + CNT_SEDGE : nullptr);
   }
 }
 
@@ -139,7 +139,7 @@ FR_DEV void tile_large(WarpState& w, const BatchFrame& F, float* sC, int tile, i
     for (int s = lane; s < spp; s += 32) {
       V3 d = sample_dir(a, px, py, s, pix);
       float t = 0.0f;
-      int f = closest_hit(a.mesh, a.cam.o, d, t, a.err, cnt ? cnt + 4 : nullptr);
+      int f = closest_hit(a.mesh, a.cam.o, d, t, a.err, cnt ? cnt + CNT_INTERIOR : nullptr);
       sample_adjoints(a, w.g, sC, w.sL, true, px, py, s, make_int2(f, __float_as_int(t)), dv, cnt);
     }
   }
@@ -208,7 +208,7 @@ FR_DEV void batch_step_body(const BatchArgs& b) {
     skip = __shfl_sync(0xffffffffu, skip, 0);
     if (skip) continue;
     const long long base = (long long)it.y * b.pedge_chunk;
-    unsigned long long* cnt_p = b.counters ? b.counters + 8 : nullptr;
+    unsigned long long* cnt_p = b.counters ? b.counters + CNT_PEDGE : nullptr;
     for (int k = lane; k < b.pedge_chunk; k += 32) {
       long long t = base + k;
       if (t < F.n_pedge) pedge_sample(w.a, w.g, t, cnt_p);
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(256, 3) k_batch_fwd(PhaseArgs p) {
   if (valid) dv = pixel_loss(F, pix, V3{v0 * inv, v1 * inv, v2 * inv}, s == 0, lacc);
   bool adj = valid && hit.x >= 0 && (dv.x != 0.0f || dv.y != 0.0f || dv.z != 0.0f);
   if (tid < total) g.hits[tid] = adj ? hit : make_int2(-1, 0);
-  if (adj) interior_sample(a, g, sC, sL, pix, s, d, hit.x, __int_as_float(hit.y), dv, cnt ? cnt + 4 : nullptr);
+  if (adj) interior_sample(a, g, sC, sL, pix, s, d, hit.x, __int_as_float(hit.y), dv, cnt ? cnt + CNT_INTERIOR : nullptr);
   for (int off = 16; off > 0; off >>= 1) lacc += __shfl_xor_sync(0xffffffffu, lacc, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lacc;
   __syncthreads();
@@ -343,7 +343,7 @@ FR_DEV void batch_sedge_body(const PhaseArgs& p) {
     flip = face_flip(a.mesh, fh, d);
     x32 = hit_point(a.cam.o, d, __int_as_float(hit.y));
   }
-  sedge_pick_and_add(a, gb, j, valid, d, x32, fh, flip, pix, s, wrgb, p.counters ? p.counters + 12 : nullptr);
+  sedge_pick_and_add(a, gb, j, valid, d, x32, fh, flip, pix, s, wrgb, p.counters ? p.counters + CNT_SEDGE : nullptr);
 }
 
 __global__ void __launch_bounds__(256, 3) k_batch_sedge3(PhaseArgs p) { batch_sedge_body(p); }
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(256, 4) k_batch_pedge(PhaseArgs p) {
   const GradBufs& gb = *reinterpret_cast<const GradBufs*>(g_raw);
   long long tid = (long long)(blockIdx.x - p.block_start[f]) * blockDim.x + threadIdx.x;
   if (tid >= (long long)a.W * a.H * a.spp) return;
-  pedge_sample(a, gb, tid, p.counters ? p.counters + 8 : nullptr);
+  pedge_sample(a, gb, tid, p.counters ? p.counters + CNT_PEDGE : nullptr);
 }
 
 // The persistent kernel at three register budgets (launch bounds of 256

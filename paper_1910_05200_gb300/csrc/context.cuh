@@ -39,7 +39,7 @@ using fr::DevBVH;
 using fr::Light;
 using fr::CS;
 
-constexpr int NCOUNT = 16;   // work counters: 4 per render kernel
+constexpr int NCOUNT = fr::CNT_TOTAL;   // work counters: 5 per render kernel
 constexpr int NPHASE = 7;    // timed phases
 enum { PH_GEOMETRY = 0, PH_FORWARD, PH_INTERIOR, PH_PEDGE, PH_SEDGE, PH_ADJOINT, PH_LOSS };
 

@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(256, 3) k_bwd_interior(RenderArgs a, GradBufs 
   long long total = (long long)tiled_pixel_count(a.W, a.H) * spp;
   int ip = (int)(tid / spp), s = (int)(tid - (long long)ip * spp);
   int px = 0, py = 0;
-  unsigned long long* cnt = a.counters ? a.counters + 4 : nullptr;    // interior: 4..7
+  unsigned long long* cnt = a.counters ? a.counters + CNT_INTERIOR : nullptr;
   bool in_image = tid < total && tile_pixel(ip, a.W, a.H, px, py);
   if (tid < total && !in_image && gb.hits) gb.hits[tid] = make_int2(-1, 0);
   if (in_image) {
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(256, 3) k_bwd_interior(RenderArgs a, GradBufs 
 __global__ void __launch_bounds__(256, 4) k_bwd_pedge(RenderArgs a, GradBufs gb) {
   long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= (long long)a.W * a.H * a.spp) return;
-  pedge_sample(a, gb, tid, a.counters ? a.counters + 8 : nullptr);    // primary edges: counters 8..11
+  pedge_sample(a, gb, tid, a.counters ? a.counters + CNT_PEDGE : nullptr);
 }
 
 // One thread per (light, camera sample), light-major: a warp serves one light
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(256, 4) k_bwd_sedge(RenderArgs a, GradBufs gb)
     flip = face_flip(a.mesh, f, d);
     x32 = hit_point(a.cam.o, d, t);
   }
-  sedge_pick_and_add(a, gb, j, valid, d, x32, f, flip, pix, s, wrgb, a.counters ? a.counters + 12 : nullptr);
+  sedge_pick_and_add(a, gb, j, valid, d, x32, f, flip, pix, s, wrgb, a.counters ? a.counters + CNT_SEDGE : nullptr);
 }
 
 }  // namespace fr

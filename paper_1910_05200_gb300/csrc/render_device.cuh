@@ -499,7 +499,7 @@ FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int
   }
   int stack[STACK];
   int sp = 0, node = 0, steps = 0;
-  unsigned long long nvis = 0, nedge = 0;
+  unsigned long long nvis = 0, nedge = 0, nclip = 0;
   while (true) {
     if (++steps > MAX_STEPS) { atomicOr(a.err, ERR_STEPS); break; }
     ++nvis;
@@ -557,6 +557,7 @@ FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int
           if (!packed_silhouette(R, x, f1)) continue;
           float4 r0 = R[0];
           float t0, t1;
+          ++nclip;
           if (!shadow_clip(v3(r0), v3(r1), x, L, hs, a.kappa, t0, t1)) continue;
           int id = __float_as_int(r0.w);
           uint32_t key = philox(a.seed, a.iter, pix, (uint32_t)s, (uint32_t)(TAG_SEDGE_PICK << 8 | j), (uint32_t)id).x;
@@ -578,7 +579,7 @@ FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int
   }
 done:
   if (cnt && (threadIdx.x & 31) == 0) { atomicAdd(cnt + 2, nvis); }
-  if (cnt) atomicAdd(cnt + 3, nedge);
+  if (cnt) { atomicAdd(cnt + 3, nedge); atomicAdd(cnt + 4, nclip); }
   return P;
 }
 

@@ -304,7 +304,7 @@ class Renderer:
         return dict(zip(self.PHASES, out.tolist()))
 
     def counters(self):
-        out = np.zeros(16, np.uint64)
+        out = np.zeros(20, np.uint64)
         self._check(self.lib.fr_get_counters(self.ctx, _hptr(out)), "fr_get_counters")
         return out
 

@@ -12,12 +12,15 @@ from __future__ import annotations
 # FLOPs per operation
 NODE_VISIT = 40        # two child slab tests: 6 sub, 6 mul, 10 min/max, 2 cmp each
 TRI_TEST = 40          # watertight test: 9 sub, 6 mul + 6 sub (shear), 9 edge-fn ops, 3+6 for T, div
-EDGE_NODE_VISIT = 200  # two children: box vs 5 pyramid planes (~55) + normal-cone test (~45) each
-EDGE_TEST = 110        # 2 silhouette tests (16) + clip of 2 endpoints against 5 planes (~94)
+EDGE_NODE_VISIT = 200  # two children: box vs 5 pyramid planes (~45) + normal-cone test (~55) each
+EDGE_TEST = 20         # adjacency check + 2 silhouette plane tests (3 sub, 3 mul, 2 add each)
+CLIP_TEST = 90         # clip of both endpoints against the 5 planes of the light pyramid
 
-# Counting in k_bwd_sedge: the edge-BVH descent is shared by the 32 lanes of
-# a warp (one traversal of the warp's bounding sphere), so an edge-BVH visit
-# is counted once per warp; edge tests are per lane.
+# Counter layout (fr_get_counters): 5 per kernel -- ray BVH nodes, triangle
+# tests, edge-hierarchy nodes (once per warp: the 32 lanes share one descent),
+# edge tests (per lane), clip tests -- for forward, interior, primary edges,
+# shadow edges.
+K_FWD, K_INTERIOR, K_PEDGE, K_SEDGE = 0, 5, 10, 15
 
 # DRAM bytes of one k_bwd_sedge launch at 256x256x16 spp from a 1-pass ncu
 # capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum);
@@ -31,22 +34,24 @@ SMS = 152
 FP32_LANES = 128
 
 
+def _kernel_flops(cnt, k):
+    return (cnt[k] * NODE_VISIT + cnt[k + 1] * TRI_TEST + cnt[k + 2] * EDGE_NODE_VISIT + cnt[k + 3] * EDGE_TEST
+            + cnt[k + 4] * CLIP_TEST)
+
+
 def forward_flops(cnt, samples: int, n_on: int) -> float:
-    return cnt[0] * NODE_VISIT + cnt[1] * TRI_TEST + samples * n_on * SHADE_FWD
+    return _kernel_flops(cnt, K_FWD) + samples * n_on * SHADE_FWD
 
 
 def backward_flops(cnt, samples: int, n_on: int) -> float:
-    """All backward kernels: counters 4..15."""
+    """All backward kernels."""
     shading = samples * (N_LIGHTS * SHADE_BWD + 2 * n_on * SHADE_FWD)
-    trav = 0
-    for k in (4, 8, 12):
-        trav += cnt[k] * NODE_VISIT + cnt[k + 1] * TRI_TEST + cnt[k + 2] * EDGE_NODE_VISIT + cnt[k + 3] * EDGE_TEST
-    return trav + shading
+    return sum(_kernel_flops(cnt, k) for k in (K_INTERIOR, K_PEDGE, K_SEDGE)) + shading
 
 
 def sedge_flops(cnt) -> float:
-    """Shadow-edge kernel: counters 12..15 (its shadow rays, its edge search)."""
-    return cnt[12] * NODE_VISIT + cnt[13] * TRI_TEST + cnt[14] * EDGE_NODE_VISIT + cnt[15] * EDGE_TEST
+    """Shadow-edge kernel: its shadow rays and its edge search."""
+    return _kernel_flops(cnt, K_SEDGE)
 
 
 def fp32_peak_tflops(sm_mhz: float | None) -> float:
