@@ -75,11 +75,22 @@ typedef struct fr_config {
   float shadow_tmin;
   float clip_kappa;
   int32_t n_lights;  /* 1..32 */
+  /* Readings of what the paper leaves open:
+   * brdf_model 0 = Beckmann D with the Cook-Torrance V-cavity G, 1 = GGX D
+   * with the separable Smith G (beckmann_m is then GGX alpha);
+   * fresnel 0 = F folded into c_spec, 1 = Schlick F with c_spec as the
+   * reflectance at normal incidence;
+   * light_layout 0 = Fibonacci points on the hemisphere, 1 = the 20 upper
+   * vertices of a once-subdivided icosahedron (needs n_lights = 20). */
+  int32_t brdf_model;
+  int32_t fresnel;
+  int32_t light_layout;
 } fr_config;
 
 /* Fill *cfg with the library defaults (tan_half_fov 0.275, d_cam 4,
  * light_radius 3, light_side 0.6, beckmann_m 0.3, eps_pedge 1e-3,
- * eps_sedge 2e-4, shadow_tmin 1e-4, clip_kappa 1e-5, n_lights 20). */
+ * eps_sedge 2e-4, shadow_tmin 1e-4, clip_kappa 1e-5, n_lights 20,
+ * brdf_model 0, fresnel 0, light_layout 0). */
 void fr_default_config(fr_config* cfg);
 
 /* Per-call render options.  Samples are drawn from Philox4x32-10 keyed by

@@ -132,6 +132,9 @@ struct OracleConfig {
   float eps_pedge, eps_sedge, shadow_tmin, clip_kappa;
   int32_t n_lights, shade_mode, n_threads, terms;
   int32_t value_mesh;   // 0: values on the FP64 posed mesh; 1: on the posed mesh rounded to FP32
+  int32_t brdf_model;   // 0 Beckmann D + Cook-Torrance V-cavity G; 1 GGX D + separable Smith G
+  int32_t fresnel;      // 0 F folded into c_spec; 1 Schlick F with c_spec as normal-incidence reflectance
+  int32_t light_layout; // 0 Fibonacci hemisphere; 1 upper 20 vertices of a once-subdivided icosahedron
 };
 struct OracleScene {
   int32_t V, F, K_id, K_exp, K_alb;
@@ -161,14 +164,63 @@ struct Light {           // one square area light; float frame is the definition
   float c[3], e1[3], e2[3], dl[3];   // centre, in-plane axes, unit direction from origin
 };
 
-// Light stage: Fibonacci points on the hemisphere z >= 0 (camera side), each
-// a square facing the origin.
-std::vector<Light> light_stage(int n, double radius) {
+// Light directions on the hemisphere z >= 0 (camera side).
+// Layout 0: Fibonacci points, height (k + 1/2)/n, azimuth k times the golden
+// angle pi (3 - sqrt 5).  Layout 1 (20 lights): the icosahedron with vertices
+// the cyclic permutations of (0, +-1, +-phi), once subdivided (unit vertices
+// plus the unit midpoints of its 30 edges: 42 directions), rotated about the
+// x axis so that (0, 1, phi^2) points along +z; the 20 directions strictly
+// above the horizon, ordered by height (descending) and then azimuth; a
+// component below 1e-12 counts as exactly zero.
+std::vector<std::array<double, 3>> stage_directions(int n, int layout) {
+  std::vector<std::array<double, 3>> out;
+  if (layout != 1) {
+    const double golden = PI * (3.0 - std::sqrt(5.0));
+    for (int k = 0; k < n; ++k) {
+      double z = (k + 0.5) / n, rho = std::sqrt(1.0 - z * z);
+      out.push_back({rho * std::cos(k * golden), rho * std::sin(k * golden), z});
+    }
+    return out;
+  }
+  const double g = (1.0 + std::sqrt(5.0)) / 2.0, s = 1.0 / std::sqrt(1.0 + g * g);
+  const double ico[12][3] = {{0, 1, g}, {0, -1, g}, {0, 1, -g}, {0, -1, -g}, {1, g, 0}, {-1, g, 0},
+                             {1, -g, 0}, {-1, -g, 0}, {g, 0, 1}, {-g, 0, 1}, {g, 0, -1}, {-g, 0, -1}};
+  std::vector<std::array<double, 3>> dirs;
+  for (auto& v : ico) dirs.push_back({v[0] * s, v[1] * s, v[2] * s});
+  // neighbours on the unit icosahedron have cosine 1/sqrt(5)
+  for (int i = 0; i < 12; ++i)
+    for (int j = i + 1; j < 12; ++j) {
+      double c = dirs[i][0] * dirs[j][0] + dirs[i][1] * dirs[j][1] + dirs[i][2] * dirs[j][2];
+      if (std::fabs(c - 1.0 / std::sqrt(5.0)) > 1e-9) continue;
+      double m[3] = {dirs[i][0] + dirs[j][0], dirs[i][1] + dirs[j][1], dirs[i][2] + dirs[j][2]};
+      double l = std::sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+      dirs.push_back({m[0] / l, m[1] / l, m[2] / l});
+    }
+  const double ang = std::atan2(1.0, g * g);
+  const double Rm[3][3] = {{1, 0, 0}, {0, std::cos(ang), -std::sin(ang)}, {0, std::sin(ang), std::cos(ang)}};
+  for (auto& d : dirs) {
+    std::array<double, 3> r{};
+    for (int i = 0; i < 3; ++i) {
+      r[i] = Rm[i][0] * d[0] + Rm[i][1] * d[1] + Rm[i][2] * d[2];
+      if (std::fabs(r[i]) < 1e-12) r[i] = 0.0;   // round-off zeros made exact, so ties order alike
+    }
+    if (r[2] > 1e-9) out.push_back(r);
+  }
+  std::stable_sort(out.begin(), out.end(), [](const std::array<double, 3>& p, const std::array<double, 3>& q) {
+    if (std::fabs(p[2] - q[2]) > 1e-9) return p[2] > q[2];
+    return std::atan2(p[1], p[0]) < std::atan2(q[1], q[0]);
+  });
+  out.resize(n);
+  return out;
+}
+
+// Light stage: one square per direction, centred at radius * d and facing
+// the origin; e1 = normalize(+y x d), e2 = d x e1.
+std::vector<Light> light_stage(int n, double radius, int layout) {
+  std::vector<std::array<double, 3>> dirs = stage_directions(n, layout);
   std::vector<Light> L(n);
-  const double ga = PI * (3.0 - std::sqrt(5.0));
   for (int k = 0; k < n; ++k) {
-    double z = (k + 0.5) / n, r = std::sqrt(1.0 - z * z), ph = k * ga;
-    double d[3] = {r * std::cos(ph), r * std::sin(ph), z};
+    const double* d = dirs[k].data();
     // e1 = normalize(up x d) with up = +y; e2 = d x e1
     double e1[3] = {d[2], 0.0, -d[0]};
     double n1 = std::sqrt(e1[0] * e1[0] + e1[2] * e1[2]);
@@ -366,7 +418,7 @@ int prepare(Render& r) {
   }
   int rc = build_edges(r);
   if (rc) return rc;
-  r.lights = light_stage(r.NL, r.cfg->light_radius);
+  r.lights = light_stage(r.NL, r.cfg->light_radius, r.cfg->light_layout);
   // Camera: pinhole at (0,0,d_cam) looking down -z, square pixels.
   const OracleConfig& c = *r.cfg;
   r.cam_o[0] = 0.0f; r.cam_o[1] = 0.0f; r.cam_o[2] = c.d_cam;
@@ -496,9 +548,23 @@ template <class T> void bilinear(const T& u, const T& v, int* idx, T* w) {
 
 // Unshadowed integrand of one light at light point y, without the light's area:
 // h = l (x) f_r(wi, wo) cos_x cos_y / d^2   (RGB).
+// Reflectance readings (the Face Modeling paragraph names Cook-Torrance
+// without its terms): roughness m; model 0 = Beckmann distribution
+// exp(-tan^2/m^2) / (pi m^2 cos^4) with the V-cavity masking
+// min(1, 2 (n.h)(n.wo)/(wo.h), 2 (n.h)(n.wi)/(wo.h)); model 1 = GGX
+// distribution a^2 / (pi ((n.h)^2 (a^2 - 1) + 1)^2), a = m, with Smith
+// masking G1(wi) G1(wo), G1(c) = 2c / (c + sqrt(a^2 + (1 - a^2) c^2));
+// fresnel 0: the specular term is scaled by c_spec; fresnel 1: by Schlick's
+// c_spec + (1 - c_spec)(1 - wo.h)^5.
+struct Brdf {
+  double m;
+  int model, fresnel;
+};
+inline Brdf brdf_of(const OracleConfig& c) { return Brdf{(double)c.beckmann_m, c.brdf_model, c.fresnel}; }
+
 template <class T>
 V3<T> light_integrand(const V3<T>& x, const V3<T>& ns, const V3<T>& wo, const V3<T>& rho, const T& cs,
-                      const V3<T>& l, const V3<double>& y, const V3<double>& dl, double m) {
+                      const V3<T>& l, const V3<double>& y, const V3<double>& dl, const Brdf& b) {
   V3<T> w = lift<T>(y) - x;
   T d2 = dot(w, w);
   V3<T> wi = w / sqrt(d2);
@@ -507,18 +573,33 @@ V3<T> light_integrand(const V3<T>& x, const V3<T>& ns, const V3<T>& wo, const V3
   T cy = dot(lift<T>(dl), wi);
   if (!(val(cy) > 0.0)) return V3<T>();
   T co = dot(ns, wo);
-  T spec(0.0);
+  T spec(0.0), F = cs;
   if (val(co) > 0.0) {
     V3<T> h = normalize(wi + wo);
     T ch = dot(ns, h), oh = dot(wo, h);
     T ch2 = ch * ch;
-    T tan2 = (T(1.0) - ch2) / ch2;
-    T D = exp(-tan2 / (m * m)) / (PI * m * m * ch2 * ch2);
-    T G = tmin(T(1.0), tmin(T(2.0) * ch * co / oh, T(2.0) * ch * ci / oh));
+    const double m = b.m;
+    T D, G;
+    if (b.model == 0) {
+      T tan2 = (T(1.0) - ch2) / ch2;
+      D = exp(-tan2 / (m * m)) / (PI * m * m * ch2 * ch2);
+      G = tmin(T(1.0), tmin(T(2.0) * ch * co / oh, T(2.0) * ch * ci / oh));
+    } else {
+      const double a2 = m * m;
+      T den = ch2 * (a2 - 1.0) + T(1.0);
+      D = T(a2) / (PI * den * den);
+      T gi = T(2.0) * ci / (ci + sqrt(T(a2) + (1.0 - a2) * ci * ci));
+      T go = T(2.0) * co / (co + sqrt(T(a2) + (1.0 - a2) * co * co));
+      G = gi * go;
+    }
     spec = D * G / (T(4.0) * ci * co);
+    if (b.fresnel) {
+      T q = T(1.0) - oh;
+      F = cs + (T(1.0) - cs) * (q * q * q * q * q);
+    }
   }
   T geo = ci * cy / d2;
-  T sp = cs * spec;
+  T sp = F * spec;
   return V3<T>(l.x * (rho.x / PI + sp) * geo, l.y * (rho.y / PI + sp) * geo, l.z * (rho.z / PI + sp) * geo);
 }
 
@@ -577,7 +658,7 @@ V3<double> radiance(const Render& r, const float* o, const float* d, int tag, ui
     ++n_vis;
     const float* l = r.lightrgb(j);
     V3<double> hv = light_integrand<double>(S.x, S.ns, S.wo, S.rho, cs, V3<double>(l[0], l[1], l[2]),
-                                            widen(y32), widen(r.lights[j].dl), r.cfg->beckmann_m);
+                                            widen(y32), widen(r.lights[j].dl), brdf_of(*r.cfg));
     L = L + hv * area;
   }
   if (aux) {
@@ -680,7 +761,7 @@ void interior_sample(const Render& r, const float* o, const float* d, const Hit&
     if (!visible(r, x32, y32, h.f, flip)) continue;
     const float* l = r.lightrgb(j);
     V3<DI> lv(DI::var(l[0], 31), DI::var(l[1], 32), DI::var(l[2], 33));
-    V3<DI> hv = light_integrand<DI>(S.x, S.ns, S.wo, S.rho, cs, lv, widen(y32), widen(r.lights[j].dl), r.cfg->beckmann_m);
+    V3<DI> hv = light_integrand<DI>(S.x, S.ns, S.wo, S.rho, cs, lv, widen(y32), widen(r.lights[j].dl), brdf_of(*r.cfg));
     double w[3] = {dimg[0] * inv_spp * area, dimg[1] * inv_spp * area, dimg[2] * inv_spp * area};
     double gin[NI];
     for (int k = 0; k < NI; ++k) gin[k] = w[0] * hv.x.d[k] + w[1] * hv.y.d[k] + w[2] * hv.z.d[k];
@@ -894,8 +975,8 @@ void shadow_edge_sample(const Render& r, const float* o, const float* d, const H
   const float* l = r.lightrgb(j);
   V3<double> lv(l[0], l[1], l[2]);
   V3<double> gp, gm;
-  if (vp) gp = light_integrand<double>(S.x, S.ns, S.wo, S.rho, cs, lv, widen(yp), widen(L.dl), c.beckmann_m);
-  if (vm) gm = light_integrand<double>(S.x, S.ns, S.wo, S.rho, cs, lv, widen(ym), widen(L.dl), c.beckmann_m);
+  if (vp) gp = light_integrand<double>(S.x, S.ns, S.wo, S.rho, cs, lv, widen(yp), widen(L.dl), brdf_of(c));
+  if (vm) gm = light_integrand<double>(S.x, S.ns, S.wo, S.rho, cs, lv, widen(ym), widen(L.dl), brdf_of(c));
   double delta = wrgb[0] * (gm.x - gp.x) + wrgb[1] * (gm.y - gp.y) + wrgb[2] * (gm.z - gp.z);
   if (delta == 0.0) return;
   double dmass = std::fabs(wrgb[0]) * (std::fabs(gm.x) + std::fabs(gp.x)) +
@@ -1058,8 +1139,9 @@ int oracle_n_edges(const OracleConfig* cfg, const OracleScene* sc, const float* 
   return (int)r.edges.size();
 }
 
-void oracle_light_stage(int32_t n, float radius, float* out /*[n*12]: c, e1, e2, dl*/) {
-  std::vector<Light> L = light_stage(n, radius);
+void oracle_light_stage(int32_t n, float radius, int32_t layout, float* out /*[n*12]: c, e1, e2, dl*/) {
+  if (layout == 1 && n != 20) return;
+  std::vector<Light> L = light_stage(n, radius, layout);
   for (int k = 0; k < n; ++k)
     for (int i = 0; i < 3; ++i) {
       out[12 * k + i] = L[k].c[i]; out[12 * k + 3 + i] = L[k].e1[i];
@@ -1230,13 +1312,13 @@ double oracle_loss(const OracleConfig* cfg, const OracleScene* sc, const float* 
 void oracle_light_estimate(const OracleConfig* cfg, const double* x, const double* ns, const double* wo,
                            const double* rho, double cs, const float* lrgb, int32_t j, float u2, float u3,
                            double* out) {
-  std::vector<Light> L = light_stage(cfg->n_lights, cfg->light_radius);
+  std::vector<Light> L = light_stage(cfg->n_lights, cfg->light_radius, cfg->light_layout);
   float y[3];
   light_point32(L[j], cfg->light_side, u2, u3, y);
   V3<double> hv = light_integrand<double>(V3<double>(x[0], x[1], x[2]), V3<double>(ns[0], ns[1], ns[2]),
                                           V3<double>(wo[0], wo[1], wo[2]), V3<double>(rho[0], rho[1], rho[2]), cs,
                                           V3<double>(lrgb[0], lrgb[1], lrgb[2]), widen(y), widen(L[j].dl),
-                                          cfg->beckmann_m);
+                                          brdf_of(*cfg));
   double A = (double)cfg->light_side * cfg->light_side;
   out[0] = hv.x * A; out[1] = hv.y * A; out[2] = hv.z * A;
 }
@@ -1249,7 +1331,7 @@ void oracle_brdf(const OracleConfig* cfg, const double* n, const double* wi, con
   V3<double> hv = light_integrand<double>(x, V3<double>(n[0], n[1], n[2]), V3<double>(wo[0], wo[1], wo[2]),
                                           V3<double>(rho, rho, rho), cs, V3<double>(1, 1, 1),
                                           V3<double>(wi[0], wi[1], wi[2]), V3<double>(wi[0], wi[1], wi[2]),
-                                          cfg->beckmann_m);
+                                          brdf_of(*cfg));
   double ci = n[0] * wi[0] + n[1] * wi[1] + n[2] * wi[2];
   *out = ci > 0 ? hv.x / ci : 0.0;
 }
@@ -1273,7 +1355,7 @@ int oracle_point_shade(const OracleConfig* cfg, const OracleScene* sc, const flo
   double cs = cspec_value(r, S.u, S.v);
   const float* l = r.lightrgb(j);
   V3<double> hv = light_integrand<double>(S.x, S.ns, S.wo, S.rho, cs, V3<double>(l[0], l[1], l[2]), widen(y32),
-                                          widen(r.lights[j].dl), cfg->beckmann_m);
+                                          widen(r.lights[j].dl), brdf_of(*cfg));
   double A = (double)cfg->light_side * cfg->light_side;
   out[0] = hv.x * A; out[1] = hv.y * A; out[2] = hv.z * A;
   return 0;

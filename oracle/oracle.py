@@ -41,7 +41,8 @@ class OracleConfig(C.Structure):
                 ("eps_sedge", C.c_float), ("shadow_tmin", C.c_float),
                 ("clip_kappa", C.c_float),
                 ("n_lights", C.c_int32), ("shade_mode", C.c_int32),
-                ("n_threads", C.c_int32), ("terms", C.c_int32), ("value_mesh", C.c_int32)]
+                ("n_threads", C.c_int32), ("terms", C.c_int32), ("value_mesh", C.c_int32),
+                ("brdf_model", C.c_int32), ("fresnel", C.c_int32), ("light_layout", C.c_int32)]
 
 
 class OracleScene(C.Structure):
@@ -55,7 +56,7 @@ class OracleScene(C.Structure):
 # Scene constants (one reading of what the paper leaves open).
 DEFAULTS = dict(tan_half_fov=0.275, d_cam=4.0, light_radius=3.0, light_side=0.6,
                 beckmann_m=0.3, eps_pedge=1e-3, eps_sedge=2e-4, shadow_tmin=1e-4,
-                clip_kappa=1e-5, n_lights=20)
+                clip_kappa=1e-5, n_lights=20, brdf_model=0, fresnel=0, light_layout=0)
 
 
 def default_config(W=64, H=64, spp=4, seed=0, iter=0, shade_mode=0, n_threads=0, terms=0,
@@ -82,7 +83,7 @@ class Oracle:
         vp = C.c_void_p
         L.oracle_philox.argtypes = [C.c_uint32] * 6 + [vp]
         L.oracle_n_edges.argtypes = [vp, vp, vp, vp]
-        L.oracle_light_stage.argtypes = [C.c_int32, C.c_float, vp]
+        L.oracle_light_stage.argtypes = [C.c_int32, C.c_float, C.c_int32, vp]
         L.oracle_geometry.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.oracle_render.argtypes = [vp, vp, vp, vp, C.c_int32, vp, vp, vp]
         L.oracle_render_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -125,9 +126,11 @@ class Oracle:
         self.lib.oracle_n_edges(C.byref(cfg), C.byref(s), _ptr(th), _ptr(out))
         return out
 
-    def light_stage(self, n=20, radius=3.0):
+    def light_stage(self, n=20, radius=3.0, layout=0):
+        """[n, 12]: centre, e1, e2, unit direction of each light (layout 0
+        Fibonacci, 1 icosphere, n = 20 only)."""
         out = np.zeros((n, 12), np.float32)
-        self.lib.oracle_light_stage(n, radius, _ptr(out))
+        self.lib.oracle_light_stage(n, radius, layout, _ptr(out))
         return out
 
     def geometry(self, cfg, scene, theta):

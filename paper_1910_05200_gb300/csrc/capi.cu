@@ -191,13 +191,66 @@ template <class T> cudaError_t upload(DBuf<T>& b, const T* h, size_t n, cudaStre
   return cudaStreamSynchronize(s);
 }
 
-// Light stage: Fibonacci points on the hemisphere z >= 0, squares facing the origin.
-std::vector<Light> make_lights(int n, double radius) {
+// Unit directions of the light stage (Face Modeling paragraph: lights on an
+// isotropically sampled hemisphere, the camera side z >= 0).
+//   layout 0: Fibonacci points, z_k = (k + 1/2)/n, azimuth k pi (3 - sqrt 5);
+//   layout 1 (n = 20): the 42 vertices of a once-subdivided icosahedron
+//     (vertices (0, +-1, +-phi) and cyclic, plus the normalised edge
+//     midpoints), turned about x so that the axis (0, 1, phi^2) becomes +z;
+//     the 20 strictly above z = 0, by height (descending) then azimuth
+//     (components below 1e-12 set to zero first).
+std::vector<std::array<double, 3>> light_dirs(int n, int layout) {
+  std::vector<std::array<double, 3>> d;
+  if (layout == 0) {
+    const double ga = 3.14159265358979323846 * (3.0 - std::sqrt(5.0));
+    for (int k = 0; k < n; ++k) {
+      double z = (k + 0.5) / n, r = std::sqrt(1.0 - z * z), ph = k * ga;
+      d.push_back({r * std::cos(ph), r * std::sin(ph), z});
+    }
+    return d;
+  }
+  const double phi = 0.5 * (1.0 + std::sqrt(5.0));
+  std::vector<std::array<double, 3>> v;
+  for (int a = -1; a <= 1; a += 2)
+    for (int b = -1; b <= 1; b += 2) {
+      v.push_back({0.0, (double)a, b * phi});
+      v.push_back({(double)a, b * phi, 0.0});
+      v.push_back({b * phi, 0.0, (double)a});
+    }
+  const double edge2 = 4.0;                  // squared edge length of this icosahedron
+  std::vector<std::array<double, 3>> all;
+  auto unit = [](std::array<double, 3> p) {
+    double l = std::sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+    return std::array<double, 3>{p[0] / l, p[1] / l, p[2] / l};
+  };
+  for (auto& p : v) all.push_back(unit(p));
+  for (size_t i = 0; i < v.size(); ++i)
+    for (size_t j = i + 1; j < v.size(); ++j) {
+      double dx = v[i][0] - v[j][0], dy = v[i][1] - v[j][1], dz = v[i][2] - v[j][2];
+      if (std::fabs(dx * dx + dy * dy + dz * dz - edge2) < 1e-9)
+        all.push_back(unit({v[i][0] + v[j][0], v[i][1] + v[j][1], v[i][2] + v[j][2]}));
+    }
+  const double th = std::atan2(1.0, phi * phi), ct = std::cos(th), st = std::sin(th);
+  for (auto& p : all) {
+    std::array<double, 3> q{p[0], p[1] * ct - p[2] * st, p[1] * st + p[2] * ct};
+    for (double& x : q)
+      if (std::fabs(x) < 1e-12) x = 0.0;        // exact zeros: symmetric directions sort alike
+    if (q[2] > 1e-9) d.push_back(q);
+  }
+  std::sort(d.begin(), d.end(), [](const std::array<double, 3>& x, const std::array<double, 3>& y) {
+    if (std::fabs(x[2] - y[2]) > 1e-9) return x[2] > y[2];
+    return std::atan2(x[1], x[0]) < std::atan2(y[1], y[0]);
+  });
+  return d;
+}
+
+// Light stage: square quads of side light_side centred at radius * d_k,
+// facing the origin; in-plane axes e1 = normalize(+y x d), e2 = d x e1.
+std::vector<Light> make_lights(int n, double radius, int layout) {
+  std::vector<std::array<double, 3>> D = light_dirs(n, layout);
   std::vector<Light> L(n);
-  const double ga = 3.14159265358979323846 * (3.0 - std::sqrt(5.0));
-  for (int k = 0; k < n; ++k) {
-    double z = (k + 0.5) / n, r = std::sqrt(1.0 - z * z), ph = k * ga;
-    double d[3] = {r * std::cos(ph), r * std::sin(ph), z};
+  for (int k = 0; k < n && k < (int)D.size(); ++k) {
+    const double* d = D[k].data();
     double e1[3] = {d[2], 0.0, -d[0]};
     double n1 = std::sqrt(e1[0] * e1[0] + e1[2] * e1[2]);
     e1[0] /= n1; e1[2] /= n1;
@@ -322,7 +375,8 @@ RenderArgs render_args(fr_ctx* c, const float* theta, const fr_render_opts* o, c
   RenderArgs a;
   a.W = o->W; a.H = o->H; a.spp = o->spp; a.seed = o->seed; a.iter = o->iter;
   a.n_lights = c->cfg.n_lights;
-  a.side = c->cfg.light_side; a.m = c->cfg.beckmann_m; a.eps_pedge = c->cfg.eps_pedge;
+  a.side = c->cfg.light_side; a.eps_pedge = c->cfg.eps_pedge;
+  a.brdf = Brdf{c->cfg.beckmann_m, c->cfg.brdf_model, c->cfg.fresnel};
   a.eps_sedge = c->cfg.eps_sedge; a.tmin = c->cfg.shadow_tmin; a.kappa = c->cfg.clip_kappa;
   a.cam = make_cam(c, o->W, o->H);
   for (int j = 0; j < c->cfg.n_lights; ++j) a.lights[j] = c->lights[j];
@@ -412,6 +466,7 @@ void fr_default_config(fr_config* c) {
   if (!c) return;
   c->tan_half_fov = 0.275f; c->d_cam = 4.0f; c->light_radius = 3.0f; c->light_side = 0.6f; c->beckmann_m = 0.3f;
   c->eps_pedge = 1e-3f; c->eps_sedge = 2e-4f; c->shadow_tmin = 1e-4f; c->clip_kappa = 1e-5f; c->n_lights = 20;
+  c->brdf_model = 0; c->fresnel = 0; c->light_layout = 0;
 }
 
 const char* fr_strerror(int32_t code) {
@@ -437,13 +492,16 @@ int fr_create(fr_ctx** out, const fr_config* cfg, int32_t device) {
   if (cfg) c = *cfg; else fr_default_config(&c);
   if (c.n_lights < 1 || c.n_lights > MAX_LIGHTS) return FR_ERR_INVALID_ARG;
   if (!(c.light_side > 0) || !(c.d_cam > 0) || !(c.tan_half_fov > 0) || !(c.beckmann_m > 0)) return FR_ERR_INVALID_ARG;
+  if (c.brdf_model < 0 || c.brdf_model > 1 || c.fresnel < 0 || c.fresnel > 1 || c.light_layout < 0 ||
+      c.light_layout > 1 || (c.light_layout == 1 && c.n_lights != 20))
+    return FR_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return FR_ERR_CUDA;
   if (cudaSetDevice(device) != cudaSuccess) return FR_ERR_CUDA;
   ctx = new fr_ctx();
   ctx->device = device;
   ctx->cfg = c;
-  ctx->lights = make_lights(c.n_lights, c.light_radius);
+  ctx->lights = make_lights(c.n_lights, c.light_radius, c.light_layout);
   if (ctx->err_flag.alloc(1) != cudaSuccess || ctx->counters.alloc(NCOUNT) != cudaSuccess ||
       ctx->n_sil.alloc(1) != cudaSuccess) {
     delete ctx;

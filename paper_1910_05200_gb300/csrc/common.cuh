@@ -385,7 +385,23 @@ struct ShadeOut {
   bool active;
 };
 
-FR_DEV ShadeOut shade_light(const Surf& S, float cs, V3 l, V3 y, V3 dl, float m) {
+// BRDF readings (the Face Modeling paragraph names Cook-Torrance without its
+// terms): model 0 = Beckmann D with the Cook-Torrance V-cavity G, model 1 =
+// GGX (Trowbridge-Reitz) D with the separable Smith G of GGX; fresnel 0 =
+// F folded into c_spec, 1 = Schlick's F with c_spec as the reflectance at
+// normal incidence.  m is the roughness (Beckmann m, or GGX alpha).
+struct Brdf {
+  float m;
+  int model, fresnel;
+};
+
+// Smith masking of GGX for one direction at cos c: 2c / (c + sqrt(a2 + (1 - a2) c^2)).
+FR_DEV float smith_g1_ggx(float c, float a2, float& r) {
+  r = sqrtf(a2 + (1.0f - a2) * c * c);
+  return 2.0f * c / (c + r);
+}
+
+FR_DEV ShadeOut shade_light(const Surf& S, float cs, V3 l, V3 y, V3 dl, const Brdf& b) {
   ShadeOut o;
   o.active = false;
   o.h = V3{0, 0, 0};
@@ -398,18 +414,30 @@ FR_DEV ShadeOut shade_light(const Surf& S, float cs, V3 l, V3 y, V3 dl, float m)
   float cy = dot(dl, wi);
   if (!(cy > 0.0f)) return o;
   float co = dot(S.ns, S.wo);
-  float spec = 0.0f;
+  float spec = 0.0f, F = cs;
   if (co > 0.0f) {
     V3 h = normalize(wi + S.wo);
     float ch = dot(S.ns, h), oh = dot(S.wo, h);
     float ch2 = ch * ch;
-    float tan2 = (1.0f - ch2) / ch2;
-    float D = __expf(-tan2 / (m * m)) / (PI_F * m * m * ch2 * ch2);
-    float G = fminf(1.0f, fminf(2.0f * ch * co / oh, 2.0f * ch * ci / oh));
+    const float m = b.m;
+    float D, G;
+    if (b.model == 0) {
+      float tan2 = (1.0f - ch2) / ch2;
+      D = __expf(-tan2 / (m * m)) / (PI_F * m * m * ch2 * ch2);
+      G = fminf(1.0f, fminf(2.0f * ch * co / oh, 2.0f * ch * ci / oh));
+    } else {
+      float a2 = m * m, t = ch2 * (a2 - 1.0f) + 1.0f, ri, ro;
+      D = a2 / (PI_F * t * t);
+      G = smith_g1_ggx(ci, a2, ri) * smith_g1_ggx(co, a2, ro);
+    }
     spec = D * G / (4.0f * ci * co);
+    if (b.fresnel) {
+      float q = 1.0f - oh, q2 = q * q;
+      F = cs + (1.0f - cs) * q2 * q2 * q;
+    }
   }
   float geo = ci * cy / d2;
-  float sp = cs * spec;
+  float sp = F * spec;
   o.h = V3{l.x * (S.rho.x * (1.0f / PI_F) + sp) * geo, l.y * (S.rho.y * (1.0f / PI_F) + sp) * geo,
            l.z * (S.rho.z * (1.0f / PI_F) + sp) * geo};
   o.geo = geo;

@@ -67,7 +67,8 @@ struct RenderArgs {
   int W, H, spp;
   uint32_t seed, iter;
   int n_lights;
-  float side, m, eps_pedge, eps_sedge, tmin, kappa;
+  float side, eps_pedge, eps_sedge, tmin, kappa;
+  Brdf brdf;
   Cam cam;
   Light lights[MAX_LIGHTS];
   Mesh mesh;

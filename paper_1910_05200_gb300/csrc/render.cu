@@ -90,7 +90,7 @@ FR_DEV void render_fwd_body(const RenderArgs& a, float* __restrict__ image, floa
   }
 }
 
-__global__ void __launch_bounds__(256) k_render_fwd(RenderArgs a, float* __restrict__ image) {
+__global__ void __launch_bounds__(256, 4) k_render_fwd(RenderArgs a, float* __restrict__ image) {
   render_fwd_body<false>(a, image, nullptr);
 }
 

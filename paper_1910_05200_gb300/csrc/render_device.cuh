@@ -77,7 +77,7 @@ FR_DEV V3 radiance(const RenderArgs& a, V3 o, V3 d, int tag, uint32_t c0, uint32
     V3 y = light_point(a.lights[j], a.side, unitf(q.x), unitf(q.y));
     if (!visible(a.mesh, x32, y, f, flip, a.tmin, a.err, cnt)) continue;
     ++n_vis;
-    ShadeOut sh = shade_light(S, cs, light_rgb(a, j), y, a.lights[j].dl, a.m);
+    ShadeOut sh = shade_light(S, cs, light_rgb(a, j), y, a.lights[j].dl, a.brdf);
     L += sh.h * area;
   }
   if (aux) {
@@ -105,7 +105,7 @@ FR_DEV V3 sample_dir(const RenderArgs& a, int px, int py, int s, uint32_t& pix) 
 // Interior adjoint
 
 // Reverse-mode of shade_light for one light.  G = adjoint RGB times area/spp.
-FR_DEV void shade_light_bwd(const Surf& S, float cs, V3 l, V3 y, V3 dl, float m, V3 G, V3& g_x, V3& g_ns,
+FR_DEV void shade_light_bwd(const Surf& S, float cs, V3 l, V3 y, V3 dl, const Brdf& bd, V3 G, V3& g_x, V3& g_ns,
                             V3& g_rho, float& g_cs, V3& g_l) {
   V3 w = y - S.x;
   float d2 = dot(w, w);
@@ -116,7 +116,9 @@ FR_DEV void shade_light_bwd(const Surf& S, float cs, V3 l, V3 y, V3 dl, float m,
   float cy = dot(dl, wi);
   if (!(cy > 0.0f)) return;
   float co = dot(S.ns, S.wo);
+  const float m = bd.m, a2 = m * m;
   float spec = 0.0f, D = 0.0f, Gf = 0.0f, ch = 0.0f, oh = 0.0f, g1 = 0.0f, g2 = 0.0f, hlen = 1.0f;
+  float t = 1.0f, G1i = 1.0f, G1o = 1.0f, ri = 1.0f, ro = 1.0f, F = cs, q = 0.0f, q4 = 0.0f;
   int branch = 0;
   V3 h{0, 0, 0};
   if (co > 0.0f) {
@@ -126,39 +128,62 @@ FR_DEV void shade_light_bwd(const Surf& S, float cs, V3 l, V3 y, V3 dl, float m,
     ch = dot(S.ns, h);
     oh = dot(S.wo, h);
     float ch2 = ch * ch;
-    float tan2 = (1.0f - ch2) / ch2;
-    D = __expf(-tan2 / (m * m)) / (PI_F * m * m * ch2 * ch2);
-    g1 = 2.0f * ch * co / oh;
-    g2 = 2.0f * ch * ci / oh;
-    float inner = g1 <= g2 ? g1 : g2;
-    if (1.0f <= inner) { Gf = 1.0f; branch = 0; }
-    else { Gf = inner; branch = g1 <= g2 ? 1 : 2; }
+    if (bd.model == 0) {
+      float tan2 = (1.0f - ch2) / ch2;
+      D = __expf(-tan2 / (m * m)) / (PI_F * m * m * ch2 * ch2);
+      g1 = 2.0f * ch * co / oh;
+      g2 = 2.0f * ch * ci / oh;
+      float inner = g1 <= g2 ? g1 : g2;
+      if (1.0f <= inner) { Gf = 1.0f; branch = 0; }
+      else { Gf = inner; branch = g1 <= g2 ? 1 : 2; }
+    } else {
+      t = ch2 * (a2 - 1.0f) + 1.0f;
+      D = a2 / (PI_F * t * t);
+      G1i = smith_g1_ggx(ci, a2, ri);
+      G1o = smith_g1_ggx(co, a2, ro);
+      Gf = G1i * G1o;
+    }
     spec = D * Gf / (4.0f * ci * co);
+    if (bd.fresnel) {
+      q = 1.0f - oh;
+      float q2 = q * q;
+      q4 = q2 * q2;
+      F = cs + (1.0f - cs) * q4 * q;
+    }
   }
   float geo = ci * cy / d2;
   const float ip = 1.0f / PI_F;
-  V3 F{S.rho.x * ip + cs * spec, S.rho.y * ip + cs * spec, S.rho.z * ip + cs * spec};
-  g_l += V3{G.x * F.x * geo, G.y * F.y * geo, G.z * F.z * geo};
+  const float sp = F * spec;
+  V3 Fr{S.rho.x * ip + sp, S.rho.y * ip + sp, S.rho.z * ip + sp};
+  g_l += V3{G.x * Fr.x * geo, G.y * Fr.y * geo, G.z * Fr.z * geo};
   V3 s{G.x * l.x, G.y * l.y, G.z * l.z};
   g_rho += s * (geo * ip);
   float Ssum = (s.x + s.y + s.z) * geo;
-  g_cs += Ssum * spec;
-  float d_spec = Ssum * cs;
-  float d_geo = s.x * F.x + s.y * F.y + s.z * F.z;
+  // sp = F spec with F = c_s (folded) or c_s + (1 - c_s) q^5, q = 1 - oh
+  g_cs += Ssum * spec * (bd.fresnel ? 1.0f - q4 * q : 1.0f);
+  float d_spec = Ssum * F;
+  float d_geo = s.x * Fr.x + s.y * Fr.y + s.z * Fr.z;
   float d_ci = d_geo * cy / d2;
   float d_cy = d_geo * ci / d2;
   float d_d2 = -d_geo * geo / d2;
   float d_co = 0.0f;
   V3 d_ns{0, 0, 0}, d_wi{0, 0, 0};
-  if (co > 0.0f && d_spec != 0.0f) {
+  if (co > 0.0f && Ssum != 0.0f) {
     float k4 = 4.0f * ci * co;
     float d_D = d_spec * Gf / k4, d_G = d_spec * D / k4;
     d_ci -= d_spec * spec / ci;
     d_co -= d_spec * spec / co;
-    float d_ch = 0.0f, d_oh = 0.0f;
-    if (branch == 1) { d_ch += d_G * 2.0f * co / oh; d_co += d_G * 2.0f * ch / oh; d_oh -= d_G * g1 / oh; }
-    else if (branch == 2) { d_ch += d_G * 2.0f * ci / oh; d_ci += d_G * 2.0f * ch / oh; d_oh -= d_G * g2 / oh; }
-    d_ch += d_D * D * (2.0f / (m * m * ch * ch * ch) - 4.0f / ch);
+    float d_ch = 0.0f, d_oh = bd.fresnel ? -5.0f * Ssum * spec * (1.0f - cs) * q4 : 0.0f;
+    if (bd.model == 0) {
+      if (branch == 1) { d_ch += d_G * 2.0f * co / oh; d_co += d_G * 2.0f * ch / oh; d_oh -= d_G * g1 / oh; }
+      else if (branch == 2) { d_ch += d_G * 2.0f * ci / oh; d_ci += d_G * 2.0f * ch / oh; d_oh -= d_G * g2 / oh; }
+      d_ch += d_D * D * (2.0f / (m * m * ch * ch * ch) - 4.0f / ch);
+    } else {
+      // Smith: dG1/dc = 2 a2 / (r (c + r)^2); GGX: dD/dch = -4 D ch (a2 - 1) / t
+      d_ci += d_G * G1o * 2.0f * a2 / (ri * (ci + ri) * (ci + ri));
+      d_co += d_G * G1i * 2.0f * a2 / (ro * (co + ro) * (co + ro));
+      d_ch += d_D * D * (-4.0f * ch * (a2 - 1.0f) / t);
+    }
     d_ns += h * d_ch;
     V3 d_h = S.ns * d_ch + S.wo * d_oh;
     d_wi += (d_h - h * dot(d_h, h)) * (1.0f / hlen);
@@ -249,7 +274,7 @@ FR_DEV void interior_sample(const RenderArgs& a, const GradBufs& gb, float* sC, 
     V3 y = light_point(a.lights[j], a.side, unitf(q.x), unitf(q.y));
     if (!visible(a.mesh, x32, y, f, flip, a.tmin, a.err, cnt)) continue;
     V3 g_l{0, 0, 0};
-    shade_light_bwd(S, cs, light_rgb(a, j), y, a.lights[j].dl, a.m, G, g_x, g_ns, g_rho, g_cs, g_l);
+    shade_light_bwd(S, cs, light_rgb(a, j), y, a.lights[j].dl, a.brdf, G, g_x, g_ns, g_rho, g_cs, g_l);
     atomicAdd(&sL[3 * j], g_l.x);
     atomicAdd(&sL[3 * j + 1], g_l.y);
     atomicAdd(&sL[3 * j + 2], g_l.z);
@@ -619,8 +644,8 @@ FR_DEV void sedge_contribution(const RenderArgs& a, const GradBufs& gb, int j, i
   float cs = cspec_lookup(a.cspec, S.u, S.v, idx, w4, fu, fv);
   V3 l = light_rgb(a, j);
   V3 gp{0, 0, 0}, gm{0, 0, 0};
-  if (vp) gp = shade_light(S, cs, l, yp, L.dl, a.m).h;
-  if (vm) gm = shade_light(S, cs, l, ym, L.dl, a.m).h;
+  if (vp) gp = shade_light(S, cs, l, yp, L.dl, a.brdf).h;
+  if (vm) gm = shade_light(S, cs, l, ym, L.dl, a.brdf).h;
   float delta = dot(wrgb, gm - gp);
   if (delta == 0.0f) return;
   float w = delta * (float)n_cand * (t1 - t0);

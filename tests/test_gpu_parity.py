@@ -255,3 +255,24 @@ def test_full_size_backward_masked_adjoint(oracle, full, full_r):
     ref, mass = oracle.render_backward(default_config(W=W, H=H, spp=spp, seed=3), scene, theta,
                                        dI.astype(np.float64), mass=True)
     assert_grad(g, ref, mass, what="full size, masked adjoint")
+
+
+@pytest.mark.parametrize("model,fresnel,layout", [(1, 0, 0), (0, 1, 0), (1, 1, 1)])
+def test_alternative_readings_match_oracle(oracle, fr, tiny, model, fresnel, layout):
+    """GGX + Smith, Schlick's Fresnel and the icosphere dome: light stage,
+    forward image and all gradient terms against the oracle."""
+    scene, theta, _ = tiny
+    kw = dict(brdf_model=model, fresnel=fresnel, light_layout=layout)
+    r = fr.Renderer(scene, device=0, config=fr.default_config(**kw))
+    assert np.array_equal(r.light_stage(), oracle.light_stage(20, 3.0, layout))
+    W, H, spp = 40, 33, 4
+    th = torch.tensor(theta, device="cuda:0")
+    img = r.render(th, W, H, spp, seed=6)
+    r.sync()
+    cfg = default_config(W=W, H=H, spp=spp, seed=6, **kw)
+    assert_image(img.cpu().numpy(), oracle.render(cfg, scene, theta))
+    dI = np.random.default_rng(12).normal(size=(H, W, 3)).astype(np.float32)
+    g = r.backward(th, torch.tensor(dI, device="cuda:0"), W, H, spp, seed=6).cpu().numpy()
+    r.sync()
+    ref, mass = oracle.render_backward(cfg, scene, theta, dI.astype(np.float64), mass=True)
+    assert_grad(g, ref, mass, what=f"readings {kw}")
