@@ -31,7 +31,7 @@ struct fr_batch {
   // inputs and outputs of a step
   DBuf<float> theta_s, theta_f, theta, targets, images, d_images, m;
   DBuf<uint8_t> masks;
-  bool have_targets = false, have_masks = false, have_m = false;
+  bool have_targets = false, have_masks = false;
   DBuf<double> grad_full, loss_frames, loss, grad_s, grad_f;
   // persistent kernel
   DBuf<BatchFrame> dframes;
@@ -245,7 +245,7 @@ int enqueue_step(fr_batch* b, float w1, float w2) {
   }
   long long nout = b->Ps + (long long)nF * b->Pf;
   k_batch_reduce<<<grid_for(nout, 256), 256, 0, s>>>(nF, P, ctx->K_id, ctx->K_exp, ctx->K_alb, nlv, b->theta.p,
-                                                    b->grad_full.p, b->loss_frames.p, b->have_m ? b->m.p : nullptr,
+                                                    b->grad_full.p, b->loss_frames.p, b->m.p,
                                                     w1, w2, b->grad_s.p, b->grad_f.p, b->loss.p);
   CKL();
   return FR_OK;
@@ -421,14 +421,15 @@ int fr_batch_set_targets(fr_batch* b, const float* targets, const uint8_t* masks
   cudaStream_t s = ctx->stream;
   CK(cudaMemcpyAsync(b->targets.p, targets, sizeof(float) * 3 * b->n_pix, cudaMemcpyDeviceToDevice, s));
   if (masks) CK(cudaMemcpyAsync(b->masks.p, masks, (size_t)b->n_pix, cudaMemcpyDeviceToDevice, s));
+  // the captured graph always reads the batch's own m: zero stands for "no m"
   if (m) CK(cudaMemcpyAsync(b->m.p, m, sizeof(float) * 3 * ctx->cfg.n_lights, cudaMemcpyDeviceToDevice, s));
+  else CK(cudaMemsetAsync(b->m.p, 0, sizeof(float) * 3 * MAX_LIGHTS, s));
   bool masks_now = masks != nullptr;
   if (masks_now != b->have_masks || !b->have_targets) {
     b->have_masks = masks_now;
     b->configured = false;            // the frame table records the mask pointers
     b->graph_ok = false;
   }
-  b->have_m = m != nullptr;
   b->have_targets = true;
   return FR_OK;
 }

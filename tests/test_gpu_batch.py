@@ -281,3 +281,24 @@ def test_full_size_batch_equals_single_frames(oracle, fr):
     assert_atomic_close(gs, gs_ref, shared_groups(), "full size shared")
     for f in range(len(frames)):
         assert_atomic_close(gf[f], gf_ref[f], frame_groups(), f"full size frame {f}")
+
+
+def test_targets_masks_and_prior_can_be_replaced(fr, tiny):
+    """set_targets between steps: dropping the mask adds the masked-out
+    pixels' E_data, dropping m turns the light term into w2 sum |l|^2;
+    restoring both restores the loss."""
+    c = Case(fr, tiny[0], [(16, 12), (9, 13)], 4, seed=31)
+    l_full, _, _, img = c.step()
+    c.b.set_targets(dev(c.targets))
+    l_plain, _, _, img2 = c.step()
+    assert np.array_equal(img, img2)
+    c.b.set_targets(dev(c.targets), dev(c.masks), dev(c.m))
+    l_again, _, _, _ = c.step()
+    assert l_again == pytest.approx(l_full, rel=1e-12)
+    w2 = float(np.float32(W2))
+    out = c.masks == 0
+    extra = float(np.sum((img[out].astype(np.float64) - c.targets[out]) ** 2))
+    _, tf = fr.split_theta(c.thetas.astype(np.float64))
+    lights = tf[:, 96:]
+    prior_change = w2 * float(np.sum(lights ** 2) - np.sum((lights - c.m.astype(np.float64)) ** 2))
+    assert l_plain - l_full == pytest.approx(extra + prior_change, rel=1e-9, abs=1e-9)
