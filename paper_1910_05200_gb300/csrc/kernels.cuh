@@ -227,13 +227,19 @@ size_t mlp_smem_bytes();
 int mlp_train_stride();
 void mlp_layer_offsets(int* off);
 
-// Pixel order: 8x8 tiles, row-major tiles; returns false for pixels outside the image.
+// Pixel order: 8x8 tiles, row-major tiles, Z-order within a tile (bits of
+// the in-tile index interleave x and y), so that any aligned run of 2^k
+// pixels -- the pixels of one warp's samples -- is a compact block (4x2 at 4
+// spp, 2x2 at 8 spp): the warp-wide shadow-edge search works on a small
+// group of shading points.  Returns false for pixels outside the image.
 FR_DEV bool tile_pixel(int idx, int W, int H, int& px, int& py) {
   int tiles_x = (W + 7) >> 3;
   int tile = idx >> 6, in = idx & 63;
   int tx = tile % tiles_x, ty = tile / tiles_x;
-  px = (tx << 3) + (in & 7);
-  py = (ty << 3) + (in >> 3);
+  int ix = (in & 1) | ((in >> 1) & 2) | ((in >> 2) & 4);
+  int iy = ((in >> 1) & 1) | ((in >> 2) & 2) | ((in >> 3) & 4);
+  px = (tx << 3) + ix;
+  py = (ty << 3) + iy;
   return px < W && py < H;
 }
 FR_DEV int tiled_pixel_count(int W, int H) { return ((W + 7) >> 3) * ((H + 7) >> 3) * 64; }
