@@ -25,8 +25,7 @@ K_FWD, K_INTERIOR, K_PEDGE, K_SEDGE = 0, 5, 10, 15
 # DRAM bytes of one k_bwd_sedge launch at 256x256x16 spp from a 1-pass ncu
 # capture of the kernel as it stands (dram__bytes_read.sum +
 # dram__bytes_write.sum): the edge records, hierarchies and meshes stay in L2.
-# None until the kernel as it stands has been captured.
-SEDGE_TRAFFIC_BYTES = None
+SEDGE_TRAFFIC_BYTES = 31.89e6 + 0.85e6
 SHADE_FWD = 150        # one light sample shaded (BRDF + geometry term)
 SHADE_BWD = 420        # one light sample: forward recompute + adjoint
 N_LIGHTS = 20

@@ -276,3 +276,28 @@ def test_alternative_readings_match_oracle(oracle, fr, tiny, model, fresnel, lay
     r.sync()
     ref, mass = oracle.render_backward(cfg, scene, theta, dI.astype(np.float64), mass=True)
     assert_grad(g, ref, mass, what=f"readings {kw}")
+
+
+def test_degenerate_images(oracle, tiny, tiny_r):
+    """A one-pixel image at one sample, and a face moved out of view (no
+    primary hit, no camera silhouette): black image, zero gradient."""
+    scene, theta, _ = tiny
+    th = torch.tensor(theta, device="cuda:0")
+    img = tiny_r.render(th, 1, 1, 1, seed=2)
+    tiny_r.sync()
+    ref = oracle.render(default_config(W=1, H=1, spp=1, seed=2), scene, theta)
+    assert_image(img.cpu().numpy(), ref)
+    g = tiny_r.backward(th, torch.ones(1, 1, 3, device="cuda:0"), 1, 1, 1, seed=2).cpu().numpy()
+    tiny_r.sync()
+    gref, mass = oracle.render_backward(default_config(W=1, H=1, spp=1, seed=2), scene, theta, np.ones((1, 1, 3)),
+                                        mass=True)
+    assert_grad(g, gref, mass, what="1x1")
+    away = theta.copy()
+    away[S.param_offsets()["pose"] + 3] = 50.0      # tx: far outside the field of view
+    t = torch.tensor(away, device="cuda:0")
+    img = tiny_r.render(t, 20, 12, 2)
+    assert img.abs().max().item() == 0
+    g = tiny_r.backward(t, torch.ones(12, 20, 3, device="cuda:0"), 20, 12, 2).cpu().numpy()
+    tiny_r.sync()
+    assert np.all(g == 0)
+    assert np.abs(oracle.render(default_config(W=20, H=12, spp=2), scene, away)).max() == 0
