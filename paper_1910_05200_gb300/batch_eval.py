@@ -75,7 +75,7 @@ def run(steps=5, reps=1, device=0):
     # --- the same frames one by one through the single-image entry points ------------
     dev = r.device
     th_all = torch.tensor(thetas, device=dev)
-    tg = b.split(b._keep[0])
+    tg = b.split(b.targets)
     d_images = [torch.empty(h, w, 3, device=dev) for w, h, _ in frames]
     grad = torch.zeros(th_all.shape[1], device=dev, dtype=torch.float64)
 

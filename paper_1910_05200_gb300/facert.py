@@ -382,7 +382,12 @@ class Batch:
                                                     _ptr(None if masks is None else masks.contiguous()),
                                                     _ptr(None if m is None else m.contiguous())),
                       "fr_batch_set_targets")
-        self._keep = (targets, masks, m)
+        self._keep = (targets, masks, m)     # alive until the asynchronous copies into the batch have run
+
+    @property
+    def targets(self):
+        """The packed target images last given to set_targets (or None)."""
+        return self._keep[0] if getattr(self, "_keep", None) else None
 
     def step(self, theta_shared, theta_frames, w1=0.0, w2=0.0, iter=0, images=True):
         """Returns (loss [1] FP64, grad_shared [Ps] FP64, grad_frames [F, Pf] FP64, images [n_pix, 3] or None)."""
