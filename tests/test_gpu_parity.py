@@ -221,6 +221,29 @@ def test_errors_are_reported(fr, tiny):
         fr.Renderer(bad, device=0)
 
 
+def test_large_image_and_size_limits(oracle, fr, tiny, tiny_r):
+    """A 2048 x 1536 image (sampled pixels against the oracle) and a request
+    of 2^31 samples, one beyond the limit, rejected before any work."""
+    import ctypes as C
+    scene, theta, _ = tiny
+    th = torch.tensor(theta, device="cuda:0")
+    W, H, spp = 2048, 1536, 2
+    img = tiny_r.render(th, W, H, spp, seed=8)
+    tiny_r.sync()
+    got = img.cpu().numpy().reshape(-1, 3)
+    lit = np.nonzero(got.sum(1) > 0)[0]
+    assert len(lit) > 0
+    pix = np.unique(np.concatenate([S.random_pixels(W, H, 32, seed=1),
+                                    lit[:: max(1, len(lit) // 32)][:32]])).astype(np.int32)
+    ref = oracle.render(default_config(W=W, H=H, spp=spp, seed=8), scene, theta, pixels=pix)
+    assert_image(got[pix], ref)
+    opts = fr.FrRenderOpts(8192, 8192, 32, 0, 0, 0)
+    small = torch.empty(3, device="cuda:0")
+    rc = tiny_r.lib.fr_render(tiny_r.ctx, C.c_void_p(th.data_ptr()), C.byref(opts), C.c_void_p(small.data_ptr()),
+                              None)
+    assert rc == -1 and b"too large" in tiny_r.lib.fr_last_error(tiny_r.ctx)
+
+
 # ---------------------------------------------------------------------------
 # Full size (35,709 vertices, 256 x 256, 16 spp): sampled outputs
 
