@@ -22,7 +22,8 @@ struct fr_batch {
   long long n_pix = 0;
   int nt_nodes = 0, ne_nodes = 0, nb_sil = 0;
   // per-frame buffers, frame f at offset f * (per-frame size)
-  DBuf<float4> X, Xm, nrm, ng, tv, epack, tnodes, tcones, enodes, econes, dX, dN, gs;
+  DBuf<float4> X, Xm, nrm, ng, tv, epack, tnodes, tcones, enodes, econes, e4cones, dX, dN, gs;
+  DBuf<float2> e4boxes;
   DBuf<int> tcounter, ecounter, sil, n_sil, block_count;
   DBuf<float> dXm, dL;
   // shared by the frames: albedo and its adjoint, specular-map adjoint
@@ -65,6 +66,7 @@ FrameView frame_view(fr_batch* b, int f) {
   v.alb = b->alb.p;
   v.tnodes = b->tnodes.p + (size_t)f * 4 * b->nt_nodes; v.tcones = b->tcones.p + (size_t)f * 2 * b->nt_nodes;
   v.enodes = b->enodes.p + (size_t)f * 4 * b->ne_nodes; v.econes = b->econes.p + (size_t)f * 2 * b->ne_nodes;
+  v.e4boxes = b->e4boxes.p + (size_t)f * 12 * c->n4; v.e4cones = b->e4cones.p + (size_t)f * 4 * c->n4;
   v.tcounter = b->tcounter.p + (size_t)f * b->nt_nodes; v.ecounter = b->ecounter.p + (size_t)f * b->ne_nodes;
   v.sil = b->sil.p + f * E; v.n_sil = b->n_sil.p + f; v.block_count = b->block_count.p + (size_t)f * b->nb_sil;
   v.dX = b->dX.p + f * V; v.dN = b->dN.p + f * V; v.dA = b->dA.p; v.gs = b->gs.p + f * V;
@@ -352,6 +354,7 @@ int fr_batch_create(fr_ctx* ctx, const fr_frame* frames, int32_t n_frames, int32
   BK(b->tv.alloc(nF * 3 * F)); BK(b->epack.alloc(nF * 6 * E));
   BK(b->tnodes.alloc(nF * 4 * b->nt_nodes)); BK(b->tcones.alloc(nF * 2 * b->nt_nodes));
   BK(b->enodes.alloc(nF * 4 * b->ne_nodes)); BK(b->econes.alloc(nF * 2 * b->ne_nodes));
+  BK(b->e4boxes.alloc(nF * 12 * (size_t)ctx->n4)); BK(b->e4cones.alloc(nF * 4 * (size_t)ctx->n4));
   BK(b->tcounter.alloc(nF * b->nt_nodes)); BK(b->ecounter.alloc(nF * b->ne_nodes));
   BK(b->sil.alloc(nF * E)); BK(b->n_sil.alloc(nF)); BK(b->block_count.alloc(nF * b->nb_sil));
   BK(b->dX.alloc(nF * V)); BK(b->dN.alloc(nF * V)); BK(b->gs.alloc(nF * V));
@@ -400,7 +403,7 @@ void fr_batch_destroy(fr_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   for (DBuf<float4>* p : {&b->X, &b->Xm, &b->nrm, &b->ng, &b->tv, &b->epack, &b->tnodes, &b->tcones, &b->enodes,
-                          &b->econes, &b->dX, &b->dN, &b->gs, &b->alb, &b->dA})
+                          &b->econes, &b->e4cones, &b->dX, &b->dN, &b->gs, &b->alb, &b->dA})
     p->free_();
   for (DBuf<int>* p : {&b->tcounter, &b->ecounter, &b->sil, &b->n_sil, &b->block_count, &b->queue, &b->tiles_done})
     p->free_();
@@ -408,6 +411,7 @@ void fr_batch_destroy(fr_batch* b) {
                          &b->d_images, &b->m})
     p->free_();
   for (DBuf<double>* p : {&b->grad_full, &b->loss_frames, &b->loss, &b->grad_s, &b->grad_f}) p->free_();
+  b->e4boxes.free_();
   b->masks.free_(); b->dframes.free_(); b->items.free_(); b->hits.free_(); b->iter_dev.free_();
   b->bs_fwd.free_(); b->bs_sedge.free_(); b->bs_pedge.free_();
   delete b;

@@ -263,6 +263,51 @@ std::vector<Light> make_lights(int n, double radius, int layout) {
   return L;
 }
 
+// Collapse a binary hierarchy to 4 children per node: the children of a
+// 4-wide node are the grandchildren of its binary node through internal
+// children, and the leaf children themselves.  codes4[k] holds the child
+// codes (leaf code, 4-wide node index, or EMPTY_CHILD); src4[4k + c] the
+// binary (node, slot) whose box and cone child c takes, (-1, -1) if empty.
+// A box that fails a conservative test also fails for everything below it,
+// so the 4-wide search visits the same leaves as the binary one.
+void collapse4(const HostBVH& h, std::vector<int4>& codes4, std::vector<int2>& src4) {
+  const int nb = (int)(h.nodes.size() / 4);
+  auto code = [&](int n, int s) { return reinterpret_cast<const int*>(&h.nodes[4 * n + 3])[s]; };
+  std::vector<int> to4(nb, -1), order{0};
+  to4[0] = 0;
+  codes4.assign(1, make_int4(EMPTY_CHILD, EMPTY_CHILD, EMPTY_CHILD, EMPTY_CHILD));
+  src4.assign(4, make_int2(-1, -1));
+  for (size_t q = 0; q < order.size(); ++q) {
+    const int n = order[q], k = to4[n];
+    int cc[4] = {EMPTY_CHILD, EMPTY_CHILD, EMPTY_CHILD, EMPTY_CHILD};
+    int2 ss[4] = {make_int2(-1, -1), make_int2(-1, -1), make_int2(-1, -1), make_int2(-1, -1)};
+    int used = 0;
+    auto add = [&](int c, int sn, int sl) {
+      if (!leaf_child(c)) {
+        to4[c] = (int)codes4.size();
+        codes4.push_back(make_int4(EMPTY_CHILD, EMPTY_CHILD, EMPTY_CHILD, EMPTY_CHILD));
+        src4.resize(src4.size() + 4, make_int2(-1, -1));
+        order.push_back(c);
+        c = to4[c];
+      }
+      cc[used] = c;
+      ss[used] = make_int2(sn, sl);
+      ++used;
+    };
+    for (int s = 0; s < 2; ++s) {
+      int c = code(n, s);
+      if (c == EMPTY_CHILD) continue;
+      if (leaf_child(c)) { add(c, n, s); continue; }
+      for (int s2 = 0; s2 < 2; ++s2) {
+        int c2 = code(c, s2);
+        if (c2 != EMPTY_CHILD) add(c2, c, s2);
+      }
+    }
+    codes4[k] = make_int4(cc[0], cc[1], cc[2], cc[3]);
+    for (int c = 0; c < 4; ++c) src4[4 * k + c] = ss[c];
+  }
+}
+
 int upload_bvh(fr_ctx* ctx, const HostBVH& h, DevBVH& d) {
   d.n_nodes = (int)(h.nodes.size() / 4);
   d.n_leaves = (int)h.leaf_first.size();
@@ -291,6 +336,7 @@ FrameView main_view(fr_ctx* c) {
   v.epack = c->epack.p;
   v.tnodes = c->tbvh.nodes.p; v.tcones = c->tbvh.cones.p; v.tcounter = c->tbvh.counter.p;
   v.enodes = c->ebvh.nodes.p; v.econes = c->ebvh.cones.p; v.ecounter = c->ebvh.counter.p;
+  v.e4boxes = c->e4boxes.p; v.e4cones = c->e4cones.p;
   v.sil = c->sil.p; v.n_sil = c->n_sil.p; v.block_count = c->block_count.p;
   v.dX = c->dX.p; v.dN = c->dN.p; v.dA = c->dA.p; v.gs = c->gs.p;
   v.dXm = c->dXm.p; v.dC = c->dC.p; v.dL = c->dL.p;
@@ -350,7 +396,14 @@ int prepare_geometry(fr_ctx* ctx, const float* theta, const FrameView& v) {
   CKL();
   int rc = refit(ctx, ctx->tbvh, v.tnodes, v.tcones, v.tcounter, false, v);
   if (rc) return rc;
-  return refit(ctx, ctx->ebvh, v.enodes, v.econes, v.ecounter, true, v);
+  rc = refit(ctx, ctx->ebvh, v.enodes, v.econes, v.ecounter, true, v);
+  if (rc) return rc;
+  if (ctx->n4 > 0) {
+    k_gather4<<<(4 * ctx->n4 + 255) / 256, 256, 0, s>>>(4 * ctx->n4, ctx->e4src.p, v.enodes, v.econes, v.e4boxes,
+                                                          v.e4cones);
+    CKL();
+  }
+  return FR_OK;
 }
 
 // Order-preserving list of camera-silhouette edges; block_count is the
@@ -385,6 +438,7 @@ RenderArgs render_args(fr_ctx* c, const float* theta, const fr_render_opts* o, c
   a.ebvh.bvh.nodes = v.enodes; a.ebvh.bvh.n_nodes = c->ebvh.n_nodes;
   a.ebvh.edges = c->edges_leaf.p; a.ebvh.edge_id = c->edge_id_leaf.p;
   a.ebvh.pack = v.epack; a.ebvh.verts = c->edges_leaf.p; a.ebvh.cones = v.econes;
+  a.ebvh.codes4 = c->e4codes.p; a.ebvh.boxes4 = v.e4boxes; a.ebvh.cones4 = v.e4cones;
   a.nrm = v.nrm; a.alb = v.alb; a.uv = reinterpret_cast<const float2*>(c->uv.p);
   a.cspec = theta + c->off_cspec(); a.lights_dev = theta + c->off_lights();
   a.sil = v.sil; a.n_sil = v.n_sil; a.edges_canon = c->edges_canon.p;
@@ -528,6 +582,7 @@ void fr_destroy(fr_ctx* ctx) {
   ctx->BidT.free_(); ctx->BexpT.free_(); ctx->alb_mean.free_(); ctx->BalbT.free_();
   ctx->X.free_(); ctx->Xm.free_(); ctx->alb.free_(); ctx->nrm.free_(); ctx->ng.free_(); ctx->tv.free_();
   ctx->epack.free_();
+  ctx->e4codes.free_(); ctx->e4src.free_(); ctx->e4boxes.free_(); ctx->e4cones.free_();
   ctx->sil.free_(); ctx->n_sil.free_(); ctx->block_count.free_(); ctx->err_flag.free_(); ctx->counters.free_();
   ctx->dX.free_(); ctx->dN.free_(); ctx->dA.free_(); ctx->gs.free_(); ctx->dXm.free_(); ctx->dC.free_(); ctx->dL.free_();
   ctx->hits.free_(); ctx->aov_scratch.free_();
@@ -609,6 +664,16 @@ int fr_upload_mesh(fr_ctx* ctx, const float* mean, int32_t V, const int32_t* tri
   if (rc) return rc;
   rc = upload_bvh(ctx, he2, ctx->ebvh);
   if (rc) return rc;
+  {
+    std::vector<int4> codes4;
+    std::vector<int2> src4;
+    collapse4(he2, codes4, src4);
+    ctx->n4 = (int)codes4.size();
+    CK(upload(ctx->e4codes, codes4.data(), codes4.size(), s));
+    CK(upload(ctx->e4src, src4.data(), src4.size(), s));
+    CK(ctx->e4boxes.alloc(12 * codes4.size()));
+    CK(ctx->e4cones.alloc(4 * codes4.size()));
+  }
   ctx->V = V; ctx->F = F; ctx->E = E;
   CK(ctx->X.alloc(V)); CK(ctx->Xm.alloc(V)); CK(ctx->alb.alloc(V)); CK(ctx->nrm.alloc(V));
   CK(ctx->ng.alloc(F)); CK(ctx->tv.alloc(3 * (size_t)F)); CK(ctx->epack.alloc(6 * (size_t)E));

@@ -189,7 +189,7 @@ FR_DEV float4 cone_merge(float4 c1, float4 c2) {
 
 // Child code of an absent child (root of a hierarchy with a single leaf).
 constexpr int EMPTY_CHILD = (int)0x80000000;
-FR_DEV bool leaf_child(int c) { return c < 0; }
+FR_HOST_DEV inline bool leaf_child(int c) { return c < 0; }
 FR_DEV int leaf_first(int c) { return (~c) >> 3; }
 FR_DEV int leaf_count(int c) { return ((~c) & 7) + 1; }
 

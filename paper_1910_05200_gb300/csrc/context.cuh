@@ -56,6 +56,13 @@ struct fr_ctx {
   DBuf<int4> tris, edges_canon, edges_leaf;
   DBuf<int> vf_off, vf_idx, tri_perm, edge_id_leaf;
   DevBVH tbvh, ebvh;
+  // the edge hierarchy collapsed to 4 children per node (fixed topology) and
+  // the gather table of its child slots from the binary one
+  int n4 = 0;
+  DBuf<int4> e4codes;
+  DBuf<int2> e4src;
+  DBuf<float2> e4boxes;
+  DBuf<float4> e4cones;
   // bases
   int K_id = 0, K_exp = 0, K_alb = 0;
   DBuf<float> BidT, BexpT, alb_mean, BalbT;
@@ -99,6 +106,8 @@ namespace fr {
 struct FrameView {
   float4 *X, *Xm, *alb, *nrm, *ng, *tv, *epack;
   float4 *tnodes, *tcones, *enodes, *econes;
+  float2* e4boxes;         // 4-wide edge hierarchy: child boxes and cones
+  float4* e4cones;
   int *tcounter, *ecounter;
   int *sil, *n_sil, *block_count;
   float4 *dX, *dN, *dA, *gs;

@@ -147,6 +147,25 @@ __device__ __forceinline__ void write_slot(float4* nodes, int node, int slot, V3
   N[o + 0] = lo.x; N[o + 1] = lo.y; N[o + 2] = lo.z; N[o + 3] = hi.x; N[o + 4] = hi.y; N[o + 5] = hi.z;
 }
 
+__global__ void k_gather4(int n_slots, const int2* __restrict__ src, const float4* __restrict__ nodes,
+                          const float4* __restrict__ cones, float2* __restrict__ boxes4, float4* __restrict__ cones4) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_slots) return;
+  int2 sr = src[i];
+  float b[6] = {3e38f, 3e38f, 3e38f, -3e38f, -3e38f, -3e38f};
+  float4 cn = make_float4(0.0f, 0.0f, 1.0f, CONE_FULL);
+  if (sr.x >= 0) {
+    const float* N = reinterpret_cast<const float*>(nodes + 4 * sr.x) + 6 * sr.y;
+    for (int k = 0; k < 6; ++k) b[k] = N[k];
+    cn = cones[2 * sr.x + sr.y];
+  }
+  float2* B = boxes4 + 3 * i;
+  B[0] = make_float2(b[0], b[1]);
+  B[1] = make_float2(b[2], b[3]);
+  B[2] = make_float2(b[4], b[5]);
+  cones4[i] = cn;
+}
+
 // Bottom-up refit: one thread per leaf; the second child to arrive at a node
 // computes the node's box and carries on upward.
 // Normal cone of the faces adjacent to the edges of one leaf; boundary edges

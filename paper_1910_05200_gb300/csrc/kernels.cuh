@@ -61,6 +61,11 @@ struct EdgeBVH {
   const float4* pack;     // leaf-ordered packed records, 6 float4 per edge
   const int4* verts;      // same as edges (v0, v1 read by the adjoint)
   const float4* cones;    // [n_nodes * 2] normal cones of the faces below each child
+  // the same hierarchy collapsed to 4 children per node (grandchildren of a
+  // binary node become its children), searched by the shadow-edge pass
+  const int4* codes4;     // [n4] child codes: leaf code, 4-wide node index or EMPTY_CHILD
+  const float2* boxes4;   // [n4 * 12] child c: lo.xy | lo.z, hi.x | hi.yz at float2 12k + 3c
+  const float4* cones4;   // [n4 * 4] normal cone of each child
 };
 
 struct RenderArgs {
@@ -185,6 +190,10 @@ __global__ void k_pack_edges(int E, const int4* __restrict__ edges_leaf, const i
                              const float4* __restrict__ ng, float4* __restrict__ pack);
 __global__ void k_vertex_normals(GeoArgs g);
 __global__ void k_refit(RefitArgs r);
+// Boxes and cones of the 4-wide edge hierarchy from the refitted binary one:
+// slot i takes (binary node, slot) src[i]; src.x < 0 marks an empty slot.
+__global__ void k_gather4(int n_slots, const int2* __restrict__ src, const float4* __restrict__ nodes,
+                          const float4* __restrict__ cones, float2* __restrict__ boxes4, float4* __restrict__ cones4);
 __global__ void k_silhouette_flags(SilArgs s);
 __global__ void k_silhouette_scan(SilArgs s, int nblocks);
 __global__ void k_silhouette_scatter(SilArgs s);

@@ -497,14 +497,15 @@ FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int
   if (!(lo_x.x <= hi_x.x) || a.ebvh.bvh.n_nodes == 0) return P;   // no valid lane
   const V3 rc = (lo_x + hi_x) * 0.5f;
   const float rr = len((hi_x - lo_x) * 0.5f) * 1.0001f + 1e-6f;
-  // The node test is spread over lanes 0..11: lane 6c + t holds test t of
-  // child c -- t = 0 the normal cone, t = 1 the front plane, t = 2..5 side
-  // plane t - 2 of the pyramid from rc through the light square, each
-  // dilated by the group radius rr.  Every test has the form
-  // dot(n, p - rc) >= -m with p the box corner furthest along n, except the
-  // cone.  A child is kept when its six lanes pass (one ballot).
+  // The search walks the 4-wide edge hierarchy; its node test is spread over
+  // lanes 0..23: lane 6c + t holds test t of child c -- t = 0 the normal
+  // cone, t = 1 the front plane, t = 2..5 side plane t - 2 of the pyramid
+  // from rc through the light square, each dilated by the group radius rr.
+  // Every test but the cone has the form dot(n, p - rc) >= -m with p the
+  // box corner furthest along n.  A child is kept when its six lanes pass
+  // (one ballot).
   const int lane = threadIdx.x & 31;
-  const int tc = lane < 12 ? lane / 6 : 0, tt = lane < 12 ? lane - 6 * tc : 6;
+  const int tc = lane < 24 ? lane / 6 : 0, tt = lane < 24 ? lane - 6 * tc : 6;
   V3 pn{0, 0, 0};
   float pm = 0.0f;
   if (tt == 1) {
@@ -528,48 +529,47 @@ FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int
   while (true) {
     if (++steps > MAX_STEPS) { atomicOr(a.err, ERR_STEPS); break; }
     ++nvis;
-    const float4* N = a.ebvh.bvh.nodes + 4 * node;
-    float4 b0 = N[0], b1 = N[1], b2 = N[2];
-    int4 ch = *reinterpret_cast<const int4*>(N + 3);
+    const int4 ch = a.ebvh.codes4[node];
     bool pass = true;
     if (tt < 6) {
-      const int code_c = tc ? ch.y : ch.x;
-      const V3 lo = tc ? V3{b1.z, b1.w, b2.x} : V3{b0.x, b0.y, b0.z};
-      const V3 hi = tc ? V3{b2.y, b2.z, b2.w} : V3{b0.w, b1.x, b1.y};
+      const int code_c = tc == 0 ? ch.x : (tc == 1 ? ch.y : (tc == 2 ? ch.z : ch.w));
       if (code_c == EMPTY_CHILD) {
         pass = false;
-      } else if (tt == 0) {
-        float4 cn = a.ebvh.cones[2 * node + tc];
-        if (cn.w < PI_F) {
-          V3 cb = (lo + hi) * 0.5f;
-          float rb = len((hi - lo) * 0.5f) * 1.0001f + 1e-6f + rr;
-          V3 v = rc - cb;
-          float dv2 = dot(v, v);
-          if (dv2 > rb * rb) {
-            float idv = rsqrtf(dv2);
-            float sb = rb * idv, cb2 = sqrtf(fmaxf(0.0f, 1.0f - sb * sb));
-            float sT, cT;
-            __sincosf(cn.w + 2e-3f, &sT, &cT);
-            if (cb2 * cT - sb * sT > 0.0f) {
-              float S = sb * cT + cb2 * sT;
-              float cpsi = dot(v, v3(cn)) * idv;
-              if (cpsi > S || cpsi < -S) pass = false;
+      } else {
+        const float2* B = a.ebvh.boxes4 + 12 * node + 3 * tc;
+        const float2 q0 = B[0], q1 = B[1], q2 = B[2];
+        const V3 lo{q0.x, q0.y, q1.x}, hi{q1.y, q2.x, q2.y};
+        if (tt == 0) {
+          float4 cn = a.ebvh.cones4[4 * node + tc];
+          if (cn.w < PI_F) {
+            V3 cb = (lo + hi) * 0.5f;
+            float rb = len((hi - lo) * 0.5f) * 1.0001f + 1e-6f + rr;
+            V3 v = rc - cb;
+            float dv2 = dot(v, v);
+            if (dv2 > rb * rb) {
+              float idv = rsqrtf(dv2);
+              float sb = rb * idv, cb2 = sqrtf(fmaxf(0.0f, 1.0f - sb * sb));
+              float sT, cT;
+              __sincosf(cn.w + 2e-3f, &sT, &cT);
+              if (cb2 * cT - sb * sT > 0.0f) {
+                float S = sb * cT + cb2 * sT;
+                float cpsi = dot(v, v3(cn)) * idv;
+                if (cpsi > S || cpsi < -S) pass = false;
+              }
             }
           }
+        } else {
+          V3 p{pn.x > 0 ? hi.x : lo.x, pn.y > 0 ? hi.y : lo.y, pn.z > 0 ? hi.z : lo.z};
+          pass = dot(pn, p - rc) >= -pm;
         }
-      } else {
-        V3 p{pn.x > 0 ? hi.x : lo.x, pn.y > 0 ? hi.y : lo.y, pn.z > 0 ? hi.z : lo.z};
-        pass = dot(pn, p - rc) >= -pm;
       }
     }
     const unsigned m = __ballot_sync(0xffffffffu, pass);
-    int todo[2];
-    int nt = 0;
-    if ((m & 0x3fu) == 0x3fu) todo[nt++] = ch.x;
-    if (((m >> 6) & 0x3fu) == 0x3fu) todo[nt++] = ch.y;
     int next = -1;
-    for (int k = 0; k < nt; ++k) {
-      int c2 = todo[k];
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) {
+      if (((m >> (6 * k)) & 0x3fu) != 0x3fu) continue;
+      const int c2 = k == 0 ? ch.x : (k == 1 ? ch.y : (k == 2 ? ch.z : ch.w));
       if (leaf_child(c2)) {
         int first = leaf_first(c2), n = leaf_count(c2);
         for (int i = 0; i < n; ++i) {
