@@ -12,7 +12,7 @@ from __future__ import annotations
 # FLOPs per operation
 NODE_VISIT = 40        # two child slab tests: 6 sub, 6 mul, 10 min/max, 2 cmp each
 TRI_TEST = 40          # watertight test: 9 sub, 6 mul + 6 sub (shear), 9 edge-fn ops, 3+6 for T, div
-EDGE_NODE_VISIT = 200  # two children: box vs 5 pyramid planes (~45) + normal-cone test (~55) each
+EDGE_NODE_VISIT = 400  # four children (4-wide edge hierarchy): box vs 5 pyramid planes (~45) + normal cone (~55) each
 EDGE_TEST = 20         # adjacency check + 2 silhouette plane tests (3 sub, 3 mul, 2 add each)
 CLIP_TEST = 90         # clip of both endpoints against the 5 planes of the light pyramid
 
@@ -25,7 +25,7 @@ K_FWD, K_INTERIOR, K_PEDGE, K_SEDGE = 0, 5, 10, 15
 # DRAM bytes of one k_bwd_sedge launch at 256x256x16 spp from a 1-pass ncu
 # capture of the kernel as it stands (dram__bytes_read.sum +
 # dram__bytes_write.sum): the edge records, hierarchies and meshes stay in L2.
-SEDGE_TRAFFIC_BYTES = 31.89e6 + 0.85e6
+SEDGE_TRAFFIC_BYTES = 32.65e6 + 1.15e6
 SHADE_FWD = 150        # one light sample shaded (BRDF + geometry term)
 SHADE_BWD = 420        # one light sample: forward recompute + adjoint
 N_LIGHTS = 20
