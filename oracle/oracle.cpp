@@ -29,7 +29,7 @@
 // Derivatives are forward-mode dual numbers over the same templated value
 // code, so each derivative is the exact derivative of the value code.
 //
-// Readings of points the paper leaves open (all documented in the design doc):
+// Readings of points the paper leaves open:
 // pinhole camera at (0,0,d_cam) looking down -z; light k at Fibonacci
 // direction z_k = (k+0.5)/N, phi_k = k*pi*(3-sqrt5), square of side s_L at
 // radius R_L; Beckmann D with m = 0.3, V-cavity G, F folded into c_spec;

@@ -53,7 +53,7 @@ class OracleScene(C.Structure):
                 ("alb_mean", C.c_void_p), ("B_alb", C.c_void_p)]
 
 
-# Scene constants (one reading of what the paper leaves open; see DESIGN.md).
+# Scene constants (one reading of what the paper leaves open).
 DEFAULTS = dict(tan_half_fov=0.275, d_cam=4.0, light_radius=3.0, light_side=0.6,
                 beckmann_m=0.3, eps_pedge=1e-3, eps_sedge=2e-4, shadow_tmin=1e-4,
                 clip_kappa=1e-5, n_lights=20, brdf_model=0, fresnel=0, light_layout=0)
