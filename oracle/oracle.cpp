@@ -34,6 +34,8 @@
 // direction z_k = (k+0.5)/N, phi_k = k*pi*(3-sqrt5), square of side s_L at
 // radius R_L; Beckmann D with m = 0.3, V-cavity G, F folded into c_spec;
 // R = Rz Ry Rx; E_prior = |alpha|^2 + |beta|^2 + |delta|^2 (statistical part).
+// The configuration also selects the alternatives: GGX D with Smith masking,
+// Schlick's F, and an icosphere dome of lights.
 
 #include <algorithm>
 #include <array>
