@@ -130,12 +130,14 @@ def parameter_errors(theta, truth, K=(S.K_ID, S.K_EXP, S.K_ALB)):
     return out
 
 
-def evaluate(n_targets=8, n_targets_hi=2, iters=500, spp_lo=4, spp_hi=64, device=0, denoiser_weights=None):
+def evaluate(n_targets=16, n_targets_hi=4, iters=500, spp_lo=4, spp_hi=64, device=0, denoiser_weights=None):
     """Full-face inverse problems (256x256): targets rendered at 256 spp from
     seeded ground truth (14 of 20 lights on, pose within 30 degrees); the fit
-    at spp_lo (plain, and denoised when weights are given) and at spp_hi
-    (plain).  Returns per-variant mean parameter errors, final losses and
-    time per iteration."""
+    at spp_lo (plain, and denoised when weights are given) on n_targets
+    targets and at spp_hi (plain) on the first n_targets_hi of them.  Returns
+    per-variant mean parameter errors, final losses and time per iteration,
+    each variant also averaged over the first n_targets_hi targets (the set
+    the spp_hi fit sees), and the per-target errors."""
     from . import facert
     scene, _, c = S.make_workload("full", seed=1)
     W, H = c["W"], c["H"]
@@ -158,8 +160,12 @@ def evaluate(n_targets=8, n_targets_hi=2, iters=500, spp_lo=4, spp_hi=64, device
             ms.append(res.ms_per_iter)
             if name.startswith("plain_%dspp" % spp_lo):
                 init_err.append(parameter_errors(initial_theta(), truth))
-        out[name] = {"targets": n, "param_error": {kk: float(np.mean([e[kk] for e in errs])) for kk in errs[0]},
-                     "final_loss": float(np.mean(losses)), "ms_per_iter": float(np.mean(ms))}
+        mean = lambda es: {kk: float(np.mean([e[kk] for e in es])) for kk in es[0]}
+        out[name] = {"targets": n, "param_error": mean(errs),
+                     f"param_error_first_{n_targets_hi}": mean(errs[:n_targets_hi]),
+                     "final_loss": float(np.mean(losses)),
+                     f"final_loss_first_{n_targets_hi}": float(np.mean(losses[:n_targets_hi])),
+                     "ms_per_iter": float(np.mean(ms)), "per_target": errs}
     out["initial_param_error"] = {kk: float(np.mean([e[kk] for e in init_err])) for kk in init_err[0]}
     return out
 
