@@ -204,8 +204,9 @@ int fr_sync(fr_ctx* ctx);
 
 /* Work counts of the last fr_render / fr_render_backward call (or batch
  * step), read back after a stream synchronisation.  out[20]: five counts
- * (BVH nodes visited by rays, triangle tests, edge-hierarchy nodes visited
- * -- once per warp, the search being warp-wide --, edge tests per lane,
+ * (BVH nodes visited by rays, triangle tests, nodes of the 4-wide edge
+ * hierarchy visited -- once per warp, the search being warp-wide --, edge
+ * tests per lane,
  * clip tests of edges that passed the silhouette test) for each of the
  * forward, interior, primary-edge and shadow-edge kernels, in that order.
  * Collected only when enabled with fr_set_counters(ctx, 1). */

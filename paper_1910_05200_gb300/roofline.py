@@ -17,7 +17,7 @@ EDGE_TEST = 20         # adjacency check + 2 silhouette plane tests (3 sub, 3 mu
 CLIP_TEST = 90         # clip of both endpoints against the 5 planes of the light pyramid
 
 # Counter layout (fr_get_counters): 5 per kernel -- ray BVH nodes, triangle
-# tests, edge-hierarchy nodes (once per warp: the 32 lanes share one descent),
+# tests, 4-wide edge-hierarchy nodes (once per warp: the 32 lanes share one descent),
 # edge tests (per lane), clip tests -- for forward, interior, primary edges,
 # shadow edges.
 K_FWD, K_INTERIOR, K_PEDGE, K_SEDGE = 0, 5, 10, 15
