@@ -322,7 +322,10 @@ int32_t fr_batch_n_frame(const fr_ctx* ctx);
  * pixel on a context with mesh and bases uploaded.  Allocates every buffer
  * the steps use (about 30 MB per frame for a 35,709-vertex mesh plus the
  * images).  *out receives the batch; it must be destroyed before its
- * context.  FR_ERR_INVALID_ARG for n_frames < 1, a frame with W, H < 1,
+ * context.  The batch is sized for the context's current mesh and bases:
+ * after a later fr_upload_mesh or fr_upload_bases its steps fail with
+ * FR_ERR_NOT_READY (create a new batch).  FR_ERR_INVALID_ARG for n_frames < 1,
+ * a frame with W, H < 1,
  * more than 2^31 - 1 samples in a frame, or spp that neither divides 32 nor
  * is a multiple of 32. */
 int fr_batch_create(fr_ctx* ctx, const fr_frame* frames, int32_t n_frames, int32_t spp, fr_batch** out);

@@ -53,6 +53,7 @@ struct fr_batch {
   uint64_t kernels_per_step = 0;
   int n_sms = 0;
   int occ = 0;             // blocks per SM of the configured kernel
+  uint64_t generation = 0; // the context's mesh and bases this batch was sized for
 };
 
 namespace {
@@ -291,6 +292,8 @@ int capture(fr_batch* b, float w1, float w2) {
 // when needed).
 int launch_step(fr_batch* b, const float* ts, const float* tf, float w1, float w2, uint32_t iter) {
   fr_ctx* ctx = b->ctx;
+  if (b->generation != ctx->generation)
+    return fail(ctx, FR_ERR_NOT_READY, "the mesh or bases changed after this batch was created: create a new batch");
   if (!b->have_targets) return fail(ctx, FR_ERR_NOT_READY, "fr_batch_set_targets first");
   if (!ts || !tf) return fail(ctx, FR_ERR_INVALID_ARG, "theta_shared or theta_frames is null");
   if (!b->graph_ok || w1 != b->g_w1 || w2 != b->g_w2 || ctx->counters_on != b->g_counters) {
@@ -332,6 +335,7 @@ int fr_batch_create(fr_ctx* ctx, const fr_frame* frames, int32_t n_frames, int32
   CK(cudaStreamSynchronize(ctx->stream));
   fr_batch* b = new fr_batch();
   b->ctx = ctx;
+  b->generation = ctx->generation;
   b->nF = n_frames; b->spp = spp;
   if (spp > 32) b->cfg = fr_tile_config{4, 4, 256, 2, 1, 0.0f};   // the phased launches need spp dividing 32
   b->P = ctx->n_params(); b->Ps = fr_batch_n_shared(ctx); b->Pf = fr_batch_n_frame(ctx);

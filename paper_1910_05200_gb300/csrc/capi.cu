@@ -675,6 +675,7 @@ int fr_upload_mesh(fr_ctx* ctx, const float* mean, int32_t V, const int32_t* tri
     CK(ctx->e4cones.alloc(4 * codes4.size()));
   }
   ctx->V = V; ctx->F = F; ctx->E = E;
+  ++ctx->generation;
   CK(ctx->X.alloc(V)); CK(ctx->Xm.alloc(V)); CK(ctx->alb.alloc(V)); CK(ctx->nrm.alloc(V));
   CK(ctx->ng.alloc(F)); CK(ctx->tv.alloc(3 * (size_t)F)); CK(ctx->epack.alloc(6 * (size_t)E));
   CK(ctx->sil.alloc(E)); CK(ctx->block_count.alloc((E + 255) / 256));
@@ -711,6 +712,7 @@ int fr_upload_bases(fr_ctx* ctx, const float* B_id, int32_t K_id, const float* B
   CK(upload(ctx->alb_mean, alb_mean, n3, ctx->stream));
   ctx->K_id = K_id; ctx->K_exp = K_exp; ctx->K_alb = K_alb;
   ctx->have_bases = true;
+  ++ctx->generation;
   return FR_OK;
 }
 

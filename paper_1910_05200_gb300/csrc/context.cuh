@@ -52,6 +52,7 @@ struct fr_ctx {
   // mesh
   int V = 0, F = 0, E = 0;
   bool have_mesh = false, have_bases = false;
+  uint64_t generation = 0;   // counts mesh and basis uploads (a batch is tied to one)
   DBuf<float> mean, uv;
   DBuf<int4> tris, edges_canon, edges_leaf;
   DBuf<int> vf_off, vf_idx, tri_perm, edge_id_leaf;

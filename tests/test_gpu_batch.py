@@ -302,3 +302,18 @@ def test_targets_masks_and_prior_can_be_replaced(fr, tiny):
     lights = tf[:, 96:]
     prior_change = w2 * float(np.sum(lights ** 2) - np.sum((lights - c.m.astype(np.float64)) ** 2))
     assert l_plain - l_full == pytest.approx(extra + prior_change, rel=1e-9, abs=1e-9)
+
+
+def test_batch_refuses_after_new_mesh(fr, tiny):
+    """A batch is sized for the mesh and bases of its context: after a new
+    upload its steps are refused, and a new batch works."""
+    c = Case(fr, tiny[0], [(8, 8)], 4, seed=41)
+    c.step()
+    c.r.upload(tiny[0])
+    with pytest.raises(RuntimeError, match="not uploaded|changed"):
+        c.b.step(c.ts, c.tf, W1, W2, iter=ITER)
+    b2 = fr.Batch(c.r, c.frames, 4)
+    b2.set_targets(dev(c.targets))
+    loss, _, _, _ = b2.step(c.ts, c.tf, W1, W2, iter=ITER)
+    c.r.sync()
+    assert np.isfinite(loss.item())
