@@ -81,16 +81,23 @@ typedef struct fr_config {
    * fresnel 0 = F folded into c_spec, 1 = Schlick F with c_spec as the
    * reflectance at normal incidence;
    * light_layout 0 = Fibonacci points on the hemisphere, 1 = the 20 upper
-   * vertices of a once-subdivided icosahedron (needs n_lights = 20). */
+   * vertices of a once-subdivided icosahedron (needs n_lights = 20);
+   * light_prior selects m_j of E_light (Eq. 1 names it the j-th light's mean
+   * intensity without saying over what): 0 = the caller's m (fr_loss, fr_batch_set_targets), 1 = the mean
+   * of the lights, per channel, m_jc = (1/N) sum_k l_kc, 2 = the light's own
+   * channel mean, m_jc = (l_jr + l_jg + l_jb) / 3.  In 1 and 2 m follows the
+   * lights and the gradient is taken through it (it reduces to
+   * 2 w2 (l_jc - m_jc), the deviations summing to zero). */
   int32_t brdf_model;
   int32_t fresnel;
   int32_t light_layout;
+  int32_t light_prior;
 } fr_config;
 
 /* Fill *cfg with the library defaults (tan_half_fov 0.275, d_cam 4,
  * light_radius 3, light_side 0.6, beckmann_m 0.3, eps_pedge 1e-3,
  * eps_sedge 2e-4, shadow_tmin 1e-4, clip_kappa 1e-5, n_lights 20,
- * brdf_model 0, fresnel 0, light_layout 0). */
+ * brdf_model 0, fresnel 0, light_layout 0, light_prior 0). */
 void fr_default_config(fr_config* cfg);
 
 /* Per-call render options.  Samples are drawn from Philox4x32-10 keyed by
@@ -159,9 +166,11 @@ int fr_render_backward(fr_ctx* ctx, const float* theta, const fr_render_opts* op
  *   E_data  = sum over pixels with mask != 0 of |image - target|^2,
  *   E_prior = |alpha|^2 + |beta|^2 + |delta|^2 (the statistical prior; the
  *             landmark term needs detected landmarks and is not computed),
- *   E_light = sum_j |l_j - m_j|^2, j = 1..N.
+ *   E_light = sum_j |l_j - m_j|^2, j = 1..N, m_j as fr_config.light_prior
+ *             selects.
  * theta[P], image/target[H*W*3] FP32 device; mask[H*W] uint8 device or NULL
- * (all pixels); m[3N] FP32 device or NULL (zero); loss: one FP64 device
+ * (all pixels); m[3N] FP32 device or NULL (zero), read only when
+ * light_prior is 0; loss: one FP64 device
  * scalar, overwritten; d_image[H*W*3] FP32 device or NULL, overwritten with
  * dE_data/d image; grad[P] FP64 device or NULL: the gradient of
  * w1 E_prior + w2 E_light is ADDED to it. */
@@ -332,7 +341,8 @@ int fr_batch_create(fr_ctx* ctx, const fr_frame* frames, int32_t n_frames, int32
 void fr_batch_destroy(fr_batch* b);
 
 /* Targets (packed images), masks (packed uint8, or NULL for all pixels) and
- * the light prior m[3N] (or NULL for zero): copied into the batch (device to
+ * the light prior m[3N] (or NULL for zero; used only when the context's
+ * light_prior is 0): copied into the batch (device to
  * device, on the context stream) and used by every later step. */
 int fr_batch_set_targets(fr_batch* b, const float* targets, const uint8_t* masks, const float* m);
 

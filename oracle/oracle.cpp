@@ -33,9 +33,11 @@
 // pinhole camera at (0,0,d_cam) looking down -z; light k at Fibonacci
 // direction z_k = (k+0.5)/N, phi_k = k*pi*(3-sqrt5), square of side s_L at
 // radius R_L; Beckmann D with m = 0.3, V-cavity G, F folded into c_spec;
-// R = Rz Ry Rx; E_prior = |alpha|^2 + |beta|^2 + |delta|^2 (statistical part).
+// R = Rz Ry Rx; E_prior = |alpha|^2 + |beta|^2 + |delta|^2 (statistical part);
+// m_j of E_light given by the caller.
 // The configuration also selects the alternatives: GGX D with Smith masking,
-// Schlick's F, and an icosphere dome of lights.
+// Schlick's F, an icosphere dome of lights, and m_j as the mean of the lights
+// per channel or as light j's channel mean.
 
 #include <algorithm>
 #include <array>
@@ -137,6 +139,7 @@ struct OracleConfig {
   int32_t brdf_model;   // 0 Beckmann D + Cook-Torrance V-cavity G; 1 GGX D + separable Smith G
   int32_t fresnel;      // 0 F folded into c_spec; 1 Schlick F with c_spec as normal-incidence reflectance
   int32_t light_layout; // 0 Fibonacci hemisphere; 1 upper 20 vertices of a once-subdivided icosahedron
+  int32_t light_prior;  // m_j of E_light: 0 given; 1 mean of the lights per channel; 2 light j's channel mean
 };
 struct OracleScene {
   int32_t V, F, K_id, K_exp, K_alb;
@@ -1293,16 +1296,45 @@ double oracle_loss(const OracleConfig* cfg, const OracleScene* sc, const float* 
   }
   double Ep = 0.0;
   for (int i = 0; i < lay.cspec; ++i) Ep += (double)theta[i] * theta[i];
+  // E_light = sum_j |l_j - m_j|^2.  The text leaves open what m_j averages;
+  // light_prior 0 takes the given m (zero when null) and treats it as a
+  // constant, 1 the mean of the N lights in each channel, 2 the mean of
+  // light j's three channels.  For 1 and 2, J[i][k] = dm_i/dl_k enters the
+  // derivative: dE/dl_k = 2 (l_k - m_k) - sum_i 2 (l_i - m_i) J[i][k].
+  const int NV = 3 * cfg->n_lights;
+  const float* l = theta + lay.lights;
+  std::vector<double> mv(NV, 0.0), J((size_t)NV * NV, 0.0);
+  for (int i = 0; i < NV; ++i) {
+    const int j = i / 3, c = i % 3;
+    if (cfg->light_prior == 1) {
+      for (int k = 0; k < cfg->n_lights; ++k) {
+        mv[i] += (double)l[3 * k + c];
+        J[(size_t)i * NV + 3 * k + c] = 1.0 / cfg->n_lights;
+      }
+      mv[i] /= cfg->n_lights;
+    } else if (cfg->light_prior == 2) {
+      for (int c2 = 0; c2 < 3; ++c2) {
+        mv[i] += (double)l[3 * j + c2];
+        J[(size_t)i * NV + 3 * j + c2] = 1.0 / 3.0;
+      }
+      mv[i] /= 3.0;
+    } else {
+      mv[i] = m ? (double)m[i] : 0.0;
+    }
+  }
   double El = 0.0;
-  for (int i = 0; i < 3 * cfg->n_lights; ++i) {
-    double diff = (double)theta[lay.lights + i] - (m ? (double)m[i] : 0.0);
+  for (int i = 0; i < NV; ++i) {
+    double diff = (double)l[i] - mv[i];
     El += diff * diff;
   }
   if (grad_reg) {
     for (int i = 0; i < lay.total; ++i) grad_reg[i] = 0.0;
     for (int i = 0; i < lay.cspec; ++i) grad_reg[i] = 2.0 * w1 * theta[i];
-    for (int i = 0; i < 3 * cfg->n_lights; ++i)
-      grad_reg[lay.lights + i] = 2.0 * w2 * ((double)theta[lay.lights + i] - (m ? (double)m[i] : 0.0));
+    for (int k = 0; k < NV; ++k) {
+      double g = 2.0 * ((double)l[k] - mv[k]);
+      for (int i = 0; i < NV; ++i) g -= 2.0 * ((double)l[i] - mv[i]) * J[(size_t)i * NV + k];
+      grad_reg[lay.lights + k] = w2 * g;
+    }
   }
   return Ed + (double)w1 * Ep + (double)w2 * El;
 }

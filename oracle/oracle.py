@@ -42,7 +42,8 @@ class OracleConfig(C.Structure):
                 ("clip_kappa", C.c_float),
                 ("n_lights", C.c_int32), ("shade_mode", C.c_int32),
                 ("n_threads", C.c_int32), ("terms", C.c_int32), ("value_mesh", C.c_int32),
-                ("brdf_model", C.c_int32), ("fresnel", C.c_int32), ("light_layout", C.c_int32)]
+                ("brdf_model", C.c_int32), ("fresnel", C.c_int32), ("light_layout", C.c_int32),
+                ("light_prior", C.c_int32)]
 
 
 class OracleScene(C.Structure):
@@ -56,7 +57,8 @@ class OracleScene(C.Structure):
 # Scene constants (one reading of what the paper leaves open).
 DEFAULTS = dict(tan_half_fov=0.275, d_cam=4.0, light_radius=3.0, light_side=0.6,
                 beckmann_m=0.3, eps_pedge=1e-3, eps_sedge=2e-4, shadow_tmin=1e-4,
-                clip_kappa=1e-5, n_lights=20, brdf_model=0, fresnel=0, light_layout=0)
+                clip_kappa=1e-5, n_lights=20, brdf_model=0, fresnel=0, light_layout=0,
+                light_prior=0)
 
 
 def default_config(W=64, H=64, spp=4, seed=0, iter=0, shade_mode=0, n_threads=0, terms=0,

@@ -389,11 +389,12 @@ __global__ void k_batch_gather_theta(int n_frames, int P, int K_id, int K_exp, i
 // Shared and per-frame gradients from the per-frame full gradients, plus the
 // prior and light terms of Eq. 1 counted once per parameter:
 //   loss = sum_f E_data,f + w1 (|alpha|^2 + |delta|^2 + sum_f |beta_f|^2)
-//          + w2 sum_f sum_j |l_fj - m_j|^2.
+//          + w2 sum_f sum_j |l_fj - m_j|^2,
+// m_j the caller's (prior 0) or following frame f's lights (prior 1, 2).
 // One thread per output; block 0 also reduces the loss.
 __global__ void k_batch_reduce(int n_frames, int P, int K_id, int K_exp, int K_alb, int n_light_vals,
                                const float* __restrict__ theta, const double* __restrict__ grad_full,
-                               const double* __restrict__ loss_frames, const float* __restrict__ m, float w1,
+                               const double* __restrict__ loss_frames, int prior, const float* __restrict__ m, float w1,
                                float w2, double* __restrict__ grad_s, double* __restrict__ grad_f,
                                double* __restrict__ loss) {
   const int Ps = K_id + K_alb + CS * CS, Pf = K_exp + 6 + n_light_vals;
@@ -413,7 +414,8 @@ __global__ void k_batch_reduce(int n_frames, int P, int K_id, int K_exp, int K_a
     const float* th = theta + (size_t)f * P;
     double v = grad_full[(size_t)f * P + full];
     if (full < off_d) v += 2.0 * (double)w1 * (double)th[full];
-    if (full >= off_l) v += 2.0 * (double)w2 * ((double)th[full] - (m ? (double)m[full - off_l] : 0.0));
+    if (full >= off_l)
+      v += 2.0 * (double)w2 * ((double)th[full] - light_prior_mean(th + off_l, n_light_vals / 3, prior, m, full - off_l));
     grad_f[(size_t)f * Pf + i] = v;
   }
   if (blockIdx.x == 0) {
@@ -429,7 +431,7 @@ __global__ void k_batch_reduce(int n_frames, int P, int K_id, int K_exp, int K_a
       const float* th = theta + (size_t)f * P;
       for (int i = threadIdx.x; i < K_exp; i += blockDim.x) acc += (double)w1 * (double)th[K_id + i] * (double)th[K_id + i];
       for (int i = threadIdx.x; i < n_light_vals; i += blockDim.x) {
-        double dd = (double)th[off_l + i] - (m ? (double)m[i] : 0.0);
+        double dd = (double)th[off_l + i] - light_prior_mean(th + off_l, n_light_vals / 3, prior, m, i);
         acc += (double)w2 * dd * dd;
       }
     }

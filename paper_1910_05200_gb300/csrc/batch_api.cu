@@ -248,7 +248,8 @@ int enqueue_step(fr_batch* b, float w1, float w2) {
   }
   long long nout = b->Ps + (long long)nF * b->Pf;
   k_batch_reduce<<<grid_for(nout, 256), 256, 0, s>>>(nF, P, ctx->K_id, ctx->K_exp, ctx->K_alb, nlv, b->theta.p,
-                                                    b->grad_full.p, b->loss_frames.p, b->m.p,
+                                                    b->grad_full.p, b->loss_frames.p,
+                                                    ctx->cfg.light_prior, b->m.p,
                                                     w1, w2, b->grad_s.p, b->grad_f.p, b->loss.p);
   CKL();
   return FR_OK;

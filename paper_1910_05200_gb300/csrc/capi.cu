@@ -520,7 +520,7 @@ void fr_default_config(fr_config* c) {
   if (!c) return;
   c->tan_half_fov = 0.275f; c->d_cam = 4.0f; c->light_radius = 3.0f; c->light_side = 0.6f; c->beckmann_m = 0.3f;
   c->eps_pedge = 1e-3f; c->eps_sedge = 2e-4f; c->shadow_tmin = 1e-4f; c->clip_kappa = 1e-5f; c->n_lights = 20;
-  c->brdf_model = 0; c->fresnel = 0; c->light_layout = 0;
+  c->brdf_model = 0; c->fresnel = 0; c->light_layout = 0; c->light_prior = 0;
 }
 
 const char* fr_strerror(int32_t code) {
@@ -547,7 +547,7 @@ int fr_create(fr_ctx** out, const fr_config* cfg, int32_t device) {
   if (c.n_lights < 1 || c.n_lights > MAX_LIGHTS) return FR_ERR_INVALID_ARG;
   if (!(c.light_side > 0) || !(c.d_cam > 0) || !(c.tan_half_fov > 0) || !(c.beckmann_m > 0)) return FR_ERR_INVALID_ARG;
   if (c.brdf_model < 0 || c.brdf_model > 1 || c.fresnel < 0 || c.fresnel > 1 || c.light_layout < 0 ||
-      c.light_layout > 1 || (c.light_layout == 1 && c.n_lights != 20))
+      c.light_layout > 1 || (c.light_layout == 1 && c.n_lights != 20) || c.light_prior < 0 || c.light_prior > 2)
     return FR_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return FR_ERR_CUDA;
@@ -820,7 +820,7 @@ int fr_loss(fr_ctx* ctx, const float* theta, int32_t W, int32_t H, const float* 
   k_loss_data<<<blocks, 256, 0, s>>>(n, image, target, mask, loss, d_image);
   CKL();
   k_loss_reg<<<1, 256, 0, s>>>(theta, ctx->K_id + ctx->K_exp + ctx->K_alb, ctx->off_lights(), 3 * ctx->cfg.n_lights,
-                               m, w1, w2, loss, grad);
+                               ctx->cfg.light_prior, m, w1, w2, loss, grad);
   CKL();
   ctx->mark(PH_LOSS, 1);
   return FR_OK;

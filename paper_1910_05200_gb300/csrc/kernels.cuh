@@ -179,7 +179,7 @@ __global__ void k_batch_gather_theta(int n_frames, int P, int K_id, int K_exp, i
                                      float* __restrict__ theta);
 __global__ void k_batch_reduce(int n_frames, int P, int K_id, int K_exp, int K_alb, int n_light_vals,
                                const float* __restrict__ theta, const double* __restrict__ grad_full,
-                               const double* __restrict__ loss_frames, const float* __restrict__ m, float w1,
+                               const double* __restrict__ loss_frames, int prior, const float* __restrict__ m, float w1,
                                float w2, double* __restrict__ grad_s, double* __restrict__ grad_f,
                                double* __restrict__ loss);
 
@@ -215,8 +215,26 @@ __global__ void k_bwd_sedge(RenderArgs a, GradBufs gb);
 __global__ void k_loss_data(int n_pix, const float* __restrict__ image, const float* __restrict__ target,
                             const uint8_t* __restrict__ mask, double* __restrict__ loss, float* __restrict__ d_image);
 __global__ void k_loss_reg(const float* __restrict__ theta, int n_prior, int off_lights, int n_light_vals,
-                           const float* __restrict__ m, float w1, float w2, double* __restrict__ loss,
+                           int prior, const float* __restrict__ m, float w1, float w2, double* __restrict__ loss,
                            double* __restrict__ grad);
+
+// m of E_light (Eq. 1) for light value i = 3 j + c of the n lights l[3n]:
+// prior 0 the caller's m (zero when null), 1 the mean of the lights in
+// channel c, 2 the mean of light j's channels.  FP64, summed in index order.
+__device__ inline double light_prior_mean(const float* __restrict__ l, int n, int prior,
+                                          const float* __restrict__ m, int i) {
+  if (prior == 1) {
+    const int c = i % 3;
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s += (double)l[3 * k + c];
+    return s / (double)n;
+  }
+  if (prior == 2) {
+    const int j = i / 3;
+    return ((double)l[3 * j] + (double)l[3 * j + 1] + (double)l[3 * j + 2]) / 3.0;
+  }
+  return m ? (double)m[i] : 0.0;
+}
 
 // denoiser (denoise.cu)
 __global__ void k_mlp_infer(int n_pix, const float* __restrict__ w, const float* __restrict__ aov,

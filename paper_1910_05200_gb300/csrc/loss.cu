@@ -29,9 +29,11 @@ __global__ void k_loss_data(int n_pix, const float* __restrict__ image, const fl
 }
 
 // w1 (|alpha|^2 + |beta|^2 + |delta|^2) + w2 sum_j |l_j - m_j|^2 and their
-// gradients (added to grad when it is non-null).  One block.
+// gradients (added to grad when it is non-null).  One block.  When m follows
+// the lights (prior 1, 2) the gradient through m vanishes: it is minus the
+// mean of deviations that sum to zero.
 __global__ void k_loss_reg(const float* __restrict__ theta, int n_prior, int off_lights, int n_light_vals,
-                           const float* __restrict__ m, float w1, float w2, double* __restrict__ loss,
+                           int prior, const float* __restrict__ m, float w1, float w2, double* __restrict__ loss,
                            double* __restrict__ grad) {
   __shared__ double red[32];
   double acc = 0.0;
@@ -41,7 +43,7 @@ __global__ void k_loss_reg(const float* __restrict__ theta, int n_prior, int off
     if (grad) grad[i] += 2.0 * (double)w1 * t;
   }
   for (int i = threadIdx.x; i < n_light_vals; i += blockDim.x) {
-    double d = (double)theta[off_lights + i] - (m ? (double)m[i] : 0.0);
+    double d = (double)theta[off_lights + i] - light_prior_mean(theta + off_lights, n_light_vals / 3, prior, m, i);
     acc += (double)w2 * d * d;
     if (grad) grad[off_lights + i] += 2.0 * (double)w2 * d;
   }

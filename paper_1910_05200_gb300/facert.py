@@ -25,7 +25,7 @@ class FrConfig(C.Structure):
                 ("light_side", C.c_float), ("beckmann_m", C.c_float), ("eps_pedge", C.c_float),
                 ("eps_sedge", C.c_float), ("shadow_tmin", C.c_float), ("clip_kappa", C.c_float),
                 ("n_lights", C.c_int32), ("brdf_model", C.c_int32), ("fresnel", C.c_int32),
-                ("light_layout", C.c_int32)]
+                ("light_layout", C.c_int32), ("light_prior", C.c_int32)]
 
 
 class FrRenderOpts(C.Structure):

@@ -8,7 +8,10 @@ light_layout).  For one seeded full-face parameter vector this reports
   the default one;
 * for each reading, a fit of its own render (the target) with the default
   reading (model mismatch) and with the reading itself (the inverse loop of
-  inverse.py): parameter errors against the truth and the final loss.
+  inverse.py): parameter errors against the truth and the final loss;
+* for each reading of m_j in E_light (fr_config.light_prior: the given m,
+  here zero; the mean of the lights per channel; each light's channel mean),
+  a fit of the default render: parameter errors and final loss.
 
     python -m paper_1910_05200_gb300.readings_eval [--iters N]
 """
@@ -29,6 +32,8 @@ READINGS = {
     "GGX + Smith + Schlick F": dict(brdf_model=1, fresnel=1),
     "icosphere lights": dict(light_layout=1),
 }
+
+LIGHT_PRIORS = {"m given (zero)": 0, "mean of the lights per channel": 1, "each light's channel mean": 2}
 
 
 def _rrmse(x, ref):
@@ -56,6 +61,14 @@ def run(iters=300, spp_fit=16, spp_ref=256, device=0):
             entry[label] = {"param_error": inverse.parameter_errors(res.theta, truth),
                             "final_loss": float(res.loss[-10:].mean()), "ms_per_iter": res.ms_per_iter}
         out["readings"][name] = entry
+    out["light_prior"] = {}
+    for name, prior in LIGHT_PRIORS.items():
+        r = rs[names[0]] if prior == 0 else \
+            facert.Renderer(scene, device=device, config=facert.default_config(light_prior=prior))
+        res = inverse.optimize(r, ref, W, H, spp_fit, iters=iters, seed=1)
+        out["light_prior"][name] = {"param_error": inverse.parameter_errors(res.theta, truth),
+                                    "final_loss": float(res.loss[-10:].mean()), "ms_per_iter": res.ms_per_iter}
+        r.sync()
     for r in rs.values():
         r.sync()
     return out

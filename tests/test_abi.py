@@ -43,16 +43,16 @@ def test_host_only_calls(lib):
     lib.fr_strerror.restype = C.c_char_p
     assert lib.fr_strerror(-5) == b"device traversal limit reached"
 
-    class Cfg(C.Structure):   # fr_config: 9 floats, n_lights, brdf_model, fresnel, light_layout
+    class Cfg(C.Structure):   # fr_config: 9 floats, n_lights, brdf_model, fresnel, light_layout, light_prior
         _fields_ = [(n, C.c_float) for n in ("a", "b", "c", "d", "e", "f", "g", "h", "i")] + \
-                   [(n, C.c_int32) for n in ("n", "brdf", "fresnel", "layout")]
+                   [(n, C.c_int32) for n in ("n", "brdf", "fresnel", "layout", "prior")]
 
     from paper_1910_05200_gb300 import facert
     assert C.sizeof(Cfg) == C.sizeof(facert.FrConfig)
     c = Cfg()
     lib.fr_default_config(C.byref(c))
     assert c.n == 20 and abs(c.a - 0.275) < 1e-7 and abs(c.d - 0.6) < 1e-7
-    assert (c.brdf, c.fresnel, c.layout) == (0, 0, 0)
+    assert (c.brdf, c.fresnel, c.layout, c.prior) == (0, 0, 0, 0)
     # creating a context without a GPU fails cleanly with a negative code
     h = C.c_void_p()
     rc = lib.fr_create(C.byref(h), None, 0)

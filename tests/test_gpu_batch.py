@@ -87,9 +87,9 @@ def dev(a):
 
 
 class Case:
-    def __init__(self, fr, scene, sizes, spp, seed=7):
+    def __init__(self, fr, scene, sizes, spp, seed=7, config=None):
         self.fr, self.scene, self.spp = fr, scene, spp
-        self.r = fr.Renderer(scene, device=0)
+        self.r = fr.Renderer(scene, device=0, config=config)
         self.frames, self.thetas = S.make_batch(scene, seed=seed, n_on=8, max_angle_deg=10.0, t_std=0.02,
                                                 sizes=sizes)
         self.targets = S.noise_images(self.frames, seed=seed + 1)
@@ -302,6 +302,32 @@ def test_targets_masks_and_prior_can_be_replaced(fr, tiny):
     lights = tf[:, 96:]
     prior_change = w2 * float(np.sum(lights ** 2) - np.sum((lights - c.m.astype(np.float64)) ** 2))
     assert l_plain - l_full == pytest.approx(extra + prior_change, rel=1e-9, abs=1e-9)
+
+
+@pytest.mark.parametrize("prior", [1, 2])
+def test_batch_light_prior_readings(oracle, fr, tiny, prior):
+    """m following each frame's own lights (mean per channel; each light's
+    channel mean): the light term of the batch loss and its gradient against
+    the oracle frame by frame.  A second step with w2 = 0 takes out the data
+    term; the given m is ignored."""
+    c = Case(fr, tiny[0], [(16, 12), (9, 13)], 4, seed=51, config=fr.default_config(light_prior=prior))
+    w2 = 5.0
+    l0, _, f0, _ = c.b.step(c.ts, c.tf, W1, 0.0, iter=ITER, images=False)
+    l1, _, f1, _ = c.b.step(c.ts, c.tf, W1, w2, iter=ITER, images=False)
+    c.r.sync()
+    o = S.param_offsets(*K)
+    z = np.zeros((1, 1, 3), np.float32)
+    e_light, g_light = 0.0, []
+    for f in range(len(c.frames)):
+        val, _, gr = oracle.loss(default_config(W=1, H=1, light_prior=prior), c.scene, c.thetas[f], z, z,
+                                 None, None, 0.0, w2)
+        e_light += val
+        g_light.append(gr[o["lights"]:o["lights"] + 60])
+    assert l1.item() - l0.item() == pytest.approx(e_light, rel=1e-9)
+    dg = (f1 - f0).cpu().numpy()[:, 96:]
+    for f in range(len(c.frames)):
+        ref = g_light[f]
+        assert np.all(np.abs(dg[f] - ref) <= 1e-4 * np.abs(ref).max() + 1e-6 * np.abs(ref)), f
 
 
 def test_batch_refuses_after_new_mesh(fr, tiny):

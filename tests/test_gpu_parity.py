@@ -189,6 +189,31 @@ def test_loss_matches_oracle(oracle, tiny, tiny_r):
     assert np.allclose(grad.cpu().numpy(), gref, rtol=1e-12, atol=1e-12)
 
 
+@pytest.mark.parametrize("prior", [1, 2])
+def test_light_prior_readings_match_oracle(oracle, fr, tiny, prior):
+    """E_light with m following the lights (mean per channel; each light's
+    channel mean): value and gradient against the oracle's chain rule."""
+    scene, theta, _ = tiny
+    W, H = 17, 9
+    rng = np.random.default_rng(8)
+    th = theta.copy()
+    o = S.param_offsets(scene.B_id.shape[1], scene.B_exp.shape[1], scene.B_alb.shape[1])
+    th[o["lights"]:o["lights"] + 60] = rng.uniform(0, 2, size=60)
+    img = rng.uniform(size=(H, W, 3)).astype(np.float32)
+    tgt = rng.uniform(size=(H, W, 3)).astype(np.float32)
+    m = rng.uniform(size=60).astype(np.float32)            # ignored by these readings
+    r = fr.Renderer(scene, device=0, config=fr.default_config(light_prior=prior))
+    dev = lambda a: torch.tensor(a, device="cuda:0")
+    grad = torch.zeros(len(th), device="cuda:0", dtype=torch.float64)
+    loss = r.loss(dev(th), dev(img), dev(tgt), None, dev(m), 0.3, 0.7, None, grad)
+    val, _, gref = oracle.loss(default_config(W=W, H=H, light_prior=prior), scene, th, img, tgt, None, None,
+                               0.3, 0.7)
+    assert abs(loss.item() - val) <= 1e-12 * abs(val)
+    assert np.allclose(grad.cpu().numpy(), gref, rtol=1e-12, atol=1e-12)
+    with pytest.raises(RuntimeError):
+        fr.Renderer(scene, device=0, config=fr.default_config(light_prior=3))
+
+
 def test_all_lights_off_is_black(oracle, tiny, tiny_r):
     scene, theta, _ = tiny
     th = theta.copy()

@@ -15,7 +15,12 @@ retyping its formula:
 * the oracle's gradient is the exact derivative of its own estimate
   (linearity in lights and texels, finite differences in geometry);
 * the icosphere directions are the upper half of a once-subdivided
-  icosahedron: every nearest-neighbour angle is atan(2)/2 or 36 degrees.
+  icosahedron: every nearest-neighbour angle is atan(2)/2 or 36 degrees;
+* the light prior m_j of E_light (Eq. 1), read as the mean of the lights per
+  channel or as each light's channel mean: E_light equals N times the
+  per-channel variances, or 3 times the per-light variances (numpy's var);
+  it vanishes for equal or grey lights; its gradient matches central
+  differences, which are exact for a quadratic at dyadic steps.
 """
 import math
 
@@ -24,6 +29,7 @@ import pytest
 
 from oracle import default_config
 from paper_1910_05200_gb300 import synthetic as S
+from tests import closed_forms as CF
 
 VARIANTS = [(1, 0), (0, 1), (1, 1)]          # (brdf_model, fresnel); (0, 0) is pinned in test_oracle_pins
 
@@ -155,3 +161,72 @@ def test_icosphere_light_stage(oracle):
     assert ang.min() > half_edge - 1e-4
     # the default layout is unchanged by the switch
     assert np.array_equal(oracle.light_stage(20, 3.0, layout=0), oracle.light_stage(20, 3.0))
+
+
+# ---------------------------------------------------------------------------
+# light prior readings: E_light = sum_j |l_j - m_j|^2 with m following the lights
+
+def _prior_case(seed=4):
+    sc = CF.plain_scene([(0, 0, 0), (1, 0, 0), (0, 1, 0)], [(0, 1, 2)])
+    o = S.param_offsets(0, 0, 0)
+    rng = np.random.default_rng(seed)
+    th = CF.plain_theta()
+    k = rng.integers(0, 129, size=(20, 3))
+    k[19] += (-k.sum(axis=0)) % 5                          # column sums divisible by 5:
+    L = k / 64.0                                           # values and channel means dyadic
+    th[o["lights"]:o["lights"] + 60] = L.reshape(-1)
+    img = np.zeros((1, 2, 3), np.float32)
+    return sc, th, L, img, o
+
+
+def _e_light(oracle, prior, th, sc, img, m=None, w2=1.0):
+    cfg = default_config(W=2, H=1, light_prior=prior)
+    val, _, gr = oracle.loss(cfg, sc, th, img, img, None, m, 0.0, w2)
+    return val, gr
+
+
+def test_light_prior_closed_forms(oracle):
+    sc, th, L, img, o = _prior_case()
+    v1, _ = _e_light(oracle, 1, th, sc, img)
+    assert v1 == pytest.approx(20 * np.var(L, axis=0).sum(), rel=1e-13)
+    v2, _ = _e_light(oracle, 2, th, sc, img)
+    assert v2 == pytest.approx(3 * np.var(L, axis=1).sum(), rel=1e-13)
+    # the given m is ignored when m follows the lights
+    m = np.full(60, 7.0, np.float32)
+    assert _e_light(oracle, 1, th, sc, img, m)[0] == v1 and _e_light(oracle, 2, th, sc, img, m)[0] == v2
+    # mean over lights, frozen and given, has the same value and gradient:
+    # the term through m is minus the mean of deviations that sum to zero
+    mm = np.tile(L.mean(axis=0), 20).astype(np.float32)
+    v0, g0 = _e_light(oracle, 0, th, sc, img, mm, w2=0.5)
+    v1b, g1 = _e_light(oracle, 1, th, sc, img, None, w2=0.5)
+    assert v0 == pytest.approx(v1b, rel=1e-13)
+    np.testing.assert_allclose(g1, g0, rtol=0, atol=1e-13)
+
+
+def test_light_prior_vanishes_on_equal_and_grey_lights(oracle):
+    sc, th, L, img, o = _prior_case()
+    eq = th.copy()
+    eq[o["lights"]:o["lights"] + 60] = np.tile([0.5, 1.25, 2.0], 20)
+    v, g = _e_light(oracle, 1, eq, sc, img)
+    assert v == 0.0 and np.all(g == 0.0)
+    assert _e_light(oracle, 2, eq, sc, img)[0] > 0
+    grey = th.copy()
+    grey[o["lights"]:o["lights"] + 60] = np.repeat(L[:, 0], 3)
+    v, g = _e_light(oracle, 2, grey, sc, img)
+    assert v == 0.0 and np.all(g == 0.0)
+    assert _e_light(oracle, 1, grey, sc, img)[0] > 0
+
+
+@pytest.mark.parametrize("prior", [0, 1, 2])
+def test_light_prior_gradient_central_differences(oracle, prior):
+    sc, th, L, img, o = _prior_case(seed=9)
+    m = (np.arange(60) % 5 / 4.0).astype(np.float32)
+    _, g = _e_light(oracle, prior, th, sc, img, m, w2=0.75)
+    h = 1.0 / 64
+    for k in (0, 1, 2, 7, 31, 59):
+        tp, tm = th.copy(), th.copy()
+        tp[o["lights"] + k] += h
+        tm[o["lights"] + k] -= h
+        fd = (_e_light(oracle, prior, tp, sc, img, m, w2=0.75)[0] -
+              _e_light(oracle, prior, tm, sc, img, m, w2=0.75)[0]) / (2 * h)
+        assert g[o["lights"] + k] == pytest.approx(fd, rel=1e-11, abs=1e-12)
