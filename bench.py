@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--cpu-pixels", type=int, default=768, help="cpu_baseline leg: oracle pixels (all spp)")
     ap.add_argument("--ref-pixels", type=int, default=32, help="reference arm: oracle pixels per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--api", default="step", choices=["step", "calls"],
+                    help="step: fr_step (fused render, loss and interior adjoint); calls: fr_render, fr_loss and "
+                         "fr_render_backward")
     ap.add_argument("--profile-steps", type=int, default=0, help="only run this many steps, no extras (ncu)")
     ap.add_argument("--profile-res", type=int, default=0, help="with --profile-steps: image side (small ncu case)")
     return ap.parse_args()
@@ -213,11 +216,18 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
     seed0 = 1000 * rank
 
+    def run_step(th_, tgt_, seed):
+        """One step through the public API: image, loss (returned) and gradient."""
+        if args.api == "step":
+            return r.step(th_, tgt_, W, H, spp, seed=seed, image=image, d_image=d_image, grad=grad)[1]
+        r.render(th_, W, H, spp, seed=seed, out=image)
+        ls = r.loss(th_, image, tgt_, d_image=d_image)
+        r.backward(th_, d_image, W, H, spp, seed=seed, grad=grad)
+        return ls
+
     def step(i):
         nonlocal loss
-        r.render(th, W, H, spp, seed=seed0 + i, out=image)
-        loss = r.loss(th, image, target, d_image=d_image, grad=None)
-        r.backward(th, d_image, W, H, spp, seed=seed0 + i, grad=grad)
+        loss = run_step(th, target, seed0 + i)
 
     if args.profile_steps:
         for i in range(args.profile_steps):
@@ -245,9 +255,7 @@ def run_ours(args):
     for i in range(args.steps):
         flush.zero_()
         ev[i][0].record(stream)
-        r.render(th, W, H, spp, seed=seed0 + args.warmup + i, out=image)
-        loss = r.loss(th, image, target, d_image=d_image)
-        r.backward(th, d_image, W, H, spp, seed=seed0 + args.warmup + i, grad=grad)
+        loss = run_step(th, target, seed0 + args.warmup + i)
         ev[i][1].record(stream)
         phases.append(r.timings())        # synchronises between steps (outside the step's events)
     torch.cuda.synchronize()
@@ -259,6 +267,9 @@ def run_ours(args):
     r.sync()
     ms = [a.elapsed_time(b) for a, b in ev]
     ph_mean = {k: float(np.mean([p[k] for p in phases])) for k in phases[0]}
+    if args.api == "step":      # fr_step's fused kernel is timed as the forward phase
+        ph_mean["forward_loss_interior_fused"] = ph_mean.pop("forward")
+        ph_mean.pop("interior")
     samples = W * H * spp
     t_step, value = aggregate(float(np.mean(ms)), samples, world, dev)
 
@@ -277,9 +288,7 @@ def run_ours(args):
         a.record(stream)
         th_d.copy_(th_h, non_blocking=True)
         tgt_d.copy_(tgt_h, non_blocking=True)
-        r.render(th_d, W, H, spp, seed=7 + i, out=image)
-        ls = r.loss(th_d, image, tgt_d, d_image=d_image)
-        r.backward(th_d, d_image, W, H, spp, seed=7 + i, grad=grad)
+        ls = run_step(th_d, tgt_d, 7 + i)
         grad_h.copy_(grad, non_blocking=True)
         loss_h.copy_(ls, non_blocking=True)
         b.record(stream)
@@ -312,6 +321,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": workload_config(c, scene),
+                "api": "fr_step" if args.api == "step" else "fr_render + fr_loss + fr_render_backward",
                 "ms_phases": ph_mean,
                 "e2e": {"value": world * samples / (t_e2e * 1e-3) / 1e6, "unit": "Msamples/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": t_e2e},

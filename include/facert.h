@@ -178,6 +178,25 @@ int fr_loss(fr_ctx* ctx, const float* theta, int32_t W, int32_t H, const float* 
             const uint8_t* mask, const float* m, float w1, float w2, double* loss, float* d_image,
             double* grad);
 
+/* One step of the optimisation (Eq. 1 and its gradient) in one call: the
+ * render of fr_render, the loss of fr_loss and the gradient of both,
+ *   grad = d(E_data + w1 E_prior + w2 E_light)/d theta (overwritten),
+ * all terms of fr_render_backward unless opts->terms selects some.
+ * theta[P], target[H*W*3] FP32 device; mask[H*W] uint8 device or NULL; m
+ * as fr_loss; image[H*W*3] FP32 device (written); d_image[H*W*3] FP32
+ * device (written with dE_data/d image) or NULL (a context buffer is used);
+ * loss: one FP64 device scalar (overwritten); grad[P] FP64 device.
+ * Results equal those of fr_render, fr_loss and fr_render_backward with the
+ * same opts: the image bit for bit, loss and gradient up to the order of
+ * floating-point additions.  When spp divides 32 the render, the data term's
+ * adjoint and the interior adjoint run as one kernel (a pixel's samples share
+ * a warp): each sample's interior adjoint reuses its primary hit and the
+ * shadow decisions of the lights that are on; the geometry is prepared once.
+ * Other spp run the three calls in sequence.  Timings (fr_get_timings): the
+ * fused kernel is the forward phase. */
+int fr_step(fr_ctx* ctx, const float* theta, const fr_render_opts* opts, const float* target, const uint8_t* mask,
+            const float* m, float w1, float w2, float* image, float* d_image, double* loss, double* grad);
+
 /* Geometry stage alone (Face Modeling paragraph), for inspection and tests:
  * posed vertices X[V*3] FP32, unit vertex normals N[V*3] FP32 and albedo
  * A[V*3] FP32, all device (any may be NULL).  Returns the number of camera

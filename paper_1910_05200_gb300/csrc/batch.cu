@@ -41,15 +41,17 @@ FR_DEV void flush_lights(WarpState& w, int lane) {
 }
 
 // Shading-point state of one sample for the adjoints.
+// vis: the forward's visibility bits of the sample, or null (traced again).
 FR_DEV void sample_adjoints(const RenderArgs& a, const GradBufs& g, float* sC, float* sL, bool valid, int px,
-                            int py, int s, int2 hit, V3 dv, unsigned long long* cnt) {
+                            int py, int s, int2 hit, V3 dv, unsigned long long* cnt, const uint32_t* vis = nullptr) {
   uint32_t pix = 0;
   V3 d{0, 0, -1}, x32{0, 0, 0}, wrgb{0, 0, 0};
   int flip = 1;
   valid = valid && hit.x >= 0 && (dv.x != 0.0f || dv.y != 0.0f || dv.z != 0.0f);
   if (valid) {
     d = sample_dir(a, px, py, s, pix);
-    interior_sample(a, g, sC, sL, pix, s, d, hit.x, __int_as_float(hit.y), dv, cnt ? cnt + CNT_INTERIOR : nullptr);
+    interior_sample(a, g, sC, sL, pix, s, d, hit.x, __int_as_float(hit.y), dv, cnt ? cnt + CNT_INTERIOR : nullptr,
+                    vis);
     wrgb = dv * (1.0f / (float)a.spp);
     flip = face_flip(a.mesh, hit.x, d);
     x32 = hit_point(a.cam.o, d, __int_as_float(hit.y));
@@ -95,10 +97,10 @@ FR_DEV void tile_small(WarpState& w, const BatchFrame& F, float* sC, int tile, i
     bool valid = k < nS && px < a.W && py < a.H;
     V3 L{0, 0, 0};
     int2 hit = make_int2(-1, 0);
-    uint32_t pix = 0;
+    uint32_t pix = 0, vis = 0u;
     if (valid) {
       V3 d = sample_dir(a, px, py, s, pix);
-      L = radiance(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt, nullptr, &hit);
+      L = radiance(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt, nullptr, &hit, &vis);
     }
     float v0 = L.x, v1 = L.y, v2 = L.z;
     for (int off = spp >> 1; off > 0; off >>= 1) {
@@ -108,7 +110,7 @@ FR_DEV void tile_small(WarpState& w, const BatchFrame& F, float* sC, int tile, i
     }
     V3 dv{0, 0, 0};
     if (valid) dv = pixel_loss(F, pix, V3{v0 * inv, v1 * inv, v2 * inv}, s == 0, lacc);
-    sample_adjoints(a, w.g, sC, w.sL, valid, px, py, s, hit, dv, cnt);
+    sample_adjoints(a, w.g, sC, w.sL, valid, px, py, s, hit, dv, cnt, &vis);
   }
 }
 
@@ -281,10 +283,10 @@ __global__ void __launch_bounds__(256, 3) k_batch_fwd(PhaseArgs p) {
   unsigned long long* cnt = p.counters;
   V3 L{0, 0, 0}, d{0, 0, -1};
   int2 hit = make_int2(-1, 0);
-  uint32_t pix = 0;
+  uint32_t pix = 0, vis = 0u;
   if (valid) {
     d = sample_dir(a, px, py, s, pix);
-    L = radiance(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt, nullptr, &hit);
+    L = radiance(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt, nullptr, &hit, &vis);
   }
   float v0 = L.x, v1 = L.y, v2 = L.z;
   for (int off = spp >> 1; off > 0; off >>= 1) {
@@ -298,7 +300,9 @@ __global__ void __launch_bounds__(256, 3) k_batch_fwd(PhaseArgs p) {
   if (valid) dv = pixel_loss(F, pix, V3{v0 * inv, v1 * inv, v2 * inv}, s == 0, lacc);
   bool adj = valid && hit.x >= 0 && (dv.x != 0.0f || dv.y != 0.0f || dv.z != 0.0f);
   if (tid < total) g.hits[tid] = adj ? hit : make_int2(-1, 0);
-  if (adj) interior_sample(a, g, sC, sL, pix, s, d, hit.x, __int_as_float(hit.y), dv, cnt ? cnt + CNT_INTERIOR : nullptr);
+  if (adj)
+    interior_sample(a, g, sC, sL, pix, s, d, hit.x, __int_as_float(hit.y), dv, cnt ? cnt + CNT_INTERIOR : nullptr,
+                    &vis);
   for (int off = 16; off > 0; off >>= 1) lacc += __shfl_xor_sync(0xffffffffu, lacc, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lacc;
   __syncthreads();

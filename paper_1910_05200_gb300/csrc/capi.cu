@@ -511,6 +511,32 @@ int check_opts(fr_ctx* ctx, const fr_render_opts* o) {
   return FR_OK;
 }
 
+// The backward after its interior pass: primary-visibility and shadow edge
+// passes, then the normal/geometry adjoint added into grad.
+int edges_and_adjoint(fr_ctx* ctx, const float* theta, const fr_render_opts* opts, const RenderArgs& a,
+                      const GradBufs& gb, int terms, double* grad) {
+  cudaStream_t s = ctx->stream;
+  long long tiled = (long long)(((opts->W + 7) / 8) * ((opts->H + 7) / 8)) * 64 * opts->spp;
+  if (terms & TERM_PEDGE) {
+    ctx->mark(PH_PEDGE, 0);
+    k_bwd_pedge<<<grid_for((long long)opts->W * opts->H * opts->spp, 256), 256, 0, s>>>(a, gb);
+    CKL();
+    ctx->mark(PH_PEDGE, 1);
+  }
+  if (terms & TERM_SEDGE) {
+    dim3 grid(grid_for(tiled, 256), ctx->cfg.n_lights);
+    ctx->mark(PH_SEDGE, 0);
+    k_bwd_sedge<<<grid, 256, 0, s>>>(a, gb);
+    CKL();
+    ctx->mark(PH_SEDGE, 1);
+  }
+  ctx->mark(PH_ADJOINT, 0);
+  int rc = adjoint(ctx, theta, main_view(ctx), grad, true);
+  if (rc) return rc;
+  ctx->mark(PH_ADJOINT, 1);
+  return FR_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -585,7 +611,7 @@ void fr_destroy(fr_ctx* ctx) {
   ctx->e4codes.free_(); ctx->e4src.free_(); ctx->e4boxes.free_(); ctx->e4cones.free_();
   ctx->sil.free_(); ctx->n_sil.free_(); ctx->block_count.free_(); ctx->err_flag.free_(); ctx->counters.free_();
   ctx->dX.free_(); ctx->dN.free_(); ctx->dA.free_(); ctx->gs.free_(); ctx->dXm.free_(); ctx->dC.free_(); ctx->dL.free_();
-  ctx->hits.free_(); ctx->aov_scratch.free_();
+  ctx->hits.free_(); ctx->aov_scratch.free_(); ctx->dimg.free_();
   ctx->mlp_w.free_(); ctx->mlp_m.free_(); ctx->mlp_v.free_(); ctx->mlp_g.free_(); ctx->mlp_scratch.free_();
   if (ctx->events_made)
     for (int i = 0; i < NPHASE; ++i) { cudaEventDestroy(ctx->ev[i][0]); cudaEventDestroy(ctx->ev[i][1]); }
@@ -727,7 +753,8 @@ int fr_render(fr_ctx* ctx, const float* theta, const fr_render_opts* opts, float
   rc = prepare(ctx, theta, opts->W, opts->H);
   if (rc) return rc;
   RenderArgs a = render_args(ctx, theta, opts, main_view(ctx));
-  if (ctx->counters_on) CK(cudaMemsetAsync(ctx->counters.p, 0, 4 * sizeof(unsigned long long), ctx->stream));
+  if (ctx->counters_on)
+    CK(cudaMemsetAsync(ctx->counters.p + CNT_FWD, 0, CNT_PER_KERNEL * sizeof(unsigned long long), ctx->stream));
   bool shuffle = opts->spp <= 32 && (32 % opts->spp) == 0;
   const size_t npix = (size_t)opts->W * opts->H;
   if (!shuffle) CK(cudaMemsetAsync(image, 0, sizeof(float) * 3 * npix, ctx->stream));
@@ -767,7 +794,8 @@ int fr_render_backward(fr_ctx* ctx, const float* theta, const fr_render_opts* op
   CK(cudaMemsetAsync(ctx->dA.p, 0, sizeof(float4) * V, s));
   CK(cudaMemsetAsync(ctx->dC.p, 0, sizeof(float) * CS * CS, s));
   CK(cudaMemsetAsync(ctx->dL.p, 0, sizeof(float) * 3 * MAX_LIGHTS, s));
-  if (ctx->counters_on) CK(cudaMemsetAsync(ctx->counters.p + 4, 0, 12 * sizeof(unsigned long long), s));
+  if (ctx->counters_on)
+    CK(cudaMemsetAsync(ctx->counters.p + CNT_INTERIOR, 0, (CNT_TOTAL - CNT_INTERIOR) * sizeof(unsigned long long), s));
   RenderArgs a = render_args(ctx, theta, opts, main_view(ctx));
   const int terms = opts->terms ? opts->terms : (TERM_INTERIOR | TERM_PEDGE | TERM_SEDGE);
   long long tiled = (long long)(((opts->W + 7) / 8) * ((opts->H + 7) / 8)) * 64 * opts->spp;
@@ -785,24 +813,7 @@ int fr_render_backward(fr_ctx* ctx, const float* theta, const fr_render_opts* op
     CKL();
     ctx->mark(PH_INTERIOR, 1);
   }
-  if (terms & TERM_PEDGE) {
-    ctx->mark(PH_PEDGE, 0);
-    k_bwd_pedge<<<grid_for((long long)opts->W * opts->H * opts->spp, 256), 256, 0, s>>>(a, gb);
-    CKL();
-    ctx->mark(PH_PEDGE, 1);
-  }
-  if (terms & TERM_SEDGE) {
-    dim3 grid(grid_for(tiled, 256), ctx->cfg.n_lights);
-    ctx->mark(PH_SEDGE, 0);
-    k_bwd_sedge<<<grid, 256, 0, s>>>(a, gb);
-    CKL();
-    ctx->mark(PH_SEDGE, 1);
-  }
-  ctx->mark(PH_ADJOINT, 0);
-  rc = adjoint(ctx, theta, main_view(ctx), grad, true);
-  if (rc) return rc;
-  ctx->mark(PH_ADJOINT, 1);
-  return FR_OK;
+  return edges_and_adjoint(ctx, theta, opts, a, gb, terms, grad);
 }
 
 int fr_loss(fr_ctx* ctx, const float* theta, int32_t W, int32_t H, const float* image, const float* target,
@@ -821,6 +832,69 @@ int fr_loss(fr_ctx* ctx, const float* theta, int32_t W, int32_t H, const float* 
   CKL();
   k_loss_reg<<<1, 256, 0, s>>>(theta, ctx->K_id + ctx->K_exp + ctx->K_alb, ctx->off_lights(), 3 * ctx->cfg.n_lights,
                                ctx->cfg.light_prior, m, w1, w2, loss, grad);
+  CKL();
+  ctx->mark(PH_LOSS, 1);
+  return FR_OK;
+}
+
+int fr_step(fr_ctx* ctx, const float* theta, const fr_render_opts* opts, const float* target, const uint8_t* mask,
+            const float* m, float w1, float w2, float* image, float* d_image, double* loss, double* grad) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  int rc = check_opts(ctx, opts);
+  if (rc) return rc;
+  if (!theta || !target || !image || !loss || !grad)
+    return fail(ctx, FR_ERR_INVALID_ARG, "step: theta, target, image, loss or grad is null");
+  if (!ctx->have_bases) return fail(ctx, FR_ERR_NOT_READY, "bases not uploaded");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  const size_t npix = (size_t)opts->W * opts->H;
+  if (!d_image) {
+    if (ctx->dimg.n < 3 * npix) CK(ctx->dimg.alloc(3 * npix));
+    d_image = ctx->dimg.p;
+  }
+  const int n_prior = ctx->K_id + ctx->K_exp + ctx->K_alb, nlv = 3 * ctx->cfg.n_lights;
+  if (!(opts->spp <= 32 && 32 % opts->spp == 0)) {
+    // a pixel's samples span several warps: the three calls in sequence,
+    // then the prior and light terms' gradient (their value is in *loss)
+    rc = fr_render(ctx, theta, opts, image, nullptr);
+    if (!rc) rc = fr_loss(ctx, theta, opts->W, opts->H, image, target, mask, m, w1, w2, loss, d_image, nullptr);
+    if (!rc) rc = fr_render_backward(ctx, theta, opts, d_image, grad, 0);
+    if (rc) return rc;
+    k_loss_reg<<<1, 256, 0, s>>>(theta, n_prior, ctx->off_lights(), nlv, ctx->cfg.light_prior, m, w1, w2, nullptr,
+                                 grad);
+    CKL();
+    return FR_OK;
+  }
+  rc = prepare(ctx, theta, opts->W, opts->H);
+  if (rc) return rc;
+  const int V = ctx->V;
+  CK(cudaMemsetAsync(grad, 0, sizeof(double) * ctx->n_params(), s));
+  CK(cudaMemsetAsync(loss, 0, sizeof(double), s));
+  CK(cudaMemsetAsync(ctx->dX.p, 0, sizeof(float4) * V, s));
+  CK(cudaMemsetAsync(ctx->dN.p, 0, sizeof(float4) * V, s));
+  CK(cudaMemsetAsync(ctx->dA.p, 0, sizeof(float4) * V, s));
+  CK(cudaMemsetAsync(ctx->dC.p, 0, sizeof(float) * CS * CS, s));
+  CK(cudaMemsetAsync(ctx->dL.p, 0, sizeof(float) * 3 * MAX_LIGHTS, s));
+  if (ctx->counters_on) CK(cudaMemsetAsync(ctx->counters.p, 0, CNT_TOTAL * sizeof(unsigned long long), s));
+  RenderArgs a = render_args(ctx, theta, opts, main_view(ctx));
+  const int terms = opts->terms ? opts->terms : (TERM_INTERIOR | TERM_PEDGE | TERM_SEDGE);
+  long long tiled = (long long)(((opts->W + 7) / 8) * ((opts->H + 7) / 8)) * 64 * opts->spp;
+  if ((terms & TERM_SEDGE) && ctx->hits.n < (size_t)tiled) CK(ctx->hits.alloc(tiled));
+  GradBufs gb;
+  gb.dX = ctx->dX.p; gb.dN = ctx->dN.p; gb.dA = ctx->dA.p; gb.dC = ctx->dC.p; gb.dL = ctx->dL.p;
+  gb.d_image = d_image;
+  gb.hits = (terms & TERM_SEDGE) ? ctx->hits.p : nullptr;
+  StepBufs sb;
+  sb.image = image; sb.d_image = d_image; sb.target = target; sb.mask = mask; sb.loss = loss;
+  sb.interior = (terms & TERM_INTERIOR) ? 1 : 0;
+  ctx->mark(PH_FORWARD, 0);
+  k_step_fwd<<<grid_for(tiled, 256), 256, 0, s>>>(a, gb, sb);
+  CKL();
+  ctx->mark(PH_FORWARD, 1);
+  rc = edges_and_adjoint(ctx, theta, opts, a, gb, terms, grad);
+  if (rc) return rc;
+  ctx->mark(PH_LOSS, 0);
+  k_loss_reg<<<1, 256, 0, s>>>(theta, n_prior, ctx->off_lights(), nlv, ctx->cfg.light_prior, m, w1, w2, loss, grad);
   CKL();
   ctx->mark(PH_LOSS, 1);
   return FR_OK;

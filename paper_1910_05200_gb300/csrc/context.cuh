@@ -88,6 +88,7 @@ struct fr_ctx {
   DBuf<float> dXm, dC, dL;
   DBuf<int2> hits;        // primary hit per tiled sample (backward)
   DBuf<float> aov_scratch;  // mean luminance per pixel (feature output, atomic path)
+  DBuf<float> dimg;       // dE_data/d image of fr_step when the caller passes none
   // denoiser: FP32 master weights, Adam moments, gradients, training scratch
   DBuf<float> mlp_w, mlp_m, mlp_v, mlp_g, mlp_scratch;
   bool have_mlp = false;

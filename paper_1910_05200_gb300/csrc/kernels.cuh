@@ -98,7 +98,7 @@ struct GradBufs {
   float* dC;              // [1024]
   float* dL;              // [3N]
   const float* d_image;   // [H*W*3]
-  int2* hits;             // per tiled sample: (face or -1, t bits), written by k_bwd_interior
+  int2* hits;             // per tiled sample: (face or -1, t bits), written by k_bwd_interior or k_step_fwd
 };
 
 // One frame of a batch: the render arguments and gradient buffers of that
@@ -209,6 +209,16 @@ __global__ void k_render_fwd(RenderArgs a, float* __restrict__ image);
 __global__ void k_render_fwd_aov(RenderArgs a, float* __restrict__ image, float* __restrict__ aov);
 __global__ void k_aov_finish(int n_pix, float* __restrict__ aov, const float* __restrict__ meanY);
 __global__ void k_bwd_interior(RenderArgs a, GradBufs gb);
+// Outputs and loss inputs of the fused single-image step (k_step_fwd).
+struct StepBufs {
+  float* image;           // [H*W*3]
+  float* d_image;         // [H*W*3] dE_data/d image, read by the edge passes
+  const float* target;    // [H*W*3]
+  const uint8_t* mask;    // [H*W] or null
+  double* loss;           // E_data is added
+  int interior;           // run the interior adjoint
+};
+__global__ void k_step_fwd(RenderArgs a, GradBufs gb, StepBufs sb);
 __global__ void k_bwd_pedge(RenderArgs a, GradBufs gb);
 __global__ void k_bwd_sedge(RenderArgs a, GradBufs gb);
 

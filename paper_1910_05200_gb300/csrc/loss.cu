@@ -29,7 +29,8 @@ __global__ void k_loss_data(int n_pix, const float* __restrict__ image, const fl
 }
 
 // w1 (|alpha|^2 + |beta|^2 + |delta|^2) + w2 sum_j |l_j - m_j|^2 and their
-// gradients (added to grad when it is non-null).  One block.  When m follows
+// gradients (value added to loss, gradient to grad, each when non-null).
+// One block.  When m follows
 // the lights (prior 1, 2) the gradient through m vanishes: it is minus the
 // mean of deviations that sum to zero.
 __global__ void k_loss_reg(const float* __restrict__ theta, int n_prior, int off_lights, int n_light_vals,
@@ -53,7 +54,7 @@ __global__ void k_loss_reg(const float* __restrict__ theta, int n_prior, int off
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    atomicAdd(loss, s);
+    if (loss) atomicAdd(loss, s);
   }
 }
 

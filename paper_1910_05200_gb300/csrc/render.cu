@@ -138,6 +138,77 @@ __global__ void __launch_bounds__(256, 3) k_bwd_interior(RenderArgs a, GradBufs 
     if (sL[i] != 0.0f) atomicAdd(&gb.dL[i], sL[i]);
 }
 
+// Fused render, data term and interior adjoint of one optimisation step
+// (Eq. 1), for spp dividing 32 so that a pixel's samples share a warp: the
+// pixel's mean is a shuffle reduction, its adjoint 2 mask (image - target) is
+// known in the warp that rendered it, and each sample's interior adjoint
+// starts from the same primary hit and the shadow decisions of the lights
+// that are on (only lights that are off trace shadow rays again).  The image
+// is bit-identical to k_render_fwd's; the adjoint and the hits written for the
+// edge passes equal k_loss_data's and k_bwd_interior's.
+__global__ void __launch_bounds__(256, 3) k_step_fwd(RenderArgs a, GradBufs gb, StepBufs sb) {
+  __shared__ float sC[CS * CS];
+  __shared__ float sL[3 * MAX_LIGHTS];
+  __shared__ double red[8];
+  for (int i = threadIdx.x; i < CS * CS; i += blockDim.x) sC[i] = 0.0f;
+  for (int i = threadIdx.x; i < 3 * MAX_LIGHTS; i += blockDim.x) sL[i] = 0.0f;
+  __syncthreads();
+  const int spp = a.spp;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)tiled_pixel_count(a.W, a.H) * spp;
+  const int ip = (int)(tid / spp), s = (int)(tid - (long long)ip * spp);
+  int px = 0, py = 0;
+  const bool valid = tid < total && tile_pixel(ip, a.W, a.H, px, py);
+  unsigned long long* cnt = a.counters;
+  V3 L{0, 0, 0}, d{0, 0, -1};
+  int2 hit = make_int2(-1, 0);
+  uint32_t pix = 0, vis = 0u;
+  if (valid) {
+    d = sample_dir(a, px, py, s, pix);
+    L = radiance(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt, nullptr, &hit, &vis);
+  }
+  float v0 = L.x, v1 = L.y, v2 = L.z;
+  for (int off = spp >> 1; off > 0; off >>= 1) {
+    v0 += __shfl_xor_sync(0xffffffffu, v0, off);
+    v1 += __shfl_xor_sync(0xffffffffu, v1, off);
+    v2 += __shfl_xor_sync(0xffffffffu, v2, off);
+  }
+  const float inv = 1.0f / (float)spp;
+  double lacc = 0.0;
+  float dv[3] = {0.0f, 0.0f, 0.0f};
+  if (valid) {
+    const float I[3] = {v0 * inv, v1 * inv, v2 * inv};
+    const bool in = sb.mask ? sb.mask[pix] != 0 : true;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double diff = (double)I[c] - (double)sb.target[3 * (size_t)pix + c];
+      if (in && s == 0) lacc += diff * diff;
+      dv[c] = in ? (float)(2.0 * diff) : 0.0f;
+      if (s == 0) {
+        sb.image[3 * (size_t)pix + c] = I[c];
+        sb.d_image[3 * (size_t)pix + c] = dv[c];
+      }
+    }
+  }
+  const bool adj = valid && hit.x >= 0 && (dv[0] != 0.0f || dv[1] != 0.0f || dv[2] != 0.0f);
+  if (tid < total && gb.hits) gb.hits[tid] = adj ? hit : make_int2(-1, 0);
+  if (adj && sb.interior)
+    interior_sample(a, gb, sC, sL, pix, s, d, hit.x, __int_as_float(hit.y), V3{dv[0], dv[1], dv[2]},
+                    cnt ? cnt + CNT_INTERIOR : nullptr, &vis);
+  for (int off = 16; off > 0; off >>= 1) lacc += __shfl_xor_sync(0xffffffffu, lacc, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lacc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
+    if (sum != 0.0) atomicAdd(sb.loss, sum);
+  }
+  for (int i = threadIdx.x; i < CS * CS; i += blockDim.x)
+    if (sC[i] != 0.0f) atomicAdd(&gb.dC[i], sC[i]);
+  for (int i = threadIdx.x; i < 3 * a.n_lights; i += blockDim.x)
+    if (sL[i] != 0.0f) atomicAdd(&gb.dL[i], sL[i]);
+}
+
 __global__ void __launch_bounds__(256, 4) k_bwd_pedge(RenderArgs a, GradBufs gb) {
   long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= (long long)a.W * a.H * a.spp) return;

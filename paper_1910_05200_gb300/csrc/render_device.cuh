@@ -54,12 +54,14 @@ struct SampleAux {
 };
 
 // One-sample radiance along a camera ray, lights that are on only.
-// hit (optional) receives the primary hit: face (or -1) and the bits of t.
+// hit (optional) receives the primary hit: face (or -1) and the bits of t;
+// vis (optional) bit j = light j is on and its light point is visible.
 FR_DEV V3 radiance(const RenderArgs& a, V3 o, V3 d, int tag, uint32_t c0, uint32_t c1, unsigned long long* cnt,
-                   SampleAux* aux = nullptr, int2* hit = nullptr) {
+                   SampleAux* aux = nullptr, int2* hit = nullptr, uint32_t* vis = nullptr) {
   float t;
   int f = closest_hit(a.mesh, o, d, t, a.err, cnt);
   if (hit) *hit = make_int2(f, __float_as_int(t));
+  if (vis) *vis = 0u;
   if (f < 0) return V3{0, 0, 0};
   int flip = face_flip(a.mesh, f, d);
   V3 x32 = hit_point(o, d, t);
@@ -77,6 +79,7 @@ FR_DEV V3 radiance(const RenderArgs& a, V3 o, V3 d, int tag, uint32_t c0, uint32
     V3 y = light_point(a.lights[j], a.side, unitf(q.x), unitf(q.y));
     if (!visible(a.mesh, x32, y, f, flip, a.tmin, a.err, cnt)) continue;
     ++n_vis;
+    if (vis) *vis |= 1u << j;
     ShadeOut sh = shade_light(S, cs, light_rgb(a, j), y, a.lights[j].dl, a.brdf);
     L += sh.h * area;
   }
@@ -256,8 +259,11 @@ FR_DEV void hit_adjoint(const RenderArgs& a, int f, V3 d, const Surf& S, V3 g_x,
 // every light (for dL/dl_j), shading, normals, albedo, specular map and the
 // hit point, with the sample's decisions held fixed.  sC and sL are the
 // block's shared accumulators of the specular-map and light gradients.
+// vis (optional): the forward's visibility bits of this sample (radiance
+// with the light tag): lights that are on take their shadow decision from
+// it, the others trace their shadow ray.
 FR_DEV void interior_sample(const RenderArgs& a, const GradBufs& gb, float* sC, float* sL, uint32_t pix, int s,
-                            V3 d, int f, float t, V3 dimg, unsigned long long* cnt) {
+                            V3 d, int f, float t, V3 dimg, unsigned long long* cnt, const uint32_t* vis = nullptr) {
   const int spp = a.spp;
   int flip = face_flip(a.mesh, f, d);
   V3 x32 = hit_point(a.cam.o, d, t);
@@ -272,7 +278,9 @@ FR_DEV void interior_sample(const RenderArgs& a, const GradBufs& gb, float* sC, 
   for (int j = 0; j < a.n_lights; ++j) {
     U4 q = philox(a.seed, a.iter, pix, (uint32_t)s, (uint32_t)(TAG_LIGHT << 8 | j), 0);
     V3 y = light_point(a.lights[j], a.side, unitf(q.x), unitf(q.y));
-    if (!visible(a.mesh, x32, y, f, flip, a.tmin, a.err, cnt)) continue;
+    const bool seen = (vis && light_on(a, j)) ? ((*vis >> j) & 1u) != 0u
+                                              : visible(a.mesh, x32, y, f, flip, a.tmin, a.err, cnt);
+    if (!seen) continue;
     V3 g_l{0, 0, 0};
     shade_light_bwd(S, cs, light_rgb(a, j), y, a.lights[j].dl, a.brdf, G, g_x, g_ns, g_rho, g_cs, g_l);
     atomicAdd(&sL[3 * j], g_l.x);

@@ -46,7 +46,7 @@ class FrTileConfig(C.Structure):
 
 
 EXPORTS = ["fr_default_config", "fr_create", "fr_destroy", "fr_set_stream", "fr_last_error", "fr_strerror",
-           "fr_upload_mesh", "fr_upload_bases", "fr_n_params", "fr_render", "fr_render_backward", "fr_loss",
+           "fr_upload_mesh", "fr_upload_bases", "fr_n_params", "fr_render", "fr_render_backward", "fr_loss", "fr_step",
            "fr_geometry", "fr_geometry_noalloc", "fr_vertex_grad", "fr_light_stage", "fr_sync", "fr_set_counters", "fr_get_counters", "fr_set_timing", "fr_get_timings",
            "fr_launch_count", "fr_denoiser_n_weights", "fr_denoiser_set_weights", "fr_denoiser_get_weights",
            "fr_denoise", "fr_denoiser_train_step", "fr_denoiser_get_grad", "fr_adam_step",
@@ -84,6 +84,7 @@ def load(path: str | None = None):
     L.fr_render.argtypes = [vp, vp, vp, vp, vp]
     L.fr_render_backward.argtypes = [vp, vp, vp, vp, vp, i32]
     L.fr_loss.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, f32, f32, vp, vp, vp]
+    L.fr_step.argtypes = [vp, vp, vp, vp, vp, vp, f32, f32, vp, vp, vp, vp]
     L.fr_geometry.argtypes = [vp, vp, vp, vp, vp]
     L.fr_geometry_noalloc.argtypes = [vp, vp, vp, vp, vp]
     L.fr_light_stage.argtypes = [vp, vp]
@@ -222,6 +223,22 @@ class Renderer:
         self._check(self.lib.fr_loss(self.ctx, _ptr(theta), W, H, _ptr(image), _ptr(target), _ptr(mask), _ptr(m),
                                      float(w1), float(w2), _ptr(loss), _ptr(d_image), _ptr(grad)), "fr_loss")
         return loss
+
+    def step(self, theta, target, W, H, spp, seed=0, iter=0, mask=None, m=None, w1=0.0, w2=0.0, terms=0,
+             image=None, d_image=None, grad=None):
+        """Render, loss (Eq. 1) and its gradient in one call (fr_step).
+        Returns (image [H, W, 3], loss [1] FP64, grad [P] FP64)."""
+        theta = self._theta(theta)
+        target = target.contiguous()
+        assert target.dtype == torch.float32 and target.numel() == W * H * 3
+        img = image if image is not None else torch.empty((H, W, 3), device=self.device, dtype=torch.float32)
+        g = grad if grad is not None else torch.empty(self.P, device=self.device, dtype=torch.float64)
+        loss = torch.empty(1, device=self.device, dtype=torch.float64)
+        o = self.opts(W, H, spp, seed, iter, terms)
+        self._stream()
+        self._check(self.lib.fr_step(self.ctx, _ptr(theta), C.byref(o), _ptr(target), _ptr(mask), _ptr(m),
+                                     float(w1), float(w2), _ptr(img), _ptr(d_image), _ptr(loss), _ptr(g)), "fr_step")
+        return img, loss, g
 
     def geometry(self, theta):
         theta = self._theta(theta)

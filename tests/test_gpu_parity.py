@@ -214,6 +214,82 @@ def test_light_prior_readings_match_oracle(oracle, fr, tiny, prior):
         fr.Renderer(scene, device=0, config=fr.default_config(light_prior=3))
 
 
+def _three_calls(r, th, tgt, mask, m, W, H, spp, seed, w1, w2, terms=0):
+    img = r.render(th, W, H, spp, seed=seed)
+    d_image = torch.empty_like(img)
+    loss = r.loss(th, img, tgt, mask, m, w1, w2, d_image)
+    g = r.backward(th, d_image, W, H, spp, seed=seed, terms=terms)
+    r.loss(th, img, tgt, mask, m, w1, w2, None, g)          # adds the prior and light terms' gradient
+    r.sync()
+    return img.cpu().numpy(), loss.item(), g.cpu().numpy(), d_image.cpu().numpy()
+
+
+def assert_sum_order_close(got, ref, what=""):
+    """Two GPU results that differ only in the order of floating-point atomic
+    additions: 1e-4 of the group's largest entry plus 1e-3 of the entry."""
+    for name, sl in group_slices().items():
+        o, g = ref[sl], got[sl]
+        tol = 1e-4 * np.abs(o).max() + 1e-3 * np.abs(o) + 1e-12
+        err = np.abs(g - o) / tol
+        assert err.max() <= 1.0, f"{what} {name}: {err.max():.3e} x tolerance at {int(err.argmax())}"
+
+
+@pytest.mark.parametrize("W,H,spp,terms", [(40, 33, 4, 0), (37, 29, 8, 0), (24, 24, 32, 0), (33, 17, 2, 1),
+                                           (30, 20, 3, 0), (16, 9, 64, 0)])
+def test_step_equals_render_loss_backward(oracle, fr, tiny, tiny_r, W, H, spp, terms):
+    """fr_step (fused when spp divides 32, three calls otherwise) against
+    fr_render + fr_loss + fr_render_backward: image and d_image bit for bit,
+    loss to 1e-12, gradient up to the order of atomic additions; the fused
+    case also against the oracle's loss."""
+    scene, theta, _ = tiny
+    rng = np.random.default_rng(W * 100 + spp)
+    tgt = rng.uniform(size=(H, W, 3)).astype(np.float32)
+    mask = (rng.uniform(size=(H, W)) > 0.25).astype(np.uint8)
+    m = rng.uniform(size=60).astype(np.float32)
+    dev = lambda a: torch.tensor(a, device="cuda:0")
+    th = dev(theta)
+    w1, w2 = 0.02, 0.3
+    ref_img, ref_loss, ref_g, ref_d = _three_calls(tiny_r, th, dev(tgt), dev(mask), dev(m), W, H, spp, 5, w1, w2,
+                                                   terms)
+    d_image = torch.empty(H, W, 3, device="cuda:0")
+    img, loss, g = tiny_r.step(th, dev(tgt), W, H, spp, seed=5, mask=dev(mask), m=dev(m), w1=w1, w2=w2,
+                               terms=terms, d_image=d_image)
+    tiny_r.sync()
+    assert np.array_equal(img.cpu().numpy(), ref_img)
+    assert np.array_equal(d_image.cpu().numpy(), ref_d)
+    assert abs(loss.item() - ref_loss) <= 1e-12 * abs(ref_loss)
+    assert_sum_order_close(g.cpu().numpy(), ref_g, what=f"step {W}x{H}x{spp}")
+    if spp == 4:
+        val, _, _ = oracle.loss(default_config(W=W, H=H), scene, theta, ref_img, tgt, mask, m, w1, w2)
+        assert abs(loss.item() - val) <= 1e-12 * abs(val)
+    # without d_image the context's buffer is used; the results stay the same
+    img2, loss2, g2 = tiny_r.step(th, dev(tgt), W, H, spp, seed=5, mask=dev(mask), m=dev(m), w1=w1, w2=w2,
+                                  terms=terms)
+    tiny_r.sync()
+    assert np.array_equal(img2.cpu().numpy(), ref_img) and abs(loss2.item() - ref_loss) <= 1e-12 * abs(ref_loss)
+    assert_sum_order_close(g2.cpu().numpy(), ref_g, what="step, context d_image")
+
+
+def test_counters_are_reset_per_call(fr, tiny, tiny_r):
+    """Work counters describe the latest call: two identical calls report the
+    same counts for every kernel."""
+    _, theta, _ = tiny
+    th = torch.tensor(theta, device="cuda:0")
+    W, H, spp = 32, 24, 4
+    d_image = torch.ones(H, W, 3, device="cuda:0")
+    tiny_r.set_counters(True)
+    try:
+        seen = []
+        for _ in range(2):
+            tiny_r.render(th, W, H, spp, seed=2)
+            tiny_r.backward(th, d_image, W, H, spp, seed=2)
+            seen.append(tiny_r.counters().copy())
+    finally:
+        tiny_r.set_counters(False)
+    assert np.array_equal(seen[0], seen[1]), (seen[0], seen[1])
+    assert seen[0][0] > 0 and seen[0][5] > 0 and seen[0][10] > 0 and seen[0][17] > 0
+
+
 def test_all_lights_off_is_black(oracle, tiny, tiny_r):
     scene, theta, _ = tiny
     th = theta.copy()
