@@ -86,6 +86,16 @@ def run(steps=5, reps=1, device=0):
             r.backward(th_all[f], d_images[f], w, h, spp, seed=seed, iter=i, grad=grad, accumulate=True)
 
     ms_single = _timed(per_frame, max(1, steps // 2))
+    g_f = torch.empty_like(grad)
+    images = [torch.empty(h, w, 3, device=dev) for w, h, _ in frames]
+
+    def per_frame_step(i):
+        for f, (w, h, seed) in enumerate(frames):
+            r.step(th_all[f], tg[f], w, h, spp, seed=seed, iter=i, w1=0.02, w2=0.002, image=images[f],
+                   d_image=d_images[f], grad=g_f)
+            grad.add_(g_f)
+
+    ms_single_step = _timed(per_frame_step, max(1, steps // 2))
     r.sync()
     return {
         "workload": f"{len(frames)} frames, full face (35,709 verts / 70,789 tris), square crops "
@@ -100,6 +110,8 @@ def run(steps=5, reps=1, device=0):
         "kernels_per_step": kernels_per_step,
         "ms_per_step_single_image_calls": ms_single,
         "speedup_vs_single_image_calls": ms_single / ms,
+        "ms_per_step_single_image_fr_step": ms_single_step,
+        "speedup_vs_single_image_fr_step": ms_single_step / ms,
     }
 
 

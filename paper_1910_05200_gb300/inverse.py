@@ -12,9 +12,11 @@ Algorithm 1 are not in the paper):
     4. specular map              (the added Cook-Torrance step)
     5. lights                    (the added light step)
 
-Every step of an iteration runs in the library: render (optionally with the
-denoiser features), loss, gradient, Adam (fr_adam_step; a learning rate of 0
-freezes a group).  Samples change every iteration (Philox key (seed, iter)).
+Every step of an iteration runs in the library: render, loss and gradient
+in one fr_step call (or, with the denoiser, render with its features, the
+network, loss and gradient as separate calls), then Adam (fr_adam_step; a
+learning rate of 0 freezes a group).  Samples change every iteration
+(Philox key (seed, iter)).
 """
 from __future__ import annotations
 
@@ -80,10 +82,12 @@ class Result:
 
 
 def optimize(r, target, W, H, spp, iters=500, seed=0, theta0=None, w1=0.02, w2=0.002, m=None,
-             denoise=False, rates=LEARNING_RATES) -> Result:
+             denoise=False, rates=LEARNING_RATES, api="step") -> Result:
     """Fit theta to the target image [H, W, 3] (device).  With denoise, the
     loss is taken on the denoised render and its residual is the image
-    adjoint handed to the renderer (the network must be set on r)."""
+    adjoint handed to the renderer (the network must be set on r).  api
+    "calls" runs render, loss and backward as three calls instead of fr_step
+    (same results up to the order of floating-point additions)."""
     dev = r.device
     th = torch.tensor(initial_theta() if theta0 is None else theta0, device=dev)
     P = th.numel()
@@ -91,6 +95,7 @@ def optimize(r, target, W, H, spp, iters=500, seed=0, theta0=None, w1=0.02, w2=0
     vel = torch.zeros(P, device=dev)
     grad = torch.zeros(P, device=dev, dtype=torch.float64)
     d_image = torch.empty(H, W, 3, device=dev)
+    image = torch.empty(H, W, 3, device=dev)
     stages = schedule(iters)
     lrs = [torch.tensor(lr_vector(g, rates=rates), device=dev) for _, _, g in STAGES]
     losses = torch.zeros(iters, device=dev, dtype=torch.float64)
@@ -103,14 +108,18 @@ def optimize(r, target, W, H, spp, iters=500, seed=0, theta0=None, w1=0.02, w2=0
             vel.zero_()
             step_in_stage = 0
         step_in_stage += 1
-        if denoise:
-            _, aov = r.render(th, W, H, spp, seed=seed, iter=it, aov=True)
-            img = r.denoise(aov)
+        if denoise or api != "step":
+            if denoise:
+                _, aov = r.render(th, W, H, spp, seed=seed, iter=it, aov=True)
+                img = r.denoise(aov)
+            else:
+                img = r.render(th, W, H, spp, seed=seed, iter=it, out=image)
+            grad.zero_()
+            losses[it:it + 1] = r.loss(th, img, target, m=m, w1=w1, w2=w2, d_image=d_image, grad=grad)
+            r.backward(th, d_image, W, H, spp, seed=seed, iter=it, grad=grad, accumulate=True)
         else:
-            img = r.render(th, W, H, spp, seed=seed, iter=it)
-        grad.zero_()
-        losses[it:it + 1] = r.loss(th, img, target, m=m, w1=w1, w2=w2, d_image=d_image, grad=grad)
-        r.backward(th, d_image, W, H, spp, seed=seed, iter=it, grad=grad, accumulate=True)
+            losses[it:it + 1] = r.step(th, target, W, H, spp, seed=seed, iter=it, m=m, w1=w1, w2=w2,
+                                       image=image, d_image=d_image, grad=grad)[1]
         r.adam_step(th, grad, mom, vel, lrs[stages[it]], step_in_stage)
     ev1.record()
     torch.cuda.synchronize()
@@ -167,6 +176,23 @@ def evaluate(n_targets=16, n_targets_hi=4, iters=500, spp_lo=4, spp_hi=64, devic
                      f"final_loss_first_{n_targets_hi}": float(np.mean(losses[:n_targets_hi])),
                      "ms_per_iter": float(np.mean(ms)), "per_target": errs}
     out["initial_param_error"] = {kk: float(np.mean([e[kk] for e in init_err])) for kk in init_err[0]}
+    return out
+
+
+def iteration_times(iters=60, spps=(4, 64), device=0):
+    """Time per inverse iteration (render, loss, gradient, Adam) on the first
+    target of evaluate(), through fr_step and through the three calls."""
+    from . import facert
+    scene, _, c = S.make_workload("full", seed=1)
+    W, H = c["W"], c["H"]
+    r = facert.Renderer(scene, device=device)
+    truth = S.make_theta(scene, seed=500, n_on=c["n_on"], max_angle_deg=30, t_std=0.05)
+    target = r.render(torch.tensor(truth, device=r.device), W, H, 256, seed=9)
+    out = {}
+    for spp in spps:
+        for api in ("step", "calls"):
+            optimize(r, target, W, H, spp, iters=5, seed=0, api=api)            # warm-up
+            out[f"{spp}spp_{api}"] = optimize(r, target, W, H, spp, iters=iters, seed=0, api=api).ms_per_iter
     return out
 
 
