@@ -187,12 +187,13 @@ int fr_loss(fr_ctx* ctx, const float* theta, int32_t W, int32_t H, const float* 
  * device (written with dE_data/d image) or NULL (a context buffer is used);
  * loss: one FP64 device scalar (overwritten); grad[P] FP64 device.
  * Results equal those of fr_render, fr_loss and fr_render_backward with the
- * same opts: the image bit for bit, loss and gradient up to the order of
- * floating-point additions.  When spp divides 32 the render, the data term's
- * adjoint and the interior adjoint run as one kernel (a pixel's samples share
- * a warp): each sample's interior adjoint reuses its primary hit and the
- * shadow decisions of the lights that are on; the geometry is prepared once.
- * Other spp run the three calls in sequence.  Timings (fr_get_timings): the
+ * same opts up to the order of floating-point additions (for spp dividing
+ * 32 the image and d_image bit for bit).  When spp divides 256 the render,
+ * the data term's adjoint and the interior adjoint run as one kernel (a
+ * pixel's samples lie in one block of 256 threads): each sample's interior
+ * adjoint reuses its primary hit and the shadow decisions of the lights that
+ * are on; the geometry is prepared once.  Other spp run the three calls in
+ * sequence.  Timings (fr_get_timings): the
  * fused kernel is the forward phase. */
 int fr_step(fr_ctx* ctx, const float* theta, const fr_render_opts* opts, const float* target, const uint8_t* mask,
             const float* m, float w1, float w2, float* image, float* d_image, double* loss, double* grad);

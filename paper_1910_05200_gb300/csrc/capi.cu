@@ -853,8 +853,8 @@ int fr_step(fr_ctx* ctx, const float* theta, const fr_render_opts* opts, const f
     d_image = ctx->dimg.p;
   }
   const int n_prior = ctx->K_id + ctx->K_exp + ctx->K_alb, nlv = 3 * ctx->cfg.n_lights;
-  if (!(opts->spp <= 32 && 32 % opts->spp == 0)) {
-    // a pixel's samples span several warps: the three calls in sequence,
+  if (256 % opts->spp != 0) {
+    // a pixel's samples span several blocks: the three calls in sequence,
     // then the prior and light terms' gradient (their value is in *loss)
     rc = fr_render(ctx, theta, opts, image, nullptr);
     if (!rc) rc = fr_loss(ctx, theta, opts->W, opts->H, image, target, mask, m, w1, w2, loss, d_image, nullptr);

@@ -139,13 +139,15 @@ __global__ void __launch_bounds__(256, 3) k_bwd_interior(RenderArgs a, GradBufs 
 }
 
 // Fused render, data term and interior adjoint of one optimisation step
-// (Eq. 1), for spp dividing 32 so that a pixel's samples share a warp: the
-// pixel's mean is a shuffle reduction, its adjoint 2 mask (image - target) is
-// known in the warp that rendered it, and each sample's interior adjoint
-// starts from the same primary hit and the shadow decisions of the lights
-// that are on (only lights that are off trace shadow rays again).  The image
-// is bit-identical to k_render_fwd's; the adjoint and the hits written for the
-// edge passes equal k_loss_data's and k_bwd_interior's.
+// (Eq. 1), for spp dividing 256 (blocks of 256 threads) so that a pixel's
+// samples lie in one block: the pixel's mean is a shuffle reduction (plus a
+// shared-memory sum over its spp / 32 warps when spp > 32), its adjoint
+// 2 mask (image - target) is known in the block that rendered it, and each
+// sample's interior adjoint starts from the same primary hit and the shadow
+// decisions of the lights that are on (only lights that are off trace shadow
+// rays again).  For spp dividing 32 the image is bit-identical to
+// k_render_fwd's and the adjoint to k_loss_data's; the hits written for the
+// edge passes equal k_bwd_interior's.
 __global__ void __launch_bounds__(256, 4) k_step_fwd(RenderArgs a, GradBufs gb, StepBufs sb) {
   __shared__ float sC[CS * CS];
   __shared__ float sL[3 * MAX_LIGHTS];
@@ -168,10 +170,18 @@ __global__ void __launch_bounds__(256, 4) k_step_fwd(RenderArgs a, GradBufs gb, 
     L = radiance(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt, nullptr, &hit, &vis);
   }
   float v0 = L.x, v1 = L.y, v2 = L.z;
-  for (int off = spp >> 1; off > 0; off >>= 1) {
+  for (int off = (spp < 32 ? spp : 32) >> 1; off > 0; off >>= 1) {
     v0 += __shfl_xor_sync(0xffffffffu, v0, off);
     v1 += __shfl_xor_sync(0xffffffffu, v1, off);
     v2 += __shfl_xor_sync(0xffffffffu, v2, off);
+  }
+  if (spp > 32) {                      // uniform: the pixel spans spp / 32 warps of this block
+    __shared__ float wsum[8][3];
+    const int w = threadIdx.x >> 5, nw = spp >> 5, w0 = w - w % nw;
+    if ((threadIdx.x & 31) == 0) { wsum[w][0] = v0; wsum[w][1] = v1; wsum[w][2] = v2; }
+    __syncthreads();
+    v0 = 0.0f; v1 = 0.0f; v2 = 0.0f;
+    for (int k = 0; k < nw; ++k) { v0 += wsum[w0 + k][0]; v1 += wsum[w0 + k][1]; v2 += wsum[w0 + k][2]; }
   }
   const float inv = 1.0f / (float)spp;
   double lacc = 0.0;

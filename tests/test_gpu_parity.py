@@ -235,12 +235,13 @@ def assert_sum_order_close(got, ref, what=""):
 
 
 @pytest.mark.parametrize("W,H,spp,terms", [(40, 33, 4, 0), (37, 29, 8, 0), (24, 24, 32, 0), (33, 17, 2, 1),
-                                           (30, 20, 3, 0), (16, 9, 64, 0)])
+                                           (30, 20, 3, 0), (16, 9, 64, 0), (9, 7, 256, 0), (10, 6, 96, 0)])
 def test_step_equals_render_loss_backward(oracle, fr, tiny, tiny_r, W, H, spp, terms):
-    """fr_step (fused when spp divides 32, three calls otherwise) against
-    fr_render + fr_loss + fr_render_backward: image and d_image bit for bit,
-    loss to 1e-12, gradient up to the order of atomic additions; the fused
-    case also against the oracle's loss."""
+    """fr_step (fused when spp divides 256, three calls otherwise) against
+    fr_render + fr_loss + fr_render_backward: image and d_image bit for bit
+    where spp divides 32 or the three calls run (else to FP32 rounding: the
+    pixel sums are added in another order), loss to 1e-12, gradient up to the
+    order of atomic additions; the 4-spp case also against the oracle's loss."""
     scene, theta, _ = tiny
     rng = np.random.default_rng(W * 100 + spp)
     tgt = rng.uniform(size=(H, W, 3)).astype(np.float32)
@@ -255,9 +256,15 @@ def test_step_equals_render_loss_backward(oracle, fr, tiny, tiny_r, W, H, spp, t
     img, loss, g = tiny_r.step(th, dev(tgt), W, H, spp, seed=5, mask=dev(mask), m=dev(m), w1=w1, w2=w2,
                                terms=terms, d_image=d_image)
     tiny_r.sync()
-    assert np.array_equal(img.cpu().numpy(), ref_img)
-    assert np.array_equal(d_image.cpu().numpy(), ref_d)
-    assert abs(loss.item() - ref_loss) <= 1e-12 * abs(ref_loss)
+    exact = spp <= 32 or 256 % spp != 0
+    if exact:
+        assert np.array_equal(img.cpu().numpy(), ref_img)
+        assert np.array_equal(d_image.cpu().numpy(), ref_d)
+        assert abs(loss.item() - ref_loss) <= 1e-12 * abs(ref_loss)
+    else:
+        np.testing.assert_allclose(img.cpu().numpy(), ref_img, rtol=1e-5, atol=1e-7)
+        np.testing.assert_allclose(d_image.cpu().numpy(), ref_d, rtol=1e-5, atol=1e-6)
+        assert abs(loss.item() - ref_loss) <= 1e-6 * abs(ref_loss)
     assert_sum_order_close(g.cpu().numpy(), ref_g, what=f"step {W}x{H}x{spp}")
     if spp == 4:
         val, _, _ = oracle.loss(default_config(W=W, H=H), scene, theta, ref_img, tgt, mask, m, w1, w2)
@@ -266,7 +273,7 @@ def test_step_equals_render_loss_backward(oracle, fr, tiny, tiny_r, W, H, spp, t
     img2, loss2, g2 = tiny_r.step(th, dev(tgt), W, H, spp, seed=5, mask=dev(mask), m=dev(m), w1=w1, w2=w2,
                                   terms=terms)
     tiny_r.sync()
-    assert np.array_equal(img2.cpu().numpy(), ref_img) and abs(loss2.item() - ref_loss) <= 1e-12 * abs(ref_loss)
+    assert np.array_equal(img2.cpu().numpy(), img.cpu().numpy()) and abs(loss2.item() - loss.item()) <= 1e-12 * abs(ref_loss)
     assert_sum_order_close(g2.cpu().numpy(), ref_g, what="step, context d_image")
 
 
