@@ -239,9 +239,10 @@ def assert_sum_order_close(got, ref, what=""):
 def test_step_equals_render_loss_backward(oracle, fr, tiny, tiny_r, W, H, spp, terms):
     """fr_step (fused when spp divides 256, three calls otherwise) against
     fr_render + fr_loss + fr_render_backward: image and d_image bit for bit
-    where spp divides 32 or the three calls run (else to FP32 rounding: the
-    pixel sums are added in another order), loss to 1e-12, gradient up to the
-    order of atomic additions; the 4-spp case also against the oracle's loss."""
+    where spp divides 32 (both sides sum a pixel by warp shuffles; above 32
+    fr_render adds the samples atomically in no fixed order, so agreement is
+    to FP32 rounding), loss to 1e-12, gradient up to the order of atomic
+    additions; the 4-spp case also against the oracle's loss."""
     scene, theta, _ = tiny
     rng = np.random.default_rng(W * 100 + spp)
     tgt = rng.uniform(size=(H, W, 3)).astype(np.float32)
@@ -256,7 +257,7 @@ def test_step_equals_render_loss_backward(oracle, fr, tiny, tiny_r, W, H, spp, t
     img, loss, g = tiny_r.step(th, dev(tgt), W, H, spp, seed=5, mask=dev(mask), m=dev(m), w1=w1, w2=w2,
                                terms=terms, d_image=d_image)
     tiny_r.sync()
-    exact = spp <= 32 or 256 % spp != 0
+    exact = spp <= 32
     if exact:
         assert np.array_equal(img.cpu().numpy(), ref_img)
         assert np.array_equal(d_image.cpu().numpy(), ref_d)
@@ -273,7 +274,9 @@ def test_step_equals_render_loss_backward(oracle, fr, tiny, tiny_r, W, H, spp, t
     img2, loss2, g2 = tiny_r.step(th, dev(tgt), W, H, spp, seed=5, mask=dev(mask), m=dev(m), w1=w1, w2=w2,
                                   terms=terms)
     tiny_r.sync()
-    assert np.array_equal(img2.cpu().numpy(), img.cpu().numpy()) and abs(loss2.item() - loss.item()) <= 1e-12 * abs(ref_loss)
+    if exact:
+        assert np.array_equal(img2.cpu().numpy(), img.cpu().numpy())
+    assert abs(loss2.item() - loss.item()) <= (1e-12 if exact else 1e-6) * abs(ref_loss)
     assert_sum_order_close(g2.cpu().numpy(), ref_g, what="step, context d_image")
 
 
