@@ -385,7 +385,7 @@ int prepare_geometry(fr_ctx* ctx, const float* theta, const FrameView& v) {
   if (!theta) return fail(ctx, FR_ERR_INVALID_ARG, "theta is null");
   GeoArgs g = geo_args(ctx, v);
   cudaStream_t s = ctx->stream;
-  k_geometry<<<(ctx->V + 127) / 128, 128, 0, s>>>(g, theta);
+  k_geometry<<<(ctx->V + GEO_VERTS - 1) / GEO_VERTS, GEO_THREADS, 0, s>>>(g, theta);
   CKL();
   k_faces<<<(ctx->F + 255) / 256, 256, 0, s>>>(g);
   CKL();
@@ -459,10 +459,18 @@ int adjoint(fr_ctx* ctx, const float* theta, const FrameView& v, double* grad, b
   k_pose_bwd<<<152, 256, 0, s>>>(g, theta, v.dX, v.dXm, grad);
   CKL();
   const int n3 = 3 * V;
-  if (ctx->K_id) { k_basis_T<<<ctx->K_id, 256, 0, s>>>(ctx->BidT.p, ctx->K_id, n3, v.dXm, nullptr, grad, 0); CKL(); }
-  if (ctx->K_exp) { k_basis_T<<<ctx->K_exp, 256, 0, s>>>(ctx->BexpT.p, ctx->K_exp, n3, v.dXm, nullptr, grad, ctx->K_id); CKL(); }
+  if (ctx->K_id) {
+    k_basis_T<<<dim3(ctx->K_id, BASIS_SLICES), 256, 0, s>>>(ctx->BidT.p, ctx->K_id, n3, v.dXm, nullptr, grad, 0);
+    CKL();
+  }
+  if (ctx->K_exp) {
+    k_basis_T<<<dim3(ctx->K_exp, BASIS_SLICES), 256, 0, s>>>(ctx->BexpT.p, ctx->K_exp, n3, v.dXm, nullptr, grad,
+                                                            ctx->K_id);
+    CKL();
+  }
   if (ctx->K_alb && with_alb) {
-    k_basis_T<<<ctx->K_alb, 256, 0, s>>>(ctx->BalbT.p, ctx->K_alb, n3, nullptr, v.dA, grad, ctx->K_id + ctx->K_exp);
+    k_basis_T<<<dim3(ctx->K_alb, BASIS_SLICES), 256, 0, s>>>(ctx->BalbT.p, ctx->K_alb, n3, nullptr, v.dA, grad,
+                                                            ctx->K_id + ctx->K_exp);
     CKL();
   }
   if (v.dC) {

@@ -39,41 +39,62 @@ __device__ void rotation_grad(const float* pose, float* dR /*[3][9]*/) {
   Cc[6] = 0;        Cc[7] = 0;                       Cc[8] = 0;
 }
 
-// One thread per vertex.  Positions accumulate in FP64 so that their FP32
-// rounding is (up to a tie at a rounding boundary) independent of summation
-// order; albedo accumulates in FP32.  Bases are stored transposed, [K][3V].
-__global__ void k_geometry(GeoArgs g, const float* __restrict__ theta) {
+// Positions accumulate in FP64 so that their FP32 rounding is (up to a tie
+// at a rounding boundary) independent of summation order; albedo
+// accumulates in FP32.  Bases are stored transposed, [K][3V].  A block
+// covers GEO_VERTS vertices, i.e. 3 * GEO_VERTS coordinates i = 3 v + c, with
+// GEO_KSPLIT groups of three warps: group q sums the q-th quarter of the
+// basis columns for every coordinate of the block (reads coalesced along
+// i).  The quarters' partial sums meet in shared memory in a fixed order;
+// then one thread per vertex applies the pose.
+__global__ void __launch_bounds__(GEO_THREADS) k_geometry(GeoArgs g, const float* __restrict__ theta) {
   __shared__ double R[9];
   __shared__ float coef[512];
+  __shared__ double sx[GEO_KSPLIT][3 * GEO_VERTS];
+  __shared__ float sa[GEO_KSPLIT][3 * GEO_VERTS];
   const int K1 = g.K_id, K2 = g.K_exp, K3 = g.K_alb;
   if (threadIdx.x == 0) rotation(theta + g.off_pose, R);
   for (int i = threadIdx.x; i < K1 + K2 + K3; i += blockDim.x) coef[i] = theta[i];
   __syncthreads();
-  int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= g.V) return;
   const int n3 = 3 * g.V;
-  double xm[3];
-  float a[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    int i = 3 * v + c;
-    double x = (double)g.mean[i];
-    for (int k = 0; k < K1; ++k) x += (double)g.BidT[(size_t)k * n3 + i] * (double)coef[k];
-    for (int k = 0; k < K2; ++k) x += (double)g.BexpT[(size_t)k * n3 + i] * (double)coef[K1 + k];
-    xm[c] = x;
-    float al = 0.0f;
-    if (g.alb) {             // null: albedo kept from another frame of a batch
-      al = g.alb_mean[i];
-      for (int k = 0; k < K3; ++k) al += g.BalbT[(size_t)k * n3 + i] * coef[K1 + K2 + k];
+  const int q = threadIdx.x / (3 * GEO_VERTS), ii = threadIdx.x - q * (3 * GEO_VERTS);
+  const int i = 3 * GEO_VERTS * blockIdx.x + ii;
+  double x = 0.0;
+  float al = 0.0f;
+  if (i < n3) {
+    const int KG = K1 + K2, cg = (KG + GEO_KSPLIT - 1) / GEO_KSPLIT, ca = (K3 + GEO_KSPLIT - 1) / GEO_KSPLIT;
+    const int k1 = min(KG, (q + 1) * cg);
+    for (int k = q * cg; k < k1; ++k) {
+      const float* B = k < K1 ? g.BidT + (size_t)k * n3 : g.BexpT + (size_t)(k - K1) * n3;
+      x += (double)B[i] * (double)coef[k];
     }
-    a[c] = al;
+    if (g.alb) {             // null: albedo kept from another frame of a batch
+      const int a1 = min(K3, (q + 1) * ca);
+      for (int k = q * ca; k < a1; ++k) al += g.BalbT[(size_t)k * n3 + i] * coef[K1 + K2 + k];
+    }
   }
+  sx[q][ii] = x;
+  sa[q][ii] = al;
+  __syncthreads();
+  if (q == 0 && i < n3) {
+    double xm = (double)g.mean[i];
+    float a = g.alb ? g.alb_mean[i] : 0.0f;
+#pragma unroll
+    for (int r = 0; r < GEO_KSPLIT; ++r) { xm += sx[r][ii]; a += sa[r][ii]; }
+    sx[0][ii] = xm;
+    sa[0][ii] = a;
+  }
+  __syncthreads();
+  const int v = GEO_VERTS * blockIdx.x + threadIdx.x;
+  if (threadIdx.x >= GEO_VERTS || v >= g.V) return;
+  const double* xm = &sx[0][3 * threadIdx.x];
+  const float* a = &sa[0][3 * threadIdx.x];
   const float* t = theta + g.off_pose + 3;
   float X[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    double x = R[3 * c] * xm[0] + R[3 * c + 1] * xm[1] + R[3 * c + 2] * xm[2] + (double)t[c];
-    X[c] = (float)x;
+    double xw = R[3 * c] * xm[0] + R[3 * c + 1] * xm[1] + R[3 * c + 2] * xm[2] + (double)t[c];
+    X[c] = (float)xw;
   }
   g.X[v] = make_float4(X[0], X[1], X[2], 0.0f);
   g.Xm[v] = make_float4((float)xm[0], (float)xm[1], (float)xm[2], 0.0f);
@@ -390,18 +411,22 @@ __global__ void k_pose_bwd(GeoArgs g, const float* __restrict__ theta, const flo
 }
 
 // Transposed basis contraction: grad[out_off + k] += sum_i B^T[k][i] * y[i].
-// One block per coefficient k; FP32 products summed per thread, FP64 across.
+// Grid (K, BASIS_SLICES): block (k, s) sums the s-th slice of row k (FP32 per
+// thread, FP64 across the block) and adds it with one FP64 atomic, so that
+// K * BASIS_SLICES blocks stream the basis.
 __global__ void k_basis_T(const float* __restrict__ BT, int K, int n, const float* __restrict__ y,
                           const float4* __restrict__ y4, double* __restrict__ grad, int out_off) {
   __shared__ double red[32];
-  int k = blockIdx.x;
+  const int k = blockIdx.x;
   if (k >= K) return;
+  const int chunk = (n + (int)gridDim.y - 1) / (int)gridDim.y;
+  const int i0 = (int)blockIdx.y * chunk, i1 = min(n, i0 + chunk);
   const float* row = BT + (size_t)k * n;
   float acc = 0.0f;
   if (y) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += row[i] * y[i];
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc += row[i] * y[i];
   } else {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
       float4 q = y4[i / 3];
       int c = i - 3 * (i / 3);
       acc += row[i] * (c == 0 ? q.x : (c == 1 ? q.y : q.z));
@@ -414,7 +439,7 @@ __global__ void k_basis_T(const float* __restrict__ BT, int K, int n, const floa
   if (threadIdx.x == 0) {
     double s = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    grad[out_off + k] += s;
+    atomicAdd(&grad[out_off + k], s);
   }
 }
 

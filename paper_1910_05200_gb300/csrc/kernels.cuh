@@ -201,6 +201,9 @@ __global__ void k_normals_bwd_vertex(GeoArgs g, const float4* __restrict__ dN, f
 __global__ void k_normals_bwd_gather(GeoArgs g, const float4* __restrict__ gs, float4* __restrict__ dX);
 __global__ void k_pose_bwd(GeoArgs g, const float* __restrict__ theta, const float4* __restrict__ dX,
                            float* __restrict__ dXm, double* __restrict__ grad);
+// k_geometry: vertices per block, column groups, threads per block;
+// k_basis_T: slices per basis row (grid (K, BASIS_SLICES)).
+constexpr int GEO_VERTS = 32, GEO_KSPLIT = 4, GEO_THREADS = 3 * GEO_VERTS * GEO_KSPLIT, BASIS_SLICES = 16;
 __global__ void k_basis_T(const float* __restrict__ BT, int K, int n, const float* __restrict__ y,
                           const float4* __restrict__ y4, double* __restrict__ grad, int out_off);
 __global__ void k_add_small(const float* __restrict__ src, int n, double* __restrict__ grad, int off);
