@@ -330,6 +330,25 @@ def test_errors_are_reported(fr, tiny):
                   scene.alb_mean, scene.B_alb)
     with pytest.raises(RuntimeError, match="shape"):
         fr.Renderer(bad, device=0)
+    # fr_step: bad sizes and missing buffers are refused before any launch
+    th = torch.tensor(theta, device="cuda:0")
+    tgt = torch.zeros(8, 8, 3, device="cuda:0")
+    with pytest.raises(RuntimeError, match="invalid argument"):
+        r2.step(th, tgt, 8, 8, 0)
+    import ctypes as C
+    vp = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+    img = torch.empty(8, 8, 3, device="cuda:0")
+    loss = torch.empty(1, device="cuda:0", dtype=torch.float64)
+    g = torch.empty(r2.P, device="cuda:0", dtype=torch.float64)
+    o = r2.opts(8, 8, 4)
+    for missing in ("target", "image", "loss", "grad"):
+        args = dict(target=tgt, image=img, loss=loss, grad=g)
+        args[missing] = None
+        rc = fr.load().fr_step(r2.ctx, vp(th), C.byref(o), vp(args["target"]), None, None, 0.0, 0.0,
+                               vp(args["image"]), None, vp(args["loss"]), vp(args["grad"]))
+        assert rc == -1, (missing, rc)
+    with pytest.raises(RuntimeError, match="invalid argument"):
+        fr.Renderer(scene, device=0, config=fr.default_config(light_prior=-1))
 
 
 def test_large_image_and_size_limits(oracle, fr, tiny, tiny_r):
