@@ -10,8 +10,9 @@
 //                    loss and its adjoint d_image = 2 mask (image - target)
 //                    (Eq. 1 of the Optimization paragraph, per pixel), then the
 //                    interior adjoint and the shadow-edge term of the same
-//                    samples with their primary hits still in registers (no
-//                    re-trace when spp divides 32);
+//                    samples with their primary hits and the shadow
+//                    decisions of the lights that are on still in registers
+//                    (no re-trace when spp divides 32);
 //   primary-edge items  a chunk of one frame's primary-edge samples; they
 //                    read d_image anywhere in the frame, so each waits until
 //                    the frame's tile items have all published theirs.
