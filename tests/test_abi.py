@@ -60,3 +60,41 @@ def test_host_only_calls(lib):
         lib.fr_destroy(h)
     else:
         assert rc < 0
+
+
+def test_header_is_plain_c_and_links(tmp_path, lib):
+    """A C99 program includes only include/facert.h, links against the
+    library and calls host-only entry points (no GPU): the boundary needs
+    neither C++ nor CUDA nor torch headers."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_1910_05200_gb300 import build
+    src = tmp_path / "use_facert.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include "facert.h"
+int main(void) {
+  fr_config c;
+  fr_ctx* ctx = 0;
+  int rc;
+  fr_default_config(&c);
+  printf("%d %d %d %d %d %s\n", c.n_lights, c.brdf_model, c.fresnel, c.light_layout, c.light_prior,
+         fr_strerror(FR_ERR_INVALID_ARG));
+  c.light_prior = 7;                           /* refused before any device work */
+  rc = fr_create(&ctx, &c, 0);
+  printf("%d %d\n", rc, ctx == 0);
+  return 0;
+}
+''')
+    exe = tmp_path / "use_facert"
+    libdir = os.path.dirname(build.LIB)
+    subprocess.check_call([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                           "-o", str(exe), "-L", libdir, "-l:" + os.path.basename(build.LIB),
+                           "-Wl,-rpath," + libdir])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    assert out[0] == "20 0 0 0 0 invalid argument"
+    rc, null = out[1].split()
+    assert int(rc) < 0 and null == "1"
