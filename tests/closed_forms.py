@@ -118,3 +118,104 @@ def plain_theta(lights_on=(), rgb=(1.0, 1.0, 1.0), cspec=0.0):
     for j in lights_on:
         th[o["lights"] + 3 * j:o["lights"] + 3 * j + 3] = rgb
     return th
+
+
+# ---------------------------------------------------------------------------
+# exact union of planar triangles (slab decomposition) for shadows cast by
+# many occluder triangles at once
+
+def _seg_cross_x(p, q, r, s):
+    """x coordinate where segments pq and rs cross (None if they do not)."""
+    d1, d2 = q - p, s - r
+    den = d1[0] * d2[1] - d1[1] * d2[0]
+    if den == 0.0:
+        return None
+    w = r - p
+    a = (w[0] * d2[1] - w[1] * d2[0]) / den
+    b = (w[0] * d1[1] - w[1] * d1[0]) / den
+    if 0.0 < a < 1.0 and 0.0 < b < 1.0:
+        return p[0] + a * d1[0]
+    return None
+
+
+def triangle_union_pieces(tris2):
+    """Disjoint convex pieces (trapezoids, counter-clockwise) whose union is
+    the union of the 2D triangles tris2 [k][3][2].  Vertical slabs between
+    consecutive event abscissae (vertices and edge crossings) contain no event,
+    so in each slab every triangle is bounded by one lower and one upper edge
+    line and the union is a set of trapezoids found by merging intervals."""
+    T = [np.asarray(t, np.float64) for t in tris2]
+    edges = [(t[i], t[(i + 1) % 3]) for t in T for i in range(3)]
+    xs = [p[0] for t in T for p in t]
+    for i in range(len(edges)):
+        for k in range(i + 1, len(edges)):
+            x = _seg_cross_x(edges[i][0], edges[i][1], edges[k][0], edges[k][1])
+            if x is not None:
+                xs.append(x)
+    xs = np.unique(np.asarray(xs))
+    pieces = []
+
+    def line_at(e, x):
+        p, q = e
+        return p[1] + (q[1] - p[1]) * (x - p[0]) / (q[0] - p[0])
+
+    for xa, xb in zip(xs[:-1], xs[1:]):
+        if not xb > xa:
+            continue
+        xm = 0.5 * (xa + xb)
+        iv = []
+        for t in T:
+            if not (t[:, 0].min() < xm < t[:, 0].max()):
+                continue
+            es = [(t[i], t[(i + 1) % 3]) for i in range(3)
+                  if min(t[i][0], t[(i + 1) % 3][0]) < xm < max(t[i][0], t[(i + 1) % 3][0])]
+            if len(es) != 2:
+                continue
+            ys = [line_at(e, xm) for e in es]
+            lo, hi = (es[0], es[1]) if ys[0] < ys[1] else (es[1], es[0])
+            iv.append((min(ys), max(ys), lo, hi))
+        iv.sort(key=lambda r: r[0])
+        merged, cur = [], None
+        for r in iv:
+            if cur is None:
+                cur = list(r)
+            elif r[0] <= cur[1]:
+                if r[1] > cur[1]:
+                    cur[1], cur[3] = r[1], r[3]
+            else:
+                merged.append(cur)
+                cur = list(r)
+        if cur is not None:
+            merged.append(cur)
+        for _, _, lo, hi in merged:
+            pieces.append([np.array([xa, line_at(lo, xa)]), np.array([xb, line_at(lo, xb)]),
+                           np.array([xb, line_at(hi, xb)]), np.array([xa, line_at(hi, xa)])])
+    return pieces
+
+
+def lit_irradiance(x_int, n, occluders, j, x_vis=None):
+    """Irradiance at x_int (normal n) from unit-radiance light j of the stage
+    with the part hidden by the occluder triangles, as seen from x_vis
+    (default x_int), removed: E(square) - E(square intersected with the union
+    of the occluders' central projections from x_vis), Lambert's formula on
+    exact polygons.  Splitting x_vis from x_int separates the visibility
+    boundary's dependence on the shading point from that of the integrand."""
+    x_int = np.asarray(x_int, np.float64)
+    x_vis = x_int if x_vis is None else np.asarray(x_vis, np.float64)
+    quad = light_quad(j)
+    c, e1, e2, d = light_frame(j)
+    D = (c - x_vis) @ d
+    to2 = lambda p: np.array([(p - c) @ e1, (p - c) @ e2])
+    proj = []
+    for tri in occluders:
+        tri = [np.asarray(p, np.float64) for p in tri]
+        if min((p - x_vis) @ d for p in tri) <= 0:
+            continue
+        proj.append([to2(x_vis + (p - x_vis) * (D / ((p - x_vis) @ d))) for p in tri])
+    q2 = ccw([to2(p) for p in quad])
+    E = lambert_irradiance(x_int, n, quad)
+    for piece in triangle_union_pieces(proj):
+        inter = clip_polygon(ccw(piece), q2)
+        if len(inter) >= 3:
+            E -= lambert_irradiance(x_int, n, [c + p[0] * e1 + p[1] * e2 for p in inter])
+    return E

@@ -15,7 +15,10 @@ so that a dropped term, a wrong sign or index, or a transposed operand fails:
 * the primary-visibility edge term against the exact derivative of pixel
   coverage (Li et al. 2018 edge sampling)
 * the shadow-boundary edge term against the derivative of the clipped
-  polygon irradiance
+  polygon irradiance, with respect to the occluder's vertices and to the
+  receiver's (the shading point moving with its triangle), on one occluder
+  and on a cluster of occluders with many candidate edges (exact union of
+  their shadows by slab decomposition)
 * the loss of Eq. 1 on a hand-computed case
 """
 import os
@@ -418,3 +421,210 @@ def test_two_sided_shading_ignores_winding(oracle):
     b = oracle.render(cfg, CF.plain_scene(verts, [(0, 2, 1), (0, 3, 2)]), th)
     assert a.max() > 0.01
     assert np.allclose(a, b, rtol=1e-12, atol=1e-15)
+
+
+def _hit_point_on(verts, tri, o, d):
+    """Intersection of the ray o + t d with the plane of triangle tri (FP64)."""
+    P = [np.asarray(verts[k], np.float64) for k in tri]
+    n = np.cross(P[1] - P[0], P[2] - P[0])
+    t = ((P[0] - o) @ n) / (d @ n)
+    return o + t * d
+
+
+def _shadow_edge_estimates(oracle, sc, th, o, d, j, reps, seeds=8):
+    ests = []
+    for seed in range(seeds):
+        dX = oracle.shadow_edge_point(default_config(seed=seed), sc, th, o, d, j, [1.0, 0, 0], reps)
+        ests.append(dX.reshape(-1) / reps)
+    ests = np.array(ests)
+    return ests.mean(0), ests.std(0, ddof=1) / np.sqrt(seeds)
+
+
+def test_shadow_edge_term_receiver_side(oracle):
+    """The shading point x moves with its triangle (the camera ray fixed):
+    the shadow on the light square moves with it.  The estimator's
+    derivative with respect to the receiver's vertices against central
+    differences of the exact lit irradiance in which only the visibility
+    boundary sees the moved x (the integrand's own dependence on x belongs to
+    the interior term)."""
+    j = 15
+    sc, occ = _occluder_scene(j)
+    th = CF.plain_theta(lights_on=[j])
+    o = np.array([0, 0, 4], np.float32)
+    x = np.array([0.013, -0.021, 0.0])
+    d = (x.astype(np.float32) - o).astype(np.float32)
+    o64, d64 = o.astype(np.float64), d.astype(np.float64)
+    verts = sc.mean.astype(np.float64)
+    tri = (0, 1, 2)                                  # the receiver triangle under x (y < x)
+    x0 = _hit_point_on(verts, tri, o64, d64)
+    n = np.array([0, 0, 1.0])
+    occ_tris = [occ]
+    fd = np.zeros(12)
+    for i in range(12):
+        vp, vm = verts.copy(), verts.copy()
+        vp[i // 3, i % 3] += 1e-6
+        vm[i // 3, i % 3] -= 1e-6
+        fp = CF.lit_irradiance(x0, n, occ_tris, j, x_vis=_hit_point_on(vp, tri, o64, d64))
+        fm = CF.lit_irradiance(x0, n, occ_tris, j, x_vis=_hit_point_on(vm, tri, o64, d64))
+        fd[i] = (fp - fm) / 2e-6
+    mean, se = _shadow_edge_estimates(oracle, sc, th, o, d, j, 4000)
+    scale = np.abs(fd).max()
+    assert scale > 0 and np.all(fd[9:] == 0)        # vertex 3 is not on x's triangle
+    assert np.all(np.abs(mean[:12] - fd) <= 4.5 * se[:12] + 0.01 * scale), (mean[:12], fd, se[:12])
+    # the single-occluder closed form of the occluder-side pin is the same function
+    assert CF.lit_irradiance(x0, n, occ_tris, j) == pytest.approx(_lit_irradiance(x0, n, occ, j), rel=1e-12)
+
+
+def _occluder_cluster(j=15, seed=4):
+    """Receiver plane plus a cluster of small occluders between x and light j:
+    seven loose triangles at random offsets and tilts (every edge a boundary
+    edge) and a Z-folded pair whose shared edge is a silhouette seen from x."""
+    c, e1, e2, d = CF.light_frame(j)
+    rng = np.random.default_rng(seed)
+    recv = [(-2, -2, 0), (2, -2, 0), (2, 2, 0), (-2, 2, 0)]
+    verts = [np.asarray(v, np.float64) for v in recv]
+    tris = [(0, 1, 2), (0, 2, 3)]
+    occ = []
+    for _ in range(7):
+        cen = d * rng.uniform(0.8, 1.2) + e1 * rng.uniform(-0.09, 0.09) + e2 * rng.uniform(-0.09, 0.09)
+        a = rng.uniform(0, 2 * np.pi)
+        tri = []
+        for k in range(3):
+            ang = a + 2 * np.pi * k / 3 + rng.uniform(-0.3, 0.3)
+            r = rng.uniform(0.025, 0.05)
+            tri.append(cen + r * (np.cos(ang) * e1 + np.sin(ang) * e2) + rng.uniform(-0.02, 0.02) * d)
+        occ.append(tri)
+    base = d * 1.0 - 0.06 * e2
+    A, B = base - 0.05 * e1, base + 0.05 * e1
+    occ.append([A, B, base + 0.06 * e2 + 0.03 * d])
+    occ.append([B, A, base - 0.03 * e2 - 0.03 * d])
+    for t in occ[:7]:
+        k = len(verts)
+        verts += list(t)
+        tris.append((k, k + 1, k + 2))
+    k = len(verts)
+    verts += [A, B, occ[7][2], occ[8][2]]
+    tris += [(k, k + 1, k + 2), (k + 1, k, k + 3)]
+    return CF.plain_scene(np.asarray(verts), tris), occ
+
+
+def test_shadow_edge_term_many_candidates(oracle):
+    """A cluster of occluders: many candidate edges (silhouettes seen from x
+    that cross the light square), some of them inside another occluder's
+    shadow (no visibility change, no contribution).  The estimator's
+    derivatives with respect to occluder and receiver vertices against
+    central differences of the exact lit irradiance (Lambert's formula on
+    the square minus the exact union of the occluders' projections)."""
+    j = 15
+    sc, occ = _occluder_cluster(j)
+    th = CF.plain_theta(lights_on=[j])
+    o = np.array([0, 0, 4], np.float32)
+    x = np.array([0.013, -0.021, 0.0])
+    d = (x.astype(np.float32) - o).astype(np.float32)
+    o64, d64 = o.astype(np.float64), d.astype(np.float64)
+    verts = sc.mean.astype(np.float64)
+    x0 = _hit_point_on(verts, (0, 1, 2), o64, d64)
+    n = np.array([0, 0, 1.0])
+    full = CF.lambert_irradiance(x0, n, CF.light_quad(j))
+    lit = CF.lit_irradiance(x0, n, occ, j)
+    assert 0.1 * full < lit < 0.9 * full, (lit, full)        # a partial shadow
+    # candidate edges (FP64 restatement of the candidate rule: silhouette seen
+    # from x, central projection crossing the light square)
+    c, e1, e2, dl = CF.light_frame(j)
+    quad2 = CF.ccw([np.array([(p - c) @ e1, (p - c) @ e2]) for p in CF.light_quad(j)])
+    tris = sc.tris
+    edge_faces = {}
+    for f, t in enumerate(tris):
+        for k in range(3):
+            key = tuple(sorted((int(t[k]), int(t[(k + 1) % 3]))))
+            edge_faces.setdefault(key, []).append(f)
+
+    def side(f):
+        P = verts[tris[f]]
+        return np.sign(np.cross(P[1] - P[0], P[2] - P[0]) @ (x0 - P[0]))
+
+    n_cand = 0
+    D = (c - x0) @ dl
+    for (a, b), fs in edge_faces.items():
+        if 0 in fs or 1 in fs and fs == [1]:
+            continue
+        if fs[0] in (0, 1):
+            continue
+        sil = len(fs) == 1 or side(fs[0]) != side(fs[1])
+        if not sil:
+            continue
+        pa, pb = verts[a], verts[b]
+        ya = x0 + (pa - x0) * (D / ((pa - x0) @ dl))
+        yb = x0 + (pb - x0) * (D / ((pb - x0) @ dl))
+        seg = [np.array([(ya - c) @ e1, (ya - c) @ e2]), np.array([(yb - c) @ e1, (yb - c) @ e2])]
+        if len(CF.clip_polygon(seg + [seg[1] + 1e-12], quad2)) >= 2:
+            n_cand += 1
+    assert n_cand >= 10, n_cand
+    mean, se = _shadow_edge_estimates(oracle, sc, th, o, d, j, 12000)
+    checks = list(range(0, 9)) + [3 * v + k for v in (4, 5, 9, 27, 28) for k in range(3)]
+
+    def lit(vv, i):
+        if i < 12:          # a receiver vertex: x moves, the occluders stay
+            return CF.lit_irradiance(x0, n, occ, j, x_vis=_hit_point_on(vv, (0, 1, 2), o64, d64))
+        return CF.lit_irradiance(x0, n, [[vv[t] for t in tri] for tri in tris[2:]], j)
+
+    fd = np.zeros(len(checks))
+    for m, i in enumerate(checks):
+        # median of three steps: the slab decomposition can jump by rounding
+        # when two events nearly coincide at one particular step
+        est = []
+        for h in (1e-5, 2e-5, 4e-5):
+            vp, vm = verts.copy(), verts.copy()
+            vp[i // 3, i % 3] += h
+            vm[i // 3, i % 3] -= h
+            est.append((lit(vp, i) - lit(vm, i)) / (2 * h))
+        fd[m] = np.median(est)
+    got, s = mean[checks], se[checks]
+    scale = np.abs(fd).max()
+    assert scale > 0 and np.count_nonzero(np.abs(fd) > 0.05 * scale) >= 8
+    assert np.all(np.abs(got - fd) <= 4.5 * s + 0.01 * scale), np.c_[got, fd, s]
+
+
+def test_full_estimator_statistical_fd_on_tiny_face(oracle):
+    """The whole gradient estimator (interior, primary-visibility and
+    shadow-boundary terms) is unbiased for the derivative of the expected
+    image: on a 6 x 6 window astride the tiny face's silhouette, the mean of
+    the backward over 8 independent seeds x 512 spp (4,096 spp) against
+    central differences (h = 1e-3) of the expected weighted image, each side
+    rendered with common random numbers over 8 other seeds x 512 spp, for
+    identity, expression, rotation, both in-plane translations and one light.
+    The two means must agree within 3 standard errors of their difference."""
+    scene, theta, _ = S.make_workload("tiny", seed=0)
+    W = H = 64
+    cov = oracle.render(default_config(W=W, H=H, spp=4, seed=0), scene, theta).sum(-1) > 0
+    edge = cov & ~(np.roll(cov, 1, 0) & np.roll(cov, -1, 0) & np.roll(cov, 1, 1) & np.roll(cov, -1, 1))
+    ys, xs = np.nonzero(edge)
+    cy, cx = ys[len(ys) // 3], xs[len(xs) // 3]
+    pix = np.array([y * W + x for y in range(cy - 3, cy + 3) for x in range(cx - 3, cx + 3)], np.int32)
+    assert 6 <= cov.reshape(-1)[pix].sum() <= 30                      # the window straddles the silhouette
+    rng = np.random.default_rng(1)
+    wts = rng.uniform(0.5, 1.5, (len(pix), 3))
+    dI = np.zeros((H * W, 3))
+    dI[pix] = wts
+    dI = dI.reshape(H, W, 3)
+    o = S.param_offsets()
+    h, seeds, spp = 1e-3, 8, 512
+    G = np.array([oracle.render_backward(default_config(W=W, H=H, spp=spp, seed=100 + s), scene, theta, dI)
+                  for s in range(seeds)])
+    light = o["lights"] + int(np.argmax(np.abs(G[0, o["lights"]:])))     # the light channel that lights the window most
+    params = [o["alpha"], o["beta"] + 3, o["pose"], o["pose"] + 3, o["pose"] + 5, light]
+    G = G[:, params]
+    FD = np.zeros((seeds, len(params)))
+    for s in range(seeds):
+        cfg = default_config(W=W, H=H, spp=spp, seed=200 + s)
+        for m, i in enumerate(params):
+            tp, tm = theta.copy(), theta.copy()
+            tp[i] += h
+            tm[i] -= h
+            ip = oracle.render(cfg, scene, tp, pixels=pix)
+            im = oracle.render(cfg, scene, tm, pixels=pix)
+            FD[s, m] = (np.sum(wts * ip) - np.sum(wts * im)) / (np.float64(tp[i]) - np.float64(tm[i]))
+    se = np.hypot(G.std(0, ddof=1), FD.std(0, ddof=1)) / np.sqrt(seeds)
+    z = (G.mean(0) - FD.mean(0)) / se
+    assert np.all(se > 0) and np.abs(G.mean(0)).max() > 1.0
+    assert np.all(np.abs(z) <= 3.0), np.c_[G.mean(0), FD.mean(0), se, z]
