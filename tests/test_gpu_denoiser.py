@@ -18,6 +18,7 @@ import torch
 
 from oracle import default_config, mlp
 from paper_1910_05200_gb300 import synthetic as S
+from tests.parity import note
 
 pytestmark = pytest.mark.gpu
 
@@ -59,6 +60,8 @@ def test_features_match_oracle(oracle, tiny, r, W, H, spp):
         # a few ops); feature 12, E[Y^2] - E[Y]^2, cancels in FP32
         tol = 2e-5 * scale if k != 12 else 1e-4 * scale
         err = np.abs(got[..., k] - ref[..., k]).max()
+        note(f"denoiser feature {k} at {W}x{H}x{spp} (relative to its scale)", err / scale, tol / scale,
+             n=ref[..., k].size)
         assert err <= tol, (k, err, scale)
 
 
@@ -73,8 +76,13 @@ def test_inference_and_adjoint_match_reference(r):
     y_ref, _ = mlp.forward(w, f)
     jt_ref = mlp.input_adjoint(w, f, d)
     out, jt = out.cpu().numpy(), jt.cpu().numpy()
+    e_out = np.abs(out - y_ref) / np.abs(y_ref).max()
+    note("denoiser inference (relative to the output scale)", e_out.max(), 2e-3, n=out.size,
+         p9999=np.quantile(e_out, 0.9999))
     assert np.abs(out - y_ref).max() <= 2e-3 * np.abs(y_ref).max()
     rel = np.abs(jt - jt_ref) / (np.abs(jt_ref).max(axis=1, keepdims=True) + 1e-30)
+    note("denoiser input adjoint J^T (relative to each pixel's largest)", rel.max(), 5e-3, n=rel.size,
+         p9999=np.quantile(rel, 0.9999))
     assert rel.max() <= 5e-3, rel.max()     # four FP16 roundings along the adjoint chain
     # inference alone gives the same output
     out2 = r.denoise(torch.tensor(f, device="cuda:0")).cpu().numpy()
@@ -91,11 +99,14 @@ def test_train_step_gradient_and_update(r):
     g = r.denoiser_grad().astype(np.float64)
     w1 = r.denoiser_weights().astype(np.float64)
     lref, gref = mlp.loss_and_grad(w, f, tgt)
+    note("denoiser training loss", abs(loss.item() - lref) / abs(lref), 1e-4)
     assert loss.item() == pytest.approx(lref, rel=1e-4)
     o = 0
     for name, shape in mlp.SIZES:
         n = int(np.prod(shape))
         gs, rs = g[o:o + n], gref[o:o + n]
+        note(f"denoiser training gradient {name} (relative to the layer's largest)",
+             np.abs(gs - rs).max() / max(np.abs(rs).max(), 1e-300), 1e-2, n=n)
         assert np.abs(gs - rs).max() <= 1e-2 * np.abs(rs).max() + 1e-12, name
         o += n
     wref, _, _ = mlp.adam_step(w.astype(np.float64), gref, np.zeros_like(gref), np.zeros_like(gref), 1, lr)

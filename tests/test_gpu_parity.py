@@ -1,17 +1,11 @@
 """GPU path against the CPU oracle, element by element, on identical seeded inputs.
 
-Tolerances (written here, from the target accuracy of the method):
-* image: |g - o| <= 1e-4 * max(|o|, 1e-4 * mean|o|) per pixel and channel;
-  at most 0.01 % of pixels may differ by a flipped discrete decision
-* gradient: |g - o| <= max(1e-3 * max(|o|, 1e-3 * max|o| over the parameter
-  group), KAPPA * mass), where mass is the oracle's L1 mass of the component
-  (sum of absolute contributions, an edge sample counted by both of its
-  sides, propagated with absolute Jacobians) and KAPPA = 1e-4 bounds FP32
-  evaluation of one contribution (unit roundoff 6e-8 times per-sample
-  condition numbers up to ~1.5e3, reached at grazing hits).  The mass term
-  only matters for components that are sums with heavy cancellation.
-The GPU takes every discrete decision in FP32 with the oracle's order of
-operations, so flips are not expected; values differ by FP32 rounding.
+Tolerances are those of tests/parity.py: per pixel 1e-4 relative with at
+most 0.01 % flipped pixels; per gradient component 1e-3 relative with a
+floor of 1e-3 of the parameter group's largest entry.  The GPU takes every
+discrete decision in FP32 with the oracle's order of operations, so flips
+are not expected; values differ by FP32 rounding.  Every check records its
+strict error (tests/parity.py RECORD).
 """
 import numpy as np
 import pytest
@@ -19,6 +13,8 @@ import torch
 
 from oracle import default_config
 from paper_1910_05200_gb300 import synthetic as S
+from tests.parity import (KAPPA, RECORD, assert_image, check_close, check_groups, face_pixels, loss_bound,
+                          record_value)
 
 pytestmark = pytest.mark.gpu
 
@@ -49,20 +45,6 @@ def full_r(fr, full):
     return fr.Renderer(full[0], device=0)
 
 
-def image_errors(got, ref):
-    scale = np.maximum(np.abs(ref), 1e-4 * np.abs(ref).mean() + 1e-30)
-    rel = np.abs(got - ref) / scale
-    bad_px = np.any(rel > 1e-4, axis=-1)
-    return rel, bad_px
-
-
-def assert_image(got, ref):
-    rel, bad = image_errors(got, ref)
-    n = bad.size
-    allowed = int(1e-4 * n)
-    assert bad.sum() <= allowed, f"{bad.sum()} of {n} pixels off (max rel {rel.max():.3e}, allowed {allowed})"
-
-
 def group_slices(K=(80, 90, 80)):
     o = S.param_offsets(*K)
     return {"alpha": slice(o["alpha"], o["beta"]), "beta": slice(o["beta"], o["delta"]),
@@ -70,37 +52,22 @@ def group_slices(K=(80, 90, 80)):
             "pose": slice(o["pose"], o["lights"]), "lights": slice(o["lights"], o["total"])}
 
 
-KAPPA = 1e-4
-
-
-def assert_grad(got, ref, mass=None, K=(80, 90, 80), what=""):
-    report = []
-    for name, sl in group_slices(K).items():
-        o, g = ref[sl], got[sl]
-        floor = 1e-3 * np.abs(o).max()
-        if floor == 0:
-            assert np.all(np.abs(g) <= 1e-9), (what, name, np.abs(g).max())
-            continue
-        tol = 1e-3 * np.maximum(np.abs(o), floor)
-        if mass is not None:
-            tol = np.maximum(tol, KAPPA * mass[sl])
-        err = np.abs(g - o) / tol
-        strict = np.abs(g - o) / np.maximum(np.abs(o), floor)
-        report.append((name, float(strict.max()), float(err.max())))
-        assert err.max() <= 1.0, f"{what} {name}: error {err.max():.3e} x tolerance at {int(err.argmax())} " \
-                                 f"(got {g[err.argmax()]:.6e}, oracle {o[err.argmax()]:.6e})"
-    return report
+def assert_grad(got, ref, mass=None, K=(80, 90, 80), what="", named=None, **kw):
+    return check_groups(got, ref, group_slices(K), mass, named=named, what=what, **kw)
 
 
 def assert_vertex_grad(dXg, dXo, mass, what=""):
     """Per-vertex position gradient (a diagnostic below the parameter level):
     relative 1e-3 for entries above 1 % of the largest, otherwise judged
-    against that 1 % scale.  Entries that small come from a handful of
-    samples at grazing angles, where cosines are near-cancelling FP32 dot
-    products of unit vectors."""
+    against that 1 % scale or KAPPA times the entry's L1 mass.  Entries that
+    small come from a handful of samples at grazing angles, where cosines are
+    near-cancelling FP32 dot products of unit vectors."""
     floor = 1e-2 * np.abs(dXo).max()
+    strict = np.abs(dXg - dXo) / (1e-3 * np.maximum(np.abs(dXo), floor))
     tol = np.maximum(1e-3 * np.maximum(np.abs(dXo), floor), KAPPA * mass)
     err = np.abs(dXg - dXo) / tol
+    RECORD.append(dict(kind="vertex", what=what, n=int(dXo.size), max=float(strict.max()) * 1e-3,
+                       p9999=float(np.quantile(strict, 0.9999)) * 1e-3, n_mass_only=int((strict > 1).sum())))
     assert err.max() <= 1.0, f"{what}: per-vertex error {err.max():.3e} x tolerance"
 
 
@@ -125,7 +92,7 @@ def test_forward_matches_oracle(oracle, tiny, tiny_r, W, H, spp, seed):
     ref = oracle.render(default_config(W=W, H=H, spp=spp, seed=seed), scene, theta)
     if W * H > 1:
         assert ref.max() > 0
-    assert_image(img.cpu().numpy().astype(np.float64), ref)
+    assert_image(img.cpu().numpy().astype(np.float64), ref, what=f"forward {W}x{H}x{spp}")
 
 
 @pytest.mark.parametrize("terms", [1, 2, 4])
@@ -159,6 +126,29 @@ def test_backward_total_and_ragged(oracle, tiny, tiny_r):
     assert_grad(g.cpu().numpy(), ref, mass, what="all terms, ragged")
 
 
+def test_error_against_fp64_posed_mesh(oracle, tiny, tiny_r):
+    """The oracle's values on its FP64 posed mesh (decisions still taken on
+    the FP32 mesh, which is what makes sample identity possible) against the
+    GPU, which evaluates everything on the FP32 mesh.  The difference is the
+    FP32 rounding of the posed vertices (relative 6e-8 of coordinates of
+    order 1, ~1e-6 of the tiny mesh's 0.08-unit triangles) propagated through
+    the estimator, and it is measured here rather than hidden: image and
+    gradient are held to the same tolerances as on the FP32 mesh."""
+    scene, theta, _ = tiny
+    W = H = 64
+    spp = 4
+    th = torch.tensor(theta, device="cuda:0")
+    img = tiny_r.render(th, W, H, spp, seed=0)
+    cfg = default_config(W=W, H=H, spp=spp, seed=0, value_mesh=0)
+    assert_image(img.cpu().numpy().astype(np.float64), oracle.render(cfg, scene, theta),
+                 what="forward 64x64x4 vs FP64 posed mesh")
+    dI = np.random.default_rng(17).normal(size=(H, W, 3)).astype(np.float32)
+    g = tiny_r.backward(th, torch.tensor(dI, device="cuda:0"), W, H, spp, seed=0).cpu().numpy()
+    tiny_r.sync()
+    ref, mass = oracle.render_backward(cfg, scene, theta, dI.astype(np.float64), mass=True)
+    assert_grad(g, ref, mass, what="all terms 64x64x4 vs FP64 posed mesh")
+
+
 def test_autograd_function(fr, tiny_r, tiny):
     scene, theta, _ = tiny
     th = torch.tensor(theta, device="cuda:0", requires_grad=True)
@@ -166,9 +156,8 @@ def test_autograd_function(fr, tiny_r, tiny):
     w = torch.randn(32, 32, 3, device="cuda:0", generator=torch.Generator("cuda:0").manual_seed(0))
     (img * w).sum().backward()
     direct = tiny_r.backward(th.detach(), w, 32, 32, 2, 11)
-    # FP32 atomics make two backward passes differ in the last bits
-    d = direct.cpu().numpy()
-    assert_grad(th.grad.double().cpu().numpy(), d, np.abs(d) * 10.0, what="autograd vs direct")
+    # the same kernels: the two passes differ only in the order of FP32 atomic additions
+    assert_sum_order_close(th.grad.double().cpu().numpy(), direct.cpu().numpy(), what="autograd vs direct")
 
 
 def test_loss_matches_oracle(oracle, tiny, tiny_r):
@@ -184,8 +173,9 @@ def test_loss_matches_oracle(oracle, tiny, tiny_r):
     grad = torch.zeros(len(theta), device="cuda:0", dtype=torch.float64)
     loss = tiny_r.loss(dev(theta), dev(img), dev(tgt), dev(mask), dev(m), 0.3, 0.7, d_image, grad)
     val, dref, gref = oracle.loss(default_config(W=W, H=H), scene, theta, img, tgt, mask, m, 0.3, 0.7)
-    assert abs(loss.item() - val) <= 1e-12 * abs(val)
-    assert np.allclose(d_image.cpu().numpy(), dref, rtol=1e-7, atol=0)
+    record_value("loss E_data + w1 E_prior + w2 E_light", loss.item(), val, 1e-12)
+    record_value("loss d_image", d_image.cpu().numpy()[dref != 0], dref[dref != 0], 1e-7)
+    assert np.all(d_image.cpu().numpy()[dref == 0] == 0)
     assert np.allclose(grad.cpu().numpy(), gref, rtol=1e-12, atol=1e-12)
 
 
@@ -208,7 +198,7 @@ def test_light_prior_readings_match_oracle(oracle, fr, tiny, prior):
     loss = r.loss(dev(th), dev(img), dev(tgt), None, dev(m), 0.3, 0.7, None, grad)
     val, _, gref = oracle.loss(default_config(W=W, H=H, light_prior=prior), scene, th, img, tgt, None, None,
                                0.3, 0.7)
-    assert abs(loss.item() - val) <= 1e-12 * abs(val)
+    record_value(f"loss, light prior reading {prior}", loss.item(), val, 1e-12)
     assert np.allclose(grad.cpu().numpy(), gref, rtol=1e-12, atol=1e-12)
     with pytest.raises(RuntimeError):
         fr.Renderer(scene, device=0, config=fr.default_config(light_prior=3))
@@ -227,11 +217,7 @@ def _three_calls(r, th, tgt, mask, m, W, H, spp, seed, w1, w2, terms=0):
 def assert_sum_order_close(got, ref, what=""):
     """Two GPU results that differ only in the order of floating-point atomic
     additions: 1e-4 of the group's largest entry plus 1e-3 of the entry."""
-    for name, sl in group_slices().items():
-        o, g = ref[sl], got[sl]
-        tol = 1e-4 * np.abs(o).max() + 1e-3 * np.abs(o) + 1e-12
-        err = np.abs(g - o) / tol
-        assert err.max() <= 1.0, f"{what} {name}: {err.max():.3e} x tolerance at {int(err.argmax())}"
+    check_close(got, ref, group_slices(), what=what)
 
 
 @pytest.mark.parametrize("W,H,spp,terms", [(40, 33, 4, 0), (37, 29, 8, 0), (24, 24, 32, 0), (33, 17, 2, 1),
@@ -268,8 +254,9 @@ def test_step_equals_render_loss_backward(oracle, fr, tiny, tiny_r, W, H, spp, t
         assert abs(loss.item() - ref_loss) <= 1e-6 * abs(ref_loss)
     assert_sum_order_close(g.cpu().numpy(), ref_g, what=f"step {W}x{H}x{spp}")
     if spp == 4:
-        val, _, _ = oracle.loss(default_config(W=W, H=H), scene, theta, ref_img, tgt, mask, m, w1, w2)
-        assert abs(loss.item() - val) <= 1e-12 * abs(val)
+        o_img = oracle.render(default_config(W=W, H=H, spp=spp, seed=5), scene, theta)
+        val, _, _ = oracle.loss(default_config(W=W, H=H), scene, theta, o_img, tgt, mask, m, w1, w2)
+        record_value(f"fr_step loss {W}x{H}x{spp}", loss.item(), val, loss_bound(o_img, tgt, mask) / abs(val))
     # without d_image the context's buffer is used; the results stay the same
     img2, loss2, g2 = tiny_r.step(th, dev(tgt), W, H, spp, seed=5, mask=dev(mask), m=dev(m), w1=w1, w2=w2,
                                   terms=terms)
@@ -366,7 +353,7 @@ def test_large_image_and_size_limits(oracle, fr, tiny, tiny_r):
     pix = np.unique(np.concatenate([S.random_pixels(W, H, 32, seed=1),
                                     lit[:: max(1, len(lit) // 32)][:32]])).astype(np.int32)
     ref = oracle.render(default_config(W=W, H=H, spp=spp, seed=8), scene, theta, pixels=pix)
-    assert_image(got[pix], ref)
+    assert_image(got[pix], ref, what="forward 2048x1536x2 sampled")
     opts = fr.FrRenderOpts(8192, 8192, 32, 0, 0, 0)
     small = torch.empty(3, device="cuda:0")
     rc = tiny_r.lib.fr_render(tiny_r.ctx, C.c_void_p(th.data_ptr()), C.byref(opts), C.c_void_p(small.data_ptr()),
@@ -382,13 +369,14 @@ def test_full_size_forward_sampled_pixels(oracle, full, full_r):
     W, H, spp = c["W"], c["H"], c["spp"]
     img = full_r.render(torch.tensor(theta, device="cuda:0"), W, H, spp, seed=3)
     full_r.sync()
-    pix = S.random_pixels(W, H, 48, seed=5)
-    # include pixels on the face and its silhouette
+    cfg = default_config(W=W, H=H, spp=spp, seed=3)
+    # random pixels and pixels on the face (projected vertices of the oracle's mesh)
+    pix = np.unique(np.concatenate([S.random_pixels(W, H, 48, seed=5),
+                                    face_pixels(oracle, cfg, scene, theta, 48, seed=6)])).astype(np.int32)
     got = img.cpu().numpy().reshape(-1, 3)
-    lit = np.nonzero(got.sum(1) > 0)[0]
-    pix = np.unique(np.concatenate([pix, lit[:: max(1, len(lit) // 48)][:48]])).astype(np.int32)
-    ref = oracle.render(default_config(W=W, H=H, spp=spp, seed=3), scene, theta, pixels=pix)
-    assert_image(got[pix], ref)
+    ref = oracle.render(cfg, scene, theta, pixels=pix)
+    assert (ref.sum(1) > 0).sum() >= 40
+    assert_image(got[pix], ref, what="full face forward 256x256x16 sampled")
 
 
 def test_full_size_backward_masked_adjoint(oracle, full, full_r):
@@ -396,18 +384,43 @@ def test_full_size_backward_masked_adjoint(oracle, full, full_r):
     scene, theta, c = full
     W, H, spp = c["W"], c["H"], c["spp"]
     th = torch.tensor(theta, device="cuda:0")
-    img = full_r.render(th, W, H, spp, seed=3).cpu().numpy().reshape(-1, 3)
-    lit = np.nonzero(img.sum(1) > 0)[0]
+    cfg = default_config(W=W, H=H, spp=spp, seed=3)
     rng = np.random.default_rng(0)
-    pix = rng.choice(lit, size=12, replace=False)
+    pix = face_pixels(oracle, cfg, scene, theta, 12, seed=0)
     dI = np.zeros((H * W, 3), np.float32)
     dI[pix] = rng.normal(size=(len(pix), 3))
     dI = dI.reshape(H, W, 3)
     g = full_r.backward(th, torch.tensor(dI, device="cuda:0"), W, H, spp, seed=3).cpu().numpy()
     full_r.sync()
-    ref, mass = oracle.render_backward(default_config(W=W, H=H, spp=spp, seed=3), scene, theta,
-                                       dI.astype(np.float64), mass=True)
+    ref, mass = oracle.render_backward(cfg, scene, theta, dI.astype(np.float64), mass=True)
     assert_grad(g, ref, mass, what="full size, masked adjoint")
+
+
+def test_full_size_step_masked(oracle, full, full_r):
+    """fr_step, the benchmarked call, at full size in its benchmarked launch
+    configuration: E_data restricted by the mask to a few pixels on the face,
+    a black target (d_image = 2 image there), w1 = w2 = 0.  Image on those
+    pixels, loss and gradient against the oracle."""
+    scene, theta, c = full
+    W, H, spp = c["W"], c["H"], c["spp"]
+    th = torch.tensor(theta, device="cuda:0")
+    cfg = default_config(W=W, H=H, spp=spp, seed=4)
+    pix = face_pixels(oracle, cfg, scene, theta, 12, seed=2)
+    mask = np.zeros(H * W, np.uint8)
+    mask[pix] = 1
+    tgt = torch.zeros(H, W, 3, device="cuda:0")
+    img, loss, g = full_r.step(th, tgt, W, H, spp, seed=4, mask=torch.tensor(mask.reshape(H, W), device="cuda:0"))
+    full_r.sync()
+    ref = oracle.render(cfg, scene, theta, pixels=pix)
+    assert (ref.sum(1) > 0).sum() >= 10
+    assert_image(img.cpu().numpy().reshape(-1, 3)[pix], ref, what="fr_step full face 256x256x16 masked pixels")
+    e_ref = float(np.sum(ref ** 2))
+    record_value("fr_step full face loss (masked pixels)", loss.item(), e_ref,
+                 loss_bound(ref, np.zeros_like(ref)) / e_ref)
+    dI = np.zeros((H * W, 3))
+    dI[pix] = 2.0 * ref
+    gref, mass = oracle.render_backward(cfg, scene, theta, dI.reshape(H, W, 3), mass=True)
+    assert_grad(g.cpu().numpy(), gref, mass, what="fr_step full face gradient (masked pixels)")
 
 
 @pytest.mark.parametrize("model,fresnel,layout", [(1, 0, 0), (0, 1, 0), (1, 1, 1)])
@@ -423,12 +436,14 @@ def test_alternative_readings_match_oracle(oracle, fr, tiny, model, fresnel, lay
     img = r.render(th, W, H, spp, seed=6)
     r.sync()
     cfg = default_config(W=W, H=H, spp=spp, seed=6, **kw)
-    assert_image(img.cpu().numpy(), oracle.render(cfg, scene, theta))
+    assert_image(img.cpu().numpy(), oracle.render(cfg, scene, theta), what=f"readings {kw} forward")
     dI = np.random.default_rng(12).normal(size=(H, W, 3)).astype(np.float32)
     g = r.backward(th, torch.tensor(dI, device="cuda:0"), W, H, spp, seed=6).cpu().numpy()
     r.sync()
     ref, mass = oracle.render_backward(cfg, scene, theta, dI.astype(np.float64), mass=True)
-    assert_grad(g, ref, mass, what=f"readings {kw}")
+    # named exceptions (tests/parity.py): components with a cancellation ratio
+    # of 300 or more, against 1e-5 of their mass
+    assert_grad(g, ref, mass, what=f"readings {kw}", cancel=300.0, kappa=1e-5)
 
 
 def test_degenerate_images(oracle, tiny, tiny_r):
@@ -439,7 +454,7 @@ def test_degenerate_images(oracle, tiny, tiny_r):
     img = tiny_r.render(th, 1, 1, 1, seed=2)
     tiny_r.sync()
     ref = oracle.render(default_config(W=1, H=1, spp=1, seed=2), scene, theta)
-    assert_image(img.cpu().numpy(), ref)
+    assert_image(img.cpu().numpy(), ref, what="forward 1x1x1")
     g = tiny_r.backward(th, torch.ones(1, 1, 3, device="cuda:0"), 1, 1, 1, seed=2).cpu().numpy()
     tiny_r.sync()
     gref, mass = oracle.render_backward(default_config(W=1, H=1, spp=1, seed=2), scene, theta, np.ones((1, 1, 3)),
