@@ -298,23 +298,35 @@ def run_ours(args):
     h2d = th_h.numel() * 4 + tgt_h.numel() * 4
     d2h = grad_h.numel() * 8 + 8
 
-    # --- roofline of the dominant kernel (shadow-edge search) ---------------
+    # --- roofline: the dominant kernel and the whole step -------------------
+    # counters of one step through the benchmarked call (reset by the call)
     r.set_counters(True)
-    r.backward(th, d_image, W, H, spp, seed=seed0 + args.warmup, grad=grad)
+    run_step(th, target, seed0 + args.warmup)
     cnt = [int(x) for x in r.counters()]
     r.set_counters(False)
     from paper_1910_05200_gb300 import roofline as RF
+    peaks = facert.probe_peaks(local)            # measured FMA and L2 roofs, SM count
+    clk = clocks.summary()
+    peak = peaks["fp32_tflops"]
     flops_sedge = float(RF.sedge_flops(cnt))
     t_sedge = ph_mean["shadow_edges"] * 1e-3
-    clk = clocks.summary()
-    peak = RF.fp32_peak_tflops(clk.get("sm_mhz"))
     achieved = flops_sedge / t_sedge / 1e12
+    flops_step = float(RF.step_flops(cnt, samples, c["n_on"]))
+    step_achieved = flops_step / (t_step * 1e-3) / 1e12
+    l2_bytes = RF.SEDGE_L2_BYTES
     roof = {"bound": "alu", "kernel": "k_bwd_sedge (shadow-boundary edge search)", "achieved": achieved,
             "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": RF.SEDGE_TRAFFIC_BYTES,
-            "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x median SM clock under load",
+            "peak_note": "measured: FP32 FMA probe (fr_probe_peaks) on this GPU, best of 5 runs",
+            "peak_nominal": RF.fp32_peak_tflops(clk.get("sm_mhz") or 2070.0, peaks["sm_count"]),
+            "sm_count": peaks["sm_count"],
+            "l2_peak_gbs": peaks["l2_read_gbs"],
+            "l2_bytes": l2_bytes,
+            "l2_frac": (l2_bytes / t_sedge / 1e9 / peaks["l2_read_gbs"]) if l2_bytes else None,
             "flops_per_launch": flops_sedge, "ms_per_launch": ph_mean["shadow_edges"],
             "counts_sedge": dict(zip(("ray_nodes", "tri_tests", "edge_nodes_per_warp", "edge_tests", "clip_tests"),
-                                     cnt[RF.K_SEDGE:RF.K_SEDGE + 5]))}
+                                     cnt[RF.K_SEDGE:RF.K_SEDGE + 5])),
+            "step": {"flops_per_step": flops_step, "ms_per_step": t_step, "achieved": step_achieved,
+                     "frac": step_achieved / peak, "unit": "TFLOP/s"}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Msamples/s", "n_gpus": world, "steps": args.steps,

@@ -214,9 +214,19 @@ int fr_geometry(fr_ctx* ctx, const float* theta, float* X, float* N, float* A);
  * with FR_ERR_INVALID_ARG.  The array is shared by every call on a device and
  * kept until the process exits; calls whose GPU work overlaps race on it.
  * The first call on a device looks up the array's device address (set-up);
- * make that first call before any stream capture.  Calls no cudaMalloc or
- * cudaFree. */
+ * make that first call before any stream capture.  The address is kept for
+ * the life of the process: after cudaDeviceReset (or any other reset of the
+ * device's primary context) it is stale, so do not call this entry point on
+ * that device again.  Calls no cudaMalloc or cudaFree. */
 int fr_geometry_noalloc(fr_ctx* ctx, const float* theta, float* X, float* N, float* A);
+
+/* Camera-silhouette edges found by the last geometry preparation on this
+ * context (any call that renders, differentiates or returns geometry): their
+ * canonical edge ids in increasing order, written to out[cap] (host; the
+ * first cap of them).  Canonical edges are the mesh's edges sorted by
+ * (smaller vertex, larger vertex).  Returns their number (which may exceed
+ * cap) after a stream synchronisation.  For inspection and tests. */
+int fr_silhouettes(fr_ctx* ctx, int32_t* out, int32_t cap);
 
 /* Per-vertex position gradient of the last fr_render_backward on this
  * context (after the normals adjoint, before the pose and basis
@@ -230,6 +240,19 @@ int fr_light_stage(const fr_ctx* ctx, float* out);
  * flag) if a kernel hit its traversal stack or step limit since the last
  * fr_sync, FR_ERR_CUDA if the stream reported an error, else FR_OK. */
 int fr_sync(fr_ctx* ctx);
+
+/* Device-side limits of this context's later calls (a robustness guard with
+ * no counterpart in the paper).
+ *   max_steps (>= 1): node visits one traversal of a hierarchy may make
+ *     before it stops and raises FR_ERR_DEVICE_LIMIT at the next fr_sync
+ *     (default 65536; a valid hierarchy needs a few hundred);
+ *   wait_limit (>= 0): tries (about 256 ns apart) a primary-edge work item
+ *     of the persistent batch kernel waits for its frame's tiles before it
+ *     skips its samples and raises FR_ERR_DEVICE_LIMIT (default 4194304,
+ *     about a second).
+ * A call that stops at a limit leaves its outputs incomplete; the context
+ * stays usable.  FR_ERR_INVALID_ARG for values out of range. */
+int fr_set_limits(fr_ctx* ctx, int32_t max_steps, int32_t wait_limit);
 
 /* Work counts of the last fr_render / fr_render_backward call (or batch
  * step), read back after a stream synchronisation.  out[20]: five counts
@@ -291,6 +314,20 @@ int fr_adam_step(fr_ctx* ctx, float* theta, const double* grad, float* m, float*
 /* Number of kernels this context has launched since it was created (a
  * replayed batch graph counts its kernel nodes on every replay). */
 uint64_t fr_launch_count(const fr_ctx* ctx);
+
+/* Roofline denominators of this library's kernels, measured on `device`
+ * (a measurement utility with no counterpart in the paper: the render and
+ * its gradient are FP32 ALU work on data resident in L2).
+ *   fp32_tflops (host, written): best FP32 FMA throughput of the CUDA cores,
+ *     2 FLOP per FMA, over five timed runs of independent FMA chains on
+ *     every SM (TFLOP/s);
+ *   l2_read_gbs (host, written): best streaming read bandwidth of a 32 MiB
+ *     buffer resident in L2, loads that bypass L1 (GB/s);
+ *   sm_count (host, written, may be NULL): multiprocessors of the device.
+ * Allocates 32 MiB of device memory for the duration of the call, on its
+ * own stream, and frees it.  FR_ERR_CUDA for a bad device or a failed
+ * runtime call, FR_ERR_OOM if the buffer cannot be allocated. */
+int fr_probe_peaks(int32_t device, double* fp32_tflops, double* l2_read_gbs, int32_t* sm_count);
 
 /* ---------------------------------------------------------------------------
  * Batched frames.  Several frames of one face (a video, or crops of uneven

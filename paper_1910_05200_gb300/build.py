@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfacert.so")
-SOURCES = ["geometry.cu", "render.cu", "batch.cu", "loss.cu", "denoise.cu", "optim.cu", "capi.cu", "batch_api.cu"]
+SOURCES = ["geometry.cu", "render.cu", "batch.cu", "loss.cu", "denoise.cu", "optim.cu", "capi.cu", "batch_api.cu", "peaks.cu"]
 HEADERS = ["common.cuh", "kernels.cuh", "render_device.cuh", "context.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-rdc=false",

@@ -178,7 +178,7 @@ FR_DEV void batch_step_body(const BatchArgs& b) {
       int* gdst = reinterpret_cast<int*>(&w.g);
       for (int i = lane; i < (int)(sizeof(GradBufs) / 4); i += 32) gdst[i] = gsrc[i];
       __syncwarp();
-      if (lane == 0) { w.a.iter = *b.iter; w.a.counters = b.counters; w.a.err = b.err; }
+      if (lane == 0) { w.a.iter = *b.iter; w.a.counters = b.counters; w.a.err = b.err; w.a.mesh.max_steps = b.max_steps; }
       __syncwarp();
       cur = fi;
     }
@@ -203,7 +203,7 @@ FR_DEV void batch_step_body(const BatchArgs& b) {
       const volatile int* done = b.tiles_done + fi;
       int tries = 0;
       while (*done < F.n_tiles) {
-        if (++tries > BATCH_WAIT_LIMIT) { atomicOr(b.err, ERR_WAIT); skip = 1; break; }
+        if (++tries > b.wait_limit) { atomicOr(b.err, ERR_WAIT); skip = 1; break; }
         __nanosleep(256);
       }
       __threadfence();
@@ -255,6 +255,7 @@ FR_DEV int phase_frame(const PhaseArgs& p, unsigned char* a_raw, unsigned char* 
     a.iter = *p.iter;
     a.counters = p.counters;
     a.err = p.err;
+    a.mesh.max_steps = p.max_steps;
   }
   __syncthreads();
   return f;

@@ -50,6 +50,7 @@ struct fr_batch {
   cudaGraphExec_t exec = nullptr;
   bool graph_ok = false, g_counters = false;
   float g_w1 = 0.0f, g_w2 = 0.0f;
+  int g_max_steps = 0, g_wait_limit = 0;     // device limits the graph was captured with
   uint64_t kernels_per_step = 0;
   int n_sms = 0;
   int occ = 0;             // blocks per SM of the configured kernel
@@ -222,6 +223,7 @@ int enqueue_step(fr_batch* b, float w1, float w2) {
     a.tile_w = b->cfg.tile_w; a.tile_h = b->cfg.tile_h; a.pedge_chunk = b->pedge_chunk;
     a.queue = b->queue.p; a.tiles_done = b->tiles_done.p; a.iter = b->iter_dev.p; a.err = ctx->err_flag.p;
     a.counters = counters;
+    a.max_steps = ctx->max_steps; a.wait_limit = ctx->wait_limit;
     int grid = (int)std::min<long long>((long long)b->occ * b->n_sms, b->n_items);
     kernel_of(b->cfg.min_blocks)<<<grid, b->cfg.block, smem_of(b, b->cfg), s>>>(a);
     CKL();
@@ -229,6 +231,7 @@ int enqueue_step(fr_batch* b, float w1, float w2) {
     PhaseArgs pa;
     pa.frames = b->dframes.p; pa.n_frames = nF; pa.iter = b->iter_dev.p; pa.err = ctx->err_flag.p;
     pa.counters = counters;
+    pa.max_steps = ctx->max_steps;
     pa.block_start = b->bs_fwd.p;
     k_batch_fwd<<<b->nb_fwd, 256, 0, s>>>(pa);
     CKL();
@@ -286,6 +289,7 @@ int capture(fr_batch* b, float w1, float w2) {
   if (e != cudaSuccess) return fail(ctx, FR_ERR_CUDA, "graph instantiation: %s", cudaGetErrorString(e));
   b->graph_ok = true;
   b->g_w1 = w1; b->g_w2 = w2; b->g_counters = ctx->counters_on;
+  b->g_max_steps = ctx->max_steps; b->g_wait_limit = ctx->wait_limit;
   return FR_OK;
 }
 
@@ -297,7 +301,8 @@ int launch_step(fr_batch* b, const float* ts, const float* tf, float w1, float w
     return fail(ctx, FR_ERR_NOT_READY, "the mesh or bases changed after this batch was created: create a new batch");
   if (!b->have_targets) return fail(ctx, FR_ERR_NOT_READY, "fr_batch_set_targets first");
   if (!ts || !tf) return fail(ctx, FR_ERR_INVALID_ARG, "theta_shared or theta_frames is null");
-  if (!b->graph_ok || w1 != b->g_w1 || w2 != b->g_w2 || ctx->counters_on != b->g_counters) {
+  if (!b->graph_ok || w1 != b->g_w1 || w2 != b->g_w2 || ctx->counters_on != b->g_counters ||
+      ctx->max_steps != b->g_max_steps || ctx->wait_limit != b->g_wait_limit) {
     int rc = capture(b, w1, w2);
     if (rc) return rc;
   }

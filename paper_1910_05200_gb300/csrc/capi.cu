@@ -435,6 +435,7 @@ RenderArgs render_args(fr_ctx* c, const float* theta, const fr_render_opts* o, c
   for (int j = 0; j < c->cfg.n_lights; ++j) a.lights[j] = c->lights[j];
   a.mesh.X = v.X; a.mesh.ng = v.ng; a.mesh.tris = c->tris.p; a.mesh.tv = v.tv;
   a.mesh.bvh.nodes = v.tnodes; a.mesh.bvh.n_nodes = c->tbvh.n_nodes;
+  a.mesh.max_steps = c->max_steps;
   a.ebvh.bvh.nodes = v.enodes; a.ebvh.bvh.n_nodes = c->ebvh.n_nodes;
   a.ebvh.edges = c->edges_leaf.p; a.ebvh.edge_id = c->edge_id_leaf.p;
   a.ebvh.pack = v.epack; a.ebvh.verts = c->edges_leaf.p; a.ebvh.cones = v.econes;
@@ -1148,6 +1149,27 @@ int fr_geometry_noalloc(fr_ctx* ctx, const float* theta, float* X, float* N, flo
   rc = silhouettes(ctx, v);
   if (rc) return rc;
   return geometry_outputs(ctx, X, N, A);
+}
+
+int fr_silhouettes(fr_ctx* ctx, int32_t* out, int32_t cap) {
+  if (!ctx || cap < 0 || (cap > 0 && !out)) return FR_ERR_INVALID_ARG;
+  if (!ctx->have_mesh) return fail(ctx, FR_ERR_NOT_READY, "mesh not uploaded");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  int n = 0;
+  CK(cudaMemcpy(&n, ctx->n_sil.p, sizeof(int), cudaMemcpyDeviceToHost));
+  const int k = std::min(n, (int)cap);
+  if (k > 0) CK(cudaMemcpy(out, ctx->sil.p, sizeof(int) * (size_t)k, cudaMemcpyDeviceToHost));
+  return n;
+}
+
+int fr_set_limits(fr_ctx* ctx, int32_t max_steps, int32_t wait_limit) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  if (max_steps < 1 || wait_limit < 0)
+    return fail(ctx, FR_ERR_INVALID_ARG, "limits: max_steps must be >= 1 and wait_limit >= 0");
+  ctx->max_steps = max_steps;
+  ctx->wait_limit = wait_limit;
+  return FR_OK;
 }
 
 // Wait for the context stream and report device-side limit hits (traversal

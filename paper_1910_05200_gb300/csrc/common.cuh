@@ -206,7 +206,9 @@ FR_DEV bool box_hit(V3 lo, V3 hi, V3 o, V3 inv, float tmin, float tmax, float& t
 }
 
 constexpr int STACK = 48;
-constexpr int MAX_STEPS = 1 << 16;   // node visits per traversal before the error flag is raised
+// Node visits per traversal before the error flag is raised (default of
+// fr_set_limits; a traversal of a valid hierarchy needs far fewer).
+constexpr int DEFAULT_MAX_STEPS = 1 << 16;
 
 struct Mesh {
   const float4* X;      // posed vertices [V] (w unused)
@@ -214,6 +216,7 @@ struct Mesh {
   const int4* tris;     // [F] (v0, v1, v2, -)
   const float4* tv;     // triangle vertices in BVH leaf order [F*3]; tv[3i].w = original face id bits
   BVHView bvh;
+  int max_steps;        // node visits per traversal before ERR_STEPS
 };
 
 // Closest hit with ties broken toward the smaller face index.
@@ -229,7 +232,7 @@ FR_DEV int closest_hit(const Mesh& m, V3 o, V3 d, float& t_best, int* err, unsig
   unsigned long long nvis = 0, ntri = 0;
   if (m.bvh.n_nodes == 0) return -1;
   while (true) {
-    if (++steps > MAX_STEPS) { atomicOr(err, ERR_STEPS); break; }
+    if (++steps > m.max_steps) { atomicOr(err, ERR_STEPS); break; }
     ++nvis;
     const float4* N = m.bvh.nodes + 4 * node;
     float4 a = N[0], b = N[1], c = N[2];
@@ -289,7 +292,7 @@ FR_DEV bool occluded(const Mesh& m, V3 x, V3 w, int skip, float tlo, float thi, 
   unsigned long long nvis = 0, ntri = 0;
   if (m.bvh.n_nodes == 0) return false;
   while (true) {
-    if (++steps > MAX_STEPS) { atomicOr(err, ERR_STEPS); break; }
+    if (++steps > m.max_steps) { atomicOr(err, ERR_STEPS); break; }
     ++nvis;
     const float4* N = m.bvh.nodes + 4 * node;
     float4 a = N[0], b = N[1], c = N[2];

@@ -72,6 +72,9 @@ struct fr_ctx {
   DBuf<int> sil, n_sil, block_count, err_flag;
   DBuf<unsigned long long> counters;
   bool counters_on = false;
+  // device limits (fr_set_limits)
+  int max_steps = fr::DEFAULT_MAX_STEPS;
+  int wait_limit = fr::DEFAULT_WAIT_LIMIT;
   uint64_t launches = 0;
   // per-phase timing (fr_set_timing): geometry, forward, interior, primary
   // edges, shadow edges, adjoint, loss

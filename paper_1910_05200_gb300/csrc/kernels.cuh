@@ -118,9 +118,9 @@ struct BatchFrame {
 // Work items of the persistent kernel: tile items (frame, tile) first, then
 // primary-edge items (frame | PEDGE_ITEM, chunk), each group in frame order.
 constexpr int PEDGE_ITEM = 1 << 30;
-// Spin limit of a primary-edge item waiting for its frame's tiles
-// (__nanosleep(256) per try: about a second).
-constexpr int BATCH_WAIT_LIMIT = 1 << 22;
+// Default spin limit of a primary-edge item waiting for its frame's tiles
+// (__nanosleep(256) per try: about a second); fr_set_limits changes it.
+constexpr int DEFAULT_WAIT_LIMIT = 1 << 22;
 
 struct BatchArgs {
   const BatchFrame* frames;
@@ -133,6 +133,8 @@ struct BatchArgs {
   const uint32_t* iter;
   int* err;
   unsigned long long* counters;  // [16] or null, same layout as the single-image kernels
+  int max_steps;          // traversal step cap of every frame
+  int wait_limit;         // tries of a primary-edge item waiting for its frame's tiles
 };
 
 // Phase kernels of a batch (one launch per phase for all frames): block b of
@@ -146,6 +148,7 @@ struct PhaseArgs {
   const uint32_t* iter;
   int* err;
   unsigned long long* counters;  // [16] or null
+  int max_steps;            // traversal step cap of every frame
 };
 
 // Per-warp slice of k_batch_step's dynamic shared memory: the arguments of

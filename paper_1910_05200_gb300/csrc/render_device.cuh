@@ -535,7 +535,7 @@ FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int
   int sp = 0, node = 0, steps = 0;
   unsigned long long nvis = 0, nedge = 0, nclip = 0;
   while (true) {
-    if (++steps > MAX_STEPS) { atomicOr(a.err, ERR_STEPS); break; }
+    if (++steps > a.mesh.max_steps) { atomicOr(a.err, ERR_STEPS); break; }
     ++nvis;
     const int4 ch = a.ebvh.codes4[node];
     bool pass = true;

@@ -51,7 +51,21 @@ EXPORTS = ["fr_default_config", "fr_create", "fr_destroy", "fr_set_stream", "fr_
            "fr_launch_count", "fr_denoiser_n_weights", "fr_denoiser_set_weights", "fr_denoiser_get_weights",
            "fr_denoise", "fr_denoiser_train_step", "fr_denoiser_get_grad", "fr_adam_step",
            "fr_batch_n_shared", "fr_batch_n_frame", "fr_batch_create", "fr_batch_destroy", "fr_batch_set_targets",
-           "fr_batch_step", "fr_batch_autotune", "fr_batch_get_config", "fr_batch_set_config"]
+           "fr_batch_step", "fr_batch_autotune", "fr_batch_get_config", "fr_batch_set_config", "fr_probe_peaks",
+           "fr_set_limits", "fr_silhouettes"]
+
+
+def probe_peaks(device: int = 0) -> dict:
+    """Measured FP32 FMA throughput (TFLOP/s), L2 read bandwidth (GB/s) and SM
+    count of the device (fr_probe_peaks)."""
+    L = load()
+    f = C.c_double(0.0)
+    l2 = C.c_double(0.0)
+    n = C.c_int32(0)
+    rc = L.fr_probe_peaks(int(device), C.byref(f), C.byref(l2), C.byref(n))
+    if rc:
+        raise RuntimeError(f"fr_probe_peaks: {FR_ERRORS.get(rc, rc)}")
+    return {"fp32_tflops": f.value, "l2_read_gbs": l2.value, "sm_count": n.value}
 
 
 def lib_path() -> str:
@@ -96,6 +110,9 @@ def load(path: str | None = None):
     L.fr_get_timings.argtypes = [vp, vp]
     L.fr_launch_count.argtypes = [vp]
     L.fr_launch_count.restype = C.c_uint64
+    L.fr_probe_peaks.argtypes = [i32, vp, vp, vp]
+    L.fr_set_limits.argtypes = [vp, i32, i32]
+    L.fr_silhouettes.argtypes = [vp, vp, i32]
     L.fr_denoiser_n_weights.argtypes = []
     L.fr_denoiser_set_weights.argtypes = [vp, vp, i32]
     L.fr_denoiser_get_weights.argtypes = [vp, vp, i32]
@@ -265,6 +282,22 @@ class Renderer:
 
     def set_counters(self, on=True):
         self.lib.fr_set_counters(self.ctx, 1 if on else 0)
+
+    def set_limits(self, max_steps=1 << 16, wait_limit=1 << 22):
+        """Traversal step cap and batch wait limit of later calls (fr_set_limits)."""
+        self._check(self.lib.fr_set_limits(self.ctx, int(max_steps), int(wait_limit)), "fr_set_limits")
+
+    def silhouettes(self):
+        """Canonical ids of the camera-silhouette edges of the last geometry
+        preparation (fr_silhouettes), host int32 array."""
+        n = self._check(self.lib.fr_silhouettes(self.ctx, None, 0), "fr_silhouettes")
+        out = np.zeros(max(n, 1), np.int32)
+        self._check(self.lib.fr_silhouettes(self.ctx, _hptr(out), n), "fr_silhouettes")
+        return out[:n]
+
+    def sync_code(self):
+        """fr_sync's return code (0, or e.g. -5 = FR_ERR_DEVICE_LIMIT) without raising."""
+        return int(self.lib.fr_sync(self.ctx))
 
     # -- denoiser -----------------------------------------------------------------
     def set_denoiser(self, w):

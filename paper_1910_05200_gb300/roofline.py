@@ -26,11 +26,13 @@ K_FWD, K_INTERIOR, K_PEDGE, K_SEDGE = 0, 5, 10, 15
 # capture of the kernel as it stands (dram__bytes_read.sum +
 # dram__bytes_write.sum): the edge records, hierarchies and meshes stay in L2.
 SEDGE_TRAFFIC_BYTES = 32.65e6 + 1.15e6
+# L2 bytes of one k_bwd_sedge launch at 256x256x16 spp (lts__t_bytes.sum of
+# an ncu capture of the kernel as it stands); None until captured.
+SEDGE_L2_BYTES = None
 SHADE_FWD = 150        # one light sample shaded (BRDF + geometry term)
 SHADE_BWD = 420        # one light sample: forward recompute + adjoint
 N_LIGHTS = 20
 
-SMS = 152
 FP32_LANES = 128
 
 
@@ -44,9 +46,15 @@ def forward_flops(cnt, samples: int, n_on: int) -> float:
 
 
 def backward_flops(cnt, samples: int, n_on: int) -> float:
-    """All backward kernels."""
+    """All backward kernels: interior adjoint (every light), primary edges
+    (two one-sample radiance estimates per edge sample), shadow edges."""
     shading = samples * (N_LIGHTS * SHADE_BWD + 2 * n_on * SHADE_FWD)
     return sum(_kernel_flops(cnt, k) for k in (K_INTERIOR, K_PEDGE, K_SEDGE)) + shading
+
+
+def step_flops(cnt, samples: int, n_on: int) -> float:
+    """One fwd+loss+bwd step from the counters of that step."""
+    return forward_flops(cnt, samples, n_on) + backward_flops(cnt, samples, n_on)
 
 
 def sedge_flops(cnt) -> float:
@@ -54,6 +62,7 @@ def sedge_flops(cnt) -> float:
     return _kernel_flops(cnt, K_SEDGE)
 
 
-def fp32_peak_tflops(sm_mhz: float | None) -> float:
-    mhz = sm_mhz if sm_mhz else 2070.0
-    return SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+def fp32_peak_tflops(sm_mhz: float, sm_count: int) -> float:
+    """Nominal FP32 peak from the device's SM count and a clock (context for
+    the measured FMA peak, which is the denominator)."""
+    return sm_count * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12

@@ -4,10 +4,11 @@ The no-allocation variant is for callers that must not allocate device
 memory while it runs (an allocator that owns the device, a fixed memory
 budget, or a loop that cannot take the synchronisation an allocation may
 cause).  Its silhouette-compaction scratch lives in a static device array
-instead of a context buffer; its outputs must equal fr_geometry's.  Two calls
-in a row check that the shared array's leftover contents do not leak into the
-next call.  This file sorts last so that a run stopping at the first failure
-has already run every other test.
+instead of a context buffer; its outputs, and the silhouette list that the
+compaction writes, must equal fr_geometry's.  Two calls in a row check that
+the shared array's leftover contents do not leak into the next call; a mesh
+with more edges than the array covers is refused.  This file sorts last so
+that a run stopping at the first failure has already run every other test.
 """
 import ctypes as C
 
@@ -37,26 +38,47 @@ def test_noalloc_geometry_matches_fr_geometry():
     r = facert.Renderer(scene, device=0)
     lib, ctx = r.lib, r.ctx
     thetas = [theta0, S.make_theta(scene, seed=5, max_angle_deg=25.0)]
+    lists = []
     for th in thetas:                      # two calls in a row, different poses
         t = torch.tensor(th, device="cuda:0")
         torch.cuda.synchronize()
         n_ref, X_ref, N_ref, A_ref = _outputs(lib, ctx, "fr_geometry", t, r.V)
+        sil_ref = r.silhouettes()
         n_new, X_new, N_new, A_new = _outputs(lib, ctx, "fr_geometry_noalloc", t, r.V)
+        sil_new = r.silhouettes()
         assert n_new == n_ref and n_ref > 0
+        # the list the compaction through the static array wrote: the same
+        # canonical edge ids, in increasing order
+        assert np.array_equal(sil_new, sil_ref)
+        assert np.all(np.diff(sil_new) > 0)
+        lists.append(sil_new)
         # same kernels on the same inputs: the geometry tolerance of the parity tests
         assert np.abs(X_new - X_ref).max() <= 1e-6
         assert np.abs(N_new - N_ref).max() <= 2e-5
         assert np.abs(A_new - A_ref).max() <= 2e-5
-    # the silhouette list the variant leaves behind drives the gradient identically
-    t = torch.tensor(thetas[1], device="cuda:0")
-    dI = torch.randn(32, 32, 3, device="cuda:0", generator=torch.Generator("cuda:0").manual_seed(1))
-    g_ref = r.backward(t, dI, 32, 32, 2, seed=3, terms=2).cpu().numpy()
-    assert r.sync() == 0
-    r2 = facert.Renderer(scene, device=0)
-    _outputs(r2.lib, r2.ctx, "fr_geometry_noalloc", t, r2.V)
-    g_new = r2.backward(t, dI, 32, 32, 2, seed=3, terms=2).cpu().numpy()
-    scale = np.abs(g_ref).max()
-    assert np.abs(g_new - g_ref).max() <= 1e-4 * scale
+    assert not np.array_equal(lists[0], lists[1])     # the second pose has its own silhouettes
+
+
+def test_noalloc_refuses_meshes_beyond_its_array():
+    """A 593 x 593 vertex grid has 1,052,576 edges, more than the static
+    array's 4096 blocks of 256 edges: refused before any kernel runs."""
+    from paper_1910_05200_gb300 import build, facert
+    build.build()
+    n = 593
+    iy, ix = np.mgrid[0:n, 0:n]
+    verts = np.stack([ix.ravel() / (n - 1) - 0.5, iy.ravel() / (n - 1) - 0.5, np.zeros(n * n)], 1)
+    q = (iy[:-1, :-1] * n + ix[:-1, :-1]).ravel()
+    tris = np.concatenate([np.stack([q, q + 1, q + n + 1], 1), np.stack([q, q + n + 1, q + n], 1)])
+    E = 3 * (n - 1) ** 2 + 2 * (n - 1)
+    assert E > 4096 * 256
+    scene = S.Scene(verts.astype(np.float32), tris.astype(np.int32), np.zeros((n * n, 2), np.float32),
+                    np.zeros((3 * n * n, 0), np.float32), np.zeros((3 * n * n, 0), np.float32),
+                    np.full(3 * n * n, 0.5, np.float32), np.zeros((3 * n * n, 0), np.float32))
+    r = facert.Renderer(scene, device=0)
+    th = torch.zeros(r.P, device="cuda:0")
+    X = torch.empty(n * n, 3, device="cuda:0")
+    rc = r.lib.fr_geometry_noalloc(r.ctx, C.c_void_p(th.data_ptr()), C.c_void_p(X.data_ptr()), None, None)
+    assert rc == -1 and b"at most" in r.lib.fr_last_error(r.ctx)
 
 
 def test_noalloc_rejects_no_context():
