@@ -340,6 +340,153 @@ done:
   return hit;
 }
 
+// ---------------------------------------------------------------------------
+// Warp-cooperative traversal.  The 32 lanes of a warp trace their own rays
+// through one shared walk of the hierarchy: a child is entered when any lane
+// that is still searching hits its box (one ballot per child), each lane
+// tests a leaf's triangles only if its own box test passed, and the walk
+// ends when its stack is empty or no lane is searching.  Every lane ends with
+// the result of its own ray (the closest hit with ties to the smaller face
+// index, or whether any face crosses the segment), because a lane visits
+// every node its own walk would visit and a decision taken on a triangle
+// does not depend on the order in which triangles are tested.  Lanes
+// without a ray take part with active = false.  All 32 lanes of the warp
+// must call these functions together.
+//
+// The stack is warp-uniform and lives in registers: entry k in register k / 32
+// of lane k % 32.
+constexpr int WSTACK = 64;
+struct WStack { int r0, r1, sp; };
+FR_DEV void wpush(WStack& s, int v, int lane) {
+  if (s.sp < 32) { if (lane == s.sp) s.r0 = v; }
+  else if (lane == s.sp - 32) s.r1 = v;
+  ++s.sp;
+}
+FR_DEV int wpop(WStack& s) {
+  --s.sp;
+  return s.sp < 32 ? __shfl_sync(0xffffffffu, s.r0, s.sp) : __shfl_sync(0xffffffffu, s.r1, s.sp - 32);
+}
+
+FR_DEV int closest_hit_warp(const Mesh& m, bool active, V3 o, V3 d, float& t_best, int* err,
+                            unsigned long long* cnt) {
+  const int lane = threadIdx.x & 31;
+  RayPre rp = ray_pre(o, d);
+  V3 inv = V3{1.0f / d.x, 1.0f / d.y, 1.0f / d.z};
+  int best = -1;
+  t_best = __int_as_float(0x7f800000);
+  unsigned long long nvis = 0, ntri = 0;
+  if (m.bvh.n_nodes == 0 || !__any_sync(0xffffffffu, active)) return -1;
+  WStack st{0, 0, 0};
+  int node = 0, steps = 0;
+  while (true) {
+    if (++steps > m.max_steps) { if (active) atomicOr(err, ERR_STEPS); break; }
+    if (active) ++nvis;
+    const float4* N = m.bvh.nodes + 4 * node;
+    const float4 a = N[0], b = N[1], c = N[2];
+    const int4 ch = *reinterpret_cast<const int4*>(N + 3);
+    float te0 = 0.0f, te1 = 0.0f;
+    const bool h0 = active && box_hit(V3{a.x, a.y, a.z}, V3{a.w, b.x, b.y}, o, inv, 0.0f, t_best, te0);
+    const bool h1 = active && box_hit(V3{b.z, b.w, c.x}, V3{c.y, c.z, c.w}, o, inv, 0.0f, t_best, te1);
+    const unsigned m0 = __ballot_sync(0xffffffffu, h0), m1 = __ballot_sync(0xffffffffu, h1);
+    const unsigned mf = __ballot_sync(0xffffffffu, h0 && h1 && te1 < te0);
+    // near child first, by the vote of the lanes that hit both
+    const bool swap = 2 * __popc(mf) > __popc(m0 & m1);
+    int next = -1;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const bool second = (k == 1) != swap;                  // child slot taken at this step
+      const int c2 = second ? ch.y : ch.x;
+      const bool h = second ? h1 : h0;
+      if ((second ? m1 : m0) == 0u || c2 == EMPTY_CHILD) continue;
+      if (leaf_child(c2)) {
+        const int f0 = leaf_first(c2), n = leaf_count(c2);
+        for (int i = 0; i < n; ++i) {
+          const float4* T = m.tv + 3 * (f0 + i);
+          const float4 p0 = T[0], p1 = T[1], p2 = T[2];
+          if (!h) continue;
+          const int fid = __float_as_int(p0.w);
+          float tt;
+          ++ntri;
+          if (tri_hit(rp, V3{p0.x, p0.y, p0.z}, V3{p1.x, p1.y, p1.z}, V3{p2.x, p2.y, p2.z}, tt) && tt > 0.0f) {
+            if (tt < t_best || (tt == t_best && fid < best)) { t_best = tt; best = fid; }
+          }
+        }
+      } else if (next < 0) {
+        next = c2;
+      } else {
+        if (st.sp >= WSTACK) { if (active) atomicOr(err, ERR_STACK); goto done; }
+        wpush(st, c2, lane);
+      }
+    }
+    if (next >= 0) { node = next; continue; }
+    if (st.sp == 0) break;
+    node = wpop(st);
+  }
+done:
+  if (cnt && active) { atomicAdd(cnt, nvis); atomicAdd(cnt + 1, ntri); }
+  return best;
+}
+
+// Any face other than `skip` crossed by x + t w, t in (tlo, thi)?  A lane
+// stops searching at its first hit; the walk ends when no lane searches.
+FR_DEV bool occluded_warp(const Mesh& m, bool active, V3 x, V3 w, int skip, float tlo, float thi, int* err,
+                          unsigned long long* cnt) {
+  const int lane = threadIdx.x & 31;
+  RayPre rp = ray_pre(x, w);
+  V3 inv = V3{1.0f / w.x, 1.0f / w.y, 1.0f / w.z};
+  bool hit = false, live = active;
+  unsigned long long nvis = 0, ntri = 0;
+  if (m.bvh.n_nodes == 0 || !__any_sync(0xffffffffu, live)) return false;
+  WStack st{0, 0, 0};
+  int node = 0, steps = 0;
+  while (true) {
+    if (++steps > m.max_steps) { if (live) atomicOr(err, ERR_STEPS); break; }
+    if (live) ++nvis;
+    const float4* N = m.bvh.nodes + 4 * node;
+    const float4 a = N[0], b = N[1], c = N[2];
+    const int4 ch = *reinterpret_cast<const int4*>(N + 3);
+    float te0, te1;
+    const bool h0 = live && box_hit(V3{a.x, a.y, a.z}, V3{a.w, b.x, b.y}, x, inv, 0.0f, thi, te0);
+    const bool h1 = live && box_hit(V3{b.z, b.w, c.x}, V3{c.y, c.z, c.w}, x, inv, 0.0f, thi, te1);
+    const unsigned m0 = __ballot_sync(0xffffffffu, h0), m1 = __ballot_sync(0xffffffffu, h1);
+    int next = -1;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int c2 = k ? ch.y : ch.x;
+      const bool h = k ? h1 : h0;
+      if ((k ? m1 : m0) == 0u || c2 == EMPTY_CHILD) continue;
+      if (leaf_child(c2)) {
+        const int f0 = leaf_first(c2), n = leaf_count(c2);
+        for (int i = 0; i < n; ++i) {
+          const float4* T = m.tv + 3 * (f0 + i);
+          const float4 p0 = T[0], p1 = T[1], p2 = T[2];
+          if (!(h && live)) continue;
+          if (__float_as_int(p0.w) == skip) continue;
+          float tt;
+          ++ntri;
+          if (tri_hit(rp, V3{p0.x, p0.y, p0.z}, V3{p1.x, p1.y, p1.z}, V3{p2.x, p2.y, p2.z}, tt) && tt > tlo &&
+              tt < thi) {
+            hit = true;
+            live = false;
+          }
+        }
+      } else if (next < 0) {
+        next = c2;
+      } else {
+        if (st.sp >= WSTACK) { if (live) atomicOr(err, ERR_STACK); goto done; }
+        wpush(st, c2, lane);
+      }
+    }
+    if (!__any_sync(0xffffffffu, live)) break;
+    if (next >= 0) { node = next; continue; }
+    if (st.sp == 0) break;
+    node = wpop(st);
+  }
+done:
+  if (cnt && active) { atomicAdd(cnt, nvis); atomicAdd(cnt + 1, ntri); }
+  return hit;
+}
+
 FR_DEV int face_flip(const Mesh& m, int f, V3 d) {
   float4 n = m.ng[f];
   return dot3r(V3{n.x, n.y, n.z}, d) > 0.0f ? -1 : 1;
@@ -353,6 +500,20 @@ FR_DEV bool visible(const Mesh& m, V3 x, V3 y, int f, int flip, float tmin, int*
   bool gate = flip > 0 ? g > 0.0f : g < 0.0f;
   if (!gate) return false;
   return !occluded(m, x, w, f, tmin, __fsub_rn(1.0f, tmin), err, cnt);
+}
+
+// visible() for a whole warp (occluded_warp); lanes with active = false take
+// part and get false.
+FR_DEV bool visible_warp(const Mesh& m, bool active, V3 x, V3 y, int f, int flip, float tmin, int* err,
+                         unsigned long long* cnt) {
+  V3 w = sub3r(y, x);
+  bool gate = false;
+  if (active) {
+    float4 n = m.ng[f];
+    float g = dot3r(V3{n.x, n.y, n.z}, w);
+    gate = flip > 0 ? g > 0.0f : g < 0.0f;
+  }
+  return !occluded_warp(m, gate, x, w, f, tmin, __fsub_rn(1.0f, tmin), err, cnt) && gate;
 }
 
 // ---------------------------------------------------------------------------

@@ -42,10 +42,12 @@ FR_DEV void render_fwd_body(const RenderArgs& a, float* __restrict__ image, floa
 #pragma unroll
   for (int k = 0; k < NV; ++k) v[k] = 0.0f;
   uint32_t pix = 0;
-  if (valid) {
-    V3 d = sample_dir(a, px, py, s, pix);
+  {
+    // every lane takes part in the warp-cooperative traversal
+    V3 d = valid ? sample_dir(a, px, py, s, pix) : V3{0, 0, -1};
     SampleAux aux{V3{0, 0, 0}, V3{0, 0, 0}, 0.0f, 0.0f, 0.0f, 0.0f};
-    V3 L = radiance(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt, AOV ? &aux : nullptr);
+    V3 L = radiance<true>(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt, AOV ? &aux : nullptr, nullptr, nullptr,
+                          valid);
     v[0] = L.x; v[1] = L.y; v[2] = L.z;
     if (AOV) {
       v[3] = aux.n.x; v[4] = aux.n.y; v[5] = aux.n.z;
@@ -121,15 +123,21 @@ __global__ void __launch_bounds__(256, 3) k_bwd_interior(RenderArgs a, GradBufs 
   unsigned long long* cnt = a.counters ? a.counters + CNT_INTERIOR : nullptr;
   bool in_image = tid < total && tile_pixel(ip, a.W, a.H, px, py);
   if (tid < total && !in_image && gb.hits) gb.hits[tid] = make_int2(-1, 0);
-  if (in_image) {
-    uint32_t pix;
-    V3 d = sample_dir(a, px, py, s, pix);
-    const float* dI = gb.d_image + 3 * (size_t)pix;
-    V3 dimg{dI[0], dI[1], dI[2]};
+  {
+    // every lane takes part in the warp-cooperative traversals
+    uint32_t pix = 0;
+    V3 d{0, 0, -1}, dimg{0, 0, 0};
+    if (in_image) {
+      d = sample_dir(a, px, py, s, pix);
+      const float* dI = gb.d_image + 3 * (size_t)pix;
+      dimg = V3{dI[0], dI[1], dI[2]};
+    }
+    const bool want = in_image && (dimg.x != 0.0f || dimg.y != 0.0f || dimg.z != 0.0f);
     float t = 0.0f;
-    int f = (dimg.x != 0.0f || dimg.y != 0.0f || dimg.z != 0.0f) ? closest_hit(a.mesh, a.cam.o, d, t, a.err, cnt) : -1;
-    if (gb.hits) gb.hits[tid] = make_int2(f, __float_as_int(t));
-    if (f >= 0) interior_sample(a, gb, sC, sL, pix, s, d, f, t, dimg, cnt);
+    int f = closest_hit_warp(a.mesh, want, a.cam.o, d, t, a.err, cnt);
+    if (!want) { f = -1; t = 0.0f; }
+    if (in_image && gb.hits) gb.hits[tid] = make_int2(f, __float_as_int(t));
+    interior_sample<true>(a, gb, sC, sL, pix, s, d, f, t, dimg, cnt, nullptr, f >= 0);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < CS * CS; i += blockDim.x)
@@ -165,10 +173,9 @@ __global__ void __launch_bounds__(256, 4) k_step_fwd(RenderArgs a, GradBufs gb, 
   V3 L{0, 0, 0}, d{0, 0, -1};
   int2 hit = make_int2(-1, 0);
   uint32_t pix = 0, vis = 0u;
-  if (valid) {
-    d = sample_dir(a, px, py, s, pix);
-    L = radiance(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt, nullptr, &hit, &vis);
-  }
+  if (valid) d = sample_dir(a, px, py, s, pix);
+  L = radiance<true>(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt, nullptr, &hit, &vis, valid);
+  if (!valid) { hit = make_int2(-1, 0); vis = 0u; }
   float v0 = L.x, v1 = L.y, v2 = L.z;
   for (int off = (spp < 32 ? spp : 32) >> 1; off > 0; off >>= 1) {
     v0 += __shfl_xor_sync(0xffffffffu, v0, off);
@@ -202,9 +209,9 @@ __global__ void __launch_bounds__(256, 4) k_step_fwd(RenderArgs a, GradBufs gb, 
   }
   const bool adj = valid && hit.x >= 0 && (dv[0] != 0.0f || dv[1] != 0.0f || dv[2] != 0.0f);
   if (tid < total && gb.hits) gb.hits[tid] = adj ? hit : make_int2(-1, 0);
-  if (adj && sb.interior)
-    interior_sample(a, gb, sC, sL, pix, s, d, hit.x, __int_as_float(hit.y), V3{dv[0], dv[1], dv[2]},
-                    cnt ? cnt + CNT_INTERIOR : nullptr, &vis);
+  if (sb.interior)                     // uniform
+    interior_sample<true>(a, gb, sC, sL, pix, s, d, hit.x, __int_as_float(hit.y), V3{dv[0], dv[1], dv[2]},
+                          cnt ? cnt + CNT_INTERIOR : nullptr, &vis, adj);
   for (int off = 16; off > 0; off >>= 1) lacc += __shfl_xor_sync(0xffffffffu, lacc, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lacc;
   __syncthreads();
@@ -221,8 +228,8 @@ __global__ void __launch_bounds__(256, 4) k_step_fwd(RenderArgs a, GradBufs gb, 
 
 __global__ void __launch_bounds__(256, 4) k_bwd_pedge(RenderArgs a, GradBufs gb) {
   long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= (long long)a.W * a.H * a.spp) return;
-  pedge_sample(a, gb, tid, a.counters ? a.counters + CNT_PEDGE : nullptr);
+  // every lane takes part in the warp-cooperative traversals
+  pedge_sample<true>(a, gb, tid, a.counters ? a.counters + CNT_PEDGE : nullptr, tid < (long long)a.W * a.H * a.spp);
 }
 
 // One thread per (light, camera sample), light-major: a warp serves one light
@@ -255,7 +262,8 @@ __global__ void __launch_bounds__(256, 4) k_bwd_sedge(RenderArgs a, GradBufs gb)
     flip = face_flip(a.mesh, f, d);
     x32 = hit_point(a.cam.o, d, t);
   }
-  sedge_pick_and_add(a, gb, j, valid, d, x32, f, flip, pix, s, wrgb, a.counters ? a.counters + CNT_SEDGE : nullptr);
+  sedge_pick_and_add<true>(a, gb, j, valid, d, x32, f, flip, pix, s, wrgb,
+                           a.counters ? a.counters + CNT_SEDGE : nullptr);
 }
 
 }  // namespace fr

@@ -56,19 +56,33 @@ struct SampleAux {
 // One-sample radiance along a camera ray, lights that are on only.
 // hit (optional) receives the primary hit: face (or -1) and the bits of t;
 // vis (optional) bit j = light j is on and its light point is visible.
+// WARP: all 32 lanes of the warp call together (warp-cooperative traversal,
+// common.cuh); lanes without a ray pass active = false and get 0.
+template <bool WARP = false>
 FR_DEV V3 radiance(const RenderArgs& a, V3 o, V3 d, int tag, uint32_t c0, uint32_t c1, unsigned long long* cnt,
-                   SampleAux* aux = nullptr, int2* hit = nullptr, uint32_t* vis = nullptr) {
+                   SampleAux* aux = nullptr, int2* hit = nullptr, uint32_t* vis = nullptr, bool active = true) {
   float t;
-  int f = closest_hit(a.mesh, o, d, t, a.err, cnt);
+  int f;
+  if constexpr (WARP) f = closest_hit_warp(a.mesh, active, o, d, t, a.err, cnt);
+  else f = closest_hit(a.mesh, o, d, t, a.err, cnt);
   if (hit) *hit = make_int2(f, __float_as_int(t));
   if (vis) *vis = 0u;
-  if (f < 0) return V3{0, 0, 0};
-  int flip = face_flip(a.mesh, f, d);
-  V3 x32 = hit_point(o, d, t);
-  Surf S = surface(a, f, o, d, flip);
-  int idx[4];
-  float w[4], fu, fv;
-  float cs = cspec_lookup(a.cspec, S.u, S.v, idx, w, fu, fv);
+  const bool lit = f >= 0;
+  if constexpr (!WARP) {
+    if (!lit) return V3{0, 0, 0};
+  }
+  int flip = 1;
+  V3 x32{0, 0, 0};
+  Surf S;
+  float cs = 0.0f;
+  if (lit) {
+    flip = face_flip(a.mesh, f, d);
+    x32 = hit_point(o, d, t);
+    S = surface(a, f, o, d, flip);
+    int idx[4];
+    float w[4], fu, fv;
+    cs = cspec_lookup(a.cspec, S.u, S.v, idx, w, fu, fv);
+  }
   V3 L{0, 0, 0};
   const float area = a.side * a.side;
   int n_on = 0, n_vis = 0;
@@ -77,13 +91,16 @@ FR_DEV V3 radiance(const RenderArgs& a, V3 o, V3 d, int tag, uint32_t c0, uint32
     ++n_on;
     U4 q = philox(a.seed, a.iter, c0, c1, (uint32_t)(tag << 8 | j), 0);
     V3 y = light_point(a.lights[j], a.side, unitf(q.x), unitf(q.y));
-    if (!visible(a.mesh, x32, y, f, flip, a.tmin, a.err, cnt)) continue;
+    bool seen;
+    if constexpr (WARP) seen = visible_warp(a.mesh, lit, x32, y, f, flip, a.tmin, a.err, cnt);
+    else seen = visible(a.mesh, x32, y, f, flip, a.tmin, a.err, cnt);
+    if (!seen) continue;
     ++n_vis;
     if (vis) *vis |= 1u << j;
     ShadeOut sh = shade_light(S, cs, light_rgb(a, j), y, a.lights[j].dl, a.brdf);
     L += sh.h * area;
   }
-  if (aux) {
+  if (aux && lit) {
     aux->n = S.ns; aux->rho = S.rho; aux->cs = cs;
     aux->depth = t * len(d) / a.cam.dcam;
     aux->vis = n_on ? (float)n_vis / (float)n_on : 0.0f;
@@ -262,15 +279,24 @@ FR_DEV void hit_adjoint(const RenderArgs& a, int f, V3 d, const Surf& S, V3 g_x,
 // vis (optional): the forward's visibility bits of this sample (radiance
 // with the light tag): lights that are on take their shadow decision from
 // it, the others trace their shadow ray.
+// WARP: all 32 lanes call together; lanes without a sample pass active = false.
+template <bool WARP = false>
 FR_DEV void interior_sample(const RenderArgs& a, const GradBufs& gb, float* sC, float* sL, uint32_t pix, int s,
-                            V3 d, int f, float t, V3 dimg, unsigned long long* cnt, const uint32_t* vis = nullptr) {
+                            V3 d, int f, float t, V3 dimg, unsigned long long* cnt, const uint32_t* vis = nullptr,
+                            bool active = true) {
   const int spp = a.spp;
-  int flip = face_flip(a.mesh, f, d);
-  V3 x32 = hit_point(a.cam.o, d, t);
-  Surf S = surface(a, f, a.cam.o, d, flip);
-  int idx[4];
-  float w[4], fu, fv;
-  float cs = cspec_lookup(a.cspec, S.u, S.v, idx, w, fu, fv);
+  int flip = 1;
+  V3 x32{0, 0, 0};
+  Surf S;
+  int idx[4] = {0, 0, 0, 0};
+  float w[4] = {0, 0, 0, 0}, fu = 0.0f, fv = 0.0f;
+  float cs = 0.0f;
+  if (active) {
+    flip = face_flip(a.mesh, f, d);
+    x32 = hit_point(a.cam.o, d, t);
+    S = surface(a, f, a.cam.o, d, flip);
+    cs = cspec_lookup(a.cspec, S.u, S.v, idx, w, fu, fv);
+  }
   const float scale = a.side * a.side / (float)spp;
   V3 G = dimg * scale;
   V3 g_x{0, 0, 0}, g_ns{0, 0, 0}, g_rho{0, 0, 0};
@@ -278,8 +304,10 @@ FR_DEV void interior_sample(const RenderArgs& a, const GradBufs& gb, float* sC, 
   for (int j = 0; j < a.n_lights; ++j) {
     U4 q = philox(a.seed, a.iter, pix, (uint32_t)s, (uint32_t)(TAG_LIGHT << 8 | j), 0);
     V3 y = light_point(a.lights[j], a.side, unitf(q.x), unitf(q.y));
-    const bool seen = (vis && light_on(a, j)) ? ((*vis >> j) & 1u) != 0u
-                                              : visible(a.mesh, x32, y, f, flip, a.tmin, a.err, cnt);
+    bool seen;
+    if (vis && light_on(a, j)) seen = active && ((*vis >> j) & 1u) != 0u;
+    else if constexpr (WARP) seen = visible_warp(a.mesh, active, x32, y, f, flip, a.tmin, a.err, cnt);
+    else seen = visible(a.mesh, x32, y, f, flip, a.tmin, a.err, cnt);
     if (!seen) continue;
     V3 g_l{0, 0, 0};
     shade_light_bwd(S, cs, light_rgb(a, j), y, a.lights[j].dl, a.brdf, G, g_x, g_ns, g_rho, g_cs, g_l);
@@ -287,6 +315,7 @@ FR_DEV void interior_sample(const RenderArgs& a, const GradBufs& gb, float* sC, 
     atomicAdd(&sL[3 * j + 1], g_l.y);
     atomicAdd(&sL[3 * j + 2], g_l.z);
   }
+  if (!active) return;
   int4 tri = a.mesh.tris[f];
   // shading normal: ns = flip * n / |n|
   V3 nh = S.nraw * S.inv_nlen;
@@ -326,9 +355,16 @@ FR_DEV void interior_sample(const RenderArgs& a, const GradBufs& gb, float* sC, 
 // Edge sample tid (Philox keys: pixel tid / spp, sample tid % spp) of the
 // primary-visibility term.  d_image is read through L2 (__ldcg): in the batched launch another
 // block of the same launch wrote it.
-FR_DEV void pedge_sample(const RenderArgs& a, const GradBufs& gb, long long tid, unsigned long long* cnt) {
+// WARP: all 32 lanes call together; lanes without a sample pass active = false.
+template <bool WARP = false>
+FR_DEV void pedge_sample(const RenderArgs& a, const GradBufs& gb, long long tid, unsigned long long* cnt,
+                         bool active = true) {
   const int nS = *a.n_sil;
-  if (nS <= 0) return;
+  if (nS <= 0) return;                          // uniform
+  if constexpr (!WARP) {
+    if (!active) return;
+  }
+  if (!active) tid = 0;
   uint32_t pix = (uint32_t)(tid / a.spp);
   int s = (int)(tid - (long long)pix * a.spp);
   // Systematic sampling of the silhouette edges taken as one interval
@@ -351,21 +387,28 @@ FR_DEV void pedge_sample(const RenderArgs& a, const GradBufs& gb, long long tid,
   float ex = __fsub_rn(bx, ax), ey = __fsub_rn(by, ay);
   float mx = __fadd_rn(ax, __fmul_rn(u, ex)), my = __fadd_rn(ay, __fmul_rn(u, ey));
   float fx = floorf(mx), fy = floorf(my);
-  if (!(fx >= 0.0f && fx < (float)a.W && fy >= 0.0f && fy < (float)a.H)) return;
-  int ipx = (int)fx, ipy = (int)fy;
-  const float* dI = gb.d_image + 3 * ((size_t)ipy * a.W + ipx);
-  V3 dimg{__ldcg(dI), __ldcg(dI + 1), __ldcg(dI + 2)};
-  if (dimg.x == 0.0f && dimg.y == 0.0f && dimg.z == 0.0f) return;
+  bool ok = active && fx >= 0.0f && fx < (float)a.W && fy >= 0.0f && fy < (float)a.H;
+  V3 dimg{0, 0, 0};
+  if (ok) {
+    const float* dI = gb.d_image + 3 * ((size_t)(int)fy * a.W + (int)fx);
+    dimg = V3{__ldcg(dI), __ldcg(dI + 1), __ldcg(dI + 2)};
+  }
+  ok = ok && !(dimg.x == 0.0f && dimg.y == 0.0f && dimg.z == 0.0f);
   float L2 = __fmul_rn(ex, ex);
   L2 = __fadd_rn(L2, __fmul_rn(ey, ey));
   float Ln = __fsqrt_rn(L2);
-  if (Ln == 0.0f) return;
+  ok = ok && Ln != 0.0f;
+  if constexpr (!WARP) {
+    if (!ok) return;
+  }
+  if (!ok) Ln = 1.0f;
   float nx = __fdiv_rn(-ey, Ln), ny = __fdiv_rn(ex, Ln);
   float e = a.eps_pedge;
   V3 dp = camera_dir(a.cam, __fadd_rn(mx, __fmul_rn(e, nx)), __fadd_rn(my, __fmul_rn(e, ny)));
   V3 dm = camera_dir(a.cam, __fsub_rn(mx, __fmul_rn(e, nx)), __fsub_rn(my, __fmul_rn(e, ny)));
-  V3 fp = radiance(a, a.cam.o, dp, TAG_PEDGE_LIGHT, pix, (uint32_t)s, cnt);
-  V3 fm = radiance(a, a.cam.o, dm, TAG_PEDGE_LIGHT, pix, (uint32_t)s, cnt);
+  V3 fp = radiance<WARP>(a, a.cam.o, dp, TAG_PEDGE_LIGHT, pix, (uint32_t)s, cnt, nullptr, nullptr, nullptr, ok);
+  V3 fm = radiance<WARP>(a, a.cam.o, dm, TAG_PEDGE_LIGHT, pix, (uint32_t)s, cnt, nullptr, nullptr, nullptr, ok);
+  if (!ok) return;
   float delta = dot(dimg, fm - fp);
   if (delta == 0.0f) return;
   float w = delta * (float)nS / ((float)a.W * (float)a.H * (float)a.spp);
@@ -531,8 +574,8 @@ FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int
     pn = n;
     pm = (1e-4f + rr) * len(n);     // margin + dilation by the group radius
   }
-  int stack[STACK];
-  int sp = 0, node = 0, steps = 0;
+  int node = 0, steps = 0;
+  WStack wst{0, 0, 0};
   unsigned long long nvis = 0, nedge = 0, nclip = 0;
   while (true) {
     if (++steps > a.mesh.max_steps) { atomicOr(a.err, ERR_STEPS); break; }
@@ -579,7 +622,8 @@ FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int
       if (((m >> (6 * k)) & 0x3fu) != 0x3fu) continue;
       const int c2 = k == 0 ? ch.x : (k == 1 ? ch.y : (k == 2 ? ch.z : ch.w));
       if (leaf_child(c2)) {
-        int first = leaf_first(c2), n = leaf_count(c2);
+        // the exact decision-form tests, each lane on its own shading point
+        const int first = leaf_first(c2), n = leaf_count(c2);
         for (int i = 0; i < n; ++i) {
           if (!valid) continue;
           const float4* R = a.ebvh.pack + 6 * (first + i);
@@ -602,13 +646,13 @@ FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int
       } else if (next < 0) {
         next = c2;
       } else {
-        if (sp >= STACK) { atomicOr(a.err, ERR_STACK); goto done; }
-        stack[sp++] = c2;
+        if (wst.sp >= WSTACK) { atomicOr(a.err, ERR_STACK); goto done; }
+        wpush(wst, c2, lane);
       }
     }
     if (next >= 0) { node = next; continue; }
-    if (sp == 0) break;
-    node = stack[--sp];
+    if (wst.sp == 0) break;
+    node = wpop(wst);
   }
 done:
   if (cnt && (threadIdx.x & 31) == 0) { atomicAdd(cnt + 2, nvis); }
@@ -618,10 +662,14 @@ done:
 
 // Boundary term of one light given its pick: sample the clipped edge,
 // difference the integrand across the projected edge, scatter the adjoint.
+// WARP: all 32 lanes call together; lanes without a pick pass active = false.
+template <bool WARP = false>
 FR_DEV void sedge_contribution(const RenderArgs& a, const GradBufs& gb, int j, int n_cand, int slot, V3 d, V3 x32,
-                               int f, int flip, uint32_t pix, int s, V3 wrgb, unsigned long long* cnt) {
+                               int f, int flip, uint32_t pix, int s, V3 wrgb, unsigned long long* cnt,
+                               bool active = true) {
   const Light& L = a.lights[j];
   const float hs = __fmul_rn(0.5f, a.side);
+  if (!active) slot = 0;
   const float4* R = a.ebvh.pack + 6 * slot;
   float4 r0 = R[0], r1 = R[1];
   V3 A = v3(r0), B = v3(r1);
@@ -638,14 +686,24 @@ FR_DEV void sedge_contribution(const RenderArgs& a, const GradBufs& gb, int j, i
   V3 y1 = edge_proj(A, B, x32, L, Dd, t1);
   V3 nv = cross3r(L.dl, sub3r(y1, y0));
   float nl = __fsqrt_rn(dot3r(nv, nv));
-  if (nl == 0.0f) return;
+  bool ok = active && nl != 0.0f;
+  if constexpr (!WARP) {
+    if (!ok) return;
+  }
+  if (!ok) nl = 1.0f;
   nv = V3{__fdiv_rn(nv.x, nl), __fdiv_rn(nv.y, nl), __fdiv_rn(nv.z, nl)};
   const float e = a.eps_sedge;
   V3 yp{__fadd_rn(y.x, __fmul_rn(e, nv.x)), __fadd_rn(y.y, __fmul_rn(e, nv.y)), __fadd_rn(y.z, __fmul_rn(e, nv.z))};
   V3 ym{__fsub_rn(y.x, __fmul_rn(e, nv.x)), __fsub_rn(y.y, __fmul_rn(e, nv.y)), __fsub_rn(y.z, __fmul_rn(e, nv.z))};
-  bool vp = visible(a.mesh, x32, yp, f, flip, a.tmin, a.err, cnt);
-  bool vm = visible(a.mesh, x32, ym, f, flip, a.tmin, a.err, cnt);
-  if (vp == vm) return;
+  bool vp, vm;
+  if constexpr (WARP) {
+    vp = visible_warp(a.mesh, ok, x32, yp, f, flip, a.tmin, a.err, cnt);
+    vm = visible_warp(a.mesh, ok, x32, ym, f, flip, a.tmin, a.err, cnt);
+  } else {
+    vp = visible(a.mesh, x32, yp, f, flip, a.tmin, a.err, cnt);
+    vm = visible(a.mesh, x32, ym, f, flip, a.tmin, a.err, cnt);
+  }
+  if (!ok || vp == vm) return;
   Surf S = surface(a, f, a.cam.o, d, flip);
   int idx[4];
   float w4[4], fu, fv;
@@ -688,11 +746,16 @@ FR_DEV void sedge_contribution(const RenderArgs& a, const GradBufs& gb, int j, i
 
 // Shadow-edge term of one (camera sample, light j).  Warp-collective: all 32
 // lanes call it, lanes without a shading point with valid = false.
+template <bool WARP = false>
 FR_DEV void sedge_pick_and_add(const RenderArgs& a, const GradBufs& gb, int j, bool valid, V3 d, V3 x32, int f,
                                int flip, uint32_t pix, int s, V3 wrgb, unsigned long long* cnt) {
   Pick P = pick_light_warp(a, valid, x32, f, j, pix, s, cnt);
-  if (!valid || P.n == 0) return;
-  sedge_contribution(a, gb, j, P.n, P.slot, d, x32, f, flip, pix, s, wrgb, cnt);
+  if constexpr (WARP) {
+    sedge_contribution<true>(a, gb, j, P.n, P.slot, d, x32, f, flip, pix, s, wrgb, cnt, valid && P.n > 0);
+  } else {
+    if (!valid || P.n == 0) return;
+    sedge_contribution(a, gb, j, P.n, P.slot, d, x32, f, flip, pix, s, wrgb, cnt);
+  }
 }
 
 }  // namespace fr

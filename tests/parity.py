@@ -173,3 +173,18 @@ def note(what, err, tol, n=1, p9999=None):
     """Record an error the calling test measured and asserts itself."""
     RECORD.append(dict(kind="value", what=what, n=int(n), max=float(err),
                        p9999=float(err if p9999 is None else p9999), tol=float(tol)))
+
+
+def check_same_values(got, ref, what="", rel=1e-6):
+    """Two results of the same library whose decisions are identical and
+    whose values differ only by FP32 rounding (the same formulas compiled in
+    two kernels may contract multiply-adds differently): |g - r| <= rel *
+    max(|r|, 1e-3 max|r|)."""
+    g, r = np.asarray(got, np.float64), np.asarray(ref, np.float64)
+    scale = np.maximum(np.abs(r), 1e-3 * np.abs(r).max() + 1e-30)
+    e = np.abs(g - r) / scale
+    RECORD.append(dict(kind="same-library", what=what, group="values", n=int(e.size),
+                       max=float(e.max()) if e.size else 0.0, p9999=_pct(e, 0.9999), tol_frac=float(e.max() / rel)
+                       if e.size else 0.0))
+    if ASSERT:
+        assert e.size == 0 or e.max() <= rel, f"{what}: values differ by {e.max():.3e} (relative) > {rel:.1e}"

