@@ -19,13 +19,15 @@
 // All tile items come before all primary-edge items in the queue and a warp
 // only takes an item when it is running, so every tile item a primary-edge
 // item waits for is held by a running warp that does not wait: the wait
-// ends.  It is bounded all the same (BATCH_WAIT_LIMIT; ERR_WAIT on expiry).
+// ends.  It is bounded all the same (BatchArgs::wait_limit, fr_set_limits;
+// ERR_WAIT on expiry).
 //
 // Samples, decisions and per-sample arithmetic are those of the single-image
-// kernels (same device functions, same Philox keys), so when spp divides 32 a
-// frame's image is bit-identical to the single-image render of the same frame
-// (same shuffle reduction) and its gradient differs only in the order of
-// floating-point atomic additions.  spp a multiple of 32 takes each pixel in
+// kernels (same device functions, same Philox keys, the same warp-cooperative
+// traversals), so a frame's image equals the single-image render of the same
+// frame up to FP32 rounding (the same formulas compiled in another kernel may
+// contract multiply-adds differently) and its gradient differs only in that
+// and the order of floating-point atomic additions.  spp a multiple of 32 takes each pixel in
 // two passes (radiance, then the adjoints with the primary hit traced again).
 #include "render_device.cuh"
 
@@ -51,16 +53,16 @@ FR_DEV void sample_adjoints(const RenderArgs& a, const GradBufs& g, float* sC, f
   valid = valid && hit.x >= 0 && (dv.x != 0.0f || dv.y != 0.0f || dv.z != 0.0f);
   if (valid) {
     d = sample_dir(a, px, py, s, pix);
-    interior_sample(a, g, sC, sL, pix, s, d, hit.x, __int_as_float(hit.y), dv, cnt ? cnt + CNT_INTERIOR : nullptr,
-                    vis);
     wrgb = dv * (1.0f / (float)a.spp);
     flip = face_flip(a.mesh, hit.x, d);
     x32 = hit_point(a.cam.o, d, __int_as_float(hit.y));
   }
-  // shadow edges, warp-collective: every lane takes part for every light
+  // warp-collective from here: every lane takes part
+  interior_sample<true>(a, g, sC, sL, pix, s, d, hit.x, __int_as_float(hit.y), dv, cnt ? cnt + CNT_INTERIOR : nullptr,
+                        vis, valid);
   for (int j = 0; j < a.n_lights; ++j) {
     if (!light_on(a, j)) continue;                 // uniform
-    sedge_pick_and_add(a, g, j, valid, d, x32, hit.x, flip, pix, s, wrgb, cnt ? cnt + CNT_SEDGE : nullptr);
+    sedge_pick_and_add<true>(a, g, j, valid, d, x32, hit.x, flip, pix, s, wrgb, cnt ? cnt + CNT_SEDGE : nullptr);
   }
 }
 
@@ -99,9 +101,10 @@ FR_DEV void tile_small(WarpState& w, const BatchFrame& F, float* sC, int tile, i
     V3 L{0, 0, 0};
     int2 hit = make_int2(-1, 0);
     uint32_t pix = 0, vis = 0u;
-    if (valid) {
-      V3 d = sample_dir(a, px, py, s, pix);
-      L = radiance(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt, nullptr, &hit, &vis);
+    {
+      V3 d = valid ? sample_dir(a, px, py, s, pix) : V3{0, 0, -1};
+      L = radiance<true>(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt, nullptr, &hit, &vis, valid);
+      if (!valid) { hit = make_int2(-1, 0); vis = 0u; }
     }
     float v0 = L.x, v1 = L.y, v2 = L.z;
     for (int off = spp >> 1; off > 0; off >>= 1) {
@@ -129,7 +132,7 @@ FR_DEV void tile_large(WarpState& w, const BatchFrame& F, float* sC, int tile, i
     uint32_t pix = 0;
     for (int s = lane; s < spp; s += 32) {
       V3 d = sample_dir(a, px, py, s, pix);
-      acc += radiance(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt);
+      acc += radiance<true>(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt);
     }
     for (int off = 16; off > 0; off >>= 1) {
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
@@ -142,7 +145,7 @@ FR_DEV void tile_large(WarpState& w, const BatchFrame& F, float* sC, int tile, i
     for (int s = lane; s < spp; s += 32) {
       V3 d = sample_dir(a, px, py, s, pix);
       float t = 0.0f;
-      int f = closest_hit(a.mesh, a.cam.o, d, t, a.err, cnt ? cnt + CNT_INTERIOR : nullptr);
+      int f = closest_hit_warp(a.mesh, true, a.cam.o, d, t, a.err, cnt ? cnt + CNT_INTERIOR : nullptr);
       sample_adjoints(a, w.g, sC, w.sL, true, px, py, s, make_int2(f, __float_as_int(t)), dv, cnt);
     }
   }
@@ -214,7 +217,7 @@ FR_DEV void batch_step_body(const BatchArgs& b) {
     unsigned long long* cnt_p = b.counters ? b.counters + CNT_PEDGE : nullptr;
     for (int k = lane; k < b.pedge_chunk; k += 32) {
       long long t = base + k;
-      if (t < F.n_pedge) pedge_sample(w.a, w.g, t, cnt_p);
+      pedge_sample<true>(w.a, w.g, t, cnt_p, t < F.n_pedge);
     }
   }
   if (cur >= 0) flush_lights(w, lane);
@@ -286,10 +289,9 @@ __global__ void __launch_bounds__(256, 3) k_batch_fwd(PhaseArgs p) {
   V3 L{0, 0, 0}, d{0, 0, -1};
   int2 hit = make_int2(-1, 0);
   uint32_t pix = 0, vis = 0u;
-  if (valid) {
-    d = sample_dir(a, px, py, s, pix);
-    L = radiance(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt, nullptr, &hit, &vis);
-  }
+  if (valid) d = sample_dir(a, px, py, s, pix);
+  L = radiance<true>(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt, nullptr, &hit, &vis, valid);
+  if (!valid) { hit = make_int2(-1, 0); vis = 0u; }
   float v0 = L.x, v1 = L.y, v2 = L.z;
   for (int off = spp >> 1; off > 0; off >>= 1) {
     v0 += __shfl_xor_sync(0xffffffffu, v0, off);
@@ -302,9 +304,8 @@ __global__ void __launch_bounds__(256, 3) k_batch_fwd(PhaseArgs p) {
   if (valid) dv = pixel_loss(F, pix, V3{v0 * inv, v1 * inv, v2 * inv}, s == 0, lacc);
   bool adj = valid && hit.x >= 0 && (dv.x != 0.0f || dv.y != 0.0f || dv.z != 0.0f);
   if (tid < total) g.hits[tid] = adj ? hit : make_int2(-1, 0);
-  if (adj)
-    interior_sample(a, g, sC, sL, pix, s, d, hit.x, __int_as_float(hit.y), dv, cnt ? cnt + CNT_INTERIOR : nullptr,
-                    &vis);
+  interior_sample<true>(a, g, sC, sL, pix, s, d, hit.x, __int_as_float(hit.y), dv, cnt ? cnt + CNT_INTERIOR : nullptr,
+                        &vis, adj);
   for (int off = 16; off > 0; off >>= 1) lacc += __shfl_xor_sync(0xffffffffu, lacc, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lacc;
   __syncthreads();
@@ -349,7 +350,8 @@ FR_DEV void batch_sedge_body(const PhaseArgs& p) {
     flip = face_flip(a.mesh, fh, d);
     x32 = hit_point(a.cam.o, d, __int_as_float(hit.y));
   }
-  sedge_pick_and_add(a, gb, j, valid, d, x32, fh, flip, pix, s, wrgb, p.counters ? p.counters + CNT_SEDGE : nullptr);
+  sedge_pick_and_add<true>(a, gb, j, valid, d, x32, fh, flip, pix, s, wrgb,
+                           p.counters ? p.counters + CNT_SEDGE : nullptr);
 }
 
 __global__ void __launch_bounds__(256, 3) k_batch_sedge3(PhaseArgs p) { batch_sedge_body(p); }
@@ -362,8 +364,8 @@ __global__ void __launch_bounds__(256, 4) k_batch_pedge(PhaseArgs p) {
   const RenderArgs& a = *reinterpret_cast<const RenderArgs*>(a_raw);
   const GradBufs& gb = *reinterpret_cast<const GradBufs*>(g_raw);
   long long tid = (long long)(blockIdx.x - p.block_start[f]) * blockDim.x + threadIdx.x;
-  if (tid >= (long long)a.W * a.H * a.spp) return;
-  pedge_sample(a, gb, tid, p.counters ? p.counters + CNT_PEDGE : nullptr);
+  // every lane takes part in the warp-cooperative traversals
+  pedge_sample<true>(a, gb, tid, p.counters ? p.counters + CNT_PEDGE : nullptr, tid < (long long)a.W * a.H * a.spp);
 }
 
 // The persistent kernel at three register budgets (launch bounds of 256

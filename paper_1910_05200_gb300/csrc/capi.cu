@@ -993,7 +993,7 @@ int fr_denoiser_set_weights(fr_ctx* ctx, const float* w, int32_t n) {
     static bool attr_done[64] = {false};
     if (ctx->device < 64 && !attr_done[ctx->device]) {
       CK(cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_smem_bytes()));
-      CK(cudaFuncSetAttribute(k_mlp_train_fwdbwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_smem_bytes()));
+      CK(cudaFuncSetAttribute(k_mlp_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_smem_bytes()));
       CK(cudaFuncSetAttribute(k_mlp_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 4));
       attr_done[ctx->device] = true;
     }
@@ -1040,8 +1040,8 @@ int fr_denoiser_train_step(fr_ctx* ctx, const float* aov, const float* target, i
   const int NW = mlp_n_weights();
   CK(cudaMemsetAsync(ctx->mlp_g.p, 0, sizeof(float) * NW, s));
   CK(cudaMemsetAsync(loss, 0, sizeof(double), s));
-  k_mlp_train_fwdbwd<<<(n_pix + 127) / 128, 128, mlp_smem_bytes(), s>>>(n_pix, ctx->mlp_w.p, aov, target,
-                                                                        ctx->mlp_scratch.p, loss);
+  k_mlp_train_tc<<<(n_pix + 127) / 128, 256, mlp_smem_bytes(), s>>>(n_pix, ctx->mlp_w.p, aov, target,
+                                                                    ctx->mlp_scratch.p, loss);
   CKL();
   int off[8];
   mlp_layer_offsets(off);

@@ -271,84 +271,174 @@ __global__ void __launch_bounds__(256) k_mlp_infer(int n_pix, const float* __res
 }
 
 // ---------------------------------------------------------------------------
-// Training: one SIMT thread per pixel runs the forward with the same FP16
-// rounding of weights and activations, the MSE loss against target, and the
-// backward; it stores activations and pre-activation gradients for the
-// weight-gradient reduction.  Scratch layout per pixel (FP32):
+// Training.  Scratch layout per pixel (FP32), written by k_mlp_train_tc and
+// reduced by k_mlp_wgrad:
 //   h0[16] h1[64] h2[64] h3[64] | g1[64] g2[64] g3[64] g4[8]
+// (activations as the FP16 values the layers consumed; gradients with
+// respect to each layer's pre-activation).
 constexpr int TR_STRIDE = 16 + 3 * NH + 3 * NH + 8;
 
-__global__ void __launch_bounds__(128) k_mlp_train_fwdbwd(int n_pix, const float* __restrict__ w,
-                                                          const float* __restrict__ aov,
-                                                          const float* __restrict__ target,
-                                                          float* __restrict__ scratch, double* __restrict__ loss) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  MlpSmem& S = *reinterpret_cast<MlpSmem*>(smem_raw);
-  load_weights(S, w);
-  __syncthreads();
-  __shared__ double red[4];
-  int p = blockIdx.x * blockDim.x + threadIdx.x;
-  double l = 0.0;
-  if (p < n_pix) {
-    float* sc = scratch + (size_t)p * TR_STRIDE;
-    float* h0 = sc;
-    float* h1 = sc + 16;
-    float* h2 = h1 + NH;
-    float* h3 = h2 + NH;
-    float* g1 = h3 + NH;
-    float* g2 = g1 + NH;
-    float* g3 = g2 + NH;
-    float* g4 = g3 + NH;
-    const float* x = aov + 14 * (size_t)p;
-    for (int k = 0; k < 16; ++k) h0[k] = __half2float(__float2half_rn(feature(S, x, k)));
-    // forward
-    for (int n = 0; n < NH; ++n) {
-      float a = S.b1[n];
-      for (int k = 0; k < 16; ++k) a += __half2float(S.w1[n][k]) * h0[k];
-      g1[n] = a > 0.f ? 1.f : 0.f;   // ReLU mask, overwritten by the gradient below
-      h1[n] = __half2float(__float2half_rn(fmaxf(a, 0.f)));
-    }
-    for (int n = 0; n < NH; ++n) {
-      float a = S.b2[n];
-      for (int k = 0; k < NH; ++k) a += __half2float(S.w2[n][k]) * h1[k];
-      g2[n] = a > 0.f ? 1.f : 0.f;
-      h2[n] = __half2float(__float2half_rn(fmaxf(a, 0.f)));
-    }
-    for (int n = 0; n < NH; ++n) {
-      float a = S.b3[n];
-      for (int k = 0; k < NH; ++k) a += __half2float(S.w3[n][k]) * h2[k];
-      g3[n] = a > 0.f ? 1.f : 0.f;
-      h3[n] = __half2float(__float2half_rn(fmaxf(a, 0.f)));
-    }
-    float y[3];
-    for (int c = 0; c < 3; ++c) {
-      float a = S.b4[c];
-      for (int k = 0; k < NH; ++k) a += __half2float(S.w4[c][k]) * h3[k];
-      y[c] = x[c] + x[13] * S.sout * a;
-      float e = y[c] - target[3 * (size_t)p + c];
-      l += (double)e * e;
-      g4[c] = 2.0f * e * x[13] * S.sout / (float)n_pix;   // d(mean over pixels of |e|^2)/d(W4 h3 + b4)
-    }
-    for (int c = 3; c < 8; ++c) g4[c] = 0.f;
-    // backward
-    for (int k = 0; k < NH; ++k) {
-      float a = 0.f;
-      for (int c = 0; c < 3; ++c) a += __half2float(S.w4[c][k]) * g4[c];
-      g3[k] *= a;
-    }
-    for (int k = 0; k < NH; ++k) {
-      float a = 0.f;
-      for (int n = 0; n < NH; ++n) a += __half2float(S.w3[n][k]) * g3[n];
-      g2[k] *= a;
-    }
-    for (int k = 0; k < NH; ++k) {
-      float a = 0.f;
-      for (int n = 0; n < NH; ++n) a += __half2float(S.w2[n][k]) * g2[n];
-      g1[k] *= a;
+// One training pass on the tensor cores: one warp = 16 pixels, the forward
+// through the fragments of k_mlp_infer, the MSE loss against target, then the MSE gradient
+// g4 = 2 e cov s_out / n_pix and its chain through W4^T, W3^T, W2^T with the
+// forward ReLU masks.  Each pixel's g4 is scaled to unit maximum before it is
+// rounded to FP16 (the gradients are of order 1/n_pix, below FP16's range)
+// and scaled back when stored.  Activations and gradients go to the scratch
+// for k_mlp_wgrad.
+namespace {
+// A fragment (packed halves) of 4 k-chunks -> the 64 values of rows g and g+8.
+FR_DEV void store_frag_rows(const uint32_t (*A)[4], int t, float* ra, float* rb) {
+#pragma unroll
+  for (int kc = 0; kc < 4; ++kc) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      __half2 h = *reinterpret_cast<const __half2*>(&A[kc][q]);
+      const int col = 16 * kc + 2 * t + ((q & 2) ? 8 : 0);
+      float* r = (q & 1) ? rb : ra;
+      if (r) { r[col] = __low2float(h); r[col + 1] = __high2float(h); }
     }
   }
+}
+
+// adjoint_layer that also stores the FP32 gradients (times the pixel scales
+// sa, sb) of rows g and g+8.
+template <int KCH>
+FR_DEV void adjoint_layer_store(const uint32_t (*A)[4], const __half* Wt, int ldk, uint32_t mask, int lane,
+                                uint32_t (*Aout)[4], float* ra, float* rb, float sa, float sb) {
+  float C[8][4];
+  const int t = lane & 3;
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    C[nt][0] = C[nt][1] = C[nt][2] = C[nt][3] = 0.0f;
+#pragma unroll
+    for (int kc = 0; kc < KCH; ++kc) {
+      uint32_t bb0, bb1;
+      bfrag(Wt, ldk, 8 * nt, 16 * kc, lane, bb0, bb1);
+      mma16816(C[nt], A[kc], bb0, bb1);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (!((mask >> (4 * nt + r)) & 1u)) C[nt][r] = 0.0f;
+    const int col = 8 * nt + 2 * t;
+    if (ra) { ra[col] = C[nt][0] * sa; ra[col + 1] = C[nt][1] * sa; }
+    if (rb) { rb[col] = C[nt][2] * sb; rb[col + 1] = C[nt][3] * sb; }
+  }
+#pragma unroll
+  for (int kc = 0; kc < 4; ++kc) {
+    Aout[kc][0] = pack_h2(C[2 * kc][0], C[2 * kc][1]);
+    Aout[kc][1] = pack_h2(C[2 * kc][2], C[2 * kc][3]);
+    Aout[kc][2] = pack_h2(C[2 * kc + 1][0], C[2 * kc + 1][1]);
+    Aout[kc][3] = pack_h2(C[2 * kc + 1][2], C[2 * kc + 1][3]);
+  }
+}
+}  // namespace
+
+__global__ void __launch_bounds__(256) k_mlp_train_tc(int n_pix, const float* __restrict__ w,
+                                                      const float* __restrict__ aov, const float* __restrict__ target,
+                                                      float* __restrict__ scratch, double* __restrict__ loss) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  MlpSmem& S = *reinterpret_cast<MlpSmem*>(smem_raw);
+  __shared__ double red[8];
+  load_weights(S, w);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int row0 = (blockIdx.x * 8 + warp) * 16;
+  const int ra = row0 + g, rb = row0 + g + 8;
+  const bool va = ra < n_pix, vb = rb < n_pix;
+  double l = 0.0;
+  if (row0 < n_pix) {                        // uniform over the warp
+    float* sa_row = va ? scratch + (size_t)ra * TR_STRIDE : nullptr;
+    float* sb_row = vb ? scratch + (size_t)rb * TR_STRIDE : nullptr;
+    uint32_t X[1][4];
+    {
+      const float* xa = aov + 14 * (size_t)(va ? ra : 0);
+      const float* xb = aov + 14 * (size_t)(vb ? rb : 0);
+      float a0 = va ? feature(S, xa, 2 * t) : 0.f, a1 = va ? feature(S, xa, 2 * t + 1) : 0.f;
+      float b0 = vb ? feature(S, xb, 2 * t) : 0.f, b1 = vb ? feature(S, xb, 2 * t + 1) : 0.f;
+      float a2 = va ? feature(S, xa, 2 * t + 8) : 0.f, a3 = va ? feature(S, xa, 2 * t + 9) : 0.f;
+      float b2 = vb ? feature(S, xb, 2 * t + 8) : 0.f, b3 = vb ? feature(S, xb, 2 * t + 9) : 0.f;
+      X[0][0] = pack_h2(a0, a1); X[0][1] = pack_h2(b0, b1); X[0][2] = pack_h2(a2, a3); X[0][3] = pack_h2(b2, b3);
+      // h0 (the FP16-rounded standardised features), columns 2t, 2t+1, 2t+8, 2t+9
+      const uint32_t q[4] = {X[0][0], X[0][1], X[0][2], X[0][3]};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        __half2 h = *reinterpret_cast<const __half2*>(&q[i]);
+        float* r = (i & 1) ? sb_row : sa_row;
+        const int col = 2 * t + ((i & 2) ? 8 : 0);
+        if (r) { r[col] = __low2float(h); r[col + 1] = __high2float(h); }
+      }
+    }
+    uint32_t H1[4][4], H2[4][4], H3[4][4];
+    uint32_t m1, m2, m3;
+    hidden_layer<1>(X, &S.w1[0][0], LD16, S.b1, lane, H1, m1);
+    hidden_layer<4>(H1, &S.w2[0][0], LD64, S.b2, lane, H2, m2);
+    hidden_layer<4>(H2, &S.w3[0][0], LD64, S.b3, lane, H3, m3);
+    store_frag_rows(H1, t, sa_row ? sa_row + 16 : nullptr, sb_row ? sb_row + 16 : nullptr);
+    store_frag_rows(H2, t, sa_row ? sa_row + 16 + NH : nullptr, sb_row ? sb_row + 16 + NH : nullptr);
+    store_frag_rows(H3, t, sa_row ? sa_row + 16 + 2 * NH : nullptr, sb_row ? sb_row + 16 + 2 * NH : nullptr);
+    float Y[4];
+    Y[0] = S.b4[2 * t]; Y[1] = S.b4[2 * t + 1]; Y[2] = Y[0]; Y[3] = Y[1];
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc) {
+      uint32_t bb0, bb1;
+      bfrag(&S.w4[0][0], LD64, 0, 16 * kc, lane, bb0, bb1);
+      mma16816(Y, H3[kc], bb0, bb1);
+    }
+    // output gradient of rows g (r = 0) and g + 8 (r = 1), channels 2t, 2t+1
+    float g4[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int row = r == 0 ? ra : rb;
+      const bool v = r == 0 ? va : vb;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int c = 2 * t + q;
+        if (!v || c >= NOUT) continue;
+        const float* xr = aov + 14 * (size_t)row;
+        const float y = xr[c] + xr[13] * S.sout * Y[2 * r + q];
+        const float e = y - target[3 * (size_t)row + c];
+        l += (double)e * e;
+        g4[r][q] = 2.0f * e * xr[13] * S.sout / (float)n_pix;
+      }
+    }
+    // per-pixel scale of g4 (a row's three channels live in lanes t = 0, 1)
+    float sa = fmaxf(fabsf(g4[0][0]), fabsf(g4[0][1])), sb = fmaxf(fabsf(g4[1][0]), fabsf(g4[1][1]));
+    sa = fmaxf(sa, __shfl_xor_sync(0xffffffffu, sa, 1));
+    sb = fmaxf(sb, __shfl_xor_sync(0xffffffffu, sb, 1));
+    sa = fmaxf(sa, __shfl_xor_sync(0xffffffffu, sa, 2));
+    sb = fmaxf(sb, __shfl_xor_sync(0xffffffffu, sb, 2));
+    const float ia = sa > 0.f ? 1.0f / sa : 0.f, ib = sb > 0.f ? 1.0f / sb : 0.f;
+    if (t < 2) {
+      float* ga = sa_row ? sa_row + 16 + 6 * NH : nullptr;
+      float* gb = sb_row ? sb_row + 16 + 6 * NH : nullptr;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (ga) ga[2 * t + q] = g4[0][q];
+        if (gb) gb[2 * t + q] = g4[1][q];
+      }
+      if (t == 1) {
+        for (int c = 4; c < 8; ++c) {
+          if (ga) ga[c] = 0.f;
+          if (gb) gb[c] = 0.f;
+        }
+      }
+    }
+    uint32_t D[1][4];
+    D[0][0] = pack_h2(g4[0][0] * ia, g4[0][1] * ia);
+    D[0][1] = pack_h2(g4[1][0] * ib, g4[1][1] * ib);
+    D[0][2] = 0u; D[0][3] = 0u;
+    uint32_t G3[4][4], G2[4][4], G1[4][4];
+    adjoint_layer_store<1>(D, &S.w4t[0][0], LD16, m3, lane, G3, sa_row ? sa_row + 16 + 5 * NH : nullptr,
+                           sb_row ? sb_row + 16 + 5 * NH : nullptr, sa, sb);
+    adjoint_layer_store<4>(G3, &S.w3t[0][0], LD64, m2, lane, G2, sa_row ? sa_row + 16 + 4 * NH : nullptr,
+                           sb_row ? sb_row + 16 + 4 * NH : nullptr, sa, sb);
+    adjoint_layer_store<4>(G2, &S.w2t[0][0], LD64, m1, lane, G1, sa_row ? sa_row + 16 + 3 * NH : nullptr,
+                           sb_row ? sb_row + 16 + 3 * NH : nullptr, sa, sb);
+    (void)G1;
+  }
   for (int off = 16; off > 0; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
+  if (lane == 0) red[warp] = l;
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0;

@@ -255,9 +255,8 @@ __device__ inline double light_prior_mean(const float* __restrict__ l, int n, in
 // denoiser (denoise.cu)
 __global__ void k_mlp_infer(int n_pix, const float* __restrict__ w, const float* __restrict__ aov,
                             float* __restrict__ out, const float* __restrict__ d_out, float* __restrict__ d_rgb);
-__global__ void k_mlp_train_fwdbwd(int n_pix, const float* __restrict__ w, const float* __restrict__ aov,
-                                   const float* __restrict__ target, float* __restrict__ scratch,
-                                   double* __restrict__ loss);
+__global__ void k_mlp_train_tc(int n_pix, const float* __restrict__ w, const float* __restrict__ aov,
+                               const float* __restrict__ target, float* __restrict__ scratch, double* __restrict__ loss);
 __global__ void k_mlp_wgrad(int n_pix, const float* __restrict__ scratch, int g_off, int h_off, int N, int K, int Kw,
                             float* __restrict__ dW, float* __restrict__ db, int chunk);
 __global__ void k_adam(int n, float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,

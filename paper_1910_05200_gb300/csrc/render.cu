@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256, 3) k_bwd_interior(RenderArgs a, GradBufs 
 // rays again).  For spp dividing 32 the image is bit-identical to
 // k_render_fwd's and the adjoint to k_loss_data's; the hits written for the
 // edge passes equal k_bwd_interior's.
-__global__ void __launch_bounds__(256, 4) k_step_fwd(RenderArgs a, GradBufs gb, StepBufs sb) {
+__global__ void __launch_bounds__(256, 5) k_step_fwd(RenderArgs a, GradBufs gb, StepBufs sb) {
   __shared__ float sC[CS * CS];
   __shared__ float sL[3 * MAX_LIGHTS];
   __shared__ double red[8];

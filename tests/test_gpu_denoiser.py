@@ -4,8 +4,9 @@ Tolerances: the kernels round weights, inputs and hidden activations to FP16
 (unit roundoff 4.9e-4) and accumulate in FP32 in a different order than the
 reference, so an activation next to an FP16 rounding boundary can round the
 other way.  Outputs are compared at 2e-3 of their scale, the input adjoint
-(four FP16 roundings in its chain) at 5e-3, gradients at 1e-2 of each
-layer's largest entry.
+(four FP16 roundings in its chain) at 5e-3, training gradients (the
+tensor-core backward also rounds each layer's gradient to FP16; the FP64
+reference does not) at 1e-2 of each layer's largest entry.
 
 Training set: faces with random shape, expression, albedo, specular map and
 pose under one fixed light-stage configuration (the capture setting); the
@@ -110,10 +111,13 @@ def test_train_step_gradient_and_update(r):
         assert np.abs(gs - rs).max() <= 1e-2 * np.abs(rs).max() + 1e-12, name
         o += n
     wref, _, _ = mlp.adam_step(w.astype(np.float64), gref, np.zeros_like(gref), np.zeros_like(gref), 1, lr)
-    # first Adam step moves each weight by about lr * sign(g): equal wherever the sign agrees
+    # the first Adam step moves each weight by lr g / (|g| + eps): lr sign(g)
+    # wherever |g| >> eps, so equal wherever the sign agrees, up to the relative
+    # error of g for gradients near eps (the tensor-core backward rounds each
+    # layer's gradient to FP16: about 1e-3 relative)
     agree = np.sign(g) == np.sign(gref)
     assert agree.mean() > 0.99
-    assert np.abs(w1 - wref)[agree].max() <= 1e-6
+    assert np.abs(w1 - wref)[agree].max() <= 5e-3 * lr
     assert np.abs(w1 - wref).max() <= 2.0001 * lr
 
 
