@@ -25,10 +25,11 @@ K_FWD, K_INTERIOR, K_PEDGE, K_SEDGE = 0, 5, 10, 15
 # DRAM bytes of one k_bwd_sedge launch at 256x256x16 spp from a 1-pass ncu
 # capture of the kernel as it stands (dram__bytes_read.sum +
 # dram__bytes_write.sum): the edge records, hierarchies and meshes stay in L2.
-SEDGE_TRAFFIC_BYTES = 32.65e6 + 1.15e6
-# L2 bytes of one k_bwd_sedge launch at 256x256x16 spp (lts__t_bytes.sum of
-# an ncu capture of the kernel as it stands); None until captured.
-SEDGE_L2_BYTES = None
+SEDGE_TRAFFIC_BYTES = 31.61e6 + 0.19e6
+# L2 bytes of one k_bwd_sedge launch at 256x256x16 spp: lts__t_sectors.sum x
+# 32 B of a --set full capture at 128x128x16 (58.40 M sectors), scaled by the
+# samples of a launch (x4).
+SEDGE_L2_BYTES = 58.40e6 * 32 * 4
 SHADE_FWD = 150        # one light sample shaded (BRDF + geometry term)
 SHADE_BWD = 420        # one light sample: forward recompute + adjoint
 N_LIGHTS = 20
