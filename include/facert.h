@@ -187,8 +187,9 @@ int fr_loss(fr_ctx* ctx, const float* theta, int32_t W, int32_t H, const float* 
  * device (written with dE_data/d image) or NULL (a context buffer is used);
  * loss: one FP64 device scalar (overwritten); grad[P] FP64 device.
  * Results equal those of fr_render, fr_loss and fr_render_backward with the
- * same opts up to the order of floating-point additions (for spp dividing
- * 32 the image and d_image bit for bit).  When spp divides 256 the render,
+ * same opts: the same samples and decisions, values up to FP32 rounding
+ * (the same formulas compiled in another kernel) and the order of
+ * floating-point additions.  When spp divides 256 the render,
  * the data term's adjoint and the interior adjoint run as one kernel (a
  * pixel's samples lie in one block of 256 threads): each sample's interior
  * adjoint reuses its primary hit and the shadow decisions of the lights that
@@ -369,7 +370,8 @@ typedef struct fr_frame {
  *     (light-major within a frame), primary edges; blocks of 256 threads;
  *     min_blocks 3 or 4 is the register budget of the shadow-edge kernel
  *     (65536 / (256 * min_blocks) registers per thread); tile_w, tile_h and
- *     block are ignored (8x8 tiles).  Needs spp dividing 32.
+ *     block are ignored (8x8 tiles).  Needs spp dividing 256 (a pixel's
+ *     samples in one block of 256 threads; the default for such spp).
  *   fused = 1: one persistent launch whose warps take work items from a
  *     queue: tiles of tile_w x tile_h pixels (sides 1..64) that run forward,
  *     loss, interior and shadow-edge terms together, then chunks of

@@ -293,10 +293,18 @@ __global__ void __launch_bounds__(256, 3) k_batch_fwd(PhaseArgs p) {
   L = radiance<true>(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt, nullptr, &hit, &vis, valid);
   if (!valid) { hit = make_int2(-1, 0); vis = 0u; }
   float v0 = L.x, v1 = L.y, v2 = L.z;
-  for (int off = spp >> 1; off > 0; off >>= 1) {
+  for (int off = (spp < 32 ? spp : 32) >> 1; off > 0; off >>= 1) {
     v0 += __shfl_xor_sync(0xffffffffu, v0, off);
     v1 += __shfl_xor_sync(0xffffffffu, v1, off);
     v2 += __shfl_xor_sync(0xffffffffu, v2, off);
+  }
+  if (spp > 32) {                      // uniform: the pixel spans spp / 32 warps of this block
+    __shared__ float wsum[8][3];
+    const int w = threadIdx.x >> 5, nw = spp >> 5, w0 = w - w % nw;
+    if ((threadIdx.x & 31) == 0) { wsum[w][0] = v0; wsum[w][1] = v1; wsum[w][2] = v2; }
+    __syncthreads();
+    v0 = 0.0f; v1 = 0.0f; v2 = 0.0f;
+    for (int k = 0; k < nw; ++k) { v0 += wsum[w0 + k][0]; v1 += wsum[w0 + k][1]; v2 += wsum[w0 + k][2]; }
   }
   const float inv = 1.0f / (float)spp;
   double lacc = 0.0;

@@ -93,7 +93,7 @@ int check_config(fr_batch* b, const fr_tile_config& c, int* blocks_per_sm) {
   fr_ctx* ctx = b->ctx;
   if (c.fused != 0 && c.fused != 1) return fail(ctx, FR_ERR_INVALID_ARG, "fused must be 0 or 1");
   if (!c.fused) {
-    if (b->spp > 32) return fail(ctx, FR_ERR_INVALID_ARG, "the phased launches need spp dividing 32");
+    if (256 % b->spp) return fail(ctx, FR_ERR_INVALID_ARG, "the phased launches need spp dividing 256");
     if (c.min_blocks != 3 && c.min_blocks != 4)
       return fail(ctx, FR_ERR_INVALID_ARG, "phased: min_blocks must be 3 or 4, got %d", c.min_blocks);
     *blocks_per_sm = c.min_blocks;
@@ -343,7 +343,7 @@ int fr_batch_create(fr_ctx* ctx, const fr_frame* frames, int32_t n_frames, int32
   b->ctx = ctx;
   b->generation = ctx->generation;
   b->nF = n_frames; b->spp = spp;
-  if (spp > 32) b->cfg = fr_tile_config{4, 4, 256, 2, 1, 0.0f};   // the phased launches need spp dividing 32
+  if (256 % spp) b->cfg = fr_tile_config{4, 4, 256, 2, 1, 0.0f};   // the phased launches need spp dividing 256
   b->P = ctx->n_params(); b->Ps = fr_batch_n_shared(ctx); b->Pf = fr_batch_n_frame(ctx);
   b->frames.assign(frames, frames + n_frames);
   b->pix_off.resize(n_frames);
@@ -384,7 +384,7 @@ int fr_batch_create(fr_ctx* ctx, const fr_frame* frames, int32_t n_frames, int32
     b->hit_off[f] = nh;
     nh += (long long)((frames[f].W + 7) / 8) * ((frames[f].H + 7) / 8) * 64 * spp;
   }
-  BK(b->hits.alloc(spp <= 32 ? (size_t)nh : 0));
+  BK(b->hits.alloc(256 % spp == 0 ? (size_t)nh : 0));
   // BVH boxes start as the context's (child codes and empty children are
   // fixed by the topology; refits rewrite the rest)
   for (size_t f = 0; f < nF; ++f) {

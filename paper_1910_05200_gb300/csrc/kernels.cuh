@@ -165,7 +165,7 @@ FR_HOST_DEV inline size_t batch_smem_bytes(int block) {
   return batch_smem_head() + (size_t)(block / 32) * sizeof(BatchWarpState);
 }
 
-// forward + loss + interior adjoint (spp dividing 32), blocks of 256 threads
+// forward + loss + interior adjoint (spp dividing 256), blocks of 256 threads
 // over each frame's samples in 8x8-tile order; writes gb.hits for the
 // shadow-edge phase
 __global__ void k_batch_fwd(PhaseArgs p);

@@ -181,11 +181,17 @@ def test_autotuner_table_and_configuration_invariance(case):
     case.b.set_config(8, 8, 256, 4, 0)
 
 
-def test_spp_multiple_of_32(fr, tiny):
-    """spp = 64: each pixel in two passes (radiance, then the adjoints with
-    the primary hit traced again); the single-image forward sums such pixels
+@pytest.mark.parametrize("fused", [0, 1])
+def test_spp_multiple_of_32(fr, tiny, fused):
+    """spp = 64 in both launch modes: the phased launches sum a pixel's
+    samples over two warps of a block through shared memory; the persistent
+    kernel takes each pixel in two passes (radiance, then the adjoints with
+    the primary hit traced again).  The single-image forward sums such pixels
     with atomics, so images agree to rounding."""
     c = Case(fr, tiny[0], [(9, 7), (12, 10)], 64, seed=21)
+    assert c.b.config()["fused"] == 0                 # phased by default: 64 divides 256
+    if fused:
+        c.b.set_config(4, 4, 256, 2, 1)
     loss, gs, gf, img = c.step()
     imgs = c.frame_slices(img)
     tgts, masks = c.frame_slices(c.targets), c.frame_slices(c.masks)
@@ -198,19 +204,19 @@ def test_spp_multiple_of_32(fr, tiny):
         c.r.loss(th, dev(imgs[f]), dev(tgts[f]), dev(masks[f]), None, 0.0, 0.0, d_image)
         per_frame.append(c.r.backward(th, d_image, w, h, 64, seed=seed, iter=ITER).cpu().numpy())
     gs_ref, gf_ref, _ = combine(fr, per_frame, c.thetas, c.m, W1, W2)
-    assert_atomic_close(gs, gs_ref, shared_groups(), "spp 64 shared")
+    assert_atomic_close(gs, gs_ref, shared_groups(), f"spp 64 shared, fused {fused}")
     for f in range(len(c.frames)):
-        assert_atomic_close(gf[f], gf_ref[f], frame_groups(), f"spp 64 frame {f}")
+        assert_atomic_close(gf[f], gf_ref[f], frame_groups(), f"spp 64 frame {f}, fused {fused}")
 
 
 def test_unsupported_spp_is_refused(fr, case):
     for spp in (3, 48):
         with pytest.raises(RuntimeError):
             fr.Batch(case.r, [(8, 8, 0)], spp)
-    b64 = fr.Batch(case.r, [(8, 8, 0)], 64)
-    assert b64.config()["fused"] == 1
+    b96 = fr.Batch(case.r, [(8, 8, 0)], 96)
+    assert b96.config()["fused"] == 1
     with pytest.raises(RuntimeError):
-        b64.set_config(8, 8, 256, 4, 0)          # phased launches need spp dividing 32
+        b96.set_config(8, 8, 256, 4, 0)          # phased launches need spp dividing 256
 
 
 def test_invalid_configurations_are_refused(case):
