@@ -34,6 +34,9 @@
  *     with R = Rz(rz) Ry(ry) Rx(rx) in radians; P = fr_n_params(ctx).
  *   - Images are H x W x 3 FP32, row-major, pixel (px, py) at index
  *     3*(py*W + px), py = 0 at the top.
+ *   - The phases of each call (geometry, forward, interior, primary edges,
+ *     shadow edges, adjoint, loss) are marked as NVTX ranges named
+ *     "facert <phase>" around their host-side enqueue.
  */
 #ifndef FACERT_H
 #define FACERT_H

@@ -81,13 +81,31 @@ class Result:
     ms_per_iter: float
 
 
+def save_checkpoint(path, it, step_in_stage, theta, mom, vel, losses):
+    """The state of optimize() after `it` iterations, written atomically
+    (a temporary file renamed over the target)."""
+    import os
+    tmp = f"{path}.tmp{os.getpid()}.npz"
+    np.savez(tmp, it=np.int64(it), step_in_stage=np.int64(step_in_stage), theta=theta.cpu().numpy(),
+             mom=mom.cpu().numpy(), vel=vel.cpu().numpy(), losses=losses.cpu().numpy())
+    os.replace(tmp, path)
+
+
 def optimize(r, target, W, H, spp, iters=500, seed=0, theta0=None, w1=0.02, w2=0.002, m=None,
-             denoise=False, rates=LEARNING_RATES, api="step") -> Result:
+             denoise=False, rates=LEARNING_RATES, api="step", checkpoint=None, checkpoint_every=50,
+             resume=None, stop_after=None) -> Result:
     """Fit theta to the target image [H, W, 3] (device).  With denoise, the
     loss is taken on the denoised render and its residual is the image
     adjoint handed to the renderer (the network must be set on r).  api
     "calls" runs render, loss and backward as three calls instead of fr_step
-    (same results up to the order of floating-point additions)."""
+    (same results up to the order of floating-point additions).
+
+    checkpoint: a path where the state (iteration, stage step, theta, Adam
+    moments, losses) is saved every checkpoint_every iterations and at the
+    end; resume: a path written that way, from which the run continues (the
+    samples of iteration i depend only on (seed, i), so a resumed run draws
+    what an uninterrupted one would); stop_after: end after this many
+    iterations of the schedule (a run interrupted on purpose)."""
     dev = r.device
     th = torch.tensor(initial_theta() if theta0 is None else theta0, device=dev)
     P = th.numel()
@@ -100,9 +118,18 @@ def optimize(r, target, W, H, spp, iters=500, seed=0, theta0=None, w1=0.02, w2=0
     lrs = [torch.tensor(lr_vector(g, rates=rates), device=dev) for _, _, g in STAGES]
     losses = torch.zeros(iters, device=dev, dtype=torch.float64)
     step_in_stage = 0
+    start = 0
+    if resume is not None:
+        z = np.load(resume)
+        start, step_in_stage = int(z["it"]), int(z["step_in_stage"])
+        th.copy_(torch.from_numpy(z["theta"]))
+        mom.copy_(torch.from_numpy(z["mom"]))
+        vel.copy_(torch.from_numpy(z["vel"]))
+        losses[: len(z["losses"])] = torch.from_numpy(z["losses"][:iters])
+    end = iters if stop_after is None else min(iters, stop_after)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
-    for it in range(iters):
+    for it in range(start, end):
         if it > 0 and stages[it] != stages[it - 1]:
             mom.zero_()
             vel.zero_()
@@ -121,9 +148,13 @@ def optimize(r, target, W, H, spp, iters=500, seed=0, theta0=None, w1=0.02, w2=0
             losses[it:it + 1] = r.step(th, target, W, H, spp, seed=seed, iter=it, m=m, w1=w1, w2=w2,
                                        image=image, d_image=d_image, grad=grad)[1]
         r.adam_step(th, grad, mom, vel, lrs[stages[it]], step_in_stage)
+        if checkpoint is not None and (it + 1) % checkpoint_every == 0:
+            save_checkpoint(checkpoint, it + 1, step_in_stage, th, mom, vel, losses)
     ev1.record()
     torch.cuda.synchronize()
-    return Result(th.cpu().numpy(), losses.cpu().numpy(), ev0.elapsed_time(ev1) / iters)
+    if checkpoint is not None:
+        save_checkpoint(checkpoint, end, step_in_stage, th, mom, vel, losses)
+    return Result(th.cpu().numpy(), losses.cpu().numpy(), ev0.elapsed_time(ev1) / max(1, end - start))
 
 
 def parameter_errors(theta, truth, K=(S.K_ID, S.K_EXP, S.K_ALB)):

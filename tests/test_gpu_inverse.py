@@ -52,3 +52,33 @@ def test_inverse_loop_fits_tiny_face(r, tiny):
     print("loss", first, "->", last, "errors", e0, "->", e1, "ms/iter", res.ms_per_iter)
     assert last < 0.3 * first
     assert e1["lights"] < e0["lights"]
+
+
+def test_checkpoint_and_resume(r, tiny, tmp_path):
+    """A run interrupted after 30 of 60 iterations and resumed from its
+    checkpoint ends where an uninterrupted run ends: the state (theta, Adam
+    moments, stage step, losses) is restored and the samples of an iteration
+    depend only on (seed, iteration).  Two runs differ in the order of
+    floating-point atomic additions inside each gradient, which Adam
+    amplifies in components whose gradient is near zero (a flipped sign moves
+    them by the learning rate), so the runs are compared by their losses and
+    by the distance of their parameters relative to how far the second half
+    moves them."""
+    scene, _, _ = tiny
+    W = H = 24
+    truth = S.make_theta(scene, seed=22, n_on=8)
+    target = r.render(torch.tensor(truth, device="cuda:0"), W, H, 64, seed=3)
+    full = INV.optimize(r, target, W, H, 4, iters=60, seed=2)
+    ck = str(tmp_path / "state.npz")
+    part = INV.optimize(r, target, W, H, 4, iters=60, seed=2, checkpoint=ck, checkpoint_every=10, stop_after=30)
+    z = np.load(ck)
+    assert int(z["it"]) == 30 and int(z["step_in_stage"]) >= 1
+    assert np.array_equal(z["theta"], part.theta)
+    rest = INV.optimize(r, target, W, H, 4, iters=60, seed=2, resume=ck)
+    d_rest = np.linalg.norm(rest.theta - full.theta)
+    d_half = np.linalg.norm(part.theta - full.theta)
+    assert d_rest <= 0.1 * d_half, (d_rest, d_half)
+    assert d_rest <= 2e-2 * np.linalg.norm(full.theta)
+    assert np.array_equal(rest.loss[:30], part.loss[:30])          # restored from the checkpoint
+    np.testing.assert_allclose(rest.loss[:30], full.loss[:30], rtol=1e-2)
+    assert abs(rest.loss[-10:].mean() - full.loss[-10:].mean()) <= 2e-2 * full.loss[-10:].mean()
