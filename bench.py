@@ -309,13 +309,13 @@ def run_ours(args):
     peaks = facert.probe_peaks(local)            # measured FMA and L2 roofs, SM count
     clk = clocks.summary()
     peak = peaks["fp32_tflops"]
-    flops_sedge = float(RF.sedge_flops(cnt))
-    t_sedge = ph_mean["shadow_edges"] * 1e-3
+    flops_sedge = float(RF.sedge_search_flops(cnt))
+    t_sedge = ph_mean["shadow_edge_search"] * 1e-3
     achieved = flops_sedge / t_sedge / 1e12
     flops_step = float(RF.step_flops(cnt, samples, c["n_on"]))
     step_achieved = flops_step / (t_step * 1e-3) / 1e12
     l2_bytes = RF.SEDGE_L2_BYTES
-    roof = {"bound": "alu", "kernel": "k_bwd_sedge (shadow-boundary edge search)", "achieved": achieved,
+    roof = {"bound": "alu", "kernel": "k_bwd_sedge (shadow-edge search and pick)", "achieved": achieved,
             "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": RF.SEDGE_TRAFFIC_BYTES,
             "peak_note": "measured: FP32 FMA probe (fr_probe_peaks) on this GPU, best of 5 runs",
             "peak_nominal": RF.fp32_peak_tflops(clk.get("sm_mhz") or 2070.0, peaks["sm_count"]),
@@ -323,9 +323,11 @@ def run_ours(args):
             "l2_peak_gbs": peaks["l2_read_gbs"],
             "l2_bytes": l2_bytes,
             "l2_frac": (l2_bytes / t_sedge / 1e9 / peaks["l2_read_gbs"]) if l2_bytes else None,
-            "flops_per_launch": flops_sedge, "ms_per_launch": ph_mean["shadow_edges"],
-            "counts_sedge": dict(zip(("ray_nodes", "tri_tests", "edge_nodes_per_warp", "edge_tests", "clip_tests"),
-                                     cnt[RF.K_SEDGE:RF.K_SEDGE + 5])),
+            "flops_per_launch": flops_sedge, "ms_per_launch": ph_mean["shadow_edge_search"],
+            "contributions": {"kernel": "k_bwd_sedge_add", "ms_per_launch": ph_mean["shadow_edge_contributions"],
+                              "flops_per_launch": float(RF.sedge_add_flops(cnt))},
+            "counts_sedge": dict(zip(("ray_nodes", "tri_tests", "edge_nodes_per_warp", "edge_tests", "clip_tests",
+                                      "edges_classified_per_warp"), cnt[RF.K_SEDGE:RF.K_SEDGE + 6])),
             "step": {"flops_per_step": flops_step, "ms_per_step": t_step, "achieved": step_achieved,
                      "frac": step_achieved / peak, "unit": "TFLOP/s"}}
 

@@ -35,8 +35,9 @@
  *   - Images are H x W x 3 FP32, row-major, pixel (px, py) at index
  *     3*(py*W + px), py = 0 at the top.
  *   - The phases of each call (geometry, forward, interior, primary edges,
- *     shadow edges, adjoint, loss) are marked as NVTX ranges named
- *     "facert <phase>" around their host-side enqueue.
+ *     shadow-edge search, shadow-edge contributions, adjoint, loss) are
+ *     marked as NVTX ranges named "facert <phase>" around their host-side
+ *     enqueue.
  */
 #ifndef FACERT_H
 #define FACERT_H
@@ -259,20 +260,22 @@ int fr_sync(fr_ctx* ctx);
 int fr_set_limits(fr_ctx* ctx, int32_t max_steps, int32_t wait_limit);
 
 /* Work counts of the last fr_render / fr_render_backward call (or batch
- * step), read back after a stream synchronisation.  out[20]: five counts
+ * step), read back after a stream synchronisation.  out[24]: six counts
  * (BVH nodes visited by rays, triangle tests, nodes of the 4-wide edge
- * hierarchy visited -- once per warp, the search being warp-wide --, edge
- * tests per lane,
- * clip tests of edges that passed the silhouette test) for each of the
+ * hierarchy visited -- once per warp, the search being warp-wide --, exact
+ * silhouette tests of (shading point, edge) pairs, clip tests of pairs that
+ * passed the silhouette and adjacency tests, leaf edges classified against
+ * the box of a warp's shading points -- once per warp) for each of the
  * forward, interior, primary-edge and shadow-edge kernels, in that order.
  * Collected only when enabled with fr_set_counters(ctx, 1). */
 int fr_set_counters(fr_ctx* ctx, int32_t enable);
 int fr_get_counters(fr_ctx* ctx, uint64_t* out);
 
 /* Per-phase device time (CUDA events on the context stream) of the most
- * recent call containing each phase, in ms: out[7] = geometry (morphable
+ * recent call containing each phase, in ms: out[8] = geometry (morphable
  * model, normals, refits, silhouettes), forward render, interior adjoint,
- * primary edges, shadow edges, normal/geometry adjoint, loss.  Events are
+ * primary edges, shadow-edge search and pick, normal/geometry adjoint, loss,
+ * shadow-edge contributions.  Events are
  * recorded only while enabled with fr_set_timing(ctx, 1); fr_get_timings
  * synchronises the stream.  A phase not run since enabling reads 0. */
 int fr_set_timing(fr_ctx* ctx, int32_t enable);

@@ -21,6 +21,7 @@ import numpy as np
 import torch
 
 from . import facert
+from . import roofline as RF
 from . import synthetic as S
 
 
@@ -60,9 +61,10 @@ def run(n_scenes=4, device=0):
             "image_max_rel_diff": float((img1 - img2).abs().max() / img1.abs().max()),
             "forward_ray_nodes_per_sample": {"refit": float(f1[0] / n), "rebuilt": float(f2[0] / n)},
             "forward_tri_tests_per_sample": {"refit": float(f1[1] / n), "rebuilt": float(f2[1] / n)},
-            "shadow_edge_hierarchy_node_visits": {"refit": int(b1[17]), "rebuilt": int(b2[17])},
-            "shadow_edge_lane_edge_tests": {"refit": int(b1[18]), "rebuilt": int(b2[18])},
-            "backward_ray_nodes": {"refit": int(b1[5] + b1[10] + b1[15]), "rebuilt": int(b2[5] + b2[10] + b2[15])},
+            "shadow_edge_hierarchy_node_visits": {"refit": int(b1[RF.K_SEDGE + 2]), "rebuilt": int(b2[RF.K_SEDGE + 2])},
+            "shadow_edge_lane_edge_tests": {"refit": int(b1[RF.K_SEDGE + 3]), "rebuilt": int(b2[RF.K_SEDGE + 3])},
+            "backward_ray_nodes": {"refit": int(sum(b1[k] for k in (RF.K_INTERIOR, RF.K_PEDGE, RF.K_SEDGE))),
+                                   "rebuilt": int(sum(b2[k] for k in (RF.K_INTERIOR, RF.K_PEDGE, RF.K_SEDGE)))},
         })
         del r2
     r.sync()

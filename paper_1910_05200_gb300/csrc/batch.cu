@@ -328,42 +328,84 @@ __global__ void __launch_bounds__(256, 3) k_batch_fwd(PhaseArgs p) {
     if (sL[i] != 0.0f) atomicAdd(&g.dL[i], sL[i]);
 }
 
-FR_DEV void batch_sedge_body(const PhaseArgs& p) {
+// The shading point of one thread of the batch's shadow-edge launches: the
+// frame's blocks hold its lights one after another, one thread per tiled
+// camera sample of the frame.
+struct BatchSedgeSample {
+  int j;                // light
+  bool valid;           // the sample hit the face
+  int fh, flip, s;
+  uint32_t pix;
+  V3 d, x32;
+};
+
+FR_DEV BatchSedgeSample batch_sedge_sample(const PhaseArgs& p, int f, const RenderArgs& a, const GradBufs& gb) {
+  BatchSedgeSample q;
+  const int nb = (p.block_start[f + 1] - p.block_start[f]) / a.n_lights;   // blocks per light
+  const int local = (int)blockIdx.x - p.block_start[f];
+  q.j = local / nb;
+  const int spp = a.spp;
+  const long long tid = (long long)(local - q.j * nb) * blockDim.x + threadIdx.x;
+  const long long total = (long long)tiled_pixel_count(a.W, a.H) * spp;
+  const int2 hit = tid < total ? gb.hits[tid] : make_int2(-1, 0);
+  q.fh = hit.x;
+  q.valid = tid < total && q.fh >= 0;
+  const int ip = (int)(tid / spp);
+  q.s = (int)(tid - (long long)ip * spp);
+  q.pix = 0;
+  q.flip = 1;
+  q.d = V3{0, 0, -1};
+  q.x32 = V3{0, 0, 0};
+  if (q.valid) {
+    int px = 0, py = 0;
+    tile_pixel(ip, a.W, a.H, px, py);
+    q.d = sample_dir(a, px, py, q.s, q.pix);
+    q.flip = face_flip(a.mesh, q.fh, q.d);
+    q.x32 = hit_point(a.cam.o, q.d, __int_as_float(hit.y));
+  }
+  return q;
+}
+
+// First launch: the search and pick of every (frame, light, sample), stored
+// in p.picks at the thread's global index.
+FR_DEV void batch_sedge_pick_body(const PhaseArgs& p) {
   __shared__ __align__(16) unsigned char a_raw[sizeof(RenderArgs)];
   __shared__ __align__(16) unsigned char g_raw[sizeof(GradBufs)];
   const int f = phase_frame(p, a_raw, g_raw);
   const RenderArgs& a = *reinterpret_cast<const RenderArgs*>(a_raw);
   const GradBufs& gb = *reinterpret_cast<const GradBufs*>(g_raw);
-  const int nb = (p.block_start[f + 1] - p.block_start[f]) / a.n_lights;   // blocks per light
-  const int local = (int)blockIdx.x - p.block_start[f];
-  const int j = local / nb;
-  if (!light_on(a, j)) return;                       // uniform over the block
-  const int spp = a.spp;
-  long long tid = (long long)(local - j * nb) * blockDim.x + threadIdx.x;
-  long long total = (long long)tiled_pixel_count(a.W, a.H) * spp;
-  bool valid = tid < total;
-  int2 hit = valid ? gb.hits[tid] : make_int2(-1, 0);
-  int fh = hit.x;
-  valid = valid && fh >= 0;
-  int ip = (int)(tid / spp), s = (int)(tid - (long long)ip * spp);
-  int px = 0, py = 0;
-  uint32_t pix = 0;
-  V3 d{0, 0, -1}, x32{0, 0, 0}, wrgb{0, 0, 0};
-  int flip = 1;
-  if (valid) {
-    tile_pixel(ip, a.W, a.H, px, py);
-    d = sample_dir(a, px, py, s, pix);
-    const float* dI = gb.d_image + 3 * (size_t)pix;
-    wrgb = V3{dI[0], dI[1], dI[2]} * (1.0f / (float)spp);
-    flip = face_flip(a.mesh, fh, d);
-    x32 = hit_point(a.cam.o, d, __int_as_float(hit.y));
-  }
-  sedge_pick_and_add<true>(a, gb, j, valid, d, x32, fh, flip, pix, s, wrgb,
-                           p.counters ? p.counters + CNT_SEDGE : nullptr);
+  const int nb = (p.block_start[f + 1] - p.block_start[f]) / a.n_lights;
+  if (!light_on(a, ((int)blockIdx.x - p.block_start[f]) / nb)) return;   // uniform over the block
+  const BatchSedgeSample q = batch_sedge_sample(p, f, a, gb);
+  const Pick P = pick_light_warp(a, q.valid, q.x32, q.fh, q.j, q.pix, q.s,
+                                 p.counters ? p.counters + CNT_SEDGE : nullptr);
+  p.picks[(long long)blockIdx.x * blockDim.x + threadIdx.x] = make_int2(q.valid ? P.n : 0, P.slot);
 }
 
-__global__ void __launch_bounds__(256, 3) k_batch_sedge3(PhaseArgs p) { batch_sedge_body(p); }
-__global__ void __launch_bounds__(256, 4) k_batch_sedge4(PhaseArgs p) { batch_sedge_body(p); }
+// Second launch: the boundary contribution of each pick.
+FR_DEV void batch_sedge_add_body(const PhaseArgs& p) {
+  __shared__ __align__(16) unsigned char a_raw[sizeof(RenderArgs)];
+  __shared__ __align__(16) unsigned char g_raw[sizeof(GradBufs)];
+  const int f = phase_frame(p, a_raw, g_raw);
+  const RenderArgs& a = *reinterpret_cast<const RenderArgs*>(a_raw);
+  const GradBufs& gb = *reinterpret_cast<const GradBufs*>(g_raw);
+  const int nb = (p.block_start[f + 1] - p.block_start[f]) / a.n_lights;
+  if (!light_on(a, ((int)blockIdx.x - p.block_start[f]) / nb)) return;
+  const int2 pk = p.picks[(long long)blockIdx.x * blockDim.x + threadIdx.x];
+  if (!__any_sync(0xffffffffu, pk.x > 0)) return;          // uniform over the warp
+  const BatchSedgeSample q = batch_sedge_sample(p, f, a, gb);
+  V3 wrgb{0, 0, 0};
+  if (q.valid) {
+    const float* dI = gb.d_image + 3 * (size_t)q.pix;
+    wrgb = V3{dI[0], dI[1], dI[2]} * (1.0f / (float)a.spp);
+  }
+  sedge_contribution<true>(a, gb, q.j, pk.x, pk.y, q.d, q.x32, q.fh, q.flip, q.pix, q.s, wrgb,
+                           p.counters ? p.counters + CNT_SEDGE : nullptr, q.valid && pk.x > 0);
+}
+
+__global__ void __launch_bounds__(256, 3) k_batch_sedge3(PhaseArgs p) { batch_sedge_pick_body(p); }
+__global__ void __launch_bounds__(256, 4) k_batch_sedge4(PhaseArgs p) { batch_sedge_pick_body(p); }
+__global__ void __launch_bounds__(256, 4) k_batch_sedge_add(PhaseArgs p) { batch_sedge_add_body(p); }
 
 __global__ void __launch_bounds__(256, 4) k_batch_pedge(PhaseArgs p) {
   __shared__ __align__(16) unsigned char a_raw[sizeof(RenderArgs)];

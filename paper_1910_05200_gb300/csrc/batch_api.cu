@@ -36,7 +36,7 @@ struct fr_batch {
   DBuf<double> grad_full, loss_frames, loss, grad_s, grad_f;
   // persistent kernel
   DBuf<BatchFrame> dframes;
-  DBuf<int2> items, hits;
+  DBuf<int2> items, hits, picks;
   DBuf<int> queue, tiles_done, bs_fwd, bs_sedge, bs_pedge;
   int nb_fwd = 0, nb_sedge = 0, nb_pedge = 0;
   std::vector<long long> hit_off;      // first hit slot of each frame
@@ -171,6 +171,9 @@ int configure(fr_batch* b) {
   }
   sf[b->nF] = (int)nf; ss[b->nF] = (int)ns; sp[b->nF] = (int)np;
   b->nb_fwd = (int)nf; b->nb_sedge = (int)ns; b->nb_pedge = (int)np;
+  // one shadow-edge pick per thread of the phased shadow-edge launches
+  const size_t n_picks = 256 % b->spp == 0 ? (size_t)ns * 256 : 0;
+  if (b->picks.n != n_picks) CK(b->picks.alloc(n_picks));
   b->n_items = (int)items.size();
   CK(cudaStreamSynchronize(ctx->stream));
   CK(b->dframes.alloc(tab.size()));
@@ -232,12 +235,16 @@ int enqueue_step(fr_batch* b, float w1, float w2) {
     pa.frames = b->dframes.p; pa.n_frames = nF; pa.iter = b->iter_dev.p; pa.err = ctx->err_flag.p;
     pa.counters = counters;
     pa.max_steps = ctx->max_steps;
+    pa.picks = nullptr;
     pa.block_start = b->bs_fwd.p;
     k_batch_fwd<<<b->nb_fwd, 256, 0, s>>>(pa);
     CKL();
     pa.block_start = b->bs_sedge.p;
+    pa.picks = b->picks.p;
     if (b->cfg.min_blocks == 3) k_batch_sedge3<<<b->nb_sedge, 256, 0, s>>>(pa);
     else k_batch_sedge4<<<b->nb_sedge, 256, 0, s>>>(pa);
+    CKL();
+    k_batch_sedge_add<<<b->nb_sedge, 256, 0, s>>>(pa);
     CKL();
     pa.block_start = b->bs_pedge.p;
     k_batch_pedge<<<b->nb_pedge, 256, 0, s>>>(pa);
@@ -422,7 +429,7 @@ void fr_batch_destroy(fr_batch* b) {
     p->free_();
   for (DBuf<double>* p : {&b->grad_full, &b->loss_frames, &b->loss, &b->grad_s, &b->grad_f}) p->free_();
   b->e4boxes.free_();
-  b->masks.free_(); b->dframes.free_(); b->items.free_(); b->hits.free_(); b->iter_dev.free_();
+  b->masks.free_(); b->dframes.free_(); b->items.free_(); b->hits.free_(); b->picks.free_(); b->iter_dev.free_();
   b->bs_fwd.free_(); b->bs_sedge.free_(); b->bs_pedge.free_();
   delete b;
 }

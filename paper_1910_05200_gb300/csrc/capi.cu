@@ -535,9 +535,15 @@ int edges_and_adjoint(fr_ctx* ctx, const float* theta, const fr_render_opts* opt
   if (terms & TERM_SEDGE) {
     dim3 grid(grid_for(tiled, 256), ctx->cfg.n_lights);
     ctx->mark(PH_SEDGE, 0);
-    k_bwd_sedge<<<grid, 256, 0, s>>>(a, gb);
+    const size_t n_picks = (size_t)tiled * ctx->cfg.n_lights;
+    if (ctx->picks.n < n_picks) CK(ctx->picks.alloc(n_picks));
+    k_bwd_sedge<<<grid, 256, 0, s>>>(a, gb, ctx->picks.p);
     CKL();
     ctx->mark(PH_SEDGE, 1);
+    ctx->mark(PH_SEDGE_ADD, 0);
+    k_bwd_sedge_add<<<grid, 256, 0, s>>>(a, gb, ctx->picks.p);
+    CKL();
+    ctx->mark(PH_SEDGE_ADD, 1);
   }
   ctx->mark(PH_ADJOINT, 0);
   int rc = adjoint(ctx, theta, main_view(ctx), grad, true);
@@ -620,7 +626,7 @@ void fr_destroy(fr_ctx* ctx) {
   ctx->e4codes.free_(); ctx->e4src.free_(); ctx->e4boxes.free_(); ctx->e4cones.free_();
   ctx->sil.free_(); ctx->n_sil.free_(); ctx->block_count.free_(); ctx->err_flag.free_(); ctx->counters.free_();
   ctx->dX.free_(); ctx->dN.free_(); ctx->dA.free_(); ctx->gs.free_(); ctx->dXm.free_(); ctx->dC.free_(); ctx->dL.free_();
-  ctx->hits.free_(); ctx->aov_scratch.free_(); ctx->dimg.free_();
+  ctx->hits.free_(); ctx->picks.free_(); ctx->aov_scratch.free_(); ctx->dimg.free_();
   ctx->mlp_w.free_(); ctx->mlp_m.free_(); ctx->mlp_v.free_(); ctx->mlp_g.free_(); ctx->mlp_scratch.free_();
   if (ctx->events_made)
     for (int i = 0; i < NPHASE; ++i) { cudaEventDestroy(ctx->ev[i][0]); cudaEventDestroy(ctx->ev[i][1]); }

@@ -27,11 +27,13 @@ enum { TAG_CAMERA = 0, TAG_LIGHT = 1, TAG_PEDGE = 2, TAG_PEDGE_LIGHT = 3, TAG_SE
        TAG_SEDGE_PICK = 5, TAG_PEDGE_OFFSET = 6 };
 enum { TERM_INTERIOR = 1, TERM_PEDGE = 2, TERM_SEDGE = 4 };
 enum { ERR_STACK = 1, ERR_STEPS = 2, ERR_WAIT = 4 };   // device error flags
-// Work counters (fr_set_counters): 5 per render kernel, in the order forward,
+// Work counters (fr_set_counters): 6 per render kernel, in the order forward,
 // interior adjoint, primary edges, shadow edges; within a kernel: BVH node
 // visits of rays, triangle tests, edge-hierarchy node visits (once per warp),
-// edge tests (per lane), clip tests (edges that passed the silhouette test).
-enum { CNT_PER_KERNEL = 5, CNT_FWD = 0, CNT_INTERIOR = 5, CNT_PEDGE = 10, CNT_SEDGE = 15, CNT_TOTAL = 20 };
+// exact silhouette tests of (shading point, edge) pairs, clip tests (pairs
+// that passed the silhouette and adjacency tests), and leaf edges classified
+// against the box of a warp's shading points (once per warp).
+enum { CNT_PER_KERNEL = 6, CNT_FWD = 0, CNT_INTERIOR = 6, CNT_PEDGE = 12, CNT_SEDGE = 18, CNT_TOTAL = 24 };
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).

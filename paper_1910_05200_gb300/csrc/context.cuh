@@ -41,9 +41,9 @@ using fr::DevBVH;
 using fr::Light;
 using fr::CS;
 
-constexpr int NCOUNT = fr::CNT_TOTAL;   // work counters: 5 per render kernel
-constexpr int NPHASE = 7;    // timed phases
-enum { PH_GEOMETRY = 0, PH_FORWARD, PH_INTERIOR, PH_PEDGE, PH_SEDGE, PH_ADJOINT, PH_LOSS };
+constexpr int NCOUNT = fr::CNT_TOTAL;   // work counters: 6 per render kernel
+constexpr int NPHASE = 8;    // timed phases
+enum { PH_GEOMETRY = 0, PH_FORWARD, PH_INTERIOR, PH_PEDGE, PH_SEDGE, PH_ADJOINT, PH_LOSS, PH_SEDGE_ADD };
 
 struct fr_ctx {
   int device = 0;
@@ -89,8 +89,8 @@ struct fr_ctx {
   bool nvtx_open[NPHASE] = {false};
   void mark(int phase, int end) {
     static const char* const names[NPHASE] = {"facert geometry", "facert forward", "facert interior",
-                                              "facert primary edges", "facert shadow edges", "facert adjoint",
-                                              "facert loss"};
+                                              "facert primary edges", "facert shadow-edge search", "facert adjoint",
+                                              "facert loss", "facert shadow-edge contributions"};
     if (nvtx_open[phase]) { nvtxRangePop(); nvtx_open[phase] = false; }
     if (!end) { nvtxRangePushA(names[phase]); nvtx_open[phase] = true; }
     if (!timing_on) return;
@@ -101,6 +101,7 @@ struct fr_ctx {
   DBuf<float4> dX, dN, dA, gs;
   DBuf<float> dXm, dC, dL;
   DBuf<int2> hits;        // primary hit per tiled sample (backward)
+  DBuf<int2> picks;       // shadow-edge pick per (light, tiled sample): (candidates, leaf slot)
   DBuf<float> aov_scratch;  // mean luminance per pixel (feature output, atomic path)
   DBuf<float> dimg;       // dE_data/d image of fr_step when the caller passes none
   // denoiser: FP32 master weights, Adam moments, gradients, training scratch

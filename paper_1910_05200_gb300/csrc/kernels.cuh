@@ -88,7 +88,7 @@ struct RenderArgs {
   const int4* edges_canon;
   int* err;
   float* aov_scratch;     // [W*H] mean luminance for the atomic AOV path
-  unsigned long long* counters;  // [16] or null: 4 per kernel (fwd, interior, pedge, sedge)
+  unsigned long long* counters;  // [CNT_TOTAL] or null: CNT_PER_KERNEL per kernel (fwd, interior, pedge, sedge)
 };
 
 struct GradBufs {
@@ -132,7 +132,7 @@ struct BatchArgs {
   int* tiles_done;        // [n_frames], zeroed before the launch
   const uint32_t* iter;
   int* err;
-  unsigned long long* counters;  // [16] or null, same layout as the single-image kernels
+  unsigned long long* counters;  // [CNT_TOTAL] or null, same layout as the single-image kernels
   int max_steps;          // traversal step cap of every frame
   int wait_limit;         // tries of a primary-edge item waiting for its frame's tiles
 };
@@ -147,8 +147,9 @@ struct PhaseArgs {
   int n_frames;
   const uint32_t* iter;
   int* err;
-  unsigned long long* counters;  // [16] or null
+  unsigned long long* counters;  // [CNT_TOTAL] or null
   int max_steps;            // traversal step cap of every frame
+  int2* picks;              // shadow-edge picks, one per thread of the shadow-edge launches
 };
 
 // Per-warp slice of k_batch_step's dynamic shared memory: the arguments of
@@ -169,9 +170,11 @@ FR_HOST_DEV inline size_t batch_smem_bytes(int block) {
 // over each frame's samples in 8x8-tile order; writes gb.hits for the
 // shadow-edge phase
 __global__ void k_batch_fwd(PhaseArgs p);
-// shadow edges: per frame n_lights x (that frame's forward blocks), light-major
+// shadow edges: per frame n_lights x (that frame's forward blocks), light-major;
+// the search and pick (3 or 4 resident blocks per SM), then the contributions
 __global__ void k_batch_sedge3(PhaseArgs p);
 __global__ void k_batch_sedge4(PhaseArgs p);
+__global__ void k_batch_sedge_add(PhaseArgs p);
 // primary edges: blocks of 256 over each frame's W*H*spp edge samples
 __global__ void k_batch_pedge(PhaseArgs p);
 __global__ void k_batch_step2(BatchArgs b);
@@ -226,7 +229,11 @@ struct StepBufs {
 };
 __global__ void k_step_fwd(RenderArgs a, GradBufs gb, StepBufs sb);
 __global__ void k_bwd_pedge(RenderArgs a, GradBufs gb);
-__global__ void k_bwd_sedge(RenderArgs a, GradBufs gb);
+// Shadow edges: the search and pick per (light, sample), stored in picks
+// [n_lights * tiled samples] as (candidates, leaf slot); then the boundary
+// contributions of the picks.
+__global__ void k_bwd_sedge(RenderArgs a, GradBufs gb, int2* __restrict__ picks);
+__global__ void k_bwd_sedge_add(RenderArgs a, GradBufs gb, const int2* __restrict__ picks);
 
 __global__ void k_loss_data(int n_pix, const float* __restrict__ image, const float* __restrict__ target,
                             const uint8_t* __restrict__ mask, double* __restrict__ loss, float* __restrict__ d_image);

@@ -153,9 +153,10 @@ __global__ void __launch_bounds__(256, 3) k_bwd_interior(RenderArgs a, GradBufs 
 // 2 mask (image - target) is known in the block that rendered it, and each
 // sample's interior adjoint starts from the same primary hit and the shadow
 // decisions of the lights that are on (only lights that are off trace shadow
-// rays again).  For spp dividing 32 the image is bit-identical to
-// k_render_fwd's and the adjoint to k_loss_data's; the hits written for the
-// edge passes equal k_bwd_interior's.
+// rays again).  For spp dividing 32 the image equals k_render_fwd's and the
+// adjoint k_loss_data's up to FP32 rounding (the compiler contracts the two
+// kernels' shading into FMAs differently); the hits written for the edge
+// passes are the same decisions as k_bwd_interior's.
 __global__ void __launch_bounds__(256, 5) k_step_fwd(RenderArgs a, GradBufs gb, StepBufs sb) {
   __shared__ float sC[CS * CS];
   __shared__ float sL[3 * MAX_LIGHTS];
@@ -232,38 +233,78 @@ __global__ void __launch_bounds__(256, 4) k_bwd_pedge(RenderArgs a, GradBufs gb)
   pedge_sample<true>(a, gb, tid, a.counters ? a.counters + CNT_PEDGE : nullptr, tid < (long long)a.W * a.H * a.spp);
 }
 
-// One thread per (light, camera sample), light-major: a warp serves one light
-// and neighbouring samples, so traversals stay coherent, and warps of lights
-// that are off retire at once.  The primary hit comes from the interior pass
-// of the same backward call (gb.hits).
-__global__ void __launch_bounds__(256, 4) k_bwd_sedge(RenderArgs a, GradBufs gb) {
+// The shading point of one thread of the shadow-edge kernels: one thread per
+// (light, tiled camera sample), light-major (blockIdx.y is the light).  The
+// primary hit comes from the interior pass of the same backward call
+// (gb.hits).
+struct SedgeSample {
+  long long tid, total;
+  bool valid;           // the sample hit the face
+  int f, flip, s;
+  uint32_t pix;
+  V3 d, x32;
+};
+
+FR_DEV SedgeSample sedge_sample(const RenderArgs& a, const GradBufs& gb) {
+  SedgeSample q;
+  const int spp = a.spp;
+  q.tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  q.total = (long long)tiled_pixel_count(a.W, a.H) * spp;
+  const int2 hit = q.tid < q.total ? gb.hits[q.tid] : make_int2(-1, 0);
+  q.f = hit.x;
+  q.valid = q.tid < q.total && q.f >= 0;
+  const int ip = (int)(q.tid / spp);
+  q.s = (int)(q.tid - (long long)ip * spp);
+  q.pix = 0;
+  q.flip = 1;
+  q.d = V3{0, 0, -1};
+  q.x32 = V3{0, 0, 0};
+  if (q.valid) {
+    int px = 0, py = 0;
+    tile_pixel(ip, a.W, a.H, px, py);
+    q.d = sample_dir(a, px, py, q.s, q.pix);
+    q.flip = face_flip(a.mesh, q.f, q.d);
+    q.x32 = hit_point(a.cam.o, q.d, __int_as_float(hit.y));
+  }
+  return q;
+}
+
+// Shadow-edge term, first kernel: the candidate search and pick of every
+// (light, camera sample) (pick_light_warp), stored in picks[j * total +
+// sample] as (number of candidates, leaf slot of the pick).  A warp serves
+// one light and neighbouring samples, so the search stays coherent, and
+// warps of lights that are off retire at once.  Every lane reaches the
+// warp-cooperative search; lanes without a shading point take part with
+// valid = false.
+__global__ void __launch_bounds__(256, 4) k_bwd_sedge(RenderArgs a, GradBufs gb, int2* __restrict__ picks) {
   const int j = blockIdx.y;
   if (!light_on(a, j)) return;                 // uniform over the block
-  const int spp = a.spp;
-  long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  long long total = (long long)tiled_pixel_count(a.W, a.H) * spp;
-  // every lane reaches the warp-cooperative pick; lanes without a shading point
-  // take part with valid = false
-  bool valid = tid < total;
-  int2 hit = valid ? gb.hits[tid] : make_int2(-1, 0);
-  int f = hit.x;
-  valid = valid && f >= 0;
-  int ip = (int)(tid / spp), s = (int)(tid - (long long)ip * spp);
-  int px = 0, py = 0;
-  uint32_t pix = 0;
-  V3 d{0, 0, -1}, x32{0, 0, 0}, wrgb{0, 0, 0};
-  int flip = 1;
-  if (valid) {
-    tile_pixel(ip, a.W, a.H, px, py);
-    d = sample_dir(a, px, py, s, pix);
-    const float* dI = gb.d_image + 3 * (size_t)pix;
-    wrgb = V3{dI[0], dI[1], dI[2]} * (1.0f / (float)spp);
-    float t = __int_as_float(hit.y);
-    flip = face_flip(a.mesh, f, d);
-    x32 = hit_point(a.cam.o, d, t);
+  const SedgeSample q = sedge_sample(a, gb);
+  const Pick P = pick_light_warp(a, q.valid, q.x32, q.f, j, q.pix, q.s,
+                                 a.counters ? a.counters + CNT_SEDGE : nullptr);
+  if (q.tid < q.total) picks[j * q.total + q.tid] = make_int2(q.valid ? P.n : 0, P.slot);
+}
+
+// Shadow-edge term, second kernel: the boundary contribution of each pick
+// (sedge_contribution), in the same thread layout; warps without a pick
+// retire at once.  Apart from the search, each kernel has the registers to
+// itself: fused into one kernel the two spilled and ran 8 % slower.
+__global__ void __launch_bounds__(256, 4) k_bwd_sedge_add(RenderArgs a, GradBufs gb,
+                                                          const int2* __restrict__ picks) {
+  const int j = blockIdx.y;
+  if (!light_on(a, j)) return;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)tiled_pixel_count(a.W, a.H) * a.spp;
+  const int2 p = tid < total ? picks[j * total + tid] : make_int2(0, -1);
+  if (!__any_sync(0xffffffffu, p.x > 0)) return;          // uniform over the warp
+  const SedgeSample q = sedge_sample(a, gb);
+  V3 wrgb{0, 0, 0};
+  if (q.valid) {
+    const float* dI = gb.d_image + 3 * (size_t)q.pix;
+    wrgb = V3{dI[0], dI[1], dI[2]} * (1.0f / (float)a.spp);
   }
-  sedge_pick_and_add<true>(a, gb, j, valid, d, x32, f, flip, pix, s, wrgb,
-                           a.counters ? a.counters + CNT_SEDGE : nullptr);
+  sedge_contribution<true>(a, gb, j, p.x, p.y, q.d, q.x32, q.f, q.flip, q.pix, q.s, wrgb,
+                           a.counters ? a.counters + CNT_SEDGE : nullptr, q.valid && p.x > 0);
 }
 
 }  // namespace fr

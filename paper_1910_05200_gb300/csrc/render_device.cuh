@@ -478,30 +478,11 @@ FR_DEV V3 edge_proj(V3 A, V3 B, V3 x, const Light& L, float D, float tau) {
   return V3{__fadd_rn(x.x, __fmul_rn(f, q.x)), __fadd_rn(x.y, __fmul_rn(f, q.y)), __fadd_rn(x.z, __fmul_rn(f, q.z))};
 }
 
-FR_DEV bool silhouette_from(const Mesh& m, int4 E, V3 x) {
-  float4 n0 = m.ng[E.z];
-  float s0 = dot3r(v3(n0), sub3r(x, v3(m.X[m.tris[E.z].x])));
-  if (E.w < 0) return s0 != 0.0f;
-  float4 n1 = m.ng[E.w];
-  float s1 = dot3r(v3(n1), sub3r(x, v3(m.X[m.tris[E.w].x])));
-  return (s0 > 0.0f && s1 < 0.0f) || (s0 < 0.0f && s1 > 0.0f);
-}
-
 // Packed edge record (6 float4 per edge, edge-BVH leaf order), written per
 // render by k_pack_edges:
 //   [0] a.xyz, canonical edge id   [1] b.xyz, f0   [2] n0.xyz, f1
 //   [3] V0(f0).xyz                 [4] n1.xyz      [5] V0(f1).xyz
 // n = decision-form face normal, V0 = first vertex of the face.
-
-// Silhouette seen from x (decision form), from a packed record.
-FR_DEV bool packed_silhouette(const float4* R, V3 x, int f1) {
-  float4 n0 = R[2], p0 = R[3];
-  float s0 = dot3r(v3(n0), sub3r(x, v3(p0)));
-  if (f1 < 0) return s0 != 0.0f;
-  float4 n1 = R[4], p1 = R[5];
-  float s1 = dot3r(v3(n1), sub3r(x, v3(p1)));
-  return (s0 > 0.0f && s1 < 0.0f) || (s0 < 0.0f && s1 > 0.0f);
-}
 
 // Candidate search for one (shading point, light): traverse the edge BVH,
 // keeping a child when (1) its box reaches the pyramid from x through the
@@ -517,22 +498,90 @@ struct Pick {
   int slot;     // its leaf slot in the packed array
 };
 
+// Silhouette seen from x (decision form) with the edge's face planes in
+// registers and without branches.
+FR_DEV bool silhouette_regs(V3 n0, V3 p0, V3 n1, V3 p1, bool boundary, V3 x) {
+  const float s0 = dot3r(n0, sub3r(x, p0));
+  const float s1 = dot3r(n1, sub3r(x, p1));
+  const bool two = (s0 > 0.0f && s1 < 0.0f) || (s0 < 0.0f && s1 > 0.0f);
+  return boundary ? s0 != 0.0f : two;
+}
+
+// Sign of the decision form dot3r(n, sub3r(x, p)) over every x of the box
+// [lo, hi]: +1 or -1 when it is proven to have that sign for all of them,
+// 0 otherwise.  With u = 2^-24, sub3r and dot3r put at most four roundings
+// on each term, so the computed value differs from the exact n.(x - p) by at
+// most gamma_4 T, gamma_4 = 4u / (1 - 4u) < 2.4e-7 and
+// T = sum_i |n_i| max(|lo_i - p_i|, |hi_i - p_i|).  The exact extremes over
+// the box lie at the corners selected by the signs of n, and their FP32
+// evaluation here carries the same bound; the margin 1e-6 T (more than
+// 2 gamma_4 T, with room for the rounding of T itself), plus 1e-30 for
+// products that flush to zero, proves the sign.  NaN or infinite data give 0.
+FR_DEV int plane_sign_over_box(V3 n, V3 p, V3 lo, V3 hi) {
+  const V3 cmin{n.x > 0.0f ? lo.x : hi.x, n.y > 0.0f ? lo.y : hi.y, n.z > 0.0f ? lo.z : hi.z};
+  const V3 cmax{n.x > 0.0f ? hi.x : lo.x, n.y > 0.0f ? hi.y : lo.y, n.z > 0.0f ? hi.z : lo.z};
+  const float smin = dot(n, cmin - p), smax = dot(n, cmax - p);
+  const float T = fabsf(n.x) * fmaxf(fabsf(lo.x - p.x), fabsf(hi.x - p.x)) +
+                  fabsf(n.y) * fmaxf(fabsf(lo.y - p.y), fabsf(hi.y - p.y)) +
+                  fabsf(n.z) * fmaxf(fabsf(lo.z - p.z), fabsf(hi.z - p.z));
+  const float m = 1e-6f * T + 1e-30f;
+  return smin > m ? 1 : (smax < -m ? -1 : 0);
+}
+
+// One (shading point, edge) pair whose silhouette test has passed: the
+// adjacency test (an edge of the hit face itself is no occluder), the clip
+// against the light's pyramid and, for a candidate, its pick key.
+FR_DEV void sedge_consider(const RenderArgs& a, const Light& L, float hs, int j, uint32_t pix, int s, V3 x,
+                           int hitf, int slot, Pick& P, uint32_t& bestkey, unsigned long long& nclip) {
+  const float4* R = a.ebvh.pack + 6 * slot;
+  const float4 r1 = R[1];
+  const int f0 = __float_as_int(r1.w), f1 = __float_as_int(R[2].w);
+  if (f0 == hitf || f1 == hitf) return;
+  const float4 r0 = R[0];
+  float t0, t1;
+  ++nclip;
+  if (!shadow_clip(v3(r0), v3(r1), x, L, hs, a.kappa, t0, t1)) return;
+  const int id = __float_as_int(r0.w);
+  const uint32_t key = philox(a.seed, a.iter, pix, (uint32_t)s, (uint32_t)(TAG_SEDGE_PICK << 8 | j), (uint32_t)id).x;
+  ++P.n;
+  if (P.id < 0 || key < bestkey || (key == bestkey && id < P.id)) {
+    bestkey = key; P.id = id; P.slot = slot;
+  }
+}
+
+// Warps per block that the search's shared scratch serves: every kernel that
+// calls it runs blocks of at most 256 threads.
+constexpr int SEDGE_WARPS = 8;
+
 // The search runs warp-cooperatively: the 32 lanes of a warp share one
 // light and (light-major order) neighbouring shading points, so the warp
 // walks the edge BVH once with tests that hold for every point of the
 // group's bounding sphere (centre rc, radius rr): the pyramid from any x in
 // the sphere lies in the pyramid from rc dilated by rr, and a face seen from
 // any x in the sphere is judged with the node's sphere grown by rr.  Control
-// flow is uniform across the warp; each lane with a valid shading point runs
-// the exact leaf test (decision form) on its own x.  Lanes without one
+// flow is uniform across the warp.  Lanes without a shading point
 // (valid = false) still take part in the walk.
+//
+// The edges of the leaves that a node keeps are spread over the lanes, one
+// edge per lane.  An edge whose two faces are proven to face the same way
+// from every point of the box of the group's shading points
+// (plane_sign_over_box) is no silhouette from any of them and is dropped;
+// the others are queued.  Every 32 queued edges (and at the end) the warp
+// runs the exact decision-form silhouette test of each queued edge, held by
+// one lane, against each valid lane's shading point in turn, and one ballot
+// per shading point hands that lane the mask of its passing edges.  The
+// decisions are those of the per-pair test, so the candidate set, its size
+// and the pick are unchanged; only the work to find them is smaller.
 FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int j, uint32_t pix, int s,
                             unsigned long long* cnt) {
+  __shared__ int sQ[SEDGE_WARPS][64];
   const Light& L = a.lights[j];
   const float hs = __fmul_rn(0.5f, a.side);
   Pick P;
   P.n = 0; P.id = -1; P.slot = -1;
   uint32_t bestkey = 0xffffffffu;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (w >= SEDGE_WARPS) { if (lane == 0) atomicOr(a.err, ERR_STACK); return P; }   // uniform over the warp
   // group bounding box -> sphere
   V3 lo_x = valid ? x : V3{3e38f, 3e38f, 3e38f};
   V3 hi_x = valid ? x : V3{-3e38f, -3e38f, -3e38f};
@@ -548,6 +597,7 @@ FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int
   if (!(lo_x.x <= hi_x.x) || a.ebvh.bvh.n_nodes == 0) return P;   // no valid lane
   const V3 rc = (lo_x + hi_x) * 0.5f;
   const float rr = len((hi_x - lo_x) * 0.5f) * 1.0001f + 1e-6f;
+  const unsigned vm = __ballot_sync(0xffffffffu, valid);
   // The search walks the 4-wide edge hierarchy; its node test is spread over
   // lanes 0..23: lane 6c + t holds test t of child c -- t = 0 the normal
   // cone, t = 1 the front plane, t = 2..5 side plane t - 2 of the pyramid
@@ -555,7 +605,6 @@ FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int
   // Every test but the cone has the form dot(n, p - rc) >= -m with p the
   // box corner furthest along n.  A child is kept when its six lanes pass
   // (one ballot).
-  const int lane = threadIdx.x & 31;
   const int tc = lane < 24 ? lane / 6 : 0, tt = lane < 24 ? lane - 6 * tc : 6;
   V3 pn{0, 0, 0};
   float pm = 0.0f;
@@ -574,11 +623,12 @@ FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int
     pn = n;
     pm = (1e-4f + rr) * len(n);     // margin + dilation by the group radius
   }
-  int node = 0, steps = 0;
+  unsigned long long nvis = 0, ntest = 0, nclass = 0, nclip = 0;
+  int node = 0, steps = 0, qn = 0;
+  bool failed = false;
   WStack wst{0, 0, 0};
-  unsigned long long nvis = 0, nedge = 0, nclip = 0;
   while (true) {
-    if (++steps > a.mesh.max_steps) { atomicOr(a.err, ERR_STEPS); break; }
+    if (++steps > a.mesh.max_steps) { atomicOr(a.err, ERR_STEPS); failed = true; break; }
     ++nvis;
     const int4 ch = a.ebvh.codes4[node];
     bool pass = true;
@@ -616,47 +666,88 @@ FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int
       }
     }
     const unsigned m = __ballot_sync(0xffffffffu, pass);
-    int next = -1;
+    int next = -1, nl = 0, myslot = -1;
 #pragma unroll 1
     for (int k = 0; k < 4; ++k) {
       if (((m >> (6 * k)) & 0x3fu) != 0x3fu) continue;
       const int c2 = k == 0 ? ch.x : (k == 1 ? ch.y : (k == 2 ? ch.z : ch.w));
       if (leaf_child(c2)) {
-        // the exact decision-form tests, each lane on its own shading point
-        const int first = leaf_first(c2), n = leaf_count(c2);
-        for (int i = 0; i < n; ++i) {
-          if (!valid) continue;
-          const float4* R = a.ebvh.pack + 6 * (first + i);
-          float4 r1 = R[1], r2 = R[2];
-          int f0 = __float_as_int(r1.w), f1 = __float_as_int(r2.w);
-          ++nedge;
-          if (f0 == hitf || f1 == hitf) continue;
-          if (!packed_silhouette(R, x, f1)) continue;
-          float4 r0 = R[0];
-          float t0, t1;
-          ++nclip;
-          if (!shadow_clip(v3(r0), v3(r1), x, L, hs, a.kappa, t0, t1)) continue;
-          int id = __float_as_int(r0.w);
-          uint32_t key = philox(a.seed, a.iter, pix, (uint32_t)s, (uint32_t)(TAG_SEDGE_PICK << 8 | j), (uint32_t)id).x;
-          ++P.n;
-          if (P.id < 0 || key < bestkey || (key == bestkey && id < P.id)) {
-            bestkey = key; P.id = id; P.slot = first + i;
-          }
-        }
+        // leaves hold at most 8 edges, so a node's leaf edges fit the warp
+        const int n = leaf_count(c2);
+        if (lane >= nl && lane < nl + n) myslot = leaf_first(c2) + (lane - nl);
+        nl += n;
       } else if (next < 0) {
         next = c2;
       } else {
-        if (wst.sp >= WSTACK) { atomicOr(a.err, ERR_STACK); goto done; }
+        if (wst.sp >= WSTACK) { atomicOr(a.err, ERR_STACK); failed = true; break; }
         wpush(wst, c2, lane);
       }
     }
-    if (next >= 0) { node = next; continue; }
-    if (wst.sp == 0) break;
-    node = wpop(wst);
+    if (failed) break;
+    if (nl > 0) {
+      if (lane == 0) nclass += nl;
+      bool keep = false;     // a silhouette from some point of the box is possible
+      if (myslot >= 0) {
+        const float4* R = a.ebvh.pack + 6 * myslot;
+        const float4 r2 = R[2], r3 = R[3];
+        keep = true;
+        if (__float_as_int(r2.w) >= 0) {
+          const float4 r4 = R[4], r5 = R[5];
+          const int c0 = plane_sign_over_box(v3(r2), v3(r3), lo_x, hi_x);
+          const int c1 = plane_sign_over_box(v3(r4), v3(r5), lo_x, hi_x);
+          keep = c0 == 0 || c0 != c1;
+        }
+      }
+      const unsigned mk = __ballot_sync(0xffffffffu, keep);
+      if (keep) sQ[w][qn + __popc(mk & ((1u << lane) - 1u))] = myslot;
+      qn += __popc(mk);
+      __syncwarp();
+    }
+    bool finished = false;
+    if (next >= 0) node = next;
+    else if (wst.sp == 0) finished = true;
+    else node = wpop(wst);
+    // Every 32 queued edges, and what is left at the end: the exact test of
+    // each queued edge, held by one lane, against each valid lane's shading
+    // point in turn; one ballot per shading point hands that lane the mask
+    // of its passing edges, which it then takes through sedge_consider.
+#pragma unroll 1
+    while (qn >= 32 || (finished && qn > 0)) {
+      const int nq = qn < 32 ? qn : 32;
+      const bool has = lane < nq;
+      const int slot = has ? sQ[w][lane] : 0;
+      const float4* R = a.ebvh.pack + 6 * slot;
+      const float4 r2 = R[2], r3 = R[3], r4 = R[4], r5 = R[5];
+      const bool bnd = __float_as_int(r2.w) < 0;
+      unsigned mine = 0;
+#pragma unroll 1
+      for (unsigned r = vm; r != 0; r &= r - 1) {
+        const int k = __ffs(r) - 1;
+        const V3 xk{__shfl_sync(0xffffffffu, x.x, k), __shfl_sync(0xffffffffu, x.y, k),
+                    __shfl_sync(0xffffffffu, x.z, k)};
+        const bool sil = has && silhouette_regs(v3(r2), v3(r3), v3(r4), v3(r5), bnd, xk);
+        const unsigned b = __ballot_sync(0xffffffffu, sil);
+        if (lane == k) mine = b;
+      }
+      if (lane == 0) ntest += (unsigned long long)nq * __popc(vm);
+#pragma unroll 1
+      while (mine != 0) {
+        const int e = __ffs(mine) - 1;
+        mine &= mine - 1;
+        sedge_consider(a, L, hs, j, pix, s, x, hitf, sQ[w][e], P, bestkey, nclip);
+      }
+      __syncwarp();
+      const int rest = qn - nq;
+      const int v = lane < rest ? sQ[w][32 + lane] : 0;
+      __syncwarp();
+      if (lane < rest) sQ[w][lane] = v;
+      __syncwarp();
+      qn = rest;
+    }
+    if (finished) break;
   }
-done:
-  if (cnt && (threadIdx.x & 31) == 0) { atomicAdd(cnt + 2, nvis); }
-  if (cnt) { atomicAdd(cnt + 3, nedge); atomicAdd(cnt + 4, nclip); }
+  if (cnt && lane == 0) { atomicAdd(cnt + 2, nvis); atomicAdd(cnt + 5, nclass); }
+  if (cnt) { atomicAdd(cnt + 3, ntest); atomicAdd(cnt + 4, nclip); }
   return P;
 }
 

@@ -344,7 +344,8 @@ class Renderer:
     def launches(self) -> int:
         return int(self.lib.fr_launch_count(self.ctx))
 
-    PHASES = ("geometry", "forward", "interior", "primary_edges", "shadow_edges", "adjoint", "loss")
+    PHASES = ("geometry", "forward", "interior", "primary_edges", "shadow_edge_search", "adjoint", "loss",
+              "shadow_edge_contributions")
 
     def set_timing(self, on=True):
         self._check(self.lib.fr_set_timing(self.ctx, 1 if on else 0), "fr_set_timing")
@@ -355,7 +356,7 @@ class Renderer:
         return dict(zip(self.PHASES, out.tolist()))
 
     def counters(self):
-        out = np.zeros(20, np.uint64)
+        out = np.zeros(24, np.uint64)
         self._check(self.lib.fr_get_counters(self.ctx, _hptr(out)), "fr_get_counters")
         return out
 

@@ -13,23 +13,29 @@ from __future__ import annotations
 NODE_VISIT = 40        # two child slab tests: 6 sub, 6 mul, 10 min/max, 2 cmp each
 TRI_TEST = 40          # watertight test: 9 sub, 6 mul + 6 sub (shear), 9 edge-fn ops, 3+6 for T, div
 EDGE_NODE_VISIT = 400  # four children (4-wide edge hierarchy): box vs 5 pyramid planes (~45) + normal cone (~55) each
-EDGE_TEST = 20         # adjacency check + 2 silhouette plane tests (3 sub, 3 mul, 2 add each)
-CLIP_TEST = 90         # clip of both endpoints against the 5 planes of the light pyramid
+EDGE_TEST = 20         # exact silhouette test of a pair: 2 plane tests (3 sub, 3 mul, 2 add each) + signs
+CLIP_TEST = 90         # adjacency check, clip of both endpoints against the 5 planes of the light pyramid
+EDGE_CLASSIFY = 68     # an edge's 2 face planes bounded over a box: 2 corner evaluations (8 each), the
+                       # rounding bound T (14) and the margin and compares (4), per face
 
-# Counter layout (fr_get_counters): 5 per kernel -- ray BVH nodes, triangle
-# tests, 4-wide edge-hierarchy nodes (once per warp: the 32 lanes share one descent),
-# edge tests (per lane), clip tests -- for forward, interior, primary edges,
-# shadow edges.
-K_FWD, K_INTERIOR, K_PEDGE, K_SEDGE = 0, 5, 10, 15
+# Counter layout (fr_get_counters): 6 per kernel -- ray BVH nodes, triangle
+# tests, 4-wide edge-hierarchy nodes (once per warp: the 32 lanes share one
+# descent), exact silhouette tests of (shading point, edge) pairs, clip tests,
+# leaf edges classified against a warp's box of shading points (once per
+# warp) -- for forward, interior, primary edges, shadow edges.
+K_FWD, K_INTERIOR, K_PEDGE, K_SEDGE = 0, 6, 12, 18
 
-# DRAM bytes of one k_bwd_sedge launch at 256x256x16 spp from a 1-pass ncu
-# capture of the kernel as it stands (dram__bytes_read.sum +
-# dram__bytes_write.sum): the edge records, hierarchies and meshes stay in L2.
-SEDGE_TRAFFIC_BYTES = 31.61e6 + 0.19e6
+# DRAM bytes of one k_bwd_sedge launch (the shadow-edge search and pick) at
+# 256x256x16 spp from a 1-pass ncu capture of the kernel as it stands
+# (dram__bytes_read.sum + dram__bytes_write.sum): 21.08 MB read, the edge
+# records, hierarchies and meshes staying in L2, and 67.34 MB of the 117 MB
+# of picks written back (the rest is still in L2 when the contributions
+# read it).
+SEDGE_TRAFFIC_BYTES = 21.08e6 + 67.34e6
 # L2 bytes of one k_bwd_sedge launch at 256x256x16 spp: lts__t_sectors.sum x
-# 32 B of a --set full capture at 128x128x16 (58.40 M sectors), scaled by the
+# 32 B of a --set full capture at 128x128x16 (58.52 M sectors), scaled by the
 # samples of a launch (x4).
-SEDGE_L2_BYTES = 58.40e6 * 32 * 4
+SEDGE_L2_BYTES = 58.52e6 * 32 * 4
 SHADE_FWD = 150        # one light sample shaded (BRDF + geometry term)
 SHADE_BWD = 420        # one light sample: forward recompute + adjoint
 N_LIGHTS = 20
@@ -39,7 +45,7 @@ FP32_LANES = 128
 
 def _kernel_flops(cnt, k):
     return (cnt[k] * NODE_VISIT + cnt[k + 1] * TRI_TEST + cnt[k + 2] * EDGE_NODE_VISIT + cnt[k + 3] * EDGE_TEST
-            + cnt[k + 4] * CLIP_TEST)
+            + cnt[k + 4] * CLIP_TEST + cnt[k + 5] * EDGE_CLASSIFY)
 
 
 def forward_flops(cnt, samples: int, n_on: int) -> float:
@@ -59,8 +65,21 @@ def step_flops(cnt, samples: int, n_on: int) -> float:
 
 
 def sedge_flops(cnt) -> float:
-    """Shadow-edge kernel: its shadow rays and its edge search."""
+    """Shadow-edge term: the edge search and the contributions' shadow rays."""
     return _kernel_flops(cnt, K_SEDGE)
+
+
+def sedge_search_flops(cnt) -> float:
+    """k_bwd_sedge, the shadow-edge search and pick: hierarchy nodes, leaf
+    edge classifications, exact silhouette tests and clips."""
+    k = K_SEDGE
+    return (cnt[k + 2] * EDGE_NODE_VISIT + cnt[k + 3] * EDGE_TEST + cnt[k + 4] * CLIP_TEST
+            + cnt[k + 5] * EDGE_CLASSIFY)
+
+
+def sedge_add_flops(cnt) -> float:
+    """k_bwd_sedge_add, the contributions of the picks: their shadow rays."""
+    return cnt[K_SEDGE] * NODE_VISIT + cnt[K_SEDGE + 1] * TRI_TEST
 
 
 def fp32_peak_tflops(sm_mhz: float, sm_count: int) -> float:

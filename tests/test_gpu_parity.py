@@ -262,9 +262,12 @@ def test_step_equals_render_loss_backward(oracle, fr, tiny, tiny_r, W, H, spp, t
     img2, loss2, g2 = tiny_r.step(th, dev(tgt), W, H, spp, seed=5, mask=dev(mask), m=dev(m), w1=w1, w2=w2,
                                   terms=terms)
     tiny_r.sync()
-    if spp <= 32:                                  # the same kernel again: bit for bit
+    if 32 % spp == 0:          # the same kernel again, a pixel's sum in one warp: bit for bit
         assert np.array_equal(img2.cpu().numpy(), img.cpu().numpy())
-    assert abs(loss2.item() - loss.item()) <= (1e-12 if spp <= 32 else 1e-6) * abs(ref_loss)
+    else:                      # a pixel's samples may straddle two warps: atomic sums in no fixed order
+        check_same_values(img2.cpu().numpy(), img.cpu().numpy(), what=f"fr_step image again {W}x{H}x{spp}",
+                          rel=rel)
+    assert abs(loss2.item() - loss.item()) <= (1e-12 if 32 % spp == 0 else 1e-6) * abs(ref_loss)
     assert_sum_order_close(g2.cpu().numpy(), ref_g, what="step, context d_image")
 
 
@@ -285,7 +288,11 @@ def test_counters_are_reset_per_call(fr, tiny, tiny_r):
     finally:
         tiny_r.set_counters(False)
     assert np.array_equal(seen[0], seen[1]), (seen[0], seen[1])
-    assert seen[0][0] > 0 and seen[0][5] > 0 and seen[0][10] > 0 and seen[0][17] > 0
+    from paper_1910_05200_gb300 import roofline as RF
+    c = seen[0]
+    assert c[RF.K_FWD] > 0 and c[RF.K_INTERIOR] > 0 and c[RF.K_PEDGE] > 0 and c[RF.K_SEDGE + 2] > 0
+    # every shadow-edge search classifies the leaf edges it reaches
+    assert c[RF.K_SEDGE + 5] > 0
 
 
 def test_all_lights_off_is_black(oracle, tiny, tiny_r):
