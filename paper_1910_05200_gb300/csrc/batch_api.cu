@@ -68,7 +68,7 @@ FrameView frame_view(fr_batch* b, int f) {
   v.alb = b->alb.p;
   v.tnodes = b->tnodes.p + (size_t)f * 4 * b->nt_nodes; v.tcones = b->tcones.p + (size_t)f * 2 * b->nt_nodes;
   v.enodes = b->enodes.p + (size_t)f * 4 * b->ne_nodes; v.econes = b->econes.p + (size_t)f * 2 * b->ne_nodes;
-  v.e4boxes = b->e4boxes.p + (size_t)f * 12 * c->n4; v.e4cones = b->e4cones.p + (size_t)f * 4 * c->n4;
+  v.e4boxes = b->e4boxes.p + (size_t)f * 12 * c->n4; v.e4cones = b->e4cones.p + (size_t)f * 8 * c->n4;
   v.tcounter = b->tcounter.p + (size_t)f * b->nt_nodes; v.ecounter = b->ecounter.p + (size_t)f * b->ne_nodes;
   v.sil = b->sil.p + f * E; v.n_sil = b->n_sil.p + f; v.block_count = b->block_count.p + (size_t)f * b->nb_sil;
   v.dX = b->dX.p + f * V; v.dN = b->dN.p + f * V; v.dA = b->dA.p; v.gs = b->gs.p + f * V;
@@ -371,7 +371,7 @@ int fr_batch_create(fr_ctx* ctx, const fr_frame* frames, int32_t n_frames, int32
   BK(b->tv.alloc(nF * 3 * F)); BK(b->epack.alloc(nF * 6 * E));
   BK(b->tnodes.alloc(nF * 4 * b->nt_nodes)); BK(b->tcones.alloc(nF * 2 * b->nt_nodes));
   BK(b->enodes.alloc(nF * 4 * b->ne_nodes)); BK(b->econes.alloc(nF * 2 * b->ne_nodes));
-  BK(b->e4boxes.alloc(nF * 12 * (size_t)ctx->n4)); BK(b->e4cones.alloc(nF * 4 * (size_t)ctx->n4));
+  BK(b->e4boxes.alloc(nF * 12 * (size_t)ctx->n4)); BK(b->e4cones.alloc(nF * 8 * (size_t)ctx->n4));
   BK(b->tcounter.alloc(nF * b->nt_nodes)); BK(b->ecounter.alloc(nF * b->ne_nodes));
   BK(b->sil.alloc(nF * E)); BK(b->n_sil.alloc(nF)); BK(b->block_count.alloc(nF * b->nb_sil));
   BK(b->dX.alloc(nF * V)); BK(b->dN.alloc(nF * V)); BK(b->gs.alloc(nF * V));

@@ -713,7 +713,7 @@ int fr_upload_mesh(fr_ctx* ctx, const float* mean, int32_t V, const int32_t* tri
     CK(upload(ctx->e4codes, codes4.data(), codes4.size(), s));
     CK(upload(ctx->e4src, src4.data(), src4.size(), s));
     CK(ctx->e4boxes.alloc(12 * codes4.size()));
-    CK(ctx->e4cones.alloc(4 * codes4.size()));
+    CK(ctx->e4cones.alloc(8 * codes4.size()));
   }
   ctx->V = V; ctx->F = F; ctx->E = E;
   ++ctx->generation;

@@ -175,16 +175,22 @@ __global__ void k_gather4(int n_slots, const int2* __restrict__ src, const float
   int2 sr = src[i];
   float b[6] = {3e38f, 3e38f, 3e38f, -3e38f, -3e38f, -3e38f};
   float4 cn = make_float4(0.0f, 0.0f, 1.0f, CONE_FULL);
+  float4 sp = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   if (sr.x >= 0) {
     const float* N = reinterpret_cast<const float*>(nodes + 4 * sr.x) + 6 * sr.y;
     for (int k = 0; k < 6; ++k) b[k] = N[k];
     cn = cones[2 * sr.x + sr.y];
+    // bounding sphere of the box, grown for rounding
+    const V3 lo{b[0], b[1], b[2]}, hi{b[3], b[4], b[5]};
+    const V3 c = (lo + hi) * 0.5f;
+    sp = make_float4(c.x, c.y, c.z, len((hi - lo) * 0.5f) * 1.0001f + 1e-6f);
   }
   float2* B = boxes4 + 3 * i;
   B[0] = make_float2(b[0], b[1]);
   B[1] = make_float2(b[2], b[3]);
   B[2] = make_float2(b[4], b[5]);
-  cones4[i] = cn;
+  cones4[2 * i] = cn;
+  cones4[2 * i + 1] = sp;
 }
 
 // Bottom-up refit: one thread per leaf; the second child to arrive at a node

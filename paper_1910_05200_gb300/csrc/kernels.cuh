@@ -65,7 +65,8 @@ struct EdgeBVH {
   // binary node become its children), searched by the shadow-edge pass
   const int4* codes4;     // [n4] child codes: leaf code, 4-wide node index or EMPTY_CHILD
   const float2* boxes4;   // [n4 * 12] child c: lo.xy | lo.z, hi.x | hi.yz at float2 12k + 3c
-  const float4* cones4;   // [n4 * 4] normal cone of each child
+  const float4* cones4;   // [n4 * 8] child c at 8k + 2c: normal cone (axis, half-angle), then the
+                          // bounding sphere of its box (centre, radius)
 };
 
 struct RenderArgs {

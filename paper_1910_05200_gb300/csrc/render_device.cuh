@@ -636,38 +636,37 @@ FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int
       const int code_c = tc == 0 ? ch.x : (tc == 1 ? ch.y : (tc == 2 ? ch.z : ch.w));
       if (code_c == EMPTY_CHILD) {
         pass = false;
+      } else if (tt == 0) {
+        const float4* C = a.ebvh.cones4 + 2 * (4 * node + tc);
+        const float4 cn = C[0];
+        if (cn.w < PI_F) {
+          const float4 sp = C[1];     // bounding sphere of the child's box
+          float rb = sp.w + rr;
+          V3 v = rc - v3(sp);
+          float dv2 = dot(v, v);
+          if (dv2 > rb * rb) {
+            float idv = rsqrtf(dv2);
+            float sb = rb * idv, cb2 = sqrtf(fmaxf(0.0f, 1.0f - sb * sb));
+            float sT, cT;
+            __sincosf(cn.w + 2e-3f, &sT, &cT);
+            if (cb2 * cT - sb * sT > 0.0f) {
+              float S = sb * cT + cb2 * sT;
+              float cpsi = dot(v, v3(cn)) * idv;
+              if (cpsi > S || cpsi < -S) pass = false;
+            }
+          }
+        }
       } else {
         const float2* B = a.ebvh.boxes4 + 12 * node + 3 * tc;
         const float2 q0 = B[0], q1 = B[1], q2 = B[2];
         const V3 lo{q0.x, q0.y, q1.x}, hi{q1.y, q2.x, q2.y};
-        if (tt == 0) {
-          float4 cn = a.ebvh.cones4[4 * node + tc];
-          if (cn.w < PI_F) {
-            V3 cb = (lo + hi) * 0.5f;
-            float rb = len((hi - lo) * 0.5f) * 1.0001f + 1e-6f + rr;
-            V3 v = rc - cb;
-            float dv2 = dot(v, v);
-            if (dv2 > rb * rb) {
-              float idv = rsqrtf(dv2);
-              float sb = rb * idv, cb2 = sqrtf(fmaxf(0.0f, 1.0f - sb * sb));
-              float sT, cT;
-              __sincosf(cn.w + 2e-3f, &sT, &cT);
-              if (cb2 * cT - sb * sT > 0.0f) {
-                float S = sb * cT + cb2 * sT;
-                float cpsi = dot(v, v3(cn)) * idv;
-                if (cpsi > S || cpsi < -S) pass = false;
-              }
-            }
-          }
-        } else {
-          V3 p{pn.x > 0 ? hi.x : lo.x, pn.y > 0 ? hi.y : lo.y, pn.z > 0 ? hi.z : lo.z};
-          pass = dot(pn, p - rc) >= -pm;
-        }
+        V3 p{pn.x > 0 ? hi.x : lo.x, pn.y > 0 ? hi.y : lo.y, pn.z > 0 ? hi.z : lo.z};
+        pass = dot(pn, p - rc) >= -pm;
       }
     }
     const unsigned m = __ballot_sync(0xffffffffu, pass);
     int next = -1, nl = 0, myslot = -1;
-#pragma unroll 1
+#pragma unroll
     for (int k = 0; k < 4; ++k) {
       if (((m >> (6 * k)) & 0x3fu) != 0x3fu) continue;
       const int c2 = k == 0 ? ch.x : (k == 1 ? ch.y : (k == 2 ? ch.z : ch.w));
@@ -746,8 +745,13 @@ FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int
     }
     if (finished) break;
   }
-  if (cnt && lane == 0) { atomicAdd(cnt + 2, nvis); atomicAdd(cnt + 5, nclass); }
-  if (cnt) { atomicAdd(cnt + 3, ntest); atomicAdd(cnt + 4, nclip); }
+  if (cnt) {                          // one set of atomics per warp
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) nclip += __shfl_xor_sync(0xffffffffu, nclip, off);
+    if (lane == 0) {
+      atomicAdd(cnt + 2, nvis); atomicAdd(cnt + 3, ntest); atomicAdd(cnt + 4, nclip); atomicAdd(cnt + 5, nclass);
+    }
+  }
   return P;
 }
 
