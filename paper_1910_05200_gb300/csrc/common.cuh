@@ -195,12 +195,17 @@ FR_HOST_DEV inline bool leaf_child(int c) { return c < 0; }
 FR_DEV int leaf_first(int c) { return (~c) >> 3; }
 FR_DEV int leaf_count(int c) { return ((~c) & 7) + 1; }
 
-// Slab test of a ray against a box; NaN-safe (fminf/fmaxf drop NaN operands,
-// which only widens the accepted interval).
-FR_DEV bool box_hit(V3 lo, V3 hi, V3 o, V3 inv, float tmin, float tmax, float& tenter) {
-  float tx0 = (lo.x - o.x) * inv.x, tx1 = (hi.x - o.x) * inv.x;
-  float ty0 = (lo.y - o.y) * inv.y, ty1 = (hi.y - o.y) * inv.y;
-  float tz0 = (lo.z - o.z) * inv.z, tz1 = (hi.z - o.z) * inv.z;
+// Slab test of a ray against a box, one FMA per slab plane: t = lo * inv -
+// oi with oi = o * inv.  Its rounding differs from (lo - o) * inv by about
+// ulp(o inv), below the boxes' padding (pad_box: 1e-5 absolute) for scenes
+// within 100 m of the origin.  NaN-safe: fminf/fmaxf drop NaN operands,
+// which only widens the accepted interval (a ray parallel to an axis, inv =
+// +-inf, may give NaN slab values for that axis, which then reject nothing).
+FR_DEV V3 ray_oi(V3 o, V3 inv) { return V3{o.x * inv.x, o.y * inv.y, o.z * inv.z}; }
+FR_DEV bool box_hit(V3 lo, V3 hi, V3 oi, V3 inv, float tmin, float tmax, float& tenter) {
+  float tx0 = fmaf(lo.x, inv.x, -oi.x), tx1 = fmaf(hi.x, inv.x, -oi.x);
+  float ty0 = fmaf(lo.y, inv.y, -oi.y), ty1 = fmaf(hi.y, inv.y, -oi.y);
+  float tz0 = fmaf(lo.z, inv.z, -oi.z), tz1 = fmaf(hi.z, inv.z, -oi.z);
   float t0 = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), tmin));
   float t1 = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
   tenter = t0;
@@ -225,6 +230,7 @@ struct Mesh {
 FR_DEV int closest_hit(const Mesh& m, V3 o, V3 d, float& t_best, int* err, unsigned long long* cnt) {
   RayPre rp = ray_pre(o, d);
   V3 inv = V3{1.0f / d.x, 1.0f / d.y, 1.0f / d.z};
+  const V3 oi = ray_oi(o, inv);
   int best = -1;
   t_best = __int_as_float(0x7f800000);
   int stack[STACK];
@@ -240,8 +246,8 @@ FR_DEV int closest_hit(const Mesh& m, V3 o, V3 d, float& t_best, int* err, unsig
     float4 a = N[0], b = N[1], c = N[2];
     int4 ch = *reinterpret_cast<const int4*>(N + 3);
     float te0, te1;
-    bool h0 = box_hit(V3{a.x, a.y, a.z}, V3{a.w, b.x, b.y}, o, inv, 0.0f, t_best, te0);
-    bool h1 = box_hit(V3{b.z, b.w, c.x}, V3{c.y, c.z, c.w}, o, inv, 0.0f, t_best, te1);
+    bool h0 = box_hit(V3{a.x, a.y, a.z}, V3{a.w, b.x, b.y}, oi, inv, 0.0f, t_best, te0);
+    bool h1 = box_hit(V3{b.z, b.w, c.x}, V3{c.y, c.z, c.w}, oi, inv, 0.0f, t_best, te1);
     int todo[2];
     int nt = 0;
     // near child first
@@ -286,6 +292,7 @@ done:
 FR_DEV bool occluded(const Mesh& m, V3 x, V3 w, int skip, float tlo, float thi, int* err, unsigned long long* cnt) {
   RayPre rp = ray_pre(x, w);
   V3 inv = V3{1.0f / w.x, 1.0f / w.y, 1.0f / w.z};
+  const V3 oi = ray_oi(x, inv);
   int stack[STACK];
   int sp = 0;
   int node = 0;
@@ -300,8 +307,8 @@ FR_DEV bool occluded(const Mesh& m, V3 x, V3 w, int skip, float tlo, float thi, 
     float4 a = N[0], b = N[1], c = N[2];
     int4 ch = *reinterpret_cast<const int4*>(N + 3);
     float te0, te1;
-    bool h0 = box_hit(V3{a.x, a.y, a.z}, V3{a.w, b.x, b.y}, x, inv, 0.0f, thi, te0);
-    bool h1 = box_hit(V3{b.z, b.w, c.x}, V3{c.y, c.z, c.w}, x, inv, 0.0f, thi, te1);
+    bool h0 = box_hit(V3{a.x, a.y, a.z}, V3{a.w, b.x, b.y}, oi, inv, 0.0f, thi, te0);
+    bool h1 = box_hit(V3{b.z, b.w, c.x}, V3{c.y, c.z, c.w}, oi, inv, 0.0f, thi, te1);
     int todo[2];
     int nt = 0;
     if (h0) todo[nt++] = ch.x;
@@ -374,6 +381,7 @@ FR_DEV int closest_hit_warp(const Mesh& m, bool active, V3 o, V3 d, float& t_bes
   const int lane = threadIdx.x & 31;
   RayPre rp = ray_pre(o, d);
   V3 inv = V3{1.0f / d.x, 1.0f / d.y, 1.0f / d.z};
+  const V3 oi = ray_oi(o, inv);
   int best = -1;
   t_best = __int_as_float(0x7f800000);
   unsigned long long nvis = 0, ntri = 0;
@@ -387,8 +395,8 @@ FR_DEV int closest_hit_warp(const Mesh& m, bool active, V3 o, V3 d, float& t_bes
     const float4 a = N[0], b = N[1], c = N[2];
     const int4 ch = *reinterpret_cast<const int4*>(N + 3);
     float te0 = 0.0f, te1 = 0.0f;
-    const bool h0 = active && box_hit(V3{a.x, a.y, a.z}, V3{a.w, b.x, b.y}, o, inv, 0.0f, t_best, te0);
-    const bool h1 = active && box_hit(V3{b.z, b.w, c.x}, V3{c.y, c.z, c.w}, o, inv, 0.0f, t_best, te1);
+    const bool h0 = active && box_hit(V3{a.x, a.y, a.z}, V3{a.w, b.x, b.y}, oi, inv, 0.0f, t_best, te0);
+    const bool h1 = active && box_hit(V3{b.z, b.w, c.x}, V3{c.y, c.z, c.w}, oi, inv, 0.0f, t_best, te1);
     const unsigned m0 = __ballot_sync(0xffffffffu, h0), m1 = __ballot_sync(0xffffffffu, h1);
     const unsigned mf = __ballot_sync(0xffffffffu, h0 && h1 && te1 < te0);
     // near child first, by the vote of the lanes that hit both
@@ -439,6 +447,7 @@ static __device__ __noinline__ bool occluded_warp(const Mesh& m, bool active, V3
   const int lane = threadIdx.x & 31;
   RayPre rp = ray_pre(x, w);
   V3 inv = V3{1.0f / w.x, 1.0f / w.y, 1.0f / w.z};
+  const V3 oi = ray_oi(x, inv);
   bool hit = false, live = active;
   unsigned long long nvis = 0, ntri = 0;
   if (m.bvh.n_nodes == 0 || !__any_sync(0xffffffffu, live)) return false;
@@ -451,8 +460,8 @@ static __device__ __noinline__ bool occluded_warp(const Mesh& m, bool active, V3
     const float4 a = N[0], b = N[1], c = N[2];
     const int4 ch = *reinterpret_cast<const int4*>(N + 3);
     float te0, te1;
-    const bool h0 = live && box_hit(V3{a.x, a.y, a.z}, V3{a.w, b.x, b.y}, x, inv, 0.0f, thi, te0);
-    const bool h1 = live && box_hit(V3{b.z, b.w, c.x}, V3{c.y, c.z, c.w}, x, inv, 0.0f, thi, te1);
+    const bool h0 = live && box_hit(V3{a.x, a.y, a.z}, V3{a.w, b.x, b.y}, oi, inv, 0.0f, thi, te0);
+    const bool h1 = live && box_hit(V3{b.z, b.w, c.x}, V3{c.y, c.z, c.w}, oi, inv, 0.0f, thi, te1);
     const unsigned m0 = __ballot_sync(0xffffffffu, h0), m1 = __ballot_sync(0xffffffffu, h1);
     int next = -1;
 #pragma unroll
@@ -564,10 +573,17 @@ struct Brdf {
   int model, fresnel;
 };
 
+// Reciprocal for value arithmetic (radiance and derivatives, never a
+// decision): the hardware's approximate reciprocal, within 2 ulp for the
+// normal-range arguments of the shading formulas.  The formulas below divide
+// through these reciprocals, a few per light instead of one exact division
+// per quotient.
+FR_DEV float rcp(float x) { return __fdividef(1.0f, x); }
+
 // Smith masking of GGX for one direction at cos c: 2c / (c + sqrt(a2 + (1 - a2) c^2)).
 FR_DEV float smith_g1_ggx(float c, float a2, float& r) {
   r = sqrtf(a2 + (1.0f - a2) * c * c);
-  return 2.0f * c / (c + r);
+  return 2.0f * c * rcp(c + r);
 }
 
 FR_DEV ShadeOut shade_light(const Surf& S, float cs, V3 l, V3 y, V3 dl, const Brdf& b) {
@@ -577,7 +593,8 @@ FR_DEV ShadeOut shade_light(const Surf& S, float cs, V3 l, V3 y, V3 dl, const Br
   o.geo = 0; o.spec = 0;
   V3 w = y - S.x;
   float d2 = dot(w, w);
-  V3 wi = w * rsqrtf(d2);
+  const float ir = rsqrtf(d2);
+  V3 wi = w * ir;
   float ci = dot(S.ns, wi);
   if (!(ci > 0.0f)) return o;
   float cy = dot(dl, wi);
@@ -586,26 +603,28 @@ FR_DEV ShadeOut shade_light(const Surf& S, float cs, V3 l, V3 y, V3 dl, const Br
   float spec = 0.0f, F = cs;
   if (co > 0.0f) {
     V3 h = normalize(wi + S.wo);
-    float ch = dot(S.ns, h), oh = dot(S.wo, h);
+    float ch = dot(S.ns, h), oh = dot(S.wo, h);   // both > 0: wi and wo lie on the side of ns
     float ch2 = ch * ch;
-    const float m = b.m;
+    const float m = b.m, a2 = m * m, ia2 = rcp(a2);
     float D, G;
     if (b.model == 0) {
-      float tan2 = (1.0f - ch2) / ch2;
-      D = __expf(-tan2 / (m * m)) / (PI_F * m * m * ch2 * ch2);
-      G = fminf(1.0f, fminf(2.0f * ch * co / oh, 2.0f * ch * ci / oh));
+      const float ich2 = rcp(ch2);
+      const float tan2 = (1.0f - ch2) * ich2;
+      D = __expf(-tan2 * ia2) * ((1.0f / PI_F) * ia2 * ich2 * ich2);
+      G = fminf(1.0f, 2.0f * ch * rcp(oh) * fminf(co, ci));
     } else {
-      float a2 = m * m, t = ch2 * (a2 - 1.0f) + 1.0f, ri, ro;
-      D = a2 / (PI_F * t * t);
+      float t = ch2 * (a2 - 1.0f) + 1.0f, ri, ro;
+      const float it = rcp(t);
+      D = a2 * (1.0f / PI_F) * it * it;
       G = smith_g1_ggx(ci, a2, ri) * smith_g1_ggx(co, a2, ro);
     }
-    spec = D * G / (4.0f * ci * co);
+    spec = D * G * rcp(4.0f * ci * co);
     if (b.fresnel) {
       float q = 1.0f - oh, q2 = q * q;
       F = cs + (1.0f - cs) * q2 * q2 * q;
     }
   }
-  float geo = ci * cy / d2;
+  float geo = ci * cy * (ir * ir);
   float sp = F * spec;
   o.h = V3{l.x * (S.rho.x * (1.0f / PI_F) + sp) * geo, l.y * (S.rho.y * (1.0f / PI_F) + sp) * geo,
            l.z * (S.rho.z * (1.0f / PI_F) + sp) * geo};

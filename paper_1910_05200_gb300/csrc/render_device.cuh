@@ -130,40 +130,47 @@ FR_DEV void shade_light_bwd(const Surf& S, float cs, V3 l, V3 y, V3 dl, const Br
   V3 w = y - S.x;
   float d2 = dot(w, w);
   float ir = rsqrtf(d2);
+  const float id2 = ir * ir;                 // 1 / d2
   V3 wi = w * ir;
   float ci = dot(S.ns, wi);
   if (!(ci > 0.0f)) return;
   float cy = dot(dl, wi);
   if (!(cy > 0.0f)) return;
   float co = dot(S.ns, S.wo);
-  const float m = bd.m, a2 = m * m;
-  float spec = 0.0f, D = 0.0f, Gf = 0.0f, ch = 0.0f, oh = 0.0f, g1 = 0.0f, g2 = 0.0f, hlen = 1.0f;
-  float t = 1.0f, G1i = 1.0f, G1o = 1.0f, ri = 1.0f, ro = 1.0f, F = cs, q = 0.0f, q4 = 0.0f;
+  const float m = bd.m, a2 = m * m, ia2 = rcp(a2);
+  float spec = 0.0f, D = 0.0f, Gf = 0.0f, ch = 0.0f, oh = 0.0f, g1 = 0.0f, g2 = 0.0f, ihl = 1.0f;
+  float ich = 0.0f, ioh = 0.0f, ik4 = 0.0f, it = 1.0f;
+  float G1i = 1.0f, G1o = 1.0f, ri = 1.0f, ro = 1.0f, F = cs, q = 0.0f, q4 = 0.0f;
   int branch = 0;
   V3 h{0, 0, 0};
   if (co > 0.0f) {
     V3 hv = wi + S.wo;
-    hlen = len(hv);
-    h = hv * (1.0f / hlen);
-    ch = dot(S.ns, h);
+    ihl = rsqrtf(dot(hv, hv));               // 1 / |wi + wo|
+    h = hv * ihl;
+    ch = dot(S.ns, h);                       // ch, oh > 0: wi and wo lie on the side of ns
     oh = dot(S.wo, h);
+    ich = rcp(ch);
+    ioh = rcp(oh);
     float ch2 = ch * ch;
     if (bd.model == 0) {
-      float tan2 = (1.0f - ch2) / ch2;
-      D = __expf(-tan2 / (m * m)) / (PI_F * m * m * ch2 * ch2);
-      g1 = 2.0f * ch * co / oh;
-      g2 = 2.0f * ch * ci / oh;
+      const float ich2 = ich * ich;
+      float tan2 = (1.0f - ch2) * ich2;
+      D = __expf(-tan2 * ia2) * ((1.0f / PI_F) * ia2 * ich2 * ich2);
+      g1 = 2.0f * ch * co * ioh;
+      g2 = 2.0f * ch * ci * ioh;
       float inner = g1 <= g2 ? g1 : g2;
       if (1.0f <= inner) { Gf = 1.0f; branch = 0; }
       else { Gf = inner; branch = g1 <= g2 ? 1 : 2; }
     } else {
-      t = ch2 * (a2 - 1.0f) + 1.0f;
-      D = a2 / (PI_F * t * t);
+      float t = ch2 * (a2 - 1.0f) + 1.0f;
+      it = rcp(t);
+      D = a2 * (1.0f / PI_F) * it * it;
       G1i = smith_g1_ggx(ci, a2, ri);
       G1o = smith_g1_ggx(co, a2, ro);
       Gf = G1i * G1o;
     }
-    spec = D * Gf / (4.0f * ci * co);
+    ik4 = rcp(4.0f * ci * co);
+    spec = D * Gf * ik4;
     if (bd.fresnel) {
       q = 1.0f - oh;
       float q2 = q * q;
@@ -171,7 +178,7 @@ FR_DEV void shade_light_bwd(const Surf& S, float cs, V3 l, V3 y, V3 dl, const Br
       F = cs + (1.0f - cs) * q4 * q;
     }
   }
-  float geo = ci * cy / d2;
+  float geo = ci * cy * id2;
   const float ip = 1.0f / PI_F;
   const float sp = F * spec;
   V3 Fr{S.rho.x * ip + sp, S.rho.y * ip + sp, S.rho.z * ip + sp};
@@ -183,30 +190,30 @@ FR_DEV void shade_light_bwd(const Surf& S, float cs, V3 l, V3 y, V3 dl, const Br
   g_cs += Ssum * spec * (bd.fresnel ? 1.0f - q4 * q : 1.0f);
   float d_spec = Ssum * F;
   float d_geo = s.x * Fr.x + s.y * Fr.y + s.z * Fr.z;
-  float d_ci = d_geo * cy / d2;
-  float d_cy = d_geo * ci / d2;
-  float d_d2 = -d_geo * geo / d2;
+  float d_ci = d_geo * cy * id2;
+  float d_cy = d_geo * ci * id2;
+  float d_d2 = -d_geo * geo * id2;
   float d_co = 0.0f;
   V3 d_ns{0, 0, 0}, d_wi{0, 0, 0};
   if (co > 0.0f && Ssum != 0.0f) {
-    float k4 = 4.0f * ci * co;
-    float d_D = d_spec * Gf / k4, d_G = d_spec * D / k4;
-    d_ci -= d_spec * spec / ci;
-    d_co -= d_spec * spec / co;
+    float d_D = d_spec * Gf * ik4, d_G = d_spec * D * ik4;
+    // spec / ci = D Gf / (4 ci^2 co) and spec / co likewise
+    d_ci -= d_spec * spec * (4.0f * co * ik4);
+    d_co -= d_spec * spec * (4.0f * ci * ik4);
     float d_ch = 0.0f, d_oh = bd.fresnel ? -5.0f * Ssum * spec * (1.0f - cs) * q4 : 0.0f;
     if (bd.model == 0) {
-      if (branch == 1) { d_ch += d_G * 2.0f * co / oh; d_co += d_G * 2.0f * ch / oh; d_oh -= d_G * g1 / oh; }
-      else if (branch == 2) { d_ch += d_G * 2.0f * ci / oh; d_ci += d_G * 2.0f * ch / oh; d_oh -= d_G * g2 / oh; }
-      d_ch += d_D * D * (2.0f / (m * m * ch * ch * ch) - 4.0f / ch);
+      if (branch == 1) { d_ch += d_G * 2.0f * co * ioh; d_co += d_G * 2.0f * ch * ioh; d_oh -= d_G * g1 * ioh; }
+      else if (branch == 2) { d_ch += d_G * 2.0f * ci * ioh; d_ci += d_G * 2.0f * ch * ioh; d_oh -= d_G * g2 * ioh; }
+      d_ch += d_D * D * (2.0f * ia2 * ich * ich * ich - 4.0f * ich);
     } else {
       // Smith: dG1/dc = 2 a2 / (r (c + r)^2); GGX: dD/dch = -4 D ch (a2 - 1) / t
-      d_ci += d_G * G1o * 2.0f * a2 / (ri * (ci + ri) * (ci + ri));
-      d_co += d_G * G1i * 2.0f * a2 / (ro * (co + ro) * (co + ro));
-      d_ch += d_D * D * (-4.0f * ch * (a2 - 1.0f) / t);
+      d_ci += d_G * G1o * 2.0f * a2 * rcp(ri * (ci + ri) * (ci + ri));
+      d_co += d_G * G1i * 2.0f * a2 * rcp(ro * (co + ro) * (co + ro));
+      d_ch += d_D * D * (-4.0f * ch * (a2 - 1.0f) * it);
     }
     d_ns += h * d_ch;
     V3 d_h = S.ns * d_ch + S.wo * d_oh;
-    d_wi += (d_h - h * dot(d_h, h)) * (1.0f / hlen);
+    d_wi += (d_h - h * dot(d_h, h)) * ihl;
   }
   d_ns += wi * d_ci + S.wo * d_co;
   d_wi += S.ns * d_ci + dl * d_cy;
