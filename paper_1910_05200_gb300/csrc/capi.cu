@@ -23,6 +23,11 @@ namespace {
 // the edges of a leaf load independently: measured on the full face,
 // leaves of 8 edges beat 6, 4, 2 and 1.
 constexpr int EDGE_LEAF = 8;
+// Triangles per leaf of the triangle hierarchy.  The warp-cooperative walk
+// tests a leaf's triangles for every lane whose box test passed, so small
+// leaves pay: on the full face at 256x256x16, leaves of 1 / 2 / 3 / 4 / 6 /
+// 8 triangles gave steps of 16.90 / 16.42 / 16.43 / 16.73 / 17.15 / 17.87 ms.
+constexpr int TRI_LEAF = 2;
 
 // Binary BVH in the device layout of common.cuh plus the refit topology.
 struct HostBVH {
@@ -53,7 +58,7 @@ struct Builder {
   HostBVH& out;
   static constexpr int BINS = 12;
   const int LEAF;
-  Builder(const std::vector<Box>& b, HostBVH& o, int leaf = 4) : boxes(b), perm(o.perm), out(o), LEAF(leaf) {
+  Builder(const std::vector<Box>& b, HostBVH& o, int leaf) : boxes(b), perm(o.perm), out(o), LEAF(leaf) {
     size_t n = b.size();
     cen.resize(3 * n);
     perm.resize(n);
@@ -686,7 +691,7 @@ int fr_upload_mesh(fr_ctx* ctx, const float* mean, int32_t V, const int32_t* tri
     eb[e].grow(&mean[3 * edges[e].y]);
   }
   HostBVH ht, he2;
-  { Builder b(tb, ht); b.run(); }
+  { Builder b(tb, ht, TRI_LEAF); b.run(); }
   { Builder b(eb, he2, EDGE_LEAF); b.run(); }
   std::vector<int4> tris4(F), edges_leaf(E);
   for (int f = 0; f < F; ++f) tris4[f] = make_int4(tris[3 * f], tris[3 * f + 1], tris[3 * f + 2], 0);
