@@ -237,7 +237,7 @@ FR_DEV int closest_hit(const Mesh& m, V3 o, V3 d, float& t_best, int* err, unsig
   int sp = 0;
   int node = 0;
   int steps = 0;
-  unsigned long long nvis = 0, ntri = 0;
+  unsigned nvis = 0, ntri = 0;       // per walk; widened when added to the counters
   if (m.bvh.n_nodes == 0) return -1;
   while (true) {
     if (++steps > m.max_steps) { atomicOr(err, ERR_STEPS); break; }
@@ -284,7 +284,7 @@ FR_DEV int closest_hit(const Mesh& m, V3 o, V3 d, float& t_best, int* err, unsig
     node = stack[--sp];
   }
 done:
-  if (cnt) { atomicAdd(cnt, nvis); atomicAdd(cnt + 1, ntri); }
+  if (cnt) { atomicAdd(cnt, (unsigned long long)nvis); atomicAdd(cnt + 1, (unsigned long long)ntri); }
   return best;
 }
 
@@ -298,7 +298,7 @@ FR_DEV bool occluded(const Mesh& m, V3 x, V3 w, int skip, float tlo, float thi, 
   int node = 0;
   int steps = 0;
   bool hit = false;
-  unsigned long long nvis = 0, ntri = 0;
+  unsigned nvis = 0, ntri = 0;       // per walk; widened when added to the counters
   if (m.bvh.n_nodes == 0) return false;
   while (true) {
     if (++steps > m.max_steps) { atomicOr(err, ERR_STEPS); break; }
@@ -345,7 +345,7 @@ FR_DEV bool occluded(const Mesh& m, V3 x, V3 w, int skip, float tlo, float thi, 
     node = stack[--sp];
   }
 done:
-  if (cnt) { atomicAdd(cnt, nvis); atomicAdd(cnt + 1, ntri); }
+  if (cnt) { atomicAdd(cnt, (unsigned long long)nvis); atomicAdd(cnt + 1, (unsigned long long)ntri); }
   return hit;
 }
 
@@ -384,7 +384,7 @@ FR_DEV int closest_hit_warp(const Mesh& m, bool active, V3 o, V3 d, float& t_bes
   const V3 oi = ray_oi(o, inv);
   int best = -1;
   t_best = __int_as_float(0x7f800000);
-  unsigned long long nvis = 0, ntri = 0;
+  unsigned nvis = 0, ntri = 0;       // per walk; widened when added to the counters
   if (m.bvh.n_nodes == 0 || !__any_sync(0xffffffffu, active)) return -1;
   WStack st{0, 0, 0};
   int node = 0, steps = 0;
@@ -433,7 +433,7 @@ FR_DEV int closest_hit_warp(const Mesh& m, bool active, V3 o, V3 d, float& t_bes
     node = wpop(st);
   }
 done:
-  if (cnt && active) { atomicAdd(cnt, nvis); atomicAdd(cnt + 1, ntri); }
+  if (cnt && active) { atomicAdd(cnt, (unsigned long long)nvis); atomicAdd(cnt + 1, (unsigned long long)ntri); }
   return best;
 }
 
@@ -449,7 +449,7 @@ static __device__ __noinline__ bool occluded_warp(const Mesh& m, bool active, V3
   V3 inv = V3{1.0f / w.x, 1.0f / w.y, 1.0f / w.z};
   const V3 oi = ray_oi(x, inv);
   bool hit = false, live = active;
-  unsigned long long nvis = 0, ntri = 0;
+  unsigned nvis = 0, ntri = 0;       // per walk; widened when added to the counters
   if (m.bvh.n_nodes == 0 || !__any_sync(0xffffffffu, live)) return false;
   WStack st{0, 0, 0};
   int node = 0, steps = 0;
@@ -497,7 +497,7 @@ static __device__ __noinline__ bool occluded_warp(const Mesh& m, bool active, V3
     node = wpop(st);
   }
 done:
-  if (cnt && active) { atomicAdd(cnt, nvis); atomicAdd(cnt + 1, ntri); }
+  if (cnt && active) { atomicAdd(cnt, (unsigned long long)nvis); atomicAdd(cnt + 1, (unsigned long long)ntri); }
   return hit;
 }
 

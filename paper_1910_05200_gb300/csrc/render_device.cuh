@@ -539,7 +539,7 @@ FR_DEV int plane_sign_over_box(V3 n, V3 p, V3 lo, V3 hi) {
 // adjacency test (an edge of the hit face itself is no occluder), the clip
 // against the light's pyramid and, for a candidate, its pick key.
 FR_DEV void sedge_consider(const RenderArgs& a, const Light& L, float hs, int j, uint32_t pix, int s, V3 x,
-                           int hitf, int slot, Pick& P, uint32_t& bestkey, unsigned long long& nclip) {
+                           int hitf, int slot, Pick& P, uint32_t& bestkey, unsigned& nclip) {
   const float4* R = a.ebvh.pack + 6 * slot;
   const float4 r1 = R[1];
   const int f0 = __float_as_int(r1.w), f1 = __float_as_int(R[2].w);
@@ -630,7 +630,7 @@ FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int
     pn = n;
     pm = (1e-4f + rr) * len(n);     // margin + dilation by the group radius
   }
-  unsigned long long nvis = 0, ntest = 0, nclass = 0, nclip = 0;
+  unsigned nvis = 0, ntest = 0, nclass = 0, nclip = 0;   // per search; widened when added to the counters
   int node = 0, steps = 0, qn = 0;
   bool failed = false;
   WStack wst{0, 0, 0};
@@ -735,7 +735,7 @@ FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int
         const unsigned b = __ballot_sync(0xffffffffu, sil);
         if (lane == k) mine = b;
       }
-      if (lane == 0) ntest += (unsigned long long)nq * __popc(vm);
+      if (lane == 0) ntest += (unsigned)nq * __popc(vm);
 #pragma unroll 1
       while (mine != 0) {
         const int e = __ffs(mine) - 1;
@@ -756,7 +756,8 @@ FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) nclip += __shfl_xor_sync(0xffffffffu, nclip, off);
     if (lane == 0) {
-      atomicAdd(cnt + 2, nvis); atomicAdd(cnt + 3, ntest); atomicAdd(cnt + 4, nclip); atomicAdd(cnt + 5, nclass);
+      atomicAdd(cnt + 2, (unsigned long long)nvis); atomicAdd(cnt + 3, (unsigned long long)ntest);
+      atomicAdd(cnt + 4, (unsigned long long)nclip); atomicAdd(cnt + 5, (unsigned long long)nclass);
     }
   }
   return P;
