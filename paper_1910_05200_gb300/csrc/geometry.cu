@@ -174,12 +174,16 @@ __global__ void k_gather4(int n_slots, const int2* __restrict__ src, const float
   if (i >= n_slots) return;
   int2 sr = src[i];
   float b[6] = {3e38f, 3e38f, 3e38f, -3e38f, -3e38f, -3e38f};
-  float4 cn = make_float4(0.0f, 0.0f, 1.0f, CONE_FULL);
+  float4 cn = make_float4(0.0f, 0.0f, 1.0f, -1.0f);
   float4 sp = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   if (sr.x >= 0) {
     const float* N = reinterpret_cast<const float*>(nodes + 4 * sr.x) + 6 * sr.y;
     for (int k = 0; k < 6; ++k) b[k] = N[k];
     cn = cones[2 * sr.x + sr.y];
+    // the search's cone test takes cos(theta + 2e-3), the half-angle grown
+    // for rounding; a cone of pi/2 or more can prune nothing (-1)
+    const float th = cn.w + 2e-3f;
+    cn.w = th < 0.5f * PI_F ? cosf(th) : -1.0f;
     // bounding sphere of the box, grown for rounding
     const V3 lo{b[0], b[1], b[2]}, hi{b[3], b[4], b[5]};
     const V3 c = (lo + hi) * 0.5f;

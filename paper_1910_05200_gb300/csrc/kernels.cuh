@@ -65,8 +65,9 @@ struct EdgeBVH {
   // binary node become its children), searched by the shadow-edge pass
   const int4* codes4;     // [n4] child codes: leaf code, 4-wide node index or EMPTY_CHILD
   const float2* boxes4;   // [n4 * 12] child c: lo.xy | lo.z, hi.x | hi.yz at float2 12k + 3c
-  const float4* cones4;   // [n4 * 8] child c at 8k + 2c: normal cone (axis, half-angle), then the
-                          // bounding sphere of its box (centre, radius)
+  const float4* cones4;   // [n4 * 8] child c at 8k + 2c: normal cone (axis, cos of the half-angle
+                          // grown by 2e-3; -1 from pi/2 on), then the bounding sphere of its box
+                          // (centre, radius)
 };
 
 struct RenderArgs {

@@ -644,22 +644,28 @@ FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int
       if (code_c == EMPTY_CHILD) {
         pass = false;
       } else if (tt == 0) {
+        // With v from the child's bounding sphere (radius grown by rr) to
+        // rc, beta the sphere's angular radius seen from rc and theta the
+        // cone's grown half-angle (cn.w = cos theta, or -1 when theta >=
+        // pi/2): every face below is seen from the same side by every point
+        // of the group when theta + beta < pi/2 and the angle between v and
+        // the axis differs from pi/2 by more than theta + beta.  Scaled by
+        // |v|: q = |v| cos beta, rb = |v| sin beta.
         const float4* C = a.ebvh.cones4 + 2 * (4 * node + tc);
         const float4 cn = C[0];
-        if (cn.w < PI_F) {
+        if (cn.w > 0.0f) {
           const float4 sp = C[1];     // bounding sphere of the child's box
-          float rb = sp.w + rr;
-          V3 v = rc - v3(sp);
-          float dv2 = dot(v, v);
-          if (dv2 > rb * rb) {
-            float idv = rsqrtf(dv2);
-            float sb = rb * idv, cb2 = sqrtf(fmaxf(0.0f, 1.0f - sb * sb));
-            float sT, cT;
-            __sincosf(cn.w + 2e-3f, &sT, &cT);
-            if (cb2 * cT - sb * sT > 0.0f) {
-              float S = sb * cT + cb2 * sT;
-              float cpsi = dot(v, v3(cn)) * idv;
-              if (cpsi > S || cpsi < -S) pass = false;
+          const float rb = sp.w + rr;
+          const V3 v = rc - v3(sp);
+          const float e2 = dot(v, v) - rb * rb;
+          if (e2 > 0.0f) {
+            const float q = e2 * rsqrtf(e2);
+            const float s2 = 1.0f - cn.w * cn.w;        // >= 4e-6: theta >= 2e-3
+            const float sT = s2 * rsqrtf(s2);
+            if (q * cn.w > rb * sT) {
+              const float lim = rb * cn.w + q * sT;     // |v| sin(theta + beta)
+              const float c = dot(v, v3(cn));
+              if (c > lim || c < -lim) pass = false;
             }
           }
         }
