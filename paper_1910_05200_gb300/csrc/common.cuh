@@ -516,6 +516,16 @@ FR_DEV bool visible(const Mesh& m, V3 x, V3 y, int f, int flip, float tmin, int*
   return !occluded(m, x, w, f, tmin, __fsub_rn(1.0f, tmin), err, cnt);
 }
 
+// Does face f (>= 0; -1 gives false) cross the segment of rp, t in (tlo,
+// thi)?  The any-hit walk's own test on the same vertices (tv holds each
+// face's vertices in the order of tris).
+FR_DEV bool face_blocks(const Mesh& m, int f, const RayPre& rp, float tlo, float thi) {
+  if (f < 0) return false;
+  const int4 t = m.tris[f];
+  float tt;
+  return tri_hit(rp, v3(m.X[t.x]), v3(m.X[t.y]), v3(m.X[t.z]), tt) && tt > tlo && tt < thi;
+}
+
 // visible() for a whole warp (occluded_warp); lanes with active = false take
 // part and get false.
 FR_DEV bool visible_warp(const Mesh& m, bool active, V3 x, V3 y, int f, int flip, float tmin, int* err,

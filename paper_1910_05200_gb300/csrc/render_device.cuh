@@ -806,8 +806,35 @@ FR_DEV void sedge_contribution(const RenderArgs& a, const GradBufs& gb, int j, i
   V3 ym{__fsub_rn(y.x, __fmul_rn(e, nv.x)), __fsub_rn(y.y, __fmul_rn(e, nv.y)), __fsub_rn(y.z, __fmul_rn(e, nv.z))};
   bool vp, vm;
   if constexpr (WARP) {
-    vp = visible_warp(a.mesh, ok, x32, yp, f, flip, a.tmin, a.err, cnt);
-    vm = visible_warp(a.mesh, ok, x32, ym, f, flip, a.tmin, a.err, cnt);
+    // visible_warp for both light points, with one shortcut: they straddle
+    // the picked edge's shadow line, so the segment toward the shadowed one
+    // usually ends on one of the edge's two faces.  Testing those first
+    // settles it without a walk; an any-hit decision does not depend on
+    // which blocking face is found, and neither face is the hit face (the
+    // pick excludes adjacent edges).
+    const int fa = __float_as_int(r1.w), fb = __float_as_int(R[2].w);
+    const float thi = __fsub_rn(1.0f, a.tmin);
+    const V3 wp = sub3r(yp, x32), wm = sub3r(ym, x32);
+    bool gp = false, gm = false, bp = false, bm = false;
+    if (ok) {
+      const float4 n = a.mesh.ng[f];
+      const V3 nn{n.x, n.y, n.z};
+      const float sp = dot3r(nn, wp), sm = dot3r(nn, wm);
+      gp = flip > 0 ? sp > 0.0f : sp < 0.0f;
+      gm = flip > 0 ? sm > 0.0f : sm < 0.0f;
+      if (gp) {
+        const RayPre rp = ray_pre(x32, wp);
+        bp = face_blocks(a.mesh, fa, rp, a.tmin, thi) || face_blocks(a.mesh, fb, rp, a.tmin, thi);
+      }
+      if (gm) {
+        const RayPre rp = ray_pre(x32, wm);
+        bm = face_blocks(a.mesh, fa, rp, a.tmin, thi) || face_blocks(a.mesh, fb, rp, a.tmin, thi);
+      }
+    }
+    const bool op = occluded_warp(a.mesh, gp && !bp, x32, wp, f, a.tmin, thi, a.err, cnt);
+    const bool om = occluded_warp(a.mesh, gm && !bm, x32, wm, f, a.tmin, thi, a.err, cnt);
+    vp = gp && !bp && !op;
+    vm = gm && !bm && !om;
   } else {
     vp = visible(a.mesh, x32, yp, f, flip, a.tmin, a.err, cnt);
     vm = visible(a.mesh, x32, ym, f, flip, a.tmin, a.err, cnt);
