@@ -245,10 +245,10 @@ struct SedgeSample {
   V3 d, x32;
 };
 
-FR_DEV SedgeSample sedge_sample(const RenderArgs& a, const GradBufs& gb) {
+FR_DEV SedgeSample sedge_sample(const RenderArgs& a, const GradBufs& gb, long long tid) {
   SedgeSample q;
   const int spp = a.spp;
-  q.tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  q.tid = tid;
   q.total = (long long)tiled_pixel_count(a.W, a.H) * spp;
   const int2 hit = q.tid < q.total ? gb.hits[q.tid] : make_int2(-1, 0);
   q.f = hit.x;
@@ -270,19 +270,32 @@ FR_DEV SedgeSample sedge_sample(const RenderArgs& a, const GradBufs& gb) {
 }
 
 // Shadow-edge term, first kernel: the candidate search and pick of every
-// (light, camera sample) (pick_light_warp), stored in picks[j * total +
+// (light, camera sample) (pick_light_warp_n), stored in picks[j * total +
 // sample] as (number of candidates, leaf slot of the pick).  A warp serves
-// one light and neighbouring samples, so the search stays coherent, and
-// warps of lights that are off retire at once.  Every lane reaches the
-// warp-cooperative search; lanes without a shading point take part with
-// valid = false.
+// one light and 64 neighbouring samples (lane l holds samples 64 w + l and
+// 64 w + 32 + l: four pixels at 16 spp), which share one walk, so the search
+// stays coherent, and warps of lights that are off retire at once.  Every
+// lane reaches the warp-cooperative search; samples without a shading point
+// take part with valid = false.
+constexpr int SEDGE_NS = 2;
 __global__ void __launch_bounds__(256, 4) k_bwd_sedge(RenderArgs a, GradBufs gb, int2* __restrict__ picks) {
   const int j = blockIdx.y;
   if (!light_on(a, j)) return;                 // uniform over the block
-  const SedgeSample q = sedge_sample(a, gb);
-  const Pick P = pick_light_warp(a, q.valid, q.x32, q.f, j, q.pix, q.s,
-                                 a.counters ? a.counters + CNT_SEDGE : nullptr);
-  if (q.tid < q.total) picks[j * q.total + q.tid] = make_int2(q.valid ? P.n : 0, P.slot);
+  const int lane = threadIdx.x & 31;
+  const long long wbase = ((long long)blockIdx.x * blockDim.x + (threadIdx.x - lane)) * SEDGE_NS;
+  SedgeSample qs[SEDGE_NS];
+  SedgePoint pt[SEDGE_NS];
+#pragma unroll
+  for (int qi = 0; qi < SEDGE_NS; ++qi) {
+    qs[qi] = sedge_sample(a, gb, wbase + 32 * qi + lane);
+    pt[qi] = SedgePoint{qs[qi].valid, qs[qi].x32, qs[qi].f, qs[qi].pix, qs[qi].s};
+  }
+  Pick P[SEDGE_NS];
+  pick_light_warp_n<SEDGE_NS>(a, pt, j, a.counters ? a.counters + CNT_SEDGE : nullptr, P);
+#pragma unroll
+  for (int qi = 0; qi < SEDGE_NS; ++qi)
+    if (qs[qi].tid < qs[qi].total)
+      picks[j * qs[qi].total + qs[qi].tid] = make_int2(qs[qi].valid ? P[qi].n : 0, P[qi].slot);
 }
 
 // Shadow-edge term, second kernel: the boundary contribution of each pick
@@ -297,7 +310,7 @@ __global__ void __launch_bounds__(256, 4) k_bwd_sedge_add(RenderArgs a, GradBufs
   const long long total = (long long)tiled_pixel_count(a.W, a.H) * a.spp;
   const int2 p = tid < total ? picks[j * total + tid] : make_int2(0, -1);
   if (!__any_sync(0xffffffffu, p.x > 0)) return;          // uniform over the warp
-  const SedgeSample q = sedge_sample(a, gb);
+  const SedgeSample q = sedge_sample(a, gb, tid);
   V3 wrgb{0, 0, 0};
   if (q.valid) {
     const float* dI = gb.d_image + 3 * (size_t)q.pix;

@@ -579,19 +579,37 @@ constexpr int SEDGE_WARPS = 8;
 // per shading point hands that lane the mask of its passing edges.  The
 // decisions are those of the per-pair test, so the candidate set, its size
 // and the pick are unchanged; only the work to find them is smaller.
-FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int j, uint32_t pix, int s,
-                            unsigned long long* cnt) {
+// A lane's shading point for the search.
+struct SedgePoint {
+  bool valid;      // the sample hit the face
+  V3 x;            // hit point (FP32)
+  int hitf;        // hit face
+  uint32_t pix;    // pixel and sample index: the pick's Philox key
+  int s;
+};
+
+// NS shading points per lane (NS = 1 or 2): the warp's group is its 32 NS
+// points, which share the walk and the classification of the leaf edges;
+// the exact tests and the picks are per point.
+template <int NS>
+FR_DEV void pick_light_warp_n(const RenderArgs& a, const SedgePoint (&q)[NS], int j, unsigned long long* cnt,
+                              Pick (&P)[NS]) {
   __shared__ int sQ[SEDGE_WARPS][64];
   const Light& L = a.lights[j];
   const float hs = __fmul_rn(0.5f, a.side);
-  Pick P;
-  P.n = 0; P.id = -1; P.slot = -1;
-  uint32_t bestkey = 0xffffffffu;
+  uint32_t bestkey[NS];
+#pragma unroll
+  for (int qi = 0; qi < NS; ++qi) { P[qi].n = 0; P[qi].id = -1; P[qi].slot = -1; bestkey[qi] = 0xffffffffu; }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (w >= SEDGE_WARPS) { if (lane == 0) atomicOr(a.err, ERR_STACK); return P; }   // uniform over the warp
+  if (w >= SEDGE_WARPS) { if (lane == 0) atomicOr(a.err, ERR_STACK); return; }   // uniform over the warp
   // group bounding box -> sphere
-  V3 lo_x = valid ? x : V3{3e38f, 3e38f, 3e38f};
-  V3 hi_x = valid ? x : V3{-3e38f, -3e38f, -3e38f};
+  V3 lo_x{3e38f, 3e38f, 3e38f}, hi_x{-3e38f, -3e38f, -3e38f};
+#pragma unroll
+  for (int qi = 0; qi < NS; ++qi) {
+    if (!q[qi].valid) continue;
+    lo_x = V3{fminf(lo_x.x, q[qi].x.x), fminf(lo_x.y, q[qi].x.y), fminf(lo_x.z, q[qi].x.z)};
+    hi_x = V3{fmaxf(hi_x.x, q[qi].x.x), fmaxf(hi_x.y, q[qi].x.y), fmaxf(hi_x.z, q[qi].x.z)};
+  }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     lo_x.x = fminf(lo_x.x, __shfl_xor_sync(0xffffffffu, lo_x.x, off));
@@ -601,10 +619,12 @@ FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int
     hi_x.y = fmaxf(hi_x.y, __shfl_xor_sync(0xffffffffu, hi_x.y, off));
     hi_x.z = fmaxf(hi_x.z, __shfl_xor_sync(0xffffffffu, hi_x.z, off));
   }
-  if (!(lo_x.x <= hi_x.x) || a.ebvh.bvh.n_nodes == 0) return P;   // no valid lane
+  if (!(lo_x.x <= hi_x.x) || a.ebvh.bvh.n_nodes == 0) return;   // no valid point
   const V3 rc = (lo_x + hi_x) * 0.5f;
   const float rr = len((hi_x - lo_x) * 0.5f) * 1.0001f + 1e-6f;
-  const unsigned vm = __ballot_sync(0xffffffffu, valid);
+  unsigned vm[NS];
+#pragma unroll
+  for (int qi = 0; qi < NS; ++qi) vm[qi] = __ballot_sync(0xffffffffu, q[qi].valid);
   // The search walks the 4-wide edge hierarchy; its node test is spread over
   // lanes 0..23: lane 6c + t holds test t of child c -- t = 0 the normal
   // cone, t = 1 the front plane, t = 2..5 side plane t - 2 of the pyramid
@@ -731,22 +751,29 @@ FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int
       const float4* R = a.ebvh.pack + 6 * slot;
       const float4 r2 = R[2], r3 = R[3], r4 = R[4], r5 = R[5];
       const bool bnd = __float_as_int(r2.w) < 0;
-      unsigned mine = 0;
+      unsigned mine[NS];
+#pragma unroll
+      for (int qi = 0; qi < NS; ++qi) {
+        mine[qi] = 0;
 #pragma unroll 1
-      for (unsigned r = vm; r != 0; r &= r - 1) {
-        const int k = __ffs(r) - 1;
-        const V3 xk{__shfl_sync(0xffffffffu, x.x, k), __shfl_sync(0xffffffffu, x.y, k),
-                    __shfl_sync(0xffffffffu, x.z, k)};
-        const bool sil = has && silhouette_regs(v3(r2), v3(r3), v3(r4), v3(r5), bnd, xk);
-        const unsigned b = __ballot_sync(0xffffffffu, sil);
-        if (lane == k) mine = b;
+        for (unsigned r = vm[qi]; r != 0; r &= r - 1) {
+          const int k = __ffs(r) - 1;
+          const V3 xk{__shfl_sync(0xffffffffu, q[qi].x.x, k), __shfl_sync(0xffffffffu, q[qi].x.y, k),
+                      __shfl_sync(0xffffffffu, q[qi].x.z, k)};
+          const bool sil = has && silhouette_regs(v3(r2), v3(r3), v3(r4), v3(r5), bnd, xk);
+          const unsigned b = __ballot_sync(0xffffffffu, sil);
+          if (lane == k) mine[qi] = b;
+        }
+        if (lane == 0) ntest += (unsigned)nq * __popc(vm[qi]);
       }
-      if (lane == 0) ntest += (unsigned)nq * __popc(vm);
+#pragma unroll
+      for (int qi = 0; qi < NS; ++qi) {
 #pragma unroll 1
-      while (mine != 0) {
-        const int e = __ffs(mine) - 1;
-        mine &= mine - 1;
-        sedge_consider(a, L, hs, j, pix, s, x, hitf, sQ[w][e], P, bestkey, nclip);
+        while (mine[qi] != 0) {
+          const int e = __ffs(mine[qi]) - 1;
+          mine[qi] &= mine[qi] - 1;
+          sedge_consider(a, L, hs, j, q[qi].pix, q[qi].s, q[qi].x, q[qi].hitf, sQ[w][e], P[qi], bestkey[qi], nclip);
+        }
       }
       __syncwarp();
       const int rest = qn - nq;
@@ -766,7 +793,15 @@ FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int
       atomicAdd(cnt + 4, (unsigned long long)nclip); atomicAdd(cnt + 5, (unsigned long long)nclass);
     }
   }
-  return P;
+}
+
+// One shading point per lane.
+FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int j, uint32_t pix, int s,
+                            unsigned long long* cnt) {
+  const SedgePoint q[1] = {{valid, x, hitf, pix, s}};
+  Pick P[1];
+  pick_light_warp_n<1>(a, q, j, cnt, P);
+  return P[0];
 }
 
 // Boundary term of one light given its pick: sample the clipped edge,
