@@ -231,6 +231,9 @@ struct StepBufs {
 };
 __global__ void k_step_fwd(RenderArgs a, GradBufs gb, StepBufs sb);
 __global__ void k_bwd_pedge(RenderArgs a, GradBufs gb);
+// Shading points per thread of the single-image shadow-edge search (a warp's
+// 32 SEDGE_NS samples share one walk of the edge hierarchy).
+constexpr int SEDGE_NS = 2;
 // Shadow edges: the search and pick per (light, sample), stored in picks
 // [n_lights * tiled samples] as (candidates, leaf slot); then the boundary
 // contributions of the picks.

@@ -277,7 +277,6 @@ FR_DEV SedgeSample sedge_sample(const RenderArgs& a, const GradBufs& gb, long lo
 // stays coherent, and warps of lights that are off retire at once.  Every
 // lane reaches the warp-cooperative search; samples without a shading point
 // take part with valid = false.
-constexpr int SEDGE_NS = 2;
 __global__ void __launch_bounds__(256, 4) k_bwd_sedge(RenderArgs a, GradBufs gb, int2* __restrict__ picks) {
   const int j = blockIdx.y;
   if (!light_on(a, j)) return;                 // uniform over the block
