@@ -542,8 +542,11 @@ int edges_and_adjoint(fr_ctx* ctx, const float* theta, const fr_render_opts* opt
     ctx->mark(PH_SEDGE, 0);
     const size_t n_picks = (size_t)tiled * ctx->cfg.n_lights;
     if (ctx->picks.n < n_picks) CK(ctx->picks.alloc(n_picks));
-    // the search takes SEDGE_NS samples per thread
-    k_bwd_sedge<<<dim3(grid_for(tiled, 256 * SEDGE_NS), ctx->cfg.n_lights), 256, 0, s>>>(a, gb, ctx->picks.p);
+    // the search takes one or two samples per thread, by the image's size
+    if ((long long)opts->W * opts->H >= SEDGE_NS2_MIN_PIXELS)
+      k_bwd_sedge<<<dim3(grid_for(tiled, 512), ctx->cfg.n_lights), 256, 0, s>>>(a, gb, ctx->picks.p);
+    else
+      k_bwd_sedge_1<<<dim3(grid_for(tiled, 256), ctx->cfg.n_lights), 256, 0, s>>>(a, gb, ctx->picks.p);
     CKL();
     ctx->mark(PH_SEDGE, 1);
     ctx->mark(PH_SEDGE_ADD, 0);

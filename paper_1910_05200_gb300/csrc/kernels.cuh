@@ -232,12 +232,17 @@ struct StepBufs {
 __global__ void k_step_fwd(RenderArgs a, GradBufs gb, StepBufs sb);
 __global__ void k_bwd_pedge(RenderArgs a, GradBufs gb);
 // Shading points per thread of the single-image shadow-edge search (a warp's
-// 32 SEDGE_NS samples share one walk of the edge hierarchy).
-constexpr int SEDGE_NS = 2;
+// 32 NS samples share one walk of the edge hierarchy): 2 from 256 x 256
+// pixels up, 1 below.  Two points per lane halve the walks but widen the
+// group, which pays only where pixels are small: on the full face at
+// 256 x 256 x 16 the search takes 7.14 ms with 2 against 7.33 ms with 1,
+// at 128 x 128 (pixels twice the size) 4.81 against 4.10 ms.
+constexpr long long SEDGE_NS2_MIN_PIXELS = 256 * 256;
 // Shadow edges: the search and pick per (light, sample), stored in picks
 // [n_lights * tiled samples] as (candidates, leaf slot); then the boundary
 // contributions of the picks.
-__global__ void k_bwd_sedge(RenderArgs a, GradBufs gb, int2* __restrict__ picks);
+__global__ void k_bwd_sedge(RenderArgs a, GradBufs gb, int2* __restrict__ picks);     // two points per lane
+__global__ void k_bwd_sedge_1(RenderArgs a, GradBufs gb, int2* __restrict__ picks);   // one point per lane
 __global__ void k_bwd_sedge_add(RenderArgs a, GradBufs gb, const int2* __restrict__ picks);
 
 __global__ void k_loss_data(int n_pix, const float* __restrict__ image, const float* __restrict__ target,

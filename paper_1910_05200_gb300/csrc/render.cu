@@ -272,29 +272,37 @@ FR_DEV SedgeSample sedge_sample(const RenderArgs& a, const GradBufs& gb, long lo
 // Shadow-edge term, first kernel: the candidate search and pick of every
 // (light, camera sample) (pick_light_warp_n), stored in picks[j * total +
 // sample] as (number of candidates, leaf slot of the pick).  A warp serves
-// one light and 64 neighbouring samples (lane l holds samples 64 w + l and
-// 64 w + 32 + l: four pixels at 16 spp), which share one walk, so the search
-// stays coherent, and warps of lights that are off retire at once.  Every
-// lane reaches the warp-cooperative search; samples without a shading point
-// take part with valid = false.
-__global__ void __launch_bounds__(256, 4) k_bwd_sedge(RenderArgs a, GradBufs gb, int2* __restrict__ picks) {
+// one light and 32 NS neighbouring samples (lane l holds samples 32 NS w +
+// 32 q + l), which share one walk, so the search stays coherent, and warps
+// of lights that are off retire at once.  Every lane reaches the
+// warp-cooperative search; samples without a shading point take part with
+// valid = false.
+template <int NS>
+FR_DEV void bwd_sedge_body(const RenderArgs& a, const GradBufs& gb, int2* __restrict__ picks) {
   const int j = blockIdx.y;
   if (!light_on(a, j)) return;                 // uniform over the block
   const int lane = threadIdx.x & 31;
-  const long long wbase = ((long long)blockIdx.x * blockDim.x + (threadIdx.x - lane)) * SEDGE_NS;
-  SedgeSample qs[SEDGE_NS];
-  SedgePoint pt[SEDGE_NS];
+  const long long wbase = ((long long)blockIdx.x * blockDim.x + (threadIdx.x - lane)) * NS;
+  SedgeSample qs[NS];
+  SedgePoint pt[NS];
 #pragma unroll
-  for (int qi = 0; qi < SEDGE_NS; ++qi) {
+  for (int qi = 0; qi < NS; ++qi) {
     qs[qi] = sedge_sample(a, gb, wbase + 32 * qi + lane);
     pt[qi] = SedgePoint{qs[qi].valid, qs[qi].x32, qs[qi].f, qs[qi].pix, qs[qi].s};
   }
-  Pick P[SEDGE_NS];
-  pick_light_warp_n<SEDGE_NS>(a, pt, j, a.counters ? a.counters + CNT_SEDGE : nullptr, P);
+  Pick P[NS];
+  pick_light_warp_n<NS>(a, pt, j, a.counters ? a.counters + CNT_SEDGE : nullptr, P);
 #pragma unroll
-  for (int qi = 0; qi < SEDGE_NS; ++qi)
+  for (int qi = 0; qi < NS; ++qi)
     if (qs[qi].tid < qs[qi].total)
       picks[j * qs[qi].total + qs[qi].tid] = make_int2(qs[qi].valid ? P[qi].n : 0, P[qi].slot);
+}
+// two points per lane (images of 256 x 256 pixels and more), one point
+__global__ void __launch_bounds__(256, 4) k_bwd_sedge(RenderArgs a, GradBufs gb, int2* __restrict__ picks) {
+  bwd_sedge_body<2>(a, gb, picks);
+}
+__global__ void __launch_bounds__(256, 4) k_bwd_sedge_1(RenderArgs a, GradBufs gb, int2* __restrict__ picks) {
+  bwd_sedge_body<1>(a, gb, picks);
 }
 
 // Shadow-edge term, second kernel: the boundary contribution of each pick
