@@ -25,17 +25,16 @@ EDGE_CLASSIFY = 68     # an edge's 2 face planes bounded over a box: 2 corner ev
 # warp) -- for forward, interior, primary edges, shadow edges.
 K_FWD, K_INTERIOR, K_PEDGE, K_SEDGE = 0, 6, 12, 18
 
-# DRAM bytes of one k_bwd_sedge launch (the shadow-edge search and pick) at
-# 256x256x16 spp from a 1-pass ncu capture of the kernel as it stands
-# (dram__bytes_read.sum + dram__bytes_write.sum): 22.69 MB read, the edge
-# records, hierarchies and meshes staying in L2, and 66.11 MB of the 117 MB
-# of picks written back (the rest is still in L2 when the contributions
-# read it).
-SEDGE_TRAFFIC_BYTES = 22.69e6 + 66.11e6
-# L2 bytes of one k_bwd_sedge launch at 256x256x16 spp: lts__t_sectors.sum x
-# 32 B of a --set full capture at 128x128x16 (42.44 M sectors), scaled by the
-# samples of a launch (x4).
-SEDGE_L2_BYTES = 42.44e6 * 32 * 4
+# DRAM bytes of one k_bwd_sedge launch (the shadow-edge search and pick, two
+# points per lane) at 256x256x16 spp from a 1-pass ncu capture of the kernel
+# as it stands (dram__bytes_read.sum + dram__bytes_write.sum): 22.73 MB read,
+# the edge records, hierarchies and meshes staying in L2, and 74.45 MB of
+# the 117 MB of picks written back (the rest is still in L2 when the
+# contributions read it).
+SEDGE_TRAFFIC_BYTES = 22.73e6 + 74.45e6
+# L2 bytes of the same launch: lts__t_sectors.sum x 32 B from the same
+# 1-pass capture (291.43 M sectors), spills to local memory included.
+SEDGE_L2_BYTES = 291.43e6 * 32
 SHADE_FWD = 150        # one light sample shaded (BRDF + geometry term)
 SHADE_BWD = 420        # one light sample: forward recompute + adjoint
 N_LIGHTS = 20
