@@ -560,25 +560,6 @@ FR_DEV void sedge_consider(const RenderArgs& a, const Light& L, float hs, int j,
 // calls it runs blocks of at most 256 threads.
 constexpr int SEDGE_WARPS = 8;
 
-// The search runs warp-cooperatively: the 32 lanes of a warp share one
-// light and (light-major order) neighbouring shading points, so the warp
-// walks the edge BVH once with tests that hold for every point of the
-// group's bounding sphere (centre rc, radius rr): the pyramid from any x in
-// the sphere lies in the pyramid from rc dilated by rr, and a face seen from
-// any x in the sphere is judged with the node's sphere grown by rr.  Control
-// flow is uniform across the warp.  Lanes without a shading point
-// (valid = false) still take part in the walk.
-//
-// The edges of the leaves that a node keeps are spread over the lanes, one
-// edge per lane.  An edge whose two faces are proven to face the same way
-// from every point of the box of the group's shading points
-// (plane_sign_over_box) is no silhouette from any of them and is dropped;
-// the others are queued.  Every 32 queued edges (and at the end) the warp
-// runs the exact decision-form silhouette test of each queued edge, held by
-// one lane, against each valid lane's shading point in turn, and one ballot
-// per shading point hands that lane the mask of its passing edges.  The
-// decisions are those of the per-pair test, so the candidate set, its size
-// and the pick are unchanged; only the work to find them is smaller.
 // A lane's shading point for the search.
 struct SedgePoint {
   bool valid;      // the sample hit the face
@@ -588,9 +569,26 @@ struct SedgePoint {
   int s;
 };
 
-// NS shading points per lane (NS = 1 or 2): the warp's group is its 32 NS
-// points, which share the walk and the classification of the leaf edges;
-// the exact tests and the picks are per point.
+// The search runs warp-cooperatively.  Each lane holds NS shading points
+// (NS = 1 or 2); the warp's group, its 32 NS points, shares one light and
+// (light-major order) neighbouring samples, so the warp walks the edge BVH
+// once with tests that hold for every point of the group's bounding sphere
+// (centre rc, radius rr): the pyramid from any x in the sphere lies in the
+// pyramid from rc dilated by rr, and a face seen from any x in the sphere
+// is judged with the node's sphere grown by rr.  Control flow is uniform
+// across the warp.  Points without a shading point (valid = false) still
+// take part in the walk.
+//
+// The edges of the leaves that a node keeps are spread over the lanes, one
+// edge per lane.  An edge whose two faces are proven to face the same way
+// from every point of the box of the group's shading points
+// (plane_sign_over_box) is no silhouette from any of them and is dropped;
+// the others are queued.  Every 32 queued edges (and at the end) the warp
+// runs the exact decision-form silhouette test of each queued edge, held by
+// one lane, against each valid shading point in turn, and one ballot per
+// shading point hands the lane that holds it the mask of its passing edges.
+// The decisions are those of the per-pair test, so the candidate set, its
+// size and the pick are unchanged; only the work to find them is smaller.
 template <int NS>
 FR_DEV void pick_light_warp_n(const RenderArgs& a, const SedgePoint (&q)[NS], int j, unsigned long long* cnt,
                               Pick (&P)[NS]) {
