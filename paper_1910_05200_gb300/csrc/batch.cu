@@ -58,11 +58,11 @@ FR_DEV void sample_adjoints(const RenderArgs& a, const GradBufs& g, float* sC, f
     x32 = hit_point(a.cam.o, d, __int_as_float(hit.y));
   }
   // warp-collective from here: every lane takes part
-  interior_sample<true>(a, g, sC, sL, pix, s, d, hit.x, __int_as_float(hit.y), dv, cnt ? cnt + CNT_INTERIOR : nullptr,
+  interior_sample(a, g, sC, sL, pix, s, d, hit.x, __int_as_float(hit.y), dv, cnt ? cnt + CNT_INTERIOR : nullptr,
                         vis, valid);
   for (int j = 0; j < a.n_lights; ++j) {
     if (!light_on(a, j)) continue;                 // uniform
-    sedge_pick_and_add<true>(a, g, j, valid, d, x32, hit.x, flip, pix, s, wrgb, cnt ? cnt + CNT_SEDGE : nullptr);
+    sedge_pick_and_add(a, g, j, valid, d, x32, hit.x, flip, pix, s, wrgb, cnt ? cnt + CNT_SEDGE : nullptr);
   }
 }
 
@@ -103,7 +103,7 @@ FR_DEV void tile_small(WarpState& w, const BatchFrame& F, float* sC, int tile, i
     uint32_t pix = 0, vis = 0u;
     {
       V3 d = valid ? sample_dir(a, px, py, s, pix) : V3{0, 0, -1};
-      L = radiance<true>(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt, nullptr, &hit, &vis, valid);
+      L = radiance(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt, nullptr, &hit, &vis, valid);
       if (!valid) { hit = make_int2(-1, 0); vis = 0u; }
     }
     float v0 = L.x, v1 = L.y, v2 = L.z;
@@ -132,7 +132,7 @@ FR_DEV void tile_large(WarpState& w, const BatchFrame& F, float* sC, int tile, i
     uint32_t pix = 0;
     for (int s = lane; s < spp; s += 32) {
       V3 d = sample_dir(a, px, py, s, pix);
-      acc += radiance<true>(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt);
+      acc += radiance(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt);
     }
     for (int off = 16; off > 0; off >>= 1) {
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
@@ -217,7 +217,7 @@ FR_DEV void batch_step_body(const BatchArgs& b) {
     unsigned long long* cnt_p = b.counters ? b.counters + CNT_PEDGE : nullptr;
     for (int k = lane; k < b.pedge_chunk; k += 32) {
       long long t = base + k;
-      pedge_sample<true>(w.a, w.g, t, cnt_p, t < F.n_pedge);
+      pedge_sample(w.a, w.g, t, cnt_p, t < F.n_pedge);
     }
   }
   if (cur >= 0) flush_lights(w, lane);
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(256, 3) k_batch_fwd(PhaseArgs p) {
   int2 hit = make_int2(-1, 0);
   uint32_t pix = 0, vis = 0u;
   if (valid) d = sample_dir(a, px, py, s, pix);
-  L = radiance<true>(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt, nullptr, &hit, &vis, valid);
+  L = radiance(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt, nullptr, &hit, &vis, valid);
   if (!valid) { hit = make_int2(-1, 0); vis = 0u; }
   float v0 = L.x, v1 = L.y, v2 = L.z;
   for (int off = (spp < 32 ? spp : 32) >> 1; off > 0; off >>= 1) {
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(256, 3) k_batch_fwd(PhaseArgs p) {
   if (valid) dv = pixel_loss(F, pix, V3{v0 * inv, v1 * inv, v2 * inv}, s == 0, lacc);
   bool adj = valid && hit.x >= 0 && (dv.x != 0.0f || dv.y != 0.0f || dv.z != 0.0f);
   if (tid < total) g.hits[tid] = adj ? hit : make_int2(-1, 0);
-  interior_sample<true>(a, g, sC, sL, pix, s, d, hit.x, __int_as_float(hit.y), dv, cnt ? cnt + CNT_INTERIOR : nullptr,
+  interior_sample(a, g, sC, sL, pix, s, d, hit.x, __int_as_float(hit.y), dv, cnt ? cnt + CNT_INTERIOR : nullptr,
                         &vis, adj);
   for (int off = 16; off > 0; off >>= 1) lacc += __shfl_xor_sync(0xffffffffu, lacc, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lacc;
@@ -399,7 +399,7 @@ FR_DEV void batch_sedge_add_body(const PhaseArgs& p) {
     const float* dI = gb.d_image + 3 * (size_t)q.pix;
     wrgb = V3{dI[0], dI[1], dI[2]} * (1.0f / (float)a.spp);
   }
-  sedge_contribution<true>(a, gb, q.j, pk.x, pk.y, q.d, q.x32, q.fh, q.flip, q.pix, q.s, wrgb,
+  sedge_contribution(a, gb, q.j, pk.x, pk.y, q.d, q.x32, q.fh, q.flip, q.pix, q.s, wrgb,
                            p.counters ? p.counters + CNT_SEDGE : nullptr, q.valid && pk.x > 0);
 }
 
@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(256, 4) k_batch_pedge(PhaseArgs p) {
   const GradBufs& gb = *reinterpret_cast<const GradBufs*>(g_raw);
   long long tid = (long long)(blockIdx.x - p.block_start[f]) * blockDim.x + threadIdx.x;
   // every lane takes part in the warp-cooperative traversals
-  pedge_sample<true>(a, gb, tid, p.counters ? p.counters + CNT_PEDGE : nullptr, tid < (long long)a.W * a.H * a.spp);
+  pedge_sample(a, gb, tid, p.counters ? p.counters + CNT_PEDGE : nullptr, tid < (long long)a.W * a.H * a.spp);
 }
 
 // The persistent kernel at three register budgets (launch bounds of 256

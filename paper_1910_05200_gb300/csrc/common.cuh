@@ -212,7 +212,6 @@ FR_DEV bool box_hit(V3 lo, V3 hi, V3 oi, V3 inv, float tmin, float tmax, float& 
   return t0 <= t1;
 }
 
-constexpr int STACK = 48;
 // Node visits per traversal before the error flag is raised (default of
 // fr_set_limits; a traversal of a valid hierarchy needs far fewer).
 constexpr int DEFAULT_MAX_STEPS = 1 << 16;
@@ -225,129 +224,6 @@ struct Mesh {
   BVHView bvh;
   int max_steps;        // node visits per traversal before ERR_STEPS
 };
-
-// Closest hit with ties broken toward the smaller face index.
-FR_DEV int closest_hit(const Mesh& m, V3 o, V3 d, float& t_best, int* err, unsigned long long* cnt) {
-  RayPre rp = ray_pre(o, d);
-  V3 inv = V3{1.0f / d.x, 1.0f / d.y, 1.0f / d.z};
-  const V3 oi = ray_oi(o, inv);
-  int best = -1;
-  t_best = __int_as_float(0x7f800000);
-  int stack[STACK];
-  int sp = 0;
-  int node = 0;
-  int steps = 0;
-  unsigned nvis = 0, ntri = 0;       // per walk; widened when added to the counters
-  if (m.bvh.n_nodes == 0) return -1;
-  while (true) {
-    if (++steps > m.max_steps) { atomicOr(err, ERR_STEPS); break; }
-    ++nvis;
-    const float4* N = m.bvh.nodes + 4 * node;
-    float4 a = N[0], b = N[1], c = N[2];
-    int4 ch = *reinterpret_cast<const int4*>(N + 3);
-    float te0, te1;
-    bool h0 = box_hit(V3{a.x, a.y, a.z}, V3{a.w, b.x, b.y}, oi, inv, 0.0f, t_best, te0);
-    bool h1 = box_hit(V3{b.z, b.w, c.x}, V3{c.y, c.z, c.w}, oi, inv, 0.0f, t_best, te1);
-    int todo[2];
-    int nt = 0;
-    // near child first
-    if (h0 && h1) {
-      if (te1 < te0) { todo[0] = ch.y; todo[1] = ch.x; } else { todo[0] = ch.x; todo[1] = ch.y; }
-      nt = 2;
-    } else if (h0) { todo[0] = ch.x; nt = 1; }
-    else if (h1) { todo[0] = ch.y; nt = 1; }
-    int next = -1;
-    for (int k = 0; k < nt; ++k) {
-      int c2 = todo[k];
-      if (c2 == EMPTY_CHILD) continue;
-      if (leaf_child(c2)) {
-        int f0 = leaf_first(c2), n = leaf_count(c2);
-        for (int i = 0; i < n; ++i) {
-          const float4* T = m.tv + 3 * (f0 + i);
-          float4 p0 = T[0], p1 = T[1], p2 = T[2];
-          int fid = __float_as_int(p0.w);
-          float tt;
-          ++ntri;
-          if (tri_hit(rp, V3{p0.x, p0.y, p0.z}, V3{p1.x, p1.y, p1.z}, V3{p2.x, p2.y, p2.z}, tt) && tt > 0.0f) {
-            if (tt < t_best || (tt == t_best && fid < best)) { t_best = tt; best = fid; }
-          }
-        }
-      } else if (next < 0) {
-        next = c2;
-      } else {
-        if (sp >= STACK) { atomicOr(err, ERR_STACK); goto done; }
-        stack[sp++] = c2;
-      }
-    }
-    if (next >= 0) { node = next; continue; }
-    if (sp == 0) break;
-    node = stack[--sp];
-  }
-done:
-  if (cnt) { atomicAdd(cnt, (unsigned long long)nvis); atomicAdd(cnt + 1, (unsigned long long)ntri); }
-  return best;
-}
-
-// Is any face other than `skip` crossed by x + t w, t in (tlo, thi)?
-FR_DEV bool occluded(const Mesh& m, V3 x, V3 w, int skip, float tlo, float thi, int* err, unsigned long long* cnt) {
-  RayPre rp = ray_pre(x, w);
-  V3 inv = V3{1.0f / w.x, 1.0f / w.y, 1.0f / w.z};
-  const V3 oi = ray_oi(x, inv);
-  int stack[STACK];
-  int sp = 0;
-  int node = 0;
-  int steps = 0;
-  bool hit = false;
-  unsigned nvis = 0, ntri = 0;       // per walk; widened when added to the counters
-  if (m.bvh.n_nodes == 0) return false;
-  while (true) {
-    if (++steps > m.max_steps) { atomicOr(err, ERR_STEPS); break; }
-    ++nvis;
-    const float4* N = m.bvh.nodes + 4 * node;
-    float4 a = N[0], b = N[1], c = N[2];
-    int4 ch = *reinterpret_cast<const int4*>(N + 3);
-    float te0, te1;
-    bool h0 = box_hit(V3{a.x, a.y, a.z}, V3{a.w, b.x, b.y}, oi, inv, 0.0f, thi, te0);
-    bool h1 = box_hit(V3{b.z, b.w, c.x}, V3{c.y, c.z, c.w}, oi, inv, 0.0f, thi, te1);
-    int todo[2];
-    int nt = 0;
-    if (h0) todo[nt++] = ch.x;
-    if (h1) todo[nt++] = ch.y;
-    int next = -1;
-    for (int k = 0; k < nt; ++k) {
-      int c2 = todo[k];
-      if (c2 == EMPTY_CHILD) continue;
-      if (leaf_child(c2)) {
-        int f0 = leaf_first(c2), n = leaf_count(c2);
-        for (int i = 0; i < n; ++i) {
-          const float4* T = m.tv + 3 * (f0 + i);
-          float4 p0 = T[0];
-          int fid = __float_as_int(p0.w);
-          if (fid == skip) continue;
-          float4 p1 = T[1], p2 = T[2];
-          float tt;
-          ++ntri;
-          if (tri_hit(rp, V3{p0.x, p0.y, p0.z}, V3{p1.x, p1.y, p1.z}, V3{p2.x, p2.y, p2.z}, tt) && tt > tlo &&
-              tt < thi) {
-            hit = true;
-            goto done;
-          }
-        }
-      } else if (next < 0) {
-        next = c2;
-      } else {
-        if (sp >= STACK) { atomicOr(err, ERR_STACK); goto done; }
-        stack[sp++] = c2;
-      }
-    }
-    if (next >= 0) { node = next; continue; }
-    if (sp == 0) break;
-    node = stack[--sp];
-  }
-done:
-  if (cnt) { atomicAdd(cnt, (unsigned long long)nvis); atomicAdd(cnt + 1, (unsigned long long)ntri); }
-  return hit;
-}
 
 // ---------------------------------------------------------------------------
 // Warp-cooperative traversal.  The 32 lanes of a warp trace their own rays
@@ -506,16 +382,6 @@ FR_DEV int face_flip(const Mesh& m, int f, V3 d) {
   return dot3r(V3{n.x, n.y, n.z}, d) > 0.0f ? -1 : 1;
 }
 
-// Visibility of light point y from hit point x on face f seen from side `flip`.
-FR_DEV bool visible(const Mesh& m, V3 x, V3 y, int f, int flip, float tmin, int* err, unsigned long long* cnt) {
-  V3 w = sub3r(y, x);
-  float4 n = m.ng[f];
-  float g = dot3r(V3{n.x, n.y, n.z}, w);
-  bool gate = flip > 0 ? g > 0.0f : g < 0.0f;
-  if (!gate) return false;
-  return !occluded(m, x, w, f, tmin, __fsub_rn(1.0f, tmin), err, cnt);
-}
-
 // Does face f (>= 0; -1 gives false) cross the segment of rp, t in (tlo,
 // thi)?  The any-hit walk's own test on the same vertices (tv holds each
 // face's vertices in the order of tris).
@@ -526,7 +392,8 @@ FR_DEV bool face_blocks(const Mesh& m, int f, const RayPre& rp, float tlo, float
   return tri_hit(rp, v3(m.X[t.x]), v3(m.X[t.y]), v3(m.X[t.z]), tt) && tt > tlo && tt < thi;
 }
 
-// visible() for a whole warp (occluded_warp); lanes with active = false take
+// Visibility of light point y from hit point x on face f seen from side
+// `flip`, for a whole warp (occluded_warp); lanes with active = false take
 // part and get false.
 FR_DEV bool visible_warp(const Mesh& m, bool active, V3 x, V3 y, int f, int flip, float tmin, int* err,
                          unsigned long long* cnt) {

@@ -46,7 +46,7 @@ FR_DEV void render_fwd_body(const RenderArgs& a, float* __restrict__ image, floa
     // every lane takes part in the warp-cooperative traversal
     V3 d = valid ? sample_dir(a, px, py, s, pix) : V3{0, 0, -1};
     SampleAux aux{V3{0, 0, 0}, V3{0, 0, 0}, 0.0f, 0.0f, 0.0f, 0.0f};
-    V3 L = radiance<true>(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt, AOV ? &aux : nullptr, nullptr, nullptr,
+    V3 L = radiance(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt, AOV ? &aux : nullptr, nullptr, nullptr,
                           valid);
     v[0] = L.x; v[1] = L.y; v[2] = L.z;
     if (AOV) {
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(256, 3) k_bwd_interior(RenderArgs a, GradBufs 
     int f = closest_hit_warp(a.mesh, want, a.cam.o, d, t, a.err, cnt);
     if (!want) { f = -1; t = 0.0f; }
     if (in_image && gb.hits) gb.hits[tid] = make_int2(f, __float_as_int(t));
-    interior_sample<true>(a, gb, sC, sL, pix, s, d, f, t, dimg, cnt, nullptr, f >= 0);
+    interior_sample(a, gb, sC, sL, pix, s, d, f, t, dimg, cnt, nullptr, f >= 0);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < CS * CS; i += blockDim.x)
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(256, 5) k_step_fwd(RenderArgs a, GradBufs gb, 
   int2 hit = make_int2(-1, 0);
   uint32_t pix = 0, vis = 0u;
   if (valid) d = sample_dir(a, px, py, s, pix);
-  L = radiance<true>(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt, nullptr, &hit, &vis, valid);
+  L = radiance(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt, nullptr, &hit, &vis, valid);
   if (!valid) { hit = make_int2(-1, 0); vis = 0u; }
   float v0 = L.x, v1 = L.y, v2 = L.z;
   for (int off = (spp < 32 ? spp : 32) >> 1; off > 0; off >>= 1) {
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(256, 5) k_step_fwd(RenderArgs a, GradBufs gb, 
   const bool adj = valid && hit.x >= 0 && (dv[0] != 0.0f || dv[1] != 0.0f || dv[2] != 0.0f);
   if (tid < total && gb.hits) gb.hits[tid] = adj ? hit : make_int2(-1, 0);
   if (sb.interior)                     // uniform
-    interior_sample<true>(a, gb, sC, sL, pix, s, d, hit.x, __int_as_float(hit.y), V3{dv[0], dv[1], dv[2]},
+    interior_sample(a, gb, sC, sL, pix, s, d, hit.x, __int_as_float(hit.y), V3{dv[0], dv[1], dv[2]},
                           cnt ? cnt + CNT_INTERIOR : nullptr, &vis, adj);
   for (int off = 16; off > 0; off >>= 1) lacc += __shfl_xor_sync(0xffffffffu, lacc, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lacc;
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(256, 5) k_step_fwd(RenderArgs a, GradBufs gb, 
 __global__ void __launch_bounds__(256, 4) k_bwd_pedge(RenderArgs a, GradBufs gb) {
   long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   // every lane takes part in the warp-cooperative traversals
-  pedge_sample<true>(a, gb, tid, a.counters ? a.counters + CNT_PEDGE : nullptr, tid < (long long)a.W * a.H * a.spp);
+  pedge_sample(a, gb, tid, a.counters ? a.counters + CNT_PEDGE : nullptr, tid < (long long)a.W * a.H * a.spp);
 }
 
 // The shading point of one thread of the shadow-edge kernels: one thread per
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(256, 4) k_bwd_sedge_add(RenderArgs a, GradBufs
     const float* dI = gb.d_image + 3 * (size_t)q.pix;
     wrgb = V3{dI[0], dI[1], dI[2]} * (1.0f / (float)a.spp);
   }
-  sedge_contribution<true>(a, gb, j, p.x, p.y, q.d, q.x32, q.f, q.flip, q.pix, q.s, wrgb,
+  sedge_contribution(a, gb, j, p.x, p.y, q.d, q.x32, q.f, q.flip, q.pix, q.s, wrgb,
                            a.counters ? a.counters + CNT_SEDGE : nullptr, q.valid && p.x > 0);
 }
 

@@ -56,21 +56,16 @@ struct SampleAux {
 // One-sample radiance along a camera ray, lights that are on only.
 // hit (optional) receives the primary hit: face (or -1) and the bits of t;
 // vis (optional) bit j = light j is on and its light point is visible.
-// WARP: all 32 lanes of the warp call together (warp-cooperative traversal,
+// All 32 lanes of the warp call together (warp-cooperative traversal,
 // common.cuh); lanes without a ray pass active = false and get 0.
-template <bool WARP = false>
 FR_DEV V3 radiance(const RenderArgs& a, V3 o, V3 d, int tag, uint32_t c0, uint32_t c1, unsigned long long* cnt,
                    SampleAux* aux = nullptr, int2* hit = nullptr, uint32_t* vis = nullptr, bool active = true) {
   float t;
   int f;
-  if constexpr (WARP) f = closest_hit_warp(a.mesh, active, o, d, t, a.err, cnt);
-  else f = closest_hit(a.mesh, o, d, t, a.err, cnt);
+  f = closest_hit_warp(a.mesh, active, o, d, t, a.err, cnt);
   if (hit) *hit = make_int2(f, __float_as_int(t));
   if (vis) *vis = 0u;
   const bool lit = f >= 0;
-  if constexpr (!WARP) {
-    if (!lit) return V3{0, 0, 0};
-  }
   int flip = 1;
   V3 x32{0, 0, 0};
   Surf S;
@@ -92,8 +87,7 @@ FR_DEV V3 radiance(const RenderArgs& a, V3 o, V3 d, int tag, uint32_t c0, uint32
     U4 q = philox(a.seed, a.iter, c0, c1, (uint32_t)(tag << 8 | j), 0);
     V3 y = light_point(a.lights[j], a.side, unitf(q.x), unitf(q.y));
     bool seen;
-    if constexpr (WARP) seen = visible_warp(a.mesh, lit, x32, y, f, flip, a.tmin, a.err, cnt);
-    else seen = visible(a.mesh, x32, y, f, flip, a.tmin, a.err, cnt);
+    seen = visible_warp(a.mesh, lit, x32, y, f, flip, a.tmin, a.err, cnt);
     if (!seen) continue;
     ++n_vis;
     if (vis) *vis |= 1u << j;
@@ -286,8 +280,7 @@ FR_DEV void hit_adjoint(const RenderArgs& a, int f, V3 d, const Surf& S, V3 g_x,
 // vis (optional): the forward's visibility bits of this sample (radiance
 // with the light tag): lights that are on take their shadow decision from
 // it, the others trace their shadow ray.
-// WARP: all 32 lanes call together; lanes without a sample pass active = false.
-template <bool WARP = false>
+// All 32 lanes call together; lanes without a sample pass active = false.
 FR_DEV void interior_sample(const RenderArgs& a, const GradBufs& gb, float* sC, float* sL, uint32_t pix, int s,
                             V3 d, int f, float t, V3 dimg, unsigned long long* cnt, const uint32_t* vis = nullptr,
                             bool active = true) {
@@ -313,8 +306,7 @@ FR_DEV void interior_sample(const RenderArgs& a, const GradBufs& gb, float* sC, 
     V3 y = light_point(a.lights[j], a.side, unitf(q.x), unitf(q.y));
     bool seen;
     if (vis && light_on(a, j)) seen = active && ((*vis >> j) & 1u) != 0u;
-    else if constexpr (WARP) seen = visible_warp(a.mesh, active, x32, y, f, flip, a.tmin, a.err, cnt);
-    else seen = visible(a.mesh, x32, y, f, flip, a.tmin, a.err, cnt);
+    else seen = visible_warp(a.mesh, active, x32, y, f, flip, a.tmin, a.err, cnt);
     if (!seen) continue;
     V3 g_l{0, 0, 0};
     shade_light_bwd(S, cs, light_rgb(a, j), y, a.lights[j].dl, a.brdf, G, g_x, g_ns, g_rho, g_cs, g_l);
@@ -362,15 +354,11 @@ FR_DEV void interior_sample(const RenderArgs& a, const GradBufs& gb, float* sC, 
 // Edge sample tid (Philox keys: pixel tid / spp, sample tid % spp) of the
 // primary-visibility term.  d_image is read through L2 (__ldcg): in the batched launch another
 // block of the same launch wrote it.
-// WARP: all 32 lanes call together; lanes without a sample pass active = false.
-template <bool WARP = false>
+// All 32 lanes call together; lanes without a sample pass active = false.
 FR_DEV void pedge_sample(const RenderArgs& a, const GradBufs& gb, long long tid, unsigned long long* cnt,
                          bool active = true) {
   const int nS = *a.n_sil;
   if (nS <= 0) return;                          // uniform
-  if constexpr (!WARP) {
-    if (!active) return;
-  }
   if (!active) tid = 0;
   uint32_t pix = (uint32_t)(tid / a.spp);
   int s = (int)(tid - (long long)pix * a.spp);
@@ -405,16 +393,13 @@ FR_DEV void pedge_sample(const RenderArgs& a, const GradBufs& gb, long long tid,
   L2 = __fadd_rn(L2, __fmul_rn(ey, ey));
   float Ln = __fsqrt_rn(L2);
   ok = ok && Ln != 0.0f;
-  if constexpr (!WARP) {
-    if (!ok) return;
-  }
   if (!ok) Ln = 1.0f;
   float nx = __fdiv_rn(-ey, Ln), ny = __fdiv_rn(ex, Ln);
   float e = a.eps_pedge;
   V3 dp = camera_dir(a.cam, __fadd_rn(mx, __fmul_rn(e, nx)), __fadd_rn(my, __fmul_rn(e, ny)));
   V3 dm = camera_dir(a.cam, __fsub_rn(mx, __fmul_rn(e, nx)), __fsub_rn(my, __fmul_rn(e, ny)));
-  V3 fp = radiance<WARP>(a, a.cam.o, dp, TAG_PEDGE_LIGHT, pix, (uint32_t)s, cnt, nullptr, nullptr, nullptr, ok);
-  V3 fm = radiance<WARP>(a, a.cam.o, dm, TAG_PEDGE_LIGHT, pix, (uint32_t)s, cnt, nullptr, nullptr, nullptr, ok);
+  V3 fp = radiance(a, a.cam.o, dp, TAG_PEDGE_LIGHT, pix, (uint32_t)s, cnt, nullptr, nullptr, nullptr, ok);
+  V3 fm = radiance(a, a.cam.o, dm, TAG_PEDGE_LIGHT, pix, (uint32_t)s, cnt, nullptr, nullptr, nullptr, ok);
   if (!ok) return;
   float delta = dot(dimg, fm - fp);
   if (delta == 0.0f) return;
@@ -804,8 +789,7 @@ FR_DEV Pick pick_light_warp(const RenderArgs& a, bool valid, V3 x, int hitf, int
 
 // Boundary term of one light given its pick: sample the clipped edge,
 // difference the integrand across the projected edge, scatter the adjoint.
-// WARP: all 32 lanes call together; lanes without a pick pass active = false.
-template <bool WARP = false>
+// All 32 lanes call together; lanes without a pick pass active = false.
 FR_DEV void sedge_contribution(const RenderArgs& a, const GradBufs& gb, int j, int n_cand, int slot, V3 d, V3 x32,
                                int f, int flip, uint32_t pix, int s, V3 wrgb, unsigned long long* cnt,
                                bool active = true) {
@@ -829,49 +813,40 @@ FR_DEV void sedge_contribution(const RenderArgs& a, const GradBufs& gb, int j, i
   V3 nv = cross3r(L.dl, sub3r(y1, y0));
   float nl = __fsqrt_rn(dot3r(nv, nv));
   bool ok = active && nl != 0.0f;
-  if constexpr (!WARP) {
-    if (!ok) return;
-  }
   if (!ok) nl = 1.0f;
   nv = V3{__fdiv_rn(nv.x, nl), __fdiv_rn(nv.y, nl), __fdiv_rn(nv.z, nl)};
   const float e = a.eps_sedge;
   V3 yp{__fadd_rn(y.x, __fmul_rn(e, nv.x)), __fadd_rn(y.y, __fmul_rn(e, nv.y)), __fadd_rn(y.z, __fmul_rn(e, nv.z))};
   V3 ym{__fsub_rn(y.x, __fmul_rn(e, nv.x)), __fsub_rn(y.y, __fmul_rn(e, nv.y)), __fsub_rn(y.z, __fmul_rn(e, nv.z))};
-  bool vp, vm;
-  if constexpr (WARP) {
-    // visible_warp for both light points, with one shortcut: they straddle
-    // the picked edge's shadow line, so the segment toward the shadowed one
-    // usually ends on one of the edge's two faces.  Testing those first
-    // settles it without a walk; an any-hit decision does not depend on
-    // which blocking face is found, and neither face is the hit face (the
-    // pick excludes adjacent edges).
-    const int fa = __float_as_int(r1.w), fb = __float_as_int(R[2].w);
-    const float thi = __fsub_rn(1.0f, a.tmin);
-    const V3 wp = sub3r(yp, x32), wm = sub3r(ym, x32);
-    bool gp = false, gm = false, bp = false, bm = false;
-    if (ok) {
-      const float4 n = a.mesh.ng[f];
-      const V3 nn{n.x, n.y, n.z};
-      const float sp = dot3r(nn, wp), sm = dot3r(nn, wm);
-      gp = flip > 0 ? sp > 0.0f : sp < 0.0f;
-      gm = flip > 0 ? sm > 0.0f : sm < 0.0f;
-      if (gp) {
-        const RayPre rp = ray_pre(x32, wp);
-        bp = face_blocks(a.mesh, fa, rp, a.tmin, thi) || face_blocks(a.mesh, fb, rp, a.tmin, thi);
-      }
-      if (gm) {
-        const RayPre rp = ray_pre(x32, wm);
-        bm = face_blocks(a.mesh, fa, rp, a.tmin, thi) || face_blocks(a.mesh, fb, rp, a.tmin, thi);
-      }
+  // visible_warp for both light points, with one shortcut: they straddle
+  // the picked edge's shadow line, so the segment toward the shadowed one
+  // usually ends on one of the edge's two faces.  Testing those first
+  // settles it without a walk; an any-hit decision does not depend on
+  // which blocking face is found, and neither face is the hit face (the
+  // pick excludes adjacent edges).
+  const int fa = __float_as_int(r1.w), fb = __float_as_int(R[2].w);
+  const float thi = __fsub_rn(1.0f, a.tmin);
+  const V3 wp = sub3r(yp, x32), wm = sub3r(ym, x32);
+  bool gate_p = false, gate_m = false, bp = false, bm = false;
+  if (ok) {
+    const float4 n = a.mesh.ng[f];
+    const V3 nn{n.x, n.y, n.z};
+    const float sp = dot3r(nn, wp), sm = dot3r(nn, wm);
+    gate_p = flip > 0 ? sp > 0.0f : sp < 0.0f;
+    gate_m = flip > 0 ? sm > 0.0f : sm < 0.0f;
+    if (gate_p) {
+      const RayPre rp = ray_pre(x32, wp);
+      bp = face_blocks(a.mesh, fa, rp, a.tmin, thi) || face_blocks(a.mesh, fb, rp, a.tmin, thi);
     }
-    const bool op = occluded_warp(a.mesh, gp && !bp, x32, wp, f, a.tmin, thi, a.err, cnt);
-    const bool om = occluded_warp(a.mesh, gm && !bm, x32, wm, f, a.tmin, thi, a.err, cnt);
-    vp = gp && !bp && !op;
-    vm = gm && !bm && !om;
-  } else {
-    vp = visible(a.mesh, x32, yp, f, flip, a.tmin, a.err, cnt);
-    vm = visible(a.mesh, x32, ym, f, flip, a.tmin, a.err, cnt);
+    if (gate_m) {
+      const RayPre rp = ray_pre(x32, wm);
+      bm = face_blocks(a.mesh, fa, rp, a.tmin, thi) || face_blocks(a.mesh, fb, rp, a.tmin, thi);
+    }
   }
+  const bool op = occluded_warp(a.mesh, gate_p && !bp, x32, wp, f, a.tmin, thi, a.err, cnt);
+  const bool om = occluded_warp(a.mesh, gate_m && !bm, x32, wm, f, a.tmin, thi, a.err, cnt);
+  const bool vp = gate_p && !bp && !op;
+  const bool vm = gate_m && !bm && !om;
   if (!ok || vp == vm) return;
   Surf S = surface(a, f, a.cam.o, d, flip);
   int idx[4];
@@ -915,16 +890,10 @@ FR_DEV void sedge_contribution(const RenderArgs& a, const GradBufs& gb, int j, i
 
 // Shadow-edge term of one (camera sample, light j).  Warp-collective: all 32
 // lanes call it, lanes without a shading point with valid = false.
-template <bool WARP = false>
 FR_DEV void sedge_pick_and_add(const RenderArgs& a, const GradBufs& gb, int j, bool valid, V3 d, V3 x32, int f,
                                int flip, uint32_t pix, int s, V3 wrgb, unsigned long long* cnt) {
   Pick P = pick_light_warp(a, valid, x32, f, j, pix, s, cnt);
-  if constexpr (WARP) {
-    sedge_contribution<true>(a, gb, j, P.n, P.slot, d, x32, f, flip, pix, s, wrgb, cnt, valid && P.n > 0);
-  } else {
-    if (!valid || P.n == 0) return;
-    sedge_contribution(a, gb, j, P.n, P.slot, d, x32, f, flip, pix, s, wrgb, cnt);
-  }
+  sedge_contribution(a, gb, j, P.n, P.slot, d, x32, f, flip, pix, s, wrgb, cnt, valid && P.n > 0);
 }
 
 }  // namespace fr
