@@ -162,7 +162,10 @@ int fr_render(fr_ctx* ctx, const float* theta, const fr_render_opts* opts, float
  * intersection (no path storage) and adds the edge-sampling terms of Li et
  * al. 2018 for primary visibility and for shadow boundaries on the lights.
  * d_image[H*W*3] FP32 device; grad[P] FP64 device, overwritten
- * (accumulate = 0) or added to (accumulate = 1). */
+ * (accumulate = 0) or added to (accumulate = 1).  The context grows its
+ * device scratch on demand (fr_step likewise): 8 B per camera sample for the
+ * primary hits and 8 B per (light, sample) for the shadow-edge picks, 168 MB
+ * at 256 x 256 x 16 spp with 20 lights; FR_ERR_OOM if that fails. */
 int fr_render_backward(fr_ctx* ctx, const float* theta, const fr_render_opts* opts, const float* d_image,
                        double* grad, int32_t accumulate);
 
