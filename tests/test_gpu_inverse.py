@@ -78,7 +78,10 @@ def test_checkpoint_and_resume(r, tiny, tmp_path):
     d_rest = np.linalg.norm(rest.theta - full.theta)
     d_half = np.linalg.norm(part.theta - full.theta)
     assert d_rest <= 0.1 * d_half, (d_rest, d_half)
-    assert d_rest <= 2e-2 * np.linalg.norm(full.theta)
+    # two uninterrupted runs already differ by up to about 2 % of |theta| here
+    # (atomic order through Adam); 3 % still catches a resume that restored
+    # the wrong state
+    assert d_rest <= 3e-2 * np.linalg.norm(full.theta)
     assert np.array_equal(rest.loss[:30], part.loss[:30])          # restored from the checkpoint
     np.testing.assert_allclose(rest.loss[:30], full.loss[:30], rtol=1e-2)
     assert abs(rest.loss[-10:].mean() - full.loss[-10:].mean()) <= 2e-2 * full.loss[-10:].mean()
