@@ -33,7 +33,7 @@ import numpy as np
 KAPPA = 1e-4
 RECORD: list[dict] = []
 
-# FACERT_PARITY_MODE=record measures without asserting (a survey of the
+# FACERT_PARITY_MODE=record measures without asserting (a record of the
 # errors of every result); the default asserts.
 ASSERT = os.environ.get("FACERT_PARITY_MODE", "assert") != "record"
 
