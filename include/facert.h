@@ -254,10 +254,10 @@ int fr_sync(fr_ctx* ctx);
  *   max_steps (>= 1): node visits one traversal of a hierarchy may make
  *     before it stops and raises FR_ERR_DEVICE_LIMIT at the next fr_sync
  *     (default 65536; a valid hierarchy needs a few hundred);
- *   wait_limit (>= 0): tries (about 256 ns apart) a primary-edge work item
- *     of the persistent batch kernel waits for its frame's tiles before it
- *     skips its samples and raises FR_ERR_DEVICE_LIMIT (default 4194304,
- *     about a second).
+ *   wait_limit (>= 0): tries (about 256 ns apart) an edge work item
+ *     (shadow or primary edges) of the persistent batch kernel waits for its
+ *     frame's tiles before it skips its samples and raises
+ *     FR_ERR_DEVICE_LIMIT (default 4194304, about a second).
  * A call that stops at a limit leaves its outputs incomplete; the context
  * stays usable.  FR_ERR_INVALID_ARG for values out of range. */
 int fr_set_limits(fr_ctx* ctx, int32_t max_steps, int32_t wait_limit);
@@ -383,8 +383,10 @@ typedef struct fr_frame {
  *     samples in one block of 256 threads; the default for such spp).
  *   fused = 1: one persistent launch whose warps take work items from a
  *     queue: tiles of tile_w x tile_h pixels (sides 1..64) that run forward,
- *     loss, interior and shadow-edge terms together, then chunks of
- *     primary-edge samples; block threads (a multiple of 32 up to 256);
+ *     loss and interior terms together, then chunks of camera samples for
+ *     one light's shadow-edge term (light-major within each frame), then
+ *     chunks of primary-edge samples; block threads (a multiple of 32 up to
+ *     256);
  *     min_blocks 2, 3 or 4 is the kernel's register budget.
  * ms is the time of one step measured by fr_batch_autotune (0 otherwise). */
 typedef struct fr_tile_config {
@@ -419,7 +421,7 @@ int fr_batch_set_targets(fr_batch* b, const float* targets, const uint8_t* masks
  * and grad_frames[F][Pf] (FP64, overwritten), images (packed, FP32).
  * Enqueued on the context stream; the first step with a configuration or
  * weights (w1, w2) not seen before captures the graph.  A device-side
- * traversal limit or a primary-edge wait that expired is reported by the
+ * traversal limit or an edge item's wait that expired is reported by the
  * next fr_sync (FR_ERR_DEVICE_LIMIT). */
 int fr_batch_step(fr_batch* b, const float* theta_shared, const float* theta_frames, float w1, float w2,
                   uint32_t iter, double* loss, double* grad_shared, double* grad_frames, float* images);

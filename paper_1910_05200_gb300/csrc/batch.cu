@@ -4,23 +4,31 @@
 // expression, pose and lights (a video of one face, or several crops); each
 // has its own crop size.  The launch is a work queue served by warps: every
 // warp takes items on its own (no block-wide barrier while items remain, so
-// a warp with cheap samples never waits for one with costly samples):
+// a warp with cheap samples never waits for one with costly samples).  The
+// queue holds three kinds of item, in this order:
 //   tile items       a tile of one frame, taken 32 samples at a time: forward
 //                    samples, the pixel means (image), the photo-consistency
 //                    loss and its adjoint d_image = 2 mask (image - target)
 //                    (Eq. 1 of the Optimization paragraph, per pixel), then the
-//                    interior adjoint and the shadow-edge term of the same
-//                    samples with their primary hits and the shadow
-//                    decisions of the lights that are on still in registers
-//                    (no re-trace when spp divides 32);
+//                    interior adjoint of the same samples with their primary
+//                    hits and the shadow decisions of the lights that are on
+//                    still in registers (no re-trace when spp divides 32).
+//                    Each sample's primary hit goes to the frame's hit array.
+//   shadow-edge items  (frame, light, chunk of samples): the shadow-boundary
+//                    term of one light for consecutive samples of the frame,
+//                    from the stored hits and d_image.  The items of one
+//                    light of one frame follow each other in the queue, so
+//                    the warps that run at the same time search the edge
+//                    hierarchy towards the same light, as the light-major
+//                    shadow-edge launches of the single-image path do.
 //   primary-edge items  a chunk of one frame's primary-edge samples; they
-//                    read d_image anywhere in the frame, so each waits until
-//                    the frame's tile items have all published theirs.
-// All tile items come before all primary-edge items in the queue and a warp
-// only takes an item when it is running, so every tile item a primary-edge
-// item waits for is held by a running warp that does not wait: the wait
-// ends.  It is bounded all the same (BatchArgs::wait_limit, fr_set_limits;
-// ERR_WAIT on expiry).
+//                    read d_image anywhere in the frame.
+// Edge items wait until all tile items of their frame have published their
+// hits and d_image.  All tile items come before all edge items in the queue
+// and a warp only takes an item when it is running, so every tile item an
+// edge item waits for is held by a running warp that does not wait: the
+// wait ends.  It is bounded all the same (BatchArgs::wait_limit,
+// fr_set_limits; ERR_WAIT on expiry).
 //
 // Samples, decisions and per-sample arithmetic are those of the single-image
 // kernels (same device functions, same Philox keys, the same warp-cooperative
@@ -28,7 +36,7 @@
 // frame up to FP32 rounding (the same formulas compiled in another kernel may
 // contract multiply-adds differently) and its gradient differs only in that
 // and the order of floating-point atomic additions.  spp a multiple of 32 takes each pixel in
-// two passes (radiance, then the adjoints with the primary hit traced again).
+// two passes (radiance, then the interior adjoint with the primary hit traced again).
 #include "render_device.cuh"
 
 namespace fr {
@@ -41,29 +49,6 @@ FR_DEV void flush_lights(WarpState& w, int lane) {
   for (int i = lane; i < 3 * MAX_LIGHTS; i += 32)
     if (w.sL[i] != 0.0f) { atomicAdd(&w.g.dL[i], w.sL[i]); w.sL[i] = 0.0f; }
   __syncwarp();
-}
-
-// Shading-point state of one sample for the adjoints.
-// vis: the forward's visibility bits of the sample, or null (traced again).
-FR_DEV void sample_adjoints(const RenderArgs& a, const GradBufs& g, float* sC, float* sL, bool valid, int px,
-                            int py, int s, int2 hit, V3 dv, unsigned long long* cnt, const uint32_t* vis = nullptr) {
-  uint32_t pix = 0;
-  V3 d{0, 0, -1}, x32{0, 0, 0}, wrgb{0, 0, 0};
-  int flip = 1;
-  valid = valid && hit.x >= 0 && (dv.x != 0.0f || dv.y != 0.0f || dv.z != 0.0f);
-  if (valid) {
-    d = sample_dir(a, px, py, s, pix);
-    wrgb = dv * (1.0f / (float)a.spp);
-    flip = face_flip(a.mesh, hit.x, d);
-    x32 = hit_point(a.cam.o, d, __int_as_float(hit.y));
-  }
-  // warp-collective from here: every lane takes part
-  interior_sample(a, g, sC, sL, pix, s, d, hit.x, __int_as_float(hit.y), dv, cnt ? cnt + CNT_INTERIOR : nullptr,
-                        vis, valid);
-  for (int j = 0; j < a.n_lights; ++j) {
-    if (!light_on(a, j)) continue;                 // uniform
-    sedge_pick_and_add(a, g, j, valid, d, x32, hit.x, flip, pix, s, wrgb, cnt ? cnt + CNT_SEDGE : nullptr);
-  }
 }
 
 // Loss and adjoint of pixel pix from its mean I: image and d_image written
@@ -84,28 +69,28 @@ FR_DEV V3 pixel_loss(const BatchFrame& F, size_t pix, V3 I, bool write, double& 
   return V3{dv[0], dv[1], dv[2]};
 }
 
+FR_DEV bool nonzero(V3 v) { return v.x != 0.0f || v.y != 0.0f || v.z != 0.0f; }
+
 // A tile item, spp dividing 32: chunks of 32 consecutive samples hold whole
 // pixels, so each pixel's mean is a shuffle reduction within the warp.
-FR_DEV void tile_small(WarpState& w, const BatchFrame& F, float* sC, int tile, int tw, int th, double& lacc,
+__device__ __noinline__ void tile_small(WarpState& w, const BatchFrame& F, float* sC, int tile, int tw, int th, double& lacc,
                        unsigned long long* cnt) {
   const RenderArgs& a = w.a;
   const int spp = a.spp, lane = threadIdx.x & 31;
   const int tx = tile % F.tiles_x, ty = tile / F.tiles_x;
   const int nS = tw * th * spp;
+  int2* hits = F.gb.hits + (long long)tile * nS;
   const float inv = 1.0f / (float)spp;
   for (int c0 = 0; c0 < nS; c0 += 32) {
     int k = c0 + lane;
     int ip = k / spp, s = k - ip * spp;
     int px = tx * tw + ip % tw, py = ty * th + ip / tw;
     bool valid = k < nS && px < a.W && py < a.H;
-    V3 L{0, 0, 0};
     int2 hit = make_int2(-1, 0);
     uint32_t pix = 0, vis = 0u;
-    {
-      V3 d = valid ? sample_dir(a, px, py, s, pix) : V3{0, 0, -1};
-      L = radiance(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt, nullptr, &hit, &vis, valid);
-      if (!valid) { hit = make_int2(-1, 0); vis = 0u; }
-    }
+    const V3 d = valid ? sample_dir(a, px, py, s, pix) : V3{0, 0, -1};
+    const V3 L = radiance(a, a.cam.o, d, TAG_LIGHT, pix, (uint32_t)s, cnt, nullptr, &hit, &vis, valid);
+    if (!valid) { hit = make_int2(-1, 0); vis = 0u; }
     float v0 = L.x, v1 = L.y, v2 = L.z;
     for (int off = spp >> 1; off > 0; off >>= 1) {
       v0 += __shfl_xor_sync(0xffffffffu, v0, off);
@@ -114,20 +99,29 @@ FR_DEV void tile_small(WarpState& w, const BatchFrame& F, float* sC, int tile, i
     }
     V3 dv{0, 0, 0};
     if (valid) dv = pixel_loss(F, pix, V3{v0 * inv, v1 * inv, v2 * inv}, s == 0, lacc);
-    sample_adjoints(a, w.g, sC, w.sL, valid, px, py, s, hit, dv, cnt, &vis);
+    const bool adj = valid && hit.x >= 0 && nonzero(dv);
+    if (k < nS) hits[k] = adj ? hit : make_int2(-1, 0);
+    // warp-collective: every lane takes part
+    interior_sample(a, w.g, sC, w.sL, pix, s, d, hit.x, __int_as_float(hit.y), dv,
+                    cnt ? cnt + CNT_INTERIOR : nullptr, &vis, adj);
   }
 }
 
 // A tile item, spp a multiple of 32: one pixel at a time, its samples in
-// chunks of 32; pass 1 sums the radiance, pass 2 runs the adjoints.
-FR_DEV void tile_large(WarpState& w, const BatchFrame& F, float* sC, int tile, int tw, int th, double& lacc,
+// chunks of 32; pass 1 sums the radiance, pass 2 runs the interior adjoint.
+__device__ __noinline__ void tile_large(WarpState& w, const BatchFrame& F, float* sC, int tile, int tw, int th, double& lacc,
                        unsigned long long* cnt) {
   const RenderArgs& a = w.a;
   const int spp = a.spp, lane = threadIdx.x & 31;
   const int tx = tile % F.tiles_x, ty = tile / F.tiles_x;
+  int2* hits = F.gb.hits + (long long)tile * tw * th * spp;
   for (int ip = 0; ip < tw * th; ++ip) {
     int px = tx * tw + ip % tw, py = ty * th + ip / tw;
-    if (!(px < a.W && py < a.H)) continue;                       // uniform
+    int2* hp = hits + (long long)ip * spp;
+    if (!(px < a.W && py < a.H)) {                               // uniform
+      for (int s = lane; s < spp; s += 32) hp[s] = make_int2(-1, 0);
+      continue;
+    }
     V3 acc{0, 0, 0};
     uint32_t pix = 0;
     for (int s = lane; s < spp; s += 32) {
@@ -141,14 +135,89 @@ FR_DEV void tile_large(WarpState& w, const BatchFrame& F, float* sC, int tile, i
     }
     const float inv = 1.0f / (float)spp;
     V3 dv = pixel_loss(F, (size_t)py * a.W + px, acc * inv, lane == 0, lacc);
-    if (dv.x == 0.0f && dv.y == 0.0f && dv.z == 0.0f) continue;  // uniform
+    if (!nonzero(dv)) {                                          // uniform
+      for (int s = lane; s < spp; s += 32) hp[s] = make_int2(-1, 0);
+      continue;
+    }
     for (int s = lane; s < spp; s += 32) {
       V3 d = sample_dir(a, px, py, s, pix);
       float t = 0.0f;
       int f = closest_hit_warp(a.mesh, true, a.cam.o, d, t, a.err, cnt ? cnt + CNT_INTERIOR : nullptr);
-      sample_adjoints(a, w.g, sC, w.sL, true, px, py, s, make_int2(f, __float_as_int(t)), dv, cnt);
+      hp[s] = f >= 0 ? make_int2(f, __float_as_int(t)) : make_int2(-1, 0);
+      interior_sample(a, w.g, sC, w.sL, pix, s, d, f, t, dv, cnt ? cnt + CNT_INTERIOR : nullptr, nullptr, f >= 0);
     }
   }
+}
+
+// The search and the contribution of a shadow-edge item, out of line: each
+// is register-allocated on its own, within the kernel's budget.
+__device__ __noinline__ Pick sedge_pick(const RenderArgs& a, bool valid, V3 x32, int f, int j, uint32_t pix, int s,
+                                        unsigned long long* cnt) {
+  return pick_light_warp(a, valid, x32, f, j, pix, s, cnt);
+}
+__device__ __noinline__ void sedge_add(const RenderArgs& a, const GradBufs& gb, int j, Pick P, V3 d, V3 x32, int f,
+                                       int flip, uint32_t pix, int s, V3 wrgb, unsigned long long* cnt, bool active) {
+  sedge_contribution(a, gb, j, P.n, P.slot, d, x32, f, flip, pix, s, wrgb, cnt, active);
+}
+
+// A shadow-edge item: light j for the samples [k0, k0 + len) of the frame,
+// in the tile items' sample order, 32 at a time (the same warps of samples
+// as the tile items).
+__device__ __noinline__ void sedge_item(const WarpState& w, const BatchFrame& F, int j, long long k0, int len, int tw, int th,
+                       unsigned long long* cnt) {
+  const RenderArgs& a = w.a;
+  const int spp = a.spp, lane = threadIdx.x & 31;
+  const int per_tile = tw * th * spp;
+  const long long n = (long long)F.n_tiles * per_tile;
+  const float inv = 1.0f / (float)spp;
+  for (int c = 0; c < len && k0 + c < n; c += 32) {              // uniform
+    const long long k = k0 + c + lane;
+    int2 hit = k < n ? F.gb.hits[k] : make_int2(-1, 0);
+    const bool valid = hit.x >= 0;
+    V3 d{0, 0, -1}, x32{0, 0, 0}, wrgb{0, 0, 0};
+    uint32_t pix = 0;
+    int flip = 1, s = 0;
+    if (valid) {
+      const int tile = (int)(k / per_tile), r = (int)(k - (long long)tile * per_tile), ip = r / spp;
+      s = r - ip * spp;
+      const int px = (tile % F.tiles_x) * tw + ip % tw, py = (tile / F.tiles_x) * th + ip / tw;
+      d = sample_dir(a, px, py, s, pix);
+      flip = face_flip(a.mesh, hit.x, d);
+      x32 = hit_point(a.cam.o, d, __int_as_float(hit.y));
+      const float* dI = F.d_image + 3 * (size_t)pix;
+      wrgb = V3{dI[0], dI[1], dI[2]} * inv;
+    }
+    // warp-collective: every lane takes part
+    const Pick P = sedge_pick(a, valid, x32, hit.x, j, pix, s, cnt ? cnt + CNT_SEDGE : nullptr);
+    if (__any_sync(0xffffffffu, valid && P.n > 0))                 // uniform
+      sedge_add(a, w.g, j, P, d, x32, hit.x, flip, pix, s, wrgb, cnt ? cnt + CNT_SEDGE : nullptr, valid && P.n > 0);
+  }
+}
+
+// A primary-edge item: edge samples [base, base + len) of the frame.
+__device__ __noinline__ void pedge_item(const WarpState& w, const BatchFrame& F, long long base, int len,
+                                        unsigned long long* cnt) {
+  for (int k = threadIdx.x & 31; k < len; k += 32) {
+    const long long t = base + k;
+    pedge_sample(w.a, w.g, t, cnt, t < F.n_pedge);              // warp-collective
+  }
+}
+
+// Bounded wait of an edge item until every tile item of frame fi has
+// published its hits and d_image.  Returns false when the wait ran out
+// (ERR_WAIT set; the item is skipped).
+FR_DEV bool wait_tiles(const BatchArgs& b, const BatchFrame& F, int fi) {
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0) {
+    const volatile int* done = b.tiles_done + fi;
+    int tries = 0;
+    while (*done < F.n_tiles) {
+      if (++tries > b.wait_limit) { atomicOr(b.err, ERR_WAIT); ok = 0; break; }
+      __nanosleep(256);
+    }
+    __threadfence();
+  }
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
 }  // namespace
@@ -169,8 +238,8 @@ FR_DEV void batch_step_body(const BatchArgs& b) {
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= b.n_items) break;
     const int2 it = b.items[item];
-    const bool is_pedge = (it.x & PEDGE_ITEM) != 0;
-    const int fi = it.x & ~PEDGE_ITEM;
+    const bool is_pedge = (it.x & PEDGE_ITEM) != 0, is_sedge = (it.x & SEDGE_ITEM) != 0;
+    const int fi = it.x & ~(PEDGE_ITEM | SEDGE_ITEM);
     const BatchFrame& F = b.frames[fi];
     if (fi != cur) {
       if (cur >= 0) flush_lights(w, lane);
@@ -185,12 +254,12 @@ FR_DEV void batch_step_body(const BatchArgs& b) {
       __syncwarp();
       cur = fi;
     }
-    if (!is_pedge) {
+    if (!is_pedge && !is_sedge) {
       double lacc = 0.0;
       if (w.a.spp <= 32) tile_small(w, F, sC, it.y, b.tile_w, b.tile_h, lacc, b.counters);
       else tile_large(w, F, sC, it.y, b.tile_w, b.tile_h, lacc, b.counters);
       for (int off = 16; off > 0; off >>= 1) lacc += __shfl_xor_sync(0xffffffffu, lacc, off);
-      // publish the tile's d_image to the frame's primary-edge items
+      // publish the tile's hits and d_image to the frame's edge items
       __threadfence();
       __syncwarp();
       if (lane == 0) {
@@ -199,26 +268,16 @@ FR_DEV void batch_step_body(const BatchArgs& b) {
       }
       continue;
     }
-    // primary-edge item: wait (bounded) until every tile of the frame has
-    // published its d_image
-    int skip = 0;
-    if (lane == 0) {
-      const volatile int* done = b.tiles_done + fi;
-      int tries = 0;
-      while (*done < F.n_tiles) {
-        if (++tries > b.wait_limit) { atomicOr(b.err, ERR_WAIT); skip = 1; break; }
-        __nanosleep(256);
-      }
-      __threadfence();
+    if (is_sedge) {
+      const int j = it.y & (SEDGE_LIGHTS - 1);
+      if (!light_on(w.a, j)) continue;                             // uniform: no wait for a light that is off
+      if (!wait_tiles(b, F, fi)) continue;
+      sedge_item(w, F, j, (long long)(it.y >> SEDGE_LIGHT_BITS) * b.sedge_chunk, b.sedge_chunk, b.tile_w,
+                 b.tile_h, b.counters);
+      continue;
     }
-    skip = __shfl_sync(0xffffffffu, skip, 0);
-    if (skip) continue;
-    const long long base = (long long)it.y * b.pedge_chunk;
-    unsigned long long* cnt_p = b.counters ? b.counters + CNT_PEDGE : nullptr;
-    for (int k = lane; k < b.pedge_chunk; k += 32) {
-      long long t = base + k;
-      pedge_sample(w.a, w.g, t, cnt_p, t < F.n_pedge);
-    }
+    if (!wait_tiles(b, F, fi)) continue;
+    pedge_item(w, F, (long long)it.y * b.pedge_chunk, b.pedge_chunk, b.counters ? b.counters + CNT_PEDGE : nullptr);
   }
   if (cur >= 0) flush_lights(w, lane);
   __syncthreads();

@@ -42,7 +42,8 @@ struct fr_batch {
   std::vector<long long> hit_off;      // first hit slot of each frame
   DBuf<uint32_t> iter_dev;
   int n_items = 0;
-  int pedge_chunk = 1024;
+  int pedge_chunk = 32;
+  int sedge_chunk = 32;
   fr_tile_config cfg{8, 8, 256, 4, 0, 0.0f};
   bool configured = false;
   // graph of one step
@@ -131,6 +132,20 @@ int configure(fr_batch* b) {
   });
   std::vector<BatchFrame> tab(b->nF);
   std::vector<int2> items;
+  // primary hits, per frame in the sample order of the launch mode: 8x8
+  // tiles (phased) or the tile items' order (persistent); each frame's slots
+  // start on a 128-byte line
+  long long nh = 0;
+  for (int f = 0; f < b->nF; ++f) {
+    const fr_frame& q = b->frames[f];
+    b->hit_off[f] = nh;
+    const long long n = c.fused ? (long long)((q.W + c.tile_w - 1) / c.tile_w) * ((q.H + c.tile_h - 1) / c.tile_h) *
+                                      c.tile_w * c.tile_h * b->spp
+                                : (long long)((q.W + 7) / 8) * ((q.H + 7) / 8) * 64 * b->spp;
+    nh += (n + 15) & ~15LL;
+  }
+  if (c.fused || 256 % b->spp == 0)
+    if (b->hits.n < (size_t)nh) CK(b->hits.alloc((size_t)nh));
   for (int f = 0; f < b->nF; ++f) {
     const fr_frame& fr_ = b->frames[f];
     fr_render_opts o{fr_.W, fr_.H, b->spp, fr_.seed, 0u, 0};
@@ -152,6 +167,14 @@ int configure(fr_batch* b) {
   }
   for (int f : order)
     for (int t = 0; t < tab[f].n_tiles; ++t) items.push_back(make_int2(f, t));
+  if (c.fused)
+    for (int f : order) {
+      const long long n = (long long)tab[f].n_tiles * c.tile_w * c.tile_h * b->spp;
+      const long long nc = (n + b->sedge_chunk - 1) / b->sedge_chunk;
+      if (nc >= (1LL << (30 - SEDGE_LIGHT_BITS))) return fail(ctx, FR_ERR_INVALID_ARG, "frame too large for one launch");
+      for (int j = 0; j < ctx->cfg.n_lights; ++j)
+        for (long long k = 0; k < nc; ++k) items.push_back(make_int2(f | SEDGE_ITEM, (int)(k << SEDGE_LIGHT_BITS) | j));
+    }
   for (int f : order) {
     long long nc = (tab[f].n_pedge + b->pedge_chunk - 1) / b->pedge_chunk;
     for (long long k = 0; k < nc; ++k) items.push_back(make_int2(f | PEDGE_ITEM, (int)k));
@@ -224,6 +247,7 @@ int enqueue_step(fr_batch* b, float w1, float w2) {
     BatchArgs a;
     a.frames = b->dframes.p; a.items = b->items.p; a.n_items = b->n_items;
     a.tile_w = b->cfg.tile_w; a.tile_h = b->cfg.tile_h; a.pedge_chunk = b->pedge_chunk;
+    a.sedge_chunk = b->sedge_chunk;
     a.queue = b->queue.p; a.tiles_done = b->tiles_done.p; a.iter = b->iter_dev.p; a.err = ctx->err_flag.p;
     a.counters = counters;
     a.max_steps = ctx->max_steps; a.wait_limit = ctx->wait_limit;
@@ -384,14 +408,8 @@ int fr_batch_create(fr_ctx* ctx, const fr_frame* frames, int32_t n_frames, int32
   BK(b->grad_full.alloc(nF * b->P)); BK(b->loss_frames.alloc(nF)); BK(b->loss.alloc(1));
   BK(b->grad_s.alloc(b->Ps)); BK(b->grad_f.alloc(nF * b->Pf));
   BK(b->queue.alloc(1)); BK(b->tiles_done.alloc(nF)); BK(b->iter_dev.alloc(1));
-  // primary hits of the phased launches: each frame's samples in 8x8-tile order
+  // primary hits: sized for the launch mode when a configuration is set up
   b->hit_off.resize(n_frames);
-  long long nh = 0;
-  for (int f = 0; f < n_frames; ++f) {
-    b->hit_off[f] = nh;
-    nh += (long long)((frames[f].W + 7) / 8) * ((frames[f].H + 7) / 8) * 64 * spp;
-  }
-  BK(b->hits.alloc(256 % spp == 0 ? (size_t)nh : 0));
   // BVH boxes start as the context's (child codes and empty children are
   // fixed by the topology; refits rewrite the rest)
   for (size_t f = 0; f < nF; ++f) {

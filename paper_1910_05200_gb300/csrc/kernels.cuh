@@ -107,7 +107,8 @@ struct GradBufs {
 // frame plus its image, adjoint, target and loss slots (device table).
 struct BatchFrame {
   RenderArgs a;           // a.iter is replaced by *BatchArgs::iter
-  GradBufs gb;            // gb.d_image is this frame's adjoint; gb.hits unused
+  GradBufs gb;            // gb.d_image is this frame's adjoint; gb.hits its samples' primary hits, in the
+                          // sample order of the launch mode (8x8 tiles phased, tile items persistent)
   float* image;           // [H*W*3]
   float* d_image;         // [H*W*3], written by the frame's tile items
   const float* target;    // [H*W*3]
@@ -117,10 +118,16 @@ struct BatchFrame {
   long long n_pedge;      // primary-edge samples: W*H*spp
 };
 
-// Work items of the persistent kernel: tile items (frame, tile) first, then
-// primary-edge items (frame | PEDGE_ITEM, chunk), each group in frame order.
+// Work items of the persistent kernel, in queue order: tile items (frame,
+// tile), then shadow-edge items (frame | SEDGE_ITEM, chunk << SEDGE_LIGHT_BITS
+// | light) light-major within each frame, then primary-edge items (frame |
+// PEDGE_ITEM, chunk); frames in the same order in each group.
 constexpr int PEDGE_ITEM = 1 << 30;
-// Default spin limit of a primary-edge item waiting for its frame's tiles
+constexpr int SEDGE_ITEM = 1 << 29;
+constexpr int SEDGE_LIGHT_BITS = 5;
+constexpr int SEDGE_LIGHTS = 1 << SEDGE_LIGHT_BITS;
+static_assert(MAX_LIGHTS <= SEDGE_LIGHTS, "a light index must fit the shadow-edge item's light bits");
+// Default spin limit of an edge item waiting for its frame's tiles
 // (__nanosleep(256) per try: about a second); fr_set_limits changes it.
 constexpr int DEFAULT_WAIT_LIMIT = 1 << 22;
 
@@ -130,13 +137,14 @@ struct BatchArgs {
   int n_items;
   int tile_w, tile_h;     // pixels per tile item
   int pedge_chunk;        // edge samples per primary-edge item
+  int sedge_chunk;        // camera samples per shadow-edge item (a multiple of 32)
   int* queue;             // next item, zeroed before the launch
   int* tiles_done;        // [n_frames], zeroed before the launch
   const uint32_t* iter;
   int* err;
   unsigned long long* counters;  // [CNT_TOTAL] or null, same layout as the single-image kernels
   int max_steps;          // traversal step cap of every frame
-  int wait_limit;         // tries of a primary-edge item waiting for its frame's tiles
+  int wait_limit;         // tries of an edge item waiting for its frame's tiles
 };
 
 // Phase kernels of a batch (one launch per phase for all frames): block b of

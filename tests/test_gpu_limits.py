@@ -2,8 +2,8 @@
 
 Each limit is made to run out through fr_set_limits: a traversal step cap of
 one node visit (every ray and every edge search stops at once) and a batch
-wait limit of zero tries (a primary-edge item of the persistent batch kernel
-that finds its frame's tiles unfinished gives up at once).  Both are
+wait limit of zero tries (an edge item of the persistent batch kernel that
+finds its frame's tiles unfinished gives up at once).  Both are
 host-visible error returns: nothing faults and nothing spins.  The test then
 checks that the flag clears and that the next call with the default limits
 gives the same results as before.
@@ -52,8 +52,8 @@ def test_traversal_step_cap_is_reported(fr, tiny):
 
 def test_batch_wait_limit_is_reported(fr, tiny):
     """One 64 x 64 frame in the persistent kernel: its 64 tile items go to the
-    first 64 warps, and the next warps take primary-edge items while the tiles
-    still render; with a wait limit of zero those items stop at once."""
+    first 64 warps, and the next warps take edge items while the tiles still
+    render; with a wait limit of zero those items stop at once."""
     scene, _, _ = tiny
     r = fr.Renderer(scene, device=0)
     frames, thetas = S.make_batch(scene, n_frames=1, seed=9, n_on=8, max_angle_deg=10.0, t_std=0.02,
