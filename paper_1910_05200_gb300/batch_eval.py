@@ -4,7 +4,8 @@ all frames in phased launches or one persistent launch, geometry adjoints).
 
 Reports the autotuner's table (tuned on 8 of the frames, every fourth by
 size, so that the sweep stays short), the step time and throughput of the
-full batch with the chosen and the default configuration, and the same
+full batch with the chosen and the default configuration and with the
+fastest configuration of each launch mode (phased, persistent), and the same
 frames processed one by one through fr_render / fr_loss /
 fr_render_backward.  Targets are the batch's own renders of other
 parameters (seed + 1).
@@ -67,6 +68,13 @@ def run(steps=5, reps=1, device=0):
     b, ts, tf = _batch(r, frames, thetas, spp, target_thetas)
     default = b.config()
     ms_default = _timed(lambda i: b.step(ts, tf, 0.02, 0.002, iter=i, images=False), steps)
+    # the fastest configuration of each launch mode on the full batch
+    by_mode = {}
+    for fused, mode in ((0, "phased"), (1, "persistent")):
+        best = min((t for t in table if t["fused"] == fused), key=lambda t: t["ms"])
+        b.set_config(best["tile_w"], best["tile_h"], best["block"], best["min_blocks"], fused)
+        by_mode[mode] = dict(config=best, ms_per_step=_timed(
+            lambda i: b.step(ts, tf, 0.02, 0.002, iter=i, images=False), steps))
     b.set_config(chosen["tile_w"], chosen["tile_h"], chosen["block"], chosen["min_blocks"], chosen["fused"])
     l0 = r.launches()
     ms = _timed(lambda i: b.step(ts, tf, 0.02, 0.002, iter=i, images=False), steps)
@@ -105,6 +113,7 @@ def run(steps=5, reps=1, device=0):
         "autotune": {"frames": len(sub), "reps": reps, "table": table, "chosen": chosen},
         "default_config": default,
         "ms_per_step_default": ms_default,
+        "full_batch_by_mode": by_mode,
         "ms_per_step": ms,
         "msamples_per_s": samples / ms / 1e3,
         "kernels_per_step": kernels_per_step,
