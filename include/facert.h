@@ -407,6 +407,26 @@ int32_t fr_batch_n_frame(const fr_ctx* ctx);
  * a frame with W, H < 1,
  * more than 2^31 - 1 samples in a frame, or spp that neither divides 32 nor
  * is a multiple of 32. */
+/* The work-item list of the persistent launch (fused = 1) for frames
+ * [n_frames] at spp with tiles of tile_w x tile_h pixels and n_lights
+ * lights, in queue order.  Host only: no context, no GPU.  Item i is
+ * (items[2i], items[2i+1]) = (x, y):
+ *   x = f (frame index): a tile item, y = its tile (row-major, tiles of
+ *     the frame's W x H pixels);
+ *   x = f | 1 << 29: a shadow-edge item, y = k << 5 | j: light j, samples
+ *     [32 k, 32 k + 32) of the frame's samples in tile order (tile, then
+ *     pixel row-major within the tile, then sample);
+ *   x = f | 1 << 30: a primary-edge item, y = k: the frame's primary-edge
+ *     samples [32 k, 32 k + 32).
+ * All tile items come first, then the shadow-edge items (light-major within
+ * each frame), then the primary-edge items; frames with more pixels first
+ * within each group.  Writes min(cap, length) items (cap >= 0; items may be
+ * NULL when cap = 0) and the length to *n_out.  FR_ERR_INVALID_ARG for the
+ * arguments fr_batch_create or fr_batch_set_config refuses, or for a list
+ * beyond the queue's range. */
+int fr_batch_plan(const fr_frame* frames, int32_t n_frames, int32_t spp, int32_t tile_w, int32_t tile_h,
+                  int32_t n_lights, int32_t* items, int64_t cap, int64_t* n_out);
+
 int fr_batch_create(fr_ctx* ctx, const fr_frame* frames, int32_t n_frames, int32_t spp, fr_batch** out);
 void fr_batch_destroy(fr_batch* b);
 

@@ -42,8 +42,6 @@ struct fr_batch {
   std::vector<long long> hit_off;      // first hit slot of each frame
   DBuf<uint32_t> iter_dev;
   int n_items = 0;
-  int pedge_chunk = 32;
-  int sedge_chunk = 32;
   fr_tile_config cfg{8, 8, 256, 4, 0, 0.0f};
   bool configured = false;
   // graph of one step
@@ -118,20 +116,53 @@ int check_config(fr_batch* b, const fr_tile_config& c, int* blocks_per_sm) {
   return FR_OK;
 }
 
+// The persistent kernel's work items (encoding in kernels.cuh): all tile
+// items, then the shadow-edge items light-major within each frame, then the
+// primary-edge items.  Frames with more pixels come first in each group:
+// their items start early and the tail of the queue holds small items.
+// Returns null on success, else why the list does not fit its encoding.
+const char* plan_items(const fr_frame* frames, int nF, int spp, int tw, int th, int n_lights,
+                       std::vector<int2>& items) {
+  items.clear();
+  std::vector<int> order(nF);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return (long long)frames[x].W * frames[x].H > (long long)frames[y].W * frames[y].H;
+  });
+  auto n_tiles = [&](int f) {
+    return (long long)((frames[f].W + tw - 1) / tw) * ((frames[f].H + th - 1) / th);
+  };
+  long long total = 0;
+  for (int f = 0; f < nF; ++f) {
+    const long long nc = (n_tiles(f) * tw * th * spp + BATCH_SEDGE_CHUNK - 1) / BATCH_SEDGE_CHUNK;
+    const long long np = ((long long)frames[f].W * frames[f].H * spp + BATCH_PEDGE_CHUNK - 1) / BATCH_PEDGE_CHUNK;
+    if (n_tiles(f) > INT32_MAX || nc >= (1LL << (30 - SEDGE_LIGHT_BITS)) || np > INT32_MAX)
+      return "frame too large for one launch";
+    total += n_tiles(f) + nc * n_lights + np;
+  }
+  if (total > INT32_MAX / 2) return "too many work items";
+  items.reserve((size_t)total);
+  for (int f : order)
+    for (long long t = 0; t < n_tiles(f); ++t) items.push_back(make_int2(f, (int)t));
+  for (int f : order) {
+    const long long nc = (n_tiles(f) * tw * th * spp + BATCH_SEDGE_CHUNK - 1) / BATCH_SEDGE_CHUNK;
+    for (int j = 0; j < n_lights; ++j)
+      for (long long k = 0; k < nc; ++k) items.push_back(make_int2(f | SEDGE_ITEM, (int)(k << SEDGE_LIGHT_BITS) | j));
+  }
+  for (int f : order) {
+    const long long np = ((long long)frames[f].W * frames[f].H * spp + BATCH_PEDGE_CHUNK - 1) / BATCH_PEDGE_CHUNK;
+    for (long long k = 0; k < np; ++k) items.push_back(make_int2(f | PEDGE_ITEM, (int)k));
+  }
+  return nullptr;
+}
+
 // Frame table and work items for the current configuration (host -> device,
 // synchronous: never inside a capture).
 int configure(fr_batch* b) {
   fr_ctx* ctx = b->ctx;
   const fr_tile_config& c = b->cfg;
-  // frames with more pixels first: their items start early and the tail
-  // of the queue holds small items
-  std::vector<int> order(b->nF);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-    return (long long)b->frames[x].W * b->frames[x].H > (long long)b->frames[y].W * b->frames[y].H;
-  });
   std::vector<BatchFrame> tab(b->nF);
-  std::vector<int2> items;
+  std::vector<int2> items;       // the persistent kernel's; the phased launches take none
   // primary hits, per frame in the sample order of the launch mode: 8x8
   // tiles (phased) or the tile items' order (persistent); each frame's slots
   // start on a 128-byte line
@@ -165,21 +196,10 @@ int configure(fr_batch* b) {
     T.n_tiles = T.tiles_x * ((fr_.H + c.tile_h - 1) / c.tile_h);
     T.n_pedge = (long long)fr_.W * fr_.H * b->spp;
   }
-  for (int f : order)
-    for (int t = 0; t < tab[f].n_tiles; ++t) items.push_back(make_int2(f, t));
-  if (c.fused)
-    for (int f : order) {
-      const long long n = (long long)tab[f].n_tiles * c.tile_w * c.tile_h * b->spp;
-      const long long nc = (n + b->sedge_chunk - 1) / b->sedge_chunk;
-      if (nc >= (1LL << (30 - SEDGE_LIGHT_BITS))) return fail(ctx, FR_ERR_INVALID_ARG, "frame too large for one launch");
-      for (int j = 0; j < ctx->cfg.n_lights; ++j)
-        for (long long k = 0; k < nc; ++k) items.push_back(make_int2(f | SEDGE_ITEM, (int)(k << SEDGE_LIGHT_BITS) | j));
-    }
-  for (int f : order) {
-    long long nc = (tab[f].n_pedge + b->pedge_chunk - 1) / b->pedge_chunk;
-    for (long long k = 0; k < nc; ++k) items.push_back(make_int2(f | PEDGE_ITEM, (int)k));
+  if (c.fused) {
+    const char* why = plan_items(b->frames.data(), b->nF, b->spp, c.tile_w, c.tile_h, ctx->cfg.n_lights, items);
+    if (why) return fail(ctx, FR_ERR_INVALID_ARG, "%s", why);
   }
-  if (items.size() > (size_t)INT32_MAX / 2) return fail(ctx, FR_ERR_INVALID_ARG, "too many work items");
   // block tables of the phased launches (256 threads per block)
   std::vector<int> sf(b->nF + 1), ss(b->nF + 1), sp(b->nF + 1);
   long long nf = 0, ns = 0, np = 0;
@@ -202,7 +222,7 @@ int configure(fr_batch* b) {
   CK(b->dframes.alloc(tab.size()));
   CK(b->items.alloc(items.size()));
   CK(cudaMemcpy(b->dframes.p, tab.data(), sizeof(BatchFrame) * tab.size(), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(b->items.p, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice));
+  if (!items.empty()) CK(cudaMemcpy(b->items.p, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice));
   CK(b->bs_fwd.alloc(b->nF + 1));
   CK(b->bs_sedge.alloc(b->nF + 1));
   CK(b->bs_pedge.alloc(b->nF + 1));
@@ -246,8 +266,8 @@ int enqueue_step(fr_batch* b, float w1, float w2) {
   if (b->cfg.fused) {
     BatchArgs a;
     a.frames = b->dframes.p; a.items = b->items.p; a.n_items = b->n_items;
-    a.tile_w = b->cfg.tile_w; a.tile_h = b->cfg.tile_h; a.pedge_chunk = b->pedge_chunk;
-    a.sedge_chunk = b->sedge_chunk;
+    a.tile_w = b->cfg.tile_w; a.tile_h = b->cfg.tile_h; a.pedge_chunk = BATCH_PEDGE_CHUNK;
+    a.sedge_chunk = BATCH_SEDGE_CHUNK;
     a.queue = b->queue.p; a.tiles_done = b->tiles_done.p; a.iter = b->iter_dev.p; a.err = ctx->err_flag.p;
     a.counters = counters;
     a.max_steps = ctx->max_steps; a.wait_limit = ctx->wait_limit;
@@ -353,6 +373,26 @@ extern "C" {
 
 int32_t fr_batch_n_shared(const fr_ctx* ctx) { return ctx ? ctx->K_id + ctx->K_alb + CS * CS : FR_ERR_INVALID_ARG; }
 int32_t fr_batch_n_frame(const fr_ctx* ctx) { return ctx ? ctx->K_exp + 6 + 3 * ctx->cfg.n_lights : FR_ERR_INVALID_ARG; }
+
+int fr_batch_plan(const fr_frame* frames, int32_t n_frames, int32_t spp, int32_t tile_w, int32_t tile_h,
+                  int32_t n_lights, int32_t* items, int64_t cap, int64_t* n_out) {
+  if (!frames || n_frames < 1 || n_frames > 4096 || !n_out || cap < 0 || (cap > 0 && !items))
+    return FR_ERR_INVALID_ARG;
+  if (spp < 1 || (spp < 32 && 32 % spp) || (spp > 32 && spp % 32)) return FR_ERR_INVALID_ARG;
+  if (tile_w < 1 || tile_h < 1 || tile_w > 64 || tile_h > 64 || n_lights < 1 || n_lights > MAX_LIGHTS)
+    return FR_ERR_INVALID_ARG;
+  for (int f = 0; f < n_frames; ++f) {
+    const fr_frame& q = frames[f];
+    if (q.W < 1 || q.H < 1 || (long long)q.W * q.H > (1LL << 26) || (long long)q.W * q.H * spp > (1LL << 31) - 1)
+      return FR_ERR_INVALID_ARG;
+  }
+  std::vector<int2> v;
+  if (plan_items(frames, n_frames, spp, tile_w, tile_h, n_lights, v)) return FR_ERR_INVALID_ARG;
+  *n_out = (int64_t)v.size();
+  const size_t n = std::min<size_t>(v.size(), (size_t)cap);
+  for (size_t i = 0; i < n; ++i) { items[2 * i] = v[i].x; items[2 * i + 1] = v[i].y; }
+  return FR_OK;
+}
 
 int fr_batch_create(fr_ctx* ctx, const fr_frame* frames, int32_t n_frames, int32_t spp, fr_batch** out) {
   if (!ctx || !out) return FR_ERR_INVALID_ARG;

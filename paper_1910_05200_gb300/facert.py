@@ -51,7 +51,8 @@ EXPORTS = ["fr_default_config", "fr_create", "fr_destroy", "fr_set_stream", "fr_
            "fr_launch_count", "fr_denoiser_n_weights", "fr_denoiser_set_weights", "fr_denoiser_get_weights",
            "fr_denoise", "fr_denoiser_train_step", "fr_denoiser_get_grad", "fr_adam_step",
            "fr_batch_n_shared", "fr_batch_n_frame", "fr_batch_create", "fr_batch_destroy", "fr_batch_set_targets",
-           "fr_batch_step", "fr_batch_autotune", "fr_batch_get_config", "fr_batch_set_config", "fr_probe_peaks",
+           "fr_batch_step", "fr_batch_autotune", "fr_batch_get_config", "fr_batch_set_config", "fr_batch_plan",
+           "fr_probe_peaks",
            "fr_set_limits", "fr_silhouettes"]
 
 
@@ -130,6 +131,7 @@ def load(path: str | None = None):
     L.fr_batch_autotune.argtypes = [vp, vp, vp, i32, vp, i32, C.POINTER(i32)]
     L.fr_batch_get_config.argtypes = [vp, vp]
     L.fr_batch_set_config.argtypes = [vp, vp]
+    L.fr_batch_plan.argtypes = [vp, i32, i32, i32, i32, i32, vp, C.c_int64, C.POINTER(C.c_int64)]
     _LIB = L
     return L
 
@@ -473,6 +475,24 @@ class Batch:
     def set_config(self, tile_w=8, tile_h=8, block=256, min_blocks=4, fused=0):
         c = FrTileConfig(int(tile_w), int(tile_h), int(block), int(min_blocks), int(fused), 0.0)
         self.r._check(self.lib.fr_batch_set_config(self.h, C.byref(c)), "fr_batch_set_config")
+
+
+def batch_plan(frames, spp, tile_w, tile_h, n_lights=20):
+    """Work items of the persistent batch launch, in queue order (fr_batch_plan;
+    host only): an int32 array [n, 2] of (x, y) pairs."""
+    L = load()
+    frames = [(int(w), int(h), int(sd)) for w, h, sd in frames]
+    arr = (FrFrame * len(frames))(*[FrFrame(w, h, sd) for w, h, sd in frames])
+    n = C.c_int64(0)
+    args = (C.cast(arr, C.c_void_p), len(frames), int(spp), int(tile_w), int(tile_h), int(n_lights))
+    rc = L.fr_batch_plan(*args, None, 0, C.byref(n))
+    if rc:
+        raise RuntimeError(f"fr_batch_plan: {FR_ERRORS.get(rc, rc)}")
+    out = np.zeros((n.value, 2), np.int32)
+    rc = L.fr_batch_plan(*args, out.ctypes.data_as(C.c_void_p), n.value, C.byref(n))
+    if rc:
+        raise RuntimeError(f"fr_batch_plan: {FR_ERRORS.get(rc, rc)}")
+    return out
 
 
 def split_theta(theta, K=(80, 90, 80), n_lights=20):

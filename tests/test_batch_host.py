@@ -1,6 +1,7 @@
 """Host-side logic of batched frames: the seeded frame recipe and the split of
 the parameter vector into shared and per-frame parts (no GPU)."""
 import numpy as np
+import pytest
 
 from paper_1910_05200_gb300 import facert
 from paper_1910_05200_gb300 import synthetic as S
@@ -39,3 +40,55 @@ def test_noise_images_packing():
     frames = [(3, 2, 0), (5, 4, 1)]
     t = S.noise_images(frames, seed=1)
     assert t.shape == (26, 3) and t.dtype == np.float32 and t.min() >= 0 and t.max() <= 0.5
+
+
+SEDGE, PEDGE = 1 << 29, 1 << 30
+
+
+def _check_plan(frames, spp, tw, th, n_lights):
+    it = facert.batch_plan(frames, spp, tw, th, n_lights)
+    x, y = it[:, 0], it[:, 1]
+    kind = np.where(x & PEDGE, 2, np.where(x & SEDGE, 1, 0))
+    f = x & ~(PEDGE | SEDGE)
+    assert np.all(y >= 0) and np.all((f >= 0) & (f < len(frames)))
+    # tile items, then shadow-edge items, then primary-edge items: every item
+    # an edge item waits for (its frame's tiles) is ahead of it in the queue
+    assert np.all(np.diff(kind) >= 0) and set(kind.tolist()) == {0, 1, 2}
+    area = [w * h for w, h, _ in frames]
+    order = sorted(range(len(frames)), key=lambda i: -area[i])      # stable: larger frames first
+    for k in range(3):
+        seq = f[kind == k]
+        firsts = [int(v) for i, v in enumerate(seq) if i == 0 or seq[i - 1] != v]
+        assert firsts == order, (k, firsts, order)                   # each frame's items contiguous, in order
+    for i, (w, h, _) in enumerate(frames):
+        n_tiles = -(-w // tw) * -(-h // th)
+        assert sorted(y[(kind == 0) & (f == i)].tolist()) == list(range(n_tiles))
+        nc = -(-(n_tiles * tw * th * spp) // 32)
+        ys = y[(kind == 1) & (f == i)]
+        jk = [(int(v) & 31, int(v) >> 5) for v in ys]
+        assert jk == [(j, c) for j in range(n_lights) for c in range(nc)]   # light-major, each chunk once
+        npe = -(-(w * h * spp) // 32)
+        assert y[(kind == 2) & (f == i)].tolist() == list(range(npe))
+    return it
+
+
+def test_persistent_plan_order_and_coverage():
+    """The persistent launch's work items (fr_batch_plan, host only): every
+    tile, every (light, 32-sample chunk) and every primary-edge chunk of each
+    frame exactly once; tile items before all edge items, which the bounded
+    waits of the edge items rely on to end; shadow-edge items light-major."""
+    frames = [(40, 24, 1), (17, 33, 2), (64, 64, 3), (8, 5, 4), (17, 33, 5)]
+    _check_plan(frames, 4, 2, 2, 20)
+    _check_plan(frames, 16, 5, 3, 14)
+    _check_plan(frames, 64, 4, 4, 3)        # spp a multiple of 32
+    one = _check_plan([(3, 2, 0)], 1, 4, 4, 1)     # one tile of 16 tile-order samples: one chunk each
+    assert one.tolist() == [[0, 0], [SEDGE, 0], [PEDGE, 0]]
+
+
+def test_persistent_plan_refusals():
+    ok = [(16, 16, 0)]
+    for args in [(ok, 3, 2, 2, 20), (ok, 48, 2, 2, 20), (ok, 4, 0, 2, 20), (ok, 4, 2, 65, 20), (ok, 4, 2, 2, 0),
+                 (ok, 4, 2, 2, 33), ([(0, 16, 0)], 4, 2, 2, 20), ([(8192, 8193, 0)], 1, 2, 2, 20),
+                 ([(8192, 8192, 0)], 16, 1, 1, 20)]:          # the last: too many chunks for the item encoding
+        with pytest.raises(RuntimeError, match="invalid argument"):
+            facert.batch_plan(*args)
