@@ -427,6 +427,18 @@ int32_t fr_batch_n_frame(const fr_ctx* ctx);
 int fr_batch_plan(const fr_frame* frames, int32_t n_frames, int32_t spp, int32_t tile_w, int32_t tile_h,
                   int32_t n_lights, int32_t* items, int64_t cap, int64_t* n_out);
 
+/* A batch of frames[n_frames] (1..4096; W, H >= 1, W H <= 2^26 and
+ * W H spp < 2^31 each) at spp samples per pixel (dividing 32, or a multiple
+ * of 32) for the context's current mesh and bases; *out owns every
+ * per-frame buffer, allocated here.  The buffers that depend on the launch
+ * configuration (primary hits, shadow-edge picks, the persistent launch's
+ * work list) are sized at the first step with that configuration.
+ * FR_ERR_NOT_READY before the mesh and bases are uploaded,
+ * FR_ERR_INVALID_ARG for sizes out of range, FR_ERR_OOM when device memory
+ * runs out (nothing is kept).  A batch is tied to the mesh and bases it was
+ * created for: after a new upload fr_batch_step and fr_batch_autotune fail
+ * with FR_ERR_NOT_READY.
+ * fr_batch_destroy frees it (NULL is ignored). */
 int fr_batch_create(fr_ctx* ctx, const fr_frame* frames, int32_t n_frames, int32_t spp, fr_batch** out);
 void fr_batch_destroy(fr_batch* b);
 
