@@ -394,19 +394,13 @@ typedef struct fr_tile_config {
   float ms;
 } fr_tile_config;
 
+/* Ps = K_id + K_alb + 32*32, the length of theta_shared and grad_shared, and
+ * Pf = K_exp + 6 + 3N, the length of one frame's theta_frames and
+ * grad_frames row, for the context's bases and lights (FR_ERR_INVALID_ARG
+ * for a null context). */
 int32_t fr_batch_n_shared(const fr_ctx* ctx);
 int32_t fr_batch_n_frame(const fr_ctx* ctx);
 
-/* Create a batch of n_frames frames (frames: host array) at spp samples per
- * pixel on a context with mesh and bases uploaded.  Allocates every buffer
- * the steps use (about 30 MB per frame for a 35,709-vertex mesh plus the
- * images).  *out receives the batch; it must be destroyed before its
- * context.  The batch is sized for the context's current mesh and bases:
- * after a later fr_upload_mesh or fr_upload_bases its steps fail with
- * FR_ERR_NOT_READY (create a new batch).  FR_ERR_INVALID_ARG for n_frames < 1,
- * a frame with W, H < 1,
- * more than 2^31 - 1 samples in a frame, or spp that neither divides 32 nor
- * is a multiple of 32. */
 /* The work-item list of the persistent launch (fused = 1) for frames
  * [n_frames] at spp with tiles of tile_w x tile_h pixels and n_lights
  * lights, in queue order.  Host only: no context, no GPU.  Item i is
@@ -427,18 +421,20 @@ int32_t fr_batch_n_frame(const fr_ctx* ctx);
 int fr_batch_plan(const fr_frame* frames, int32_t n_frames, int32_t spp, int32_t tile_w, int32_t tile_h,
                   int32_t n_lights, int32_t* items, int64_t cap, int64_t* n_out);
 
-/* A batch of frames[n_frames] (1..4096; W, H >= 1, W H <= 2^26 and
- * W H spp < 2^31 each) at spp samples per pixel (dividing 32, or a multiple
- * of 32) for the context's current mesh and bases; *out owns every
- * per-frame buffer, allocated here.  The buffers that depend on the launch
- * configuration (primary hits, shadow-edge picks, the persistent launch's
- * work list) are sized at the first step with that configuration.
- * FR_ERR_NOT_READY before the mesh and bases are uploaded,
- * FR_ERR_INVALID_ARG for sizes out of range, FR_ERR_OOM when device memory
- * runs out (nothing is kept).  A batch is tied to the mesh and bases it was
- * created for: after a new upload fr_batch_step and fr_batch_autotune fail
- * with FR_ERR_NOT_READY.
- * fr_batch_destroy frees it (NULL is ignored). */
+/* Create a batch of frames[n_frames] (host array; 1..4096 frames, each
+ * with W, H >= 1, W H <= 2^26 and W H spp < 2^31) at spp samples per pixel
+ * (dividing 32, or a multiple of 32) on a context with mesh and bases
+ * uploaded.  Allocates every per-frame buffer the steps use (about 30 MB per
+ * frame for a 35,709-vertex mesh, plus the images); the buffers that depend
+ * on the launch configuration (primary hits, shadow-edge picks, the
+ * persistent launch's work list) are sized at the first step with that
+ * configuration.  *out receives the batch; it must be destroyed
+ * (fr_batch_destroy; NULL is ignored) before its context.  The batch is
+ * sized for the context's current mesh and bases: after a later
+ * fr_upload_mesh or fr_upload_bases, fr_batch_step and fr_batch_autotune
+ * fail with FR_ERR_NOT_READY (create a new batch).  FR_ERR_NOT_READY before
+ * the mesh and bases are uploaded, FR_ERR_INVALID_ARG for sizes out of
+ * range, FR_ERR_OOM when device memory runs out (nothing is kept). */
 int fr_batch_create(fr_ctx* ctx, const fr_frame* frames, int32_t n_frames, int32_t spp, fr_batch** out);
 void fr_batch_destroy(fr_batch* b);
 
