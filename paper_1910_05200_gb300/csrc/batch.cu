@@ -23,6 +23,10 @@
 //                    shadow-edge launches of the single-image path do.
 //   primary-edge items  a chunk of one frame's primary-edge samples; they
 //                    read d_image anywhere in the frame.
+// Each kind of item runs in a function of its own, out of line, and so do
+// the shadow-edge search and contribution: each is register-allocated on its
+// own within the kernel's budget (inlined into the kernel they spilled more
+// and ran slower).
 // Edge items wait until all tile items of their frame have published their
 // hits and d_image.  All tile items come before all edge items in the queue
 // and a warp only takes an item when it is running, so every tile item an
@@ -73,8 +77,8 @@ FR_DEV bool nonzero(V3 v) { return v.x != 0.0f || v.y != 0.0f || v.z != 0.0f; }
 
 // A tile item, spp dividing 32: chunks of 32 consecutive samples hold whole
 // pixels, so each pixel's mean is a shuffle reduction within the warp.
-__device__ __noinline__ void tile_small(WarpState& w, const BatchFrame& F, float* sC, int tile, int tw, int th, double& lacc,
-                       unsigned long long* cnt) {
+__device__ __noinline__ void tile_small(WarpState& w, const BatchFrame& F, float* sC, int tile, int tw, int th,
+                                        double& lacc, unsigned long long* cnt) {
   const RenderArgs& a = w.a;
   const int spp = a.spp, lane = threadIdx.x & 31;
   const int tx = tile % F.tiles_x, ty = tile / F.tiles_x;
@@ -109,8 +113,8 @@ __device__ __noinline__ void tile_small(WarpState& w, const BatchFrame& F, float
 
 // A tile item, spp a multiple of 32: one pixel at a time, its samples in
 // chunks of 32; pass 1 sums the radiance, pass 2 runs the interior adjoint.
-__device__ __noinline__ void tile_large(WarpState& w, const BatchFrame& F, float* sC, int tile, int tw, int th, double& lacc,
-                       unsigned long long* cnt) {
+__device__ __noinline__ void tile_large(WarpState& w, const BatchFrame& F, float* sC, int tile, int tw, int th,
+                                        double& lacc, unsigned long long* cnt) {
   const RenderArgs& a = w.a;
   const int spp = a.spp, lane = threadIdx.x & 31;
   const int tx = tile % F.tiles_x, ty = tile / F.tiles_x;
@@ -163,8 +167,8 @@ __device__ __noinline__ void sedge_add(const RenderArgs& a, const GradBufs& gb, 
 // A shadow-edge item: light j for the samples [k0, k0 + len) of the frame,
 // in the tile items' sample order, 32 at a time (the same warps of samples
 // as the tile items).
-__device__ __noinline__ void sedge_item(const WarpState& w, const BatchFrame& F, int j, long long k0, int len, int tw, int th,
-                       unsigned long long* cnt) {
+__device__ __noinline__ void sedge_item(const WarpState& w, const BatchFrame& F, int j, long long k0, int len, int tw,
+                                        int th, unsigned long long* cnt) {
   const RenderArgs& a = w.a;
   const int spp = a.spp, lane = threadIdx.x & 31;
   const int per_tile = tw * th * spp;
@@ -172,7 +176,7 @@ __device__ __noinline__ void sedge_item(const WarpState& w, const BatchFrame& F,
   const float inv = 1.0f / (float)spp;
   for (int c = 0; c < len && k0 + c < n; c += 32) {              // uniform
     const long long k = k0 + c + lane;
-    int2 hit = k < n ? F.gb.hits[k] : make_int2(-1, 0);
+    const int2 hit = k < n ? F.gb.hits[k] : make_int2(-1, 0);
     const bool valid = hit.x >= 0;
     V3 d{0, 0, -1}, x32{0, 0, 0}, wrgb{0, 0, 0};
     uint32_t pix = 0;

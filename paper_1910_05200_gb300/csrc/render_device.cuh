@@ -888,12 +888,4 @@ FR_DEV void sedge_contribution(const RenderArgs& a, const GradBufs& gb, int j, i
   hit_adjoint(a, f, d, S, gx, 0.0f, 0.0f, gb.dX);
 }
 
-// Shadow-edge term of one (camera sample, light j).  Warp-collective: all 32
-// lanes call it, lanes without a shading point with valid = false.
-FR_DEV void sedge_pick_and_add(const RenderArgs& a, const GradBufs& gb, int j, bool valid, V3 d, V3 x32, int f,
-                               int flip, uint32_t pix, int s, V3 wrgb, unsigned long long* cnt) {
-  Pick P = pick_light_warp(a, valid, x32, f, j, pix, s, cnt);
-  sedge_contribution(a, gb, j, P.n, P.slot, d, x32, f, flip, pix, s, wrgb, cnt, valid && P.n > 0);
-}
-
 }  // namespace fr
