@@ -417,7 +417,8 @@ int32_t fr_batch_n_frame(const fr_ctx* ctx);
  * within each group.  Writes min(cap, length) items (cap >= 0; items may be
  * NULL when cap = 0) and the length to *n_out.  FR_ERR_INVALID_ARG for the
  * arguments fr_batch_create or fr_batch_set_config refuses, or for a list
- * beyond the queue's range. */
+ * beyond the queue's range; FR_ERR_OOM when host memory for the list runs
+ * out. */
 int fr_batch_plan(const fr_frame* frames, int32_t n_frames, int32_t spp, int32_t tile_w, int32_t tile_h,
                   int32_t n_lights, int32_t* items, int64_t cap, int64_t* n_out);
 

@@ -3,6 +3,7 @@
 // the autotuner of the kernel's launch configuration.
 #include <algorithm>
 #include <cstring>
+#include <new>
 #include <numeric>
 #include <vector>
 
@@ -120,9 +121,10 @@ int check_config(fr_batch* b, const fr_tile_config& c, int* blocks_per_sm) {
 // items, then the shadow-edge items light-major within each frame, then the
 // primary-edge items.  Frames with more pixels come first in each group:
 // their items start early and the tail of the queue holds small items.
-// Returns null on success, else why the list does not fit its encoding.
-const char* plan_items(const fr_frame* frames, int nF, int spp, int tw, int th, int n_lights,
-                       std::vector<int2>& items) {
+// Returns FR_OK, FR_ERR_INVALID_ARG when the list does not fit its encoding
+// or FR_ERR_OOM when host memory for it runs out, with *why set.
+int plan_items(const fr_frame* frames, int nF, int spp, int tw, int th, int n_lights, std::vector<int2>& items,
+               const char** why) {
   items.clear();
   std::vector<int> order(nF);
   std::iota(order.begin(), order.end(), 0);
@@ -136,12 +138,22 @@ const char* plan_items(const fr_frame* frames, int nF, int spp, int tw, int th, 
   for (int f = 0; f < nF; ++f) {
     const long long nc = (n_tiles(f) * tw * th * spp + BATCH_SEDGE_CHUNK - 1) / BATCH_SEDGE_CHUNK;
     const long long np = ((long long)frames[f].W * frames[f].H * spp + BATCH_PEDGE_CHUNK - 1) / BATCH_PEDGE_CHUNK;
-    if (n_tiles(f) > INT32_MAX || nc >= (1LL << (30 - SEDGE_LIGHT_BITS)) || np > INT32_MAX)
-      return "frame too large for one launch";
+    if (n_tiles(f) > INT32_MAX || nc >= (1LL << (30 - SEDGE_LIGHT_BITS)) || np > INT32_MAX) {
+      *why = "frame too large for one launch";
+      return FR_ERR_INVALID_ARG;
+    }
     total += n_tiles(f) + nc * n_lights + np;
   }
-  if (total > INT32_MAX / 2) return "too many work items";
-  items.reserve((size_t)total);
+  if (total > INT32_MAX / 2) {
+    *why = "too many work items";
+    return FR_ERR_INVALID_ARG;
+  }
+  try {
+    items.reserve((size_t)total);
+  } catch (const std::bad_alloc&) {
+    *why = "out of host memory for the work items";
+    return FR_ERR_OOM;
+  }
   for (int f : order)
     for (long long t = 0; t < n_tiles(f); ++t) items.push_back(make_int2(f, (int)t));
   for (int f : order) {
@@ -153,7 +165,7 @@ const char* plan_items(const fr_frame* frames, int nF, int spp, int tw, int th, 
     const long long np = ((long long)frames[f].W * frames[f].H * spp + BATCH_PEDGE_CHUNK - 1) / BATCH_PEDGE_CHUNK;
     for (long long k = 0; k < np; ++k) items.push_back(make_int2(f | PEDGE_ITEM, (int)k));
   }
-  return nullptr;
+  return FR_OK;
 }
 
 // Frame table and work items for the current configuration (host -> device,
@@ -197,8 +209,9 @@ int configure(fr_batch* b) {
     T.n_pedge = (long long)fr_.W * fr_.H * b->spp;
   }
   if (c.fused) {
-    const char* why = plan_items(b->frames.data(), b->nF, b->spp, c.tile_w, c.tile_h, ctx->cfg.n_lights, items);
-    if (why) return fail(ctx, FR_ERR_INVALID_ARG, "%s", why);
+    const char* why = "";
+    const int rc = plan_items(b->frames.data(), b->nF, b->spp, c.tile_w, c.tile_h, ctx->cfg.n_lights, items, &why);
+    if (rc) return fail(ctx, rc, "%s", why);
   }
   // block tables of the phased launches (256 threads per block)
   std::vector<int> sf(b->nF + 1), ss(b->nF + 1), sp(b->nF + 1);
@@ -387,7 +400,9 @@ int fr_batch_plan(const fr_frame* frames, int32_t n_frames, int32_t spp, int32_t
       return FR_ERR_INVALID_ARG;
   }
   std::vector<int2> v;
-  if (plan_items(frames, n_frames, spp, tile_w, tile_h, n_lights, v)) return FR_ERR_INVALID_ARG;
+  const char* why = "";
+  const int rc = plan_items(frames, n_frames, spp, tile_w, tile_h, n_lights, v, &why);
+  if (rc) return rc;
   *n_out = (int64_t)v.size();
   const size_t n = std::min<size_t>(v.size(), (size_t)cap);
   for (size_t i = 0; i < n; ++i) { items[2 * i] = v[i].x; items[2 * i + 1] = v[i].y; }
