@@ -92,3 +92,59 @@ def test_persistent_plan_refusals():
                  ([(8192, 8192, 0)], 16, 1, 1, 20)]:          # the last: too many chunks for the item encoding
         with pytest.raises(RuntimeError, match="invalid argument"):
             facert.batch_plan(*args)
+
+
+def _simulate_queue(items, n_tiles, n_warps, rng):
+    """A model of the persistent kernel's scheduling: n_warps resident warps
+    each take the next item from the queue when idle; a tile item finishes
+    after a random time; an edge item spins until its frame's tile items have
+    all finished, then finishes after a random time.  Returns the number of
+    items finished before no warp can make progress."""
+    x = items[:, 0]
+    kind = np.where(x & PEDGE, 2, np.where(x & SEDGE, 1, 0))
+    f = x & ~(PEDGE | SEDGE)
+    done_tiles = np.zeros(len(n_tiles), np.int64)
+    nxt, finished = 0, 0
+    warps = [None] * n_warps          # (item, remaining time) or None
+    while True:
+        for w in range(n_warps):
+            if warps[w] is None and nxt < len(items):
+                warps[w] = [nxt, int(rng.integers(1, 5))]
+                nxt += 1
+        progressed = False
+        for w in range(n_warps):
+            if warps[w] is None:
+                continue
+            i, t = warps[w]
+            if kind[i] != 0 and done_tiles[f[i]] < n_tiles[f[i]]:
+                continue                  # spinning on the frame's tiles
+            progressed = True
+            warps[w][1] = t - 1
+            if warps[w][1] == 0:
+                if kind[i] == 0:
+                    done_tiles[f[i]] += 1
+                warps[w] = None
+                finished += 1
+        if not progressed:
+            return finished
+
+
+def test_persistent_queue_waits_end():
+    """However many warps are resident, every item of the plan finishes: an
+    edge item only ever waits for tile items taken before it by warps that
+    do not wait."""
+    frames = [(24, 16, 1), (9, 13, 2), (32, 20, 3)]
+    tw = th = 4
+    items = facert.batch_plan(frames, 2, tw, th, 3)
+    n_tiles = [-(-w // tw) * -(-h // th) for w, h, _ in frames]
+    rng = np.random.default_rng(0)
+    for n_warps in (1, 2, 5, 17, 64, 1000):
+        assert _simulate_queue(items, n_tiles, n_warps, rng) == len(items), n_warps
+    # the model is not vacuous: the same items with one edge item moved ahead
+    # of a tile item of its frame stall a single warp
+    bad = items.copy()
+    first_edge = int(np.argmax(bad[:, 0] & (SEDGE | PEDGE) != 0))
+    frame_of = bad[first_edge, 0] & ~(SEDGE | PEDGE)
+    tile_pos = int(np.nonzero(bad[:, 0] == frame_of)[0][0])
+    bad[[tile_pos, first_edge]] = bad[[first_edge, tile_pos]]
+    assert _simulate_queue(bad, n_tiles, 1, rng) < len(bad)
